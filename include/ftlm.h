@@ -1,0 +1,227 @@
+/*
+ * ftlm.h -- C ABI of libftlm, a GB300 (sm_103a) implementation of the hot path of
+ * the finite-temperature Lanczos method (FTLM) for spin-1/2 Heisenberg clusters
+ * (Ghassemi Tabrizi & Kuehne, "GPU-accelerated finite-temperature Lanczos method
+ * for spin Hamiltonians", arXiv 2605.26261).
+ *
+ * The path has three nested parts:
+ *   H.v      the matrix-free action of H = sum_b J_b S_i . S_j (Eq. 1, with a
+ *            coupling per bond) on one total-S^z sector, evaluated row by row as a
+ *            gather (Eq. 12-14); the state-to-index map is either the compressed
+ *            lookup table (CLT, Eq. 18-20, Algorithm 2) or combinatorial ranking
+ *            (CR, Eq. 15-17, Algorithm 1).
+ *   Lanczos  the three-term recurrence without reorthogonalization around it,
+ *            with the dot product and norm fused into the H.v launches, followed
+ *            by the small tridiagonal eigenproblem (Sec. 2, FTLM paragraph).
+ *   FTLM     the stochastic trace estimator over random start vectors and S^z
+ *            sectors, giving E(T), C(T) and chi(T) (Eq. 2-9).
+ *
+ * Conventions for every call:
+ *   - Pointers named *_dev are device pointers (cudaMalloc'd or from a caching
+ *     allocator) owned by the caller; other pointers are host memory.  Device
+ *     pointers of vectors must be 16-byte aligned.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is queued
+ *     on it asynchronously; outputs are valid once the stream reaches that point.
+ *   - Every call returns an ftlm_status; nothing aborts, throws or exits.  On a
+ *     failure ftlm_last_error() returns a message for the calling host thread.
+ *     FTLM_ECUDA means a CUDA runtime call failed (the message names it).
+ *   - No call spins on the device: there is no device-side wait to time out.
+ *   - Sector basis order: labels n = sum_k a_k 2^k with a_k = m_k + 1/2 (bit k = 1
+ *     means site k is up, Eq. 11) in increasing order; sector index = position
+ *     in that order.  A sector is fixed by its up-spin count K = N/2 + S^z
+ *     (Eq. 17), passed as two_sz = 2 S^z = 2K - N.
+ *   - dtype selects the storage and gather type of vectors: FTLM_F32 or FTLM_F64.
+ *     Dot products, norms, the tridiagonal eigenproblem and the thermodynamic
+ *     sums are FP64 in both cases.
+ */
+#ifndef FTLM_H
+#define FTLM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FTLM_OK = 0,
+    FTLM_EINVAL = 1,       /* an argument is out of range or inconsistent          */
+    FTLM_ENOMEM = 2,       /* device allocation failed / workspace too small       */
+    FTLM_EUNSUPPORTED = 3, /* valid request outside what this build implements     */
+    FTLM_ECUDA = 4,        /* a CUDA runtime call failed                           */
+    FTLM_ETIMEOUT = 5      /* reserved: a bounded device wait expired              */
+} ftlm_status;
+
+typedef enum {
+    FTLM_RANK_AUTO = 0, /* pick CR (the faster one on this GPU)                         */
+    FTLM_RANK_CLT = 1,  /* compressed lookup table: basis array + {M_b, C_b} (Eq. 18-21) */
+    FTLM_RANK_CR = 2    /* combinatorial ranking (Eq. 15-17), digit blocks via tables   */
+} ftlm_rank_mode;
+
+typedef enum { FTLM_F64 = 0, FTLM_F32 = 1 } ftlm_dtype;
+
+typedef enum { FTLM_VEC_GAUSS = 0, FTLM_VEC_RADEMACHER = 1 } ftlm_vec_dist;
+
+typedef struct ftlm_basis ftlm_basis; /* one (cluster, N, S^z) sector; opaque */
+
+#define FTLM_MAX_SITES 36
+#define FTLM_MAX_BONDS 256
+#define FTLM_MAX_LANCZOS 1024
+#define FTLM_MAX_SECTORS 64
+
+/* ---------------------------------------------------------------- sectors ---
+ * ftlm_basis_create -- set up one S^z sector of the cluster (step a1).
+ *   N          sites, 1 <= N <= FTLM_MAX_SITES.
+ *   two_sz     2 S^z; |two_sz| <= N and two_sz = N (mod 2).
+ *   n_bonds    0 <= n_bonds <= FTLM_MAX_BONDS; bond b couples sites bi[b] != bj[b]
+ *              (0 <= bi, bj < N) with J[b] (host arrays); an unordered pair may
+ *              appear only once.  H = sum_b J[b] S_bi . S_bj (Eq. 1 with J per bond).
+ *   mode       rank strategy.  CLT needs N <= 32 and stores the sorted basis
+ *              (4 D bytes) and the CLT (8 ceil(2^N/32) bytes, Eq. 21); CR stores
+ *              only small digit-block tables (Eq. 15-16) and needs D < 2^32.
+ *   stream     tables are built on it; the basis is usable by later work on any
+ *              stream once this work has completed on `stream`.
+ *   out        receives the handle; the library owns the device tables it holds.
+ * Errors: EINVAL (ranges, duplicate pair, i == j), EUNSUPPORTED (CLT with N > 32,
+ * D >= 2^32), ENOMEM, ECUDA.
+ */
+ftlm_status ftlm_basis_create(int N, int two_sz, int n_bonds, const int *bi, const int *bj,
+                              const double *J, ftlm_rank_mode mode, void *stream,
+                              ftlm_basis **out);
+
+/* Release the handle and its device tables (waits for nothing; do not destroy a
+ * basis while work that uses it is still queued).  NULL is ignored. */
+void ftlm_basis_destroy(ftlm_basis *basis);
+
+/* Sector dimension D = C(N, K). */
+ftlm_status ftlm_basis_dim(const ftlm_basis *basis, uint64_t *dim);
+
+/* Device bytes held by the basis tables (for admission by free memory). */
+ftlm_status ftlm_basis_bytes(const ftlm_basis *basis, uint64_t *table_bytes);
+
+/* Rank mode actually in use (AUTO resolved). */
+ftlm_status ftlm_basis_mode(const ftlm_basis *basis, ftlm_rank_mode *mode);
+
+/* Matrix-element updates applied by one H.v on one vector: D diagonal terms plus
+ * every off-diagonal ladder term, D + 2 sum_b C(N-2, K-1) (Eq. 10 at s = 1/2). */
+ftlm_status ftlm_basis_updates(const ftlm_basis *basis, uint64_t *updates);
+
+/* Sector labels of indices first .. first+count-1 into labels_dev (uint64[count]);
+ * CLT reads the stored basis array, CR unranks (the inverse map of Sec. 2).
+ * EINVAL when first + count > D. */
+ftlm_status ftlm_basis_labels(const ftlm_basis *basis, uint64_t first, uint64_t count,
+                              uint64_t *labels_dev, void *stream);
+
+/* Sector index of each label (uint64[count]) into index_dev (int64[count]), -1 for
+ * a label outside the sector or >= 2^N; uses the basis' own rank strategy. */
+ftlm_status ftlm_basis_rank(const ftlm_basis *basis, uint64_t count, const uint64_t *labels_dev,
+                            int64_t *index_dev, void *stream);
+
+/* CLT arrays of Eq. 18 (CLT mode only, else EUNSUPPORTED): mask_dev and prefix_dev
+ * receive ceil(2^N/32) uint32 each (occupancy masks M_b and prefix counts C_b). */
+ftlm_status ftlm_basis_clt(const ftlm_basis *basis, uint32_t *mask_dev, uint32_t *prefix_dev,
+                           void *stream);
+
+/* -------------------------------------------------------------------- H.v ---
+ * ftlm_hv -- y = H x on the sector (step a3; Eq. 12 with Eq. 13-14 at s = 1/2):
+ *   y[t] = (sum_b J_b m_i m_j) x[t] + sum_{b antiparallel in n_t} (J_b / 2) x[rank(n_t with
+ *          spins i, j exchanged)].
+ * x_dev, y_dev: D elements of dtype (float or double), contiguous; x and y must not
+ * overlap.  One thread per row, no atomics.  No scratch memory.
+ */
+ftlm_status ftlm_hv(const ftlm_basis *basis, ftlm_dtype dtype, const void *x_dev, void *y_dev,
+                    void *stream);
+
+/* ---------------------------------------------------------------- Lanczos ---
+ * Workspace bytes ftlm_lanczos / ftlm_lanczos_from need for R chains of at most M
+ * steps: two vectors of D elements of dtype plus O(R M) coefficients.  EINVAL for
+ * R < 1 or M outside 1..FTLM_MAX_LANCZOS. */
+ftlm_status ftlm_lanczos_workspace_bytes(const ftlm_basis *basis, int R, int M, ftlm_dtype dtype,
+                                         uint64_t *bytes);
+
+/* ftlm_lanczos -- R Lanczos chains (steps a2, a4, a5) on one sector.
+ *   Chain r starts from a counter-based random vector keyed by (seed, N, K, r):
+ *     u(c)  = F(key + (c+1) G), c-th output of splitmix64 from state key,
+ *             G = 0x9E3779B97F4A7C15, F the splitmix64 output function;
+ *     key   = F(F(seed + G) + (N << 48 | K << 32 | r) + G);
+ *     GAUSS:      x_t = sqrt(-2 ln U1) cos(2 pi U2), U1 = ((u(2t) >> 11) + 1) 2^-53,
+ *                 U2 = (u(2t+1) >> 11) 2^-53;
+ *     RADEMACHER: x_t = -1 if the top bit of u(t) is set, else +1;
+ *   normalized in FP64, then rounded to dtype.
+ *   Recurrence (Paige's ordering, no reorthogonalization), for j = 1 .. min(M, D):
+ *     y = H q_j - beta_{j-1} q_{j-1};  alpha_j = <q_j, y>;  w = y - alpha_j q_j;
+ *     beta_j = ||w||;  q_{j+1} = w / beta_j.
+ *   The chain stops after step j (m_eff = j) when beta_j <= tau = 100 u (3/4)
+ *   sum_b |J_b| (u = 2^-53 for F64, 2^-24 for F32).
+ *   Ritz step (FP64 on the device): theta_k, w_k = s_{k,1}^2 of the m_eff x m_eff
+ *   tridiagonal T, ascending in theta.
+ * Outputs (device, row r of chain r, each row M long, entries >= m_eff zero):
+ *   theta_dev, weight_dev: double[R*M];  m_eff_dev: int[R];
+ *   alpha_dev, beta_dev: double[R*M] or NULL (Lanczos coefficients; beta row r
+ *   holds beta_1 .. beta_{m_eff-1}).
+ * work_dev: caller-owned scratch of at least ftlm_lanczos_workspace_bytes() bytes,
+ *   256-byte aligned; its contents are overwritten.  ENOMEM when too small.
+ * The call only queues work on `stream`; it allocates nothing.
+ */
+ftlm_status ftlm_lanczos(const ftlm_basis *basis, int R, int M, uint64_t seed,
+                         ftlm_vec_dist dist, ftlm_dtype dtype, void *work_dev, uint64_t work_bytes,
+                         double *theta_dev, double *weight_dev, int *m_eff_dev, double *alpha_dev,
+                         double *beta_dev, void *stream);
+
+/* ftlm_lanczos_from -- as ftlm_lanczos, but chain r starts from the caller's vector
+ * start_dev + r*D (double[R*D], need not be normalized; a zero vector gives
+ * m_eff = 0).  Used for exact-trace runs (unit vectors) and for feeding identical
+ * start vectors to another implementation. */
+ftlm_status ftlm_lanczos_from(const ftlm_basis *basis, int R, int M, const double *start_dev,
+                              ftlm_dtype dtype, void *work_dev, uint64_t work_bytes,
+                              double *theta_dev, double *weight_dev, int *m_eff_dev,
+                              double *alpha_dev, double *beta_dev, void *stream);
+
+/* ftlm_ritz -- the Ritz step alone (a5): for each of n chains, the eigenvalues theta
+ * and first-component weights w = s_{k,1}^2 of the tridiagonal matrix with diagonal
+ * alpha_dev[c*M .. c*M+m-1] and off-diagonal beta_dev[c*M .. c*M+m-2], m = m_dev[c]
+ * (0 <= m <= M).  Implicit symmetric QR with Wilkinson shifts in FP64, one CUDA block
+ * per chain; outputs ascending, zero past m.  EINVAL for n < 0 or M outside
+ * 1..FTLM_MAX_LANCZOS. */
+ftlm_status ftlm_ritz(int n, int M, const double *alpha_dev, const double *beta_dev,
+                      const int *m_dev, double *theta_dev, double *weight_dev, void *stream);
+
+/* ------------------------------------------------------------------ thermo ---
+ * ftlm_thermo -- FTLM observables on a temperature grid (step a6, Eq. 6-9).
+ *   n_sectors computed sectors (1..FTLM_MAX_SECTORS); sector s has 2 S^z =
+ *   two_sz[s], dimension dims[s], R chains with Ritz data theta[s], weight[s]
+ *   (device double[R*M], from ftlm_lanczos) and m_eff[s] (device int[R]).  Host
+ *   arrays of device pointers.
+ *   mirror_neg != 0: each sector with S^z > 0 also stands for -S^z (identical
+ *   spectra, Sec. 2 Model paragraph).  Zeeman term -h S^z shifts sector energies
+ *   by -h S^z.  g: gyromagnetic factor.
+ *   Z = sum_sectors (D/R) sum_r sum_k w e^{-beta(E - E0)}, E0 the lowest Ritz
+ *   energy (the shift cancels in every ratio); E = <H>, C = beta^2 Var(H),
+ *   chi = g^2 beta <(S^z)^2> at h = 0 (Eq. 9), g^2 beta Var(S^z) otherwise;
+ *   mag = <S^z>.  k_B = 1.
+ *   T_dev: double[nT] > 0; E_dev, C_dev, chi_dev: double[nT]; mag_dev may be NULL.
+ */
+ftlm_status ftlm_thermo(int n_sectors, const int *two_sz, const uint64_t *dims, int R, int M,
+                        const double *const *theta, const double *const *weight,
+                        const int *const *m_eff, int mirror_neg, double g, double h, int nT,
+                        const double *T_dev, double *E_dev, double *C_dev, double *chi_dev,
+                        double *mag_dev, void *stream);
+
+/* ------------------------------------------------------------- diagnostics ---
+ * Kernel timing: while enabled, CUDA events are recorded on the launch stream
+ * around every H.v launch (ftlm_hv and the Lanczos H.v step) and every Lanczos
+ * vector-update launch.  ftlm_profile_read waits for those events, returns launch
+ * counts and summed device milliseconds since the last read, and clears them.
+ * Process-wide; thread-safe. */
+ftlm_status ftlm_profile_enable(int on);
+ftlm_status ftlm_profile_read(uint64_t *hv_launches, double *hv_ms, uint64_t *update_launches,
+                              double *update_ms);
+
+const char *ftlm_status_string(ftlm_status status);
+const char *ftlm_last_error(void); /* message of the last failure on this host thread */
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FTLM_H */

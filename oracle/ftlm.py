@@ -48,6 +48,8 @@ def lib():
         L.or_clt_lookup.argtypes = [P, P, c_u64]
         L.or_hv.restype = None
         L.or_hv.argtypes = [c_int, P, P, P, P, c_i64, P, P, P]
+        L.or_hv_range.restype = None
+        L.or_hv_range.argtypes = [c_int, P, P, P, P, c_i64, P, P, P, c_i64, c_i64]
         L.or_offdiag_terms.restype = c_i64
         L.or_offdiag_terms.argtypes = [c_int, P, P, P, c_i64]
         L.or_splitmix64_at.restype = c_u64
@@ -134,6 +136,17 @@ def hv(bonds, b, x, lut=None):
     if lut is not None:
         lut = np.ascontiguousarray(lut, dtype=np.int32)
     lib().or_hv(len(J), _p(bi), _p(bj), _p(J), _p(b), len(b), _p(lut), _p(x), _p(y))
+    return y
+
+
+def hv_range(bonds, b, x, t0, t1, lut=None, out=None):
+    """Rows t0 .. t1-1 of H x (Eq. 12-14, s = 1/2), FP64."""
+    bi, bj, J = _bonds(bonds)
+    y = np.empty(t1 - t0) if out is None else out
+    if lut is not None:
+        lut = np.ascontiguousarray(lut, dtype=np.int32)
+    lib().or_hv_range(len(J), _p(bi), _p(bj), _p(J), _p(b), len(b), _p(lut), _p(x), _p(y),
+                      int(t0), int(t1))
     return y
 
 

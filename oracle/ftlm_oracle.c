@@ -39,11 +39,11 @@
 
 static int or_bit(uint64_t n, int k) { return (int)((n >> k) & 1u); }
 
+/* Digit sum of an N-bit label (Eq. 11 with d = 2: the number of up spins). */
 static int or_digit_sum(uint64_t n, int N)
 {
-    int a = 0;
-    for (int k = 0; k < N; ++k) a += or_bit(n, k);
-    return a;
+    (void)N; /* labels passed here are below 2^N */
+    return __builtin_popcountll(n);
 }
 
 /* Sector basis (Eq. 11, Eq. 17): all labels 0 <= n < 2^N whose digit sum equals
@@ -156,14 +156,21 @@ static double or_hv_row(int nb, const int *bi, const int *bj, const double *J,
     return diag * x[t] + off;
 }
 
-/* H.v over the whole sector (Eq. 12), one output row at a time; rows are
- * independent, so the OpenMP split over rows does not change any result. */
+/* Rows t0 <= t < t1 of H.v (Eq. 12) into y[t - t0]; rows are independent, so the
+ * OpenMP split over rows does not change any result. */
+void or_hv_range(int nb, const int *bi, const int *bj, const double *J, const uint64_t *basis,
+                 int64_t D, const int32_t *lut, const double *x, double *y, int64_t t0, int64_t t1)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t t = t0; t < t1; ++t)
+        y[t - t0] = or_hv_row(nb, bi, bj, J, basis, D, lut, x, t);
+}
+
+/* H.v over the whole sector. */
 void or_hv(int nb, const int *bi, const int *bj, const double *J, const uint64_t *basis,
            int64_t D, const int32_t *lut, const double *x, double *y)
 {
-#pragma omp parallel for schedule(static)
-    for (int64_t t = 0; t < D; ++t)
-        y[t] = or_hv_row(nb, bi, bj, J, basis, D, lut, x, t);
+    or_hv_range(nb, bi, bj, J, basis, D, lut, x, y, 0, D);
 }
 
 /* Number of nonzero off-diagonal terms applied by one H.v (each valid ladder move

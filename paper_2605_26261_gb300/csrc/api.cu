@@ -1,0 +1,115 @@
+// Error reporting and kernel timing shared by every entry point.
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "ftlm_internal.cuh"
+
+namespace ftlm {
+
+namespace {
+thread_local std::string g_last_error;
+
+struct ProfRecord {
+    cudaEvent_t start, stop;
+    int kind;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRecord> g_records;
+std::vector<cudaEvent_t> g_event_pool;
+
+cudaEvent_t take_event()
+{
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+}  // namespace
+
+ftlm_status fail(ftlm_status s, const std::string &msg)
+{
+    g_last_error = msg;
+    return s;
+}
+
+ftlm_status cuda_fail(cudaError_t e, const char *what)
+{
+    g_last_error = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return FTLM_ECUDA;
+}
+
+void *profile_begin(int kind, cudaStream_t stream)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_prof_on) return nullptr;
+    ProfRecord r{take_event(), take_event(), kind};
+    if (!r.start || !r.stop) return nullptr;
+    if (cudaEventRecord(r.start, stream) != cudaSuccess) return nullptr;
+    g_records.push_back(r);
+    return reinterpret_cast<void *>(g_records.size());  // 1-based index
+}
+
+void profile_end(void *token, cudaStream_t stream)
+{
+    if (!token) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    const size_t idx = reinterpret_cast<size_t>(token) - 1;
+    if (idx < g_records.size()) cudaEventRecord(g_records[idx].stop, stream);
+}
+
+}  // namespace ftlm
+
+using namespace ftlm;
+
+extern "C" ftlm_status ftlm_profile_enable(int on)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_on = on != 0;
+    return FTLM_OK;
+}
+
+extern "C" ftlm_status ftlm_profile_read(uint64_t *hv_launches, double *hv_ms, uint64_t *update_launches,
+                                         double *update_ms)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    uint64_t n[2] = {0, 0};
+    double ms[2] = {0.0, 0.0};
+    ftlm_status st = FTLM_OK;
+    for (ProfRecord &r : g_records) {
+        float t = 0.f;
+        cudaError_t e = cudaEventSynchronize(r.stop);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.start, r.stop);
+        if (e != cudaSuccess && st == FTLM_OK) st = cuda_fail(e, "cudaEventElapsedTime");
+        n[r.kind] += 1;
+        ms[r.kind] += t;
+        g_event_pool.push_back(r.start);
+        g_event_pool.push_back(r.stop);
+    }
+    g_records.clear();
+    if (hv_launches) *hv_launches = n[kProfHv];
+    if (hv_ms) *hv_ms = ms[kProfHv];
+    if (update_launches) *update_launches = n[kProfUpdate];
+    if (update_ms) *update_ms = ms[kProfUpdate];
+    return st;
+}
+
+extern "C" const char *ftlm_status_string(ftlm_status s)
+{
+    switch (s) {
+    case FTLM_OK: return "FTLM_OK";
+    case FTLM_EINVAL: return "FTLM_EINVAL: invalid argument";
+    case FTLM_ENOMEM: return "FTLM_ENOMEM: out of device memory or workspace too small";
+    case FTLM_EUNSUPPORTED: return "FTLM_EUNSUPPORTED: outside what this build implements";
+    case FTLM_ECUDA: return "FTLM_ECUDA: CUDA runtime error";
+    case FTLM_ETIMEOUT: return "FTLM_ETIMEOUT: device wait expired";
+    }
+    return "unknown ftlm_status";
+}
+
+extern "C" const char *ftlm_last_error(void) { return g_last_error.c_str(); }

@@ -1,0 +1,449 @@
+// Sector setup (step a1): validation, digit-block rank tables, the CLT arrays and
+// the sorted basis, plus the rank/label entry points used to check them.
+//
+// Combinatorial rank at s = 1/2 (Eq. 15-17, Algorithm 1).  For s = 1/2 the table
+// D(m, A) of Eq. 15 is Pascal's triangle, D(m, A) = C(m, A), and the cumulative
+// table of Eq. 16 reduces to D_c(p, A, 1) = C(p, A), D_c(p, A, 0) = 0.  Algorithm 1
+// walks the digits p = N-1 .. 0 with A starting at A_tot = K (Eq. 17) and adds
+// C(p, A) at every set bit before decrementing A; equivalently the k-th set bit
+// from the bottom, at position p_k, contributes C(p_k, k).
+//
+// The paper's first GPU adaptation replaces the per-digit inner scan by one table
+// lookup per digit.  This build takes the same step for a whole block of digits:
+// split the label n into a low block l (the L lowest bits) and a high block h.
+// The contributions of the low bits depend only on l (their k counts only bits
+// below them): tlo[l].  The contributions of the high bits depend on h and on the
+// number of low set bits, which inside a sector is K - popcount(h): thi[h].  So
+//     rank(n) = thi[n >> L] + tlo[n & (2^L - 1)],
+// two lookups instead of N digit steps, bit-identical to Algorithm 1.  thi[h] is
+// also the number of sector labels below h * 2^L (it is defined that way for every
+// h, which keeps thi non-decreasing and lets the inverse map binary-search it).
+//
+// CLT (Eq. 18-21): blocks of 32 labels with occupancy mask M_b and prefix count
+// C_b.  At s = 1/2 the mask of block b depends only on popcount(b): label 32b + j
+// is in the sector iff popcount(j) = K - popcount(b); and C_b is the number of
+// sector labels below 32 b.  Both are computed per block in parallel; the result
+// is bit-identical to the paper's single pass over the basis plus cumulative
+// popcount sum.  M_b and C_b are stored interleaved, one 8-byte entry per block.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ftlm_internal.cuh"
+
+namespace ftlm {
+
+namespace {
+
+uint64_t g_binom[65][65];
+bool g_binom_ready = false;
+
+void init_binom()
+{
+    if (g_binom_ready) return;
+    for (int n = 0; n <= 64; ++n)
+        for (int k = 0; k <= 64; ++k)
+            g_binom[n][k] = (k == 0) ? 1 : (n == 0 ? 0 : g_binom[n - 1][k - 1] + g_binom[n - 1][k]);
+    g_binom_ready = true;
+}
+
+uint64_t binom(int n, int k)
+{
+    if (k < 0 || n < 0 || k > n) return 0;
+    return g_binom[n][k];
+}
+
+// Number of N-bit labels below v with K set bits.
+uint64_t count_below(uint64_t v, int N, int K)
+{
+    uint64_t cnt = 0;
+    int above = 0;
+    for (int p = N - 1; p >= 0; --p) {
+        if ((v >> p) & 1u) {
+            cnt += binom(p, K - above);
+            ++above;
+        }
+    }
+    return cnt;
+}
+
+int popc64(uint64_t v) { return __builtin_popcountll(v); }
+
+// ---- device kernels ---------------------------------------------------------
+
+// Inverse map t -> label through the digit-block tables: h is the last high
+// pattern with thi[h] <= t (thi is non-decreasing; the one found has room for t),
+// then the low pattern is entry t - thi[h] of popcount group K - popcount(h).
+__device__ __forceinline__ uint64_t unrank_label(uint32_t t, const SectorTables &s)
+{
+    uint32_t lo = 0, hi = s.H;
+    while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(s.thi + mid) <= t) lo = mid;
+        else hi = mid;
+    }
+    uint32_t r_lo = t - __ldg(s.thi + lo);
+    int c = s.K - __popc(lo);
+    uint32_t l = __ldg(s.ulo + __ldg(s.uoff + c) + r_lo);
+    return ((uint64_t)lo << s.L) | l;
+}
+
+__global__ void basis_fill_kernel(SectorTables s, uint32_t *basis)
+{
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < s.D;
+         t += (uint64_t)gridDim.x * blockDim.x)
+        basis[t] = (uint32_t)unrank_label((uint32_t)t, s);
+}
+
+// CLT entry of block b: occupancy mask and count of sector labels below 32 b.
+__global__ void clt_fill_kernel(int N, int K, uint64_t nblocks, const uint64_t *binom_g, uint2 *clt)
+{
+    __shared__ uint64_t sb[33 * 33];
+    for (int i = threadIdx.x; i < 33 * 33; i += blockDim.x) sb[i] = binom_g[i];
+    __syncthreads();
+    const int wbits = N < 5 ? N : 5;  // label bits inside a block
+    for (uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; b < nblocks;
+         b += (uint64_t)gridDim.x * blockDim.x) {
+        int c = K - __popcll(b);
+        uint32_t mask = 0;
+        if (c >= 0 && c <= wbits)
+            for (int j = 0; j < (1 << wbits); ++j)
+                if (__popc(j) == c) mask |= 1u << j;
+        // count_below(32 b): walk the set bits of b (label bits 5 ..) from the top
+        uint64_t cnt = 0;
+        int above = 0;
+        for (int p = N - 1; p >= 5; --p) {
+            if ((b >> (p - 5)) & 1u) {
+                int k = K - above;
+                if (k >= 0 && k <= p) cnt += sb[p * 33 + k];
+                ++above;
+            }
+        }
+        clt[b] = make_uint2(mask, (uint32_t)cnt);
+    }
+}
+
+__global__ void labels_kernel(SectorTables s, int clt_mode, uint64_t first, uint64_t count,
+                              uint64_t *out)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t t = (uint32_t)(first + i);
+        out[i] = clt_mode ? (uint64_t)__ldg(s.basis + t) : unrank_label(t, s);
+    }
+}
+
+__global__ void rank_kernel(SectorTables s, int clt_mode, uint64_t count, const uint64_t *labels,
+                            int64_t *out)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t n = labels[i];
+        int64_t r = -1;
+        if ((n >> s.N) == 0 && __popcll(n) == s.K) {
+            if (clt_mode) {
+                // Algorithm 2 / Eq. 19-20
+                uint2 e = __ldg(s.clt + (n >> 5));
+                uint32_t j = (uint32_t)(n & 31u);
+                if ((e.x >> j) & 1u) r = (int64_t)e.y + __popc(e.x & ((1u << j) - 1u));
+            } else {
+                r = (int64_t)__ldg(s.thi + (n >> s.L)) + __ldg(s.tlo + (n & s.lomask));
+            }
+        }
+        out[i] = r;
+    }
+}
+
+__global__ void clt_split_kernel(const uint2 *clt, uint64_t nblocks, uint32_t *mask, uint32_t *prefix)
+{
+    for (uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; b < nblocks;
+         b += (uint64_t)gridDim.x * blockDim.x) {
+        uint2 e = clt[b];
+        mask[b] = e.x;
+        prefix[b] = e.y;
+    }
+}
+
+int grid_for(uint64_t n, int threads, int num_sms)
+{
+    uint64_t g = (n + threads - 1) / threads;
+    uint64_t cap = (uint64_t)num_sms * 16;
+    return (int)std::max<uint64_t>(1, std::min(g, cap));
+}
+
+void free_tables(ftlm_basis *b)
+{
+    cudaFree(b->thi);
+    cudaFree(b->tlo);
+    cudaFree(b->ulo);
+    cudaFree(b->uoff);
+    cudaFree(b->basis);
+    cudaFree(b->clt);
+}
+
+}  // namespace
+
+int max_row_grid(const ftlm_basis *b) { return b->num_sms * kMaxBlocksPerSm; }
+
+int row_grid(const ftlm_basis *b, uint64_t rows, int occ)
+{
+    occ = std::max(1, std::min(occ, kMaxBlocksPerSm));
+    uint64_t need = (rows + kRowThreads - 1) / kRowThreads;
+    uint64_t cap = (uint64_t)b->num_sms * occ;
+    return (int)std::max<uint64_t>(1, std::min(need, cap));
+}
+
+}  // namespace ftlm
+
+using namespace ftlm;
+
+ftlm::SectorTables ftlm_basis::tables() const
+{
+    SectorTables s;
+    s.D = (uint32_t)D;
+    s.N = N;
+    s.K = K;
+    s.L = L;
+    s.lomask = (1u << L) - 1u;
+    s.H = (uint32_t)H;
+    s.thi = thi;
+    s.tlo = tlo;
+    s.ulo = ulo;
+    s.uoff = uoff;
+    s.basis = basis;
+    s.clt = clt;
+    return s;
+}
+
+extern "C" ftlm_status ftlm_basis_create(int N, int two_sz, int n_bonds, const int *bi,
+                                         const int *bj, const double *J, ftlm_rank_mode mode,
+                                         void *stream_, ftlm_basis **out)
+{
+    if (!out) return fail(FTLM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (N < 1 || N > FTLM_MAX_SITES) return fail(FTLM_EINVAL, "N out of range");
+    if (two_sz < -N || two_sz > N || ((two_sz + N) & 1)) return fail(FTLM_EINVAL, "bad two_sz");
+    if (n_bonds < 0) return fail(FTLM_EINVAL, "n_bonds < 0");
+    if (n_bonds > FTLM_MAX_BONDS) return fail(FTLM_EUNSUPPORTED, "more than FTLM_MAX_BONDS bonds");
+    if (n_bonds > 0 && (!bi || !bj || !J)) return fail(FTLM_EINVAL, "bond arrays are NULL");
+    if (mode != FTLM_RANK_AUTO && mode != FTLM_RANK_CLT && mode != FTLM_RANK_CR)
+        return fail(FTLM_EINVAL, "bad rank mode");
+    std::vector<std::pair<int, int>> seen;
+    for (int b = 0; b < n_bonds; ++b) {
+        int i = std::min(bi[b], bj[b]), j = std::max(bi[b], bj[b]);
+        if (i < 0 || j >= N) return fail(FTLM_EINVAL, "bond site out of range");
+        if (i == j) return fail(FTLM_EINVAL, "bond joins a site to itself");
+        if (!(J[b] == J[b]) || J[b] - J[b] != 0.0) return fail(FTLM_EINVAL, "non-finite coupling");
+        seen.emplace_back(i, j);
+    }
+    std::sort(seen.begin(), seen.end());
+    if (std::adjacent_find(seen.begin(), seen.end()) != seen.end())
+        return fail(FTLM_EINVAL, "duplicate bond");
+
+    init_binom();
+    const int K = (N + two_sz) / 2;
+    const uint64_t D = binom(N, K);
+    if (mode == FTLM_RANK_AUTO) mode = FTLM_RANK_CR;
+    if (D >= (1ull << 32)) return fail(FTLM_EUNSUPPORTED, "sector dimension >= 2^32");
+    if (mode == FTLM_RANK_CLT && N > 32) return fail(FTLM_EUNSUPPORTED, "CLT needs N <= 32");
+
+    cudaStream_t stream = (cudaStream_t)stream_;
+    ftlm_basis *b = new (std::nothrow) ftlm_basis();
+    if (!b) return fail(FTLM_ENOMEM, "host allocation failed");
+    b->N = N;
+    b->K = K;
+    b->two_sz = two_sz;
+    b->D = D;
+    b->mode = mode;
+    b->L = std::min(N, kLoBitsMax);
+    b->H = 1ull << (N - b->L);
+    b->nblocks = ((1ull << N) + 31) / 32;
+    b->updates = D + 2ull * (uint64_t)n_bonds * binom(N - 2, K - 1);
+    double jabs = 0.0;
+    for (int k = 0; k < n_bonds; ++k) jabs += std::fabs(J[k]);
+    b->tau64 = 100.0 * 0x1p-53 * 0.75 * jabs;
+    b->tau32 = 100.0 * 0x1p-24 * 0.75 * jabs;
+    cudaError_t ce = cudaGetDevice(&b->device);
+    if (ce == cudaSuccess)
+        ce = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
+    if (ce != cudaSuccess) {
+        delete b;
+        return cuda_fail(ce, "cudaGetDevice/cudaDeviceGetAttribute");
+    }
+
+    // Bond tables: CLT keeps the caller's order; CR groups by low/high block.
+    const int L = b->L;
+    double jsum4 = 0.0;
+    for (int k = 0; k < n_bonds; ++k) jsum4 += J[k] / 4.0;
+    for (BondTable *t : {&b->bonds_cr, &b->bonds_clt}) {
+        std::memset(t, 0, sizeof(*t));
+        t->nb = n_bonds;
+        t->jsum4 = jsum4;
+        t->jsum4f = (float)jsum4;
+    }
+    {
+        BondTable &t = b->bonds_clt;
+        for (int k = 0; k < n_bonds; ++k) {
+            uint64_t m = (1ull << bi[k]) | (1ull << bj[k]);
+            t.mlo[k] = (uint32_t)m;
+            t.mhi[k] = (uint32_t)(m >> 32);
+            t.jh[k] = J[k] / 2.0;
+            t.jhf[k] = (float)(J[k] / 2.0);
+        }
+        BondTable &c = b->bonds_cr;
+        int pos = 0;
+        for (int group = 0; group < 3; ++group) {
+            for (int k = 0; k < n_bonds; ++k) {
+                bool il = bi[k] < L, jl = bj[k] < L;
+                int g = (il && jl) ? 0 : (!il && !jl) ? 1 : 2;
+                if (g != group) continue;
+                uint64_t m = (1ull << bi[k]) | (1ull << bj[k]);
+                c.mlo[pos] = (uint32_t)(m & ((1ull << L) - 1));
+                c.mhi[pos] = (uint32_t)(m >> L);
+                c.jh[pos] = J[k] / 2.0;
+                c.jhf[pos] = (float)(J[k] / 2.0);
+                ++pos;
+            }
+            if (group == 0) c.n_lo = pos;
+            if (group == 1) c.n_hi = pos - c.n_lo;
+        }
+    }
+
+    // Digit-block tables on the host.
+    const uint32_t nlo = 1u << L;
+    std::vector<uint16_t> tlo(nlo), ulo(nlo);
+    std::vector<uint32_t> thi(b->H);
+    {
+        uint32_t off = 0;
+        for (int c = 0; c <= kLoBitsMax + 1; ++c) {
+            b->ulo_off[c] = off;
+            if (c <= L) off += (uint32_t)binom(L, c);
+        }
+        for (uint32_t v = 0; v < nlo; ++v) {
+            uint64_t r = 0;
+            int k = 0;
+            for (int p = 0; p < L; ++p)
+                if ((v >> p) & 1u) r += binom(p, ++k);
+            tlo[v] = (uint16_t)r;
+            ulo[b->ulo_off[popc64(v)] + r] = (uint16_t)v;
+        }
+        for (uint64_t h = 0; h < b->H; ++h) thi[h] = (uint32_t)count_below(h << L, N, K);
+    }
+
+    auto bail = [&](cudaError_t e, const char *what) {
+        free_tables(b);
+        delete b;
+        return cuda_fail(e, what);
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&b->thi, b->H * sizeof(uint32_t))) != cudaSuccess) return bail(e, "cudaMalloc(thi)");
+    if ((e = cudaMalloc(&b->tlo, nlo * sizeof(uint16_t))) != cudaSuccess) return bail(e, "cudaMalloc(tlo)");
+    if ((e = cudaMalloc(&b->ulo, nlo * sizeof(uint16_t))) != cudaSuccess) return bail(e, "cudaMalloc(ulo)");
+    if ((e = cudaMalloc(&b->uoff, sizeof(b->ulo_off))) != cudaSuccess) return bail(e, "cudaMalloc(uoff)");
+    b->table_bytes = b->H * sizeof(uint32_t) + 2ull * nlo * sizeof(uint16_t) + sizeof(b->ulo_off);
+    // Synchronous copies: the host vectors go out of scope on return.
+    if ((e = cudaMemcpy(b->thi, thi.data(), b->H * sizeof(uint32_t), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bail(e, "cudaMemcpy(thi)");
+    if ((e = cudaMemcpy(b->tlo, tlo.data(), nlo * sizeof(uint16_t), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bail(e, "cudaMemcpy(tlo)");
+    if ((e = cudaMemcpy(b->ulo, ulo.data(), nlo * sizeof(uint16_t), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bail(e, "cudaMemcpy(ulo)");
+    if ((e = cudaMemcpy(b->uoff, b->ulo_off, sizeof(b->ulo_off), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bail(e, "cudaMemcpy(uoff)");
+
+    if (mode == FTLM_RANK_CLT) {
+        if ((e = cudaMalloc(&b->basis, D * sizeof(uint32_t))) != cudaSuccess) return bail(e, "cudaMalloc(basis)");
+        if ((e = cudaMalloc(&b->clt, b->nblocks * sizeof(uint2))) != cudaSuccess) return bail(e, "cudaMalloc(clt)");
+        b->table_bytes += D * sizeof(uint32_t) + b->nblocks * sizeof(uint2);
+        uint64_t *binom_d = nullptr;
+        std::vector<uint64_t> bh(33 * 33);
+        for (int n = 0; n <= 32; ++n)
+            for (int k = 0; k <= 32; ++k) bh[n * 33 + k] = binom(n, k);
+        if ((e = cudaMalloc(&binom_d, bh.size() * sizeof(uint64_t))) != cudaSuccess) return bail(e, "cudaMalloc(binom)");
+        e = cudaMemcpy(binom_d, bh.data(), bh.size() * sizeof(uint64_t), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) {
+            basis_fill_kernel<<<grid_for(D, 256, b->num_sms), 256, 0, stream>>>(b->tables(), b->basis);
+            clt_fill_kernel<<<grid_for(b->nblocks, 256, b->num_sms), 256, 0, stream>>>(N, K, b->nblocks, binom_d, b->clt);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        cudaFree(binom_d);
+        if (e != cudaSuccess) return bail(e, "CLT build kernels");
+    }
+    *out = b;
+    return FTLM_OK;
+}
+
+extern "C" void ftlm_basis_destroy(ftlm_basis *b)
+{
+    if (!b) return;
+    free_tables(b);
+    delete b;
+}
+
+extern "C" ftlm_status ftlm_basis_dim(const ftlm_basis *b, uint64_t *dim)
+{
+    if (!b || !dim) return fail(FTLM_EINVAL, "NULL argument");
+    *dim = b->D;
+    return FTLM_OK;
+}
+
+extern "C" ftlm_status ftlm_basis_bytes(const ftlm_basis *b, uint64_t *bytes)
+{
+    if (!b || !bytes) return fail(FTLM_EINVAL, "NULL argument");
+    *bytes = b->table_bytes;
+    return FTLM_OK;
+}
+
+extern "C" ftlm_status ftlm_basis_mode(const ftlm_basis *b, ftlm_rank_mode *mode)
+{
+    if (!b || !mode) return fail(FTLM_EINVAL, "NULL argument");
+    *mode = b->mode;
+    return FTLM_OK;
+}
+
+extern "C" ftlm_status ftlm_basis_updates(const ftlm_basis *b, uint64_t *updates)
+{
+    if (!b || !updates) return fail(FTLM_EINVAL, "NULL argument");
+    *updates = b->updates;
+    return FTLM_OK;
+}
+
+extern "C" ftlm_status ftlm_basis_labels(const ftlm_basis *b, uint64_t first, uint64_t count,
+                                         uint64_t *labels_dev, void *stream)
+{
+    if (!b) return fail(FTLM_EINVAL, "NULL basis");
+    if (first > b->D || count > b->D - first) return fail(FTLM_EINVAL, "index range beyond D");
+    if (count == 0) return FTLM_OK;
+    if (!labels_dev) return fail(FTLM_EINVAL, "labels_dev is NULL");
+    labels_kernel<<<grid_for(count, 256, b->num_sms), 256, 0, (cudaStream_t)stream>>>(
+        b->tables(), b->mode == FTLM_RANK_CLT, first, count, labels_dev);
+    FTLM_CUDA(cudaGetLastError());
+    return FTLM_OK;
+}
+
+extern "C" ftlm_status ftlm_basis_rank(const ftlm_basis *b, uint64_t count, const uint64_t *labels_dev,
+                                       int64_t *index_dev, void *stream)
+{
+    if (!b) return fail(FTLM_EINVAL, "NULL basis");
+    if (count == 0) return FTLM_OK;
+    if (!labels_dev || !index_dev) return fail(FTLM_EINVAL, "NULL device pointer");
+    rank_kernel<<<grid_for(count, 256, b->num_sms), 256, 0, (cudaStream_t)stream>>>(
+        b->tables(), b->mode == FTLM_RANK_CLT, count, labels_dev, index_dev);
+    FTLM_CUDA(cudaGetLastError());
+    return FTLM_OK;
+}
+
+extern "C" ftlm_status ftlm_basis_clt(const ftlm_basis *b, uint32_t *mask_dev, uint32_t *prefix_dev,
+                                      void *stream)
+{
+    if (!b) return fail(FTLM_EINVAL, "NULL basis");
+    if (b->mode != FTLM_RANK_CLT) return fail(FTLM_EUNSUPPORTED, "basis has no CLT (CR mode)");
+    if (!mask_dev || !prefix_dev) return fail(FTLM_EINVAL, "NULL device pointer");
+    clt_split_kernel<<<grid_for(b->nblocks, 256, b->num_sms), 256, 0, (cudaStream_t)stream>>>(
+        b->clt, b->nblocks, mask_dev, prefix_dev);
+    FTLM_CUDA(cudaGetLastError());
+    return FTLM_OK;
+}

@@ -1,0 +1,128 @@
+// Internal declarations shared by the libftlm translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "ftlm.h"
+
+namespace ftlm {
+
+// Low digit block of the combinatorial rank: the L lowest label bits (L <= 14).
+constexpr int kLoBitsMax = 14;
+// Threads per block of the row-parallel kernels.
+constexpr int kRowThreads = 256;
+// Upper bound on resident blocks per SM the reduction partials are sized for.
+constexpr int kMaxBlocksPerSm = 8;
+
+// Bond list as the kernels see it (passed by value as a kernel parameter, so every
+// lane of a warp reads the same entry through the constant bank).  For the CR
+// kernels the bonds are sorted into three groups by where their two sites fall
+// relative to the low digit block: [0, n_lo) both low, [n_lo, n_lo + n_hi) both
+// high, the rest one of each.  mlo/mhi are the site bits inside the low block and
+// the high block (shifted down by L).  For the CLT kernel mlo holds the whole
+// two-bit mask (N <= 32) and the list keeps the caller's order.
+struct BondTable {
+    int nb;
+    int n_lo;
+    int n_hi;
+    int pad;
+    double jsum4;  // sum_b J_b / 4 : the diagonal when every bond is parallel
+    float jsum4f;
+    float padf;
+    uint32_t mlo[FTLM_MAX_BONDS];
+    uint32_t mhi[FTLM_MAX_BONDS];
+    double jh[FTLM_MAX_BONDS];  // J_b / 2, the ladder coefficient (Eq. 13-14 at s = 1/2)
+    float jhf[FTLM_MAX_BONDS];
+};
+
+// Scalars of one Lanczos chain, kept on the device between launches.  The stored
+// vector u_j is un-normalized: q_j = u_j / s_cur.
+struct ChainState {
+    double s_cur;      // s_j   (norm of the start vector, then beta_{j-1})
+    double s_prev;     // s_{j-1}
+    double beta_prev;  // beta_{j-1} (0 at j = 1)
+    double alpha;      // alpha_j of the step in flight
+    int m_eff;         // steps completed when the chain ended
+    int stopped;       // set once beta_j <= tau (or a zero start vector)
+    unsigned int counter;  // blocks finished in the current launch
+    int pad;
+};
+
+// Device-side tables of one sector, in the form the kernels take them.
+struct SectorTables {
+    uint32_t D;          // sector dimension (< 2^32)
+    int N, K, L;         // sites, up spins, low-block bits
+    uint32_t lomask;     // (1 << L) - 1
+    uint32_t H;          // 2^(N - L): high-block patterns
+    const uint32_t *thi; // [H]  number of sector labels below h * 2^L
+    const uint16_t *tlo; // [2^L] rank of a low pattern among patterns of its popcount
+    const uint16_t *ulo; // [2^L] patterns grouped by popcount, ascending (inverse of tlo)
+    const uint32_t *uoff; // [kLoBitsMax + 2] start of popcount group c in ulo
+    const uint32_t *basis;  // CLT mode: sorted labels [D]
+    const uint2 *clt;       // CLT mode: {M_b, C_b} per 32-label block
+};
+
+}  // namespace ftlm
+
+struct ftlm_basis {
+    int N, K, two_sz;
+    uint64_t D;
+    ftlm_rank_mode mode;
+    int L;
+    uint64_t H;
+    uint64_t nblocks;  // CLT blocks ceil(2^N / 32)
+    uint64_t updates;
+    uint64_t table_bytes;
+    double tau64, tau32;
+    int device, num_sms;
+    ftlm::BondTable bonds_cr;
+    ftlm::BondTable bonds_clt;
+    uint32_t ulo_off[ftlm::kLoBitsMax + 2];
+    uint32_t *thi;
+    uint16_t *tlo;
+    uint16_t *ulo;
+    uint32_t *uoff;
+    uint32_t *basis;
+    uint2 *clt;
+
+    ftlm::SectorTables tables() const;
+};
+
+namespace ftlm {
+
+// ---- error reporting (api.cu) --------------------------------------------
+ftlm_status fail(ftlm_status s, const std::string &msg);
+ftlm_status cuda_fail(cudaError_t e, const char *what);
+#define FTLM_CUDA(call)                                   \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return ftlm::cuda_fail(e_, #call); \
+    } while (0)
+
+// ---- kernel timing (api.cu) ----------------------------------------------
+enum ProfileKind { kProfHv = 0, kProfUpdate = 1 };
+// Returns an opaque token (or nullptr when profiling is off) for a launch about to
+// be queued on `stream`; profile_end records the stop event.
+void *profile_begin(int kind, cudaStream_t stream);
+void profile_end(void *token, cudaStream_t stream);
+
+// ---- launch helpers --------------------------------------------------------
+// Blocks for a persistent row-parallel kernel: min(rows / threads, SMs * occupancy).
+int row_grid(const ftlm_basis *b, uint64_t rows, int occupancy_blocks_per_sm);
+int max_row_grid(const ftlm_basis *b);
+
+// Lanczos epilogue of the H.v launch (hv.cu).
+struct LanczosHv {
+    const void *u_prev;  // = y buffer (in place)
+    ChainState *st;
+    double *partials;
+    double *alpha_out;   // alpha_j destination
+    int j;
+};
+ftlm_status launch_hv(const ftlm_basis *b, ftlm_dtype dtype, const void *x, void *y,
+                      const LanczosHv *epi, cudaStream_t stream);
+
+}  // namespace ftlm

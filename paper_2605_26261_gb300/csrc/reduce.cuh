@@ -1,0 +1,63 @@
+// Deterministic FP64 reductions for the row-parallel kernels.
+//
+// Each block reduces its per-thread partial sums in a fixed tree (warp shuffle,
+// then one warp over the per-warp sums) and stores one partial per block.  The
+// last block to finish -- found with a fence and an atomic ticket, no waiting --
+// adds the per-block partials in index order and publishes the total.  For a
+// fixed grid the summation order never changes, so results are bit-reproducible.
+#pragma once
+
+#include "ftlm_internal.cuh"
+
+namespace ftlm {
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;  // use lane 0's value: lanes may differ in the last bit
+}
+
+// Sum over the block; the result is valid in thread 0.
+template <int THREADS>
+__device__ __forceinline__ double block_sum(double v)
+{
+    __shared__ double sh[THREADS / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (w == 0) {
+        r = (lane < THREADS / 32) ? sh[lane] : 0.0;
+        r = warp_sum(r);
+    }
+    __syncthreads();
+    return r;
+}
+
+// Publish this block's partial; returns true (in every thread) in the last block
+// of the grid to arrive.
+__device__ __forceinline__ bool publish_partial(double part, double *partials, unsigned int *counter)
+{
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = part;
+        __threadfence();
+        unsigned int ticket = atomicAdd(counter, 1u);
+        last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    return last;
+}
+
+// Fixed-order total of partials[0 .. n-1]; call from warp 0, valid in lane 0.
+__device__ __forceinline__ double total_of_partials(const double *partials, int n)
+{
+    const int lane = threadIdx.x & 31;
+    double v = 0.0;
+    for (int i = lane; i < n; i += 32) v += __ldcg(partials + i);
+    return warp_sum(v);
+}
+
+}  // namespace ftlm

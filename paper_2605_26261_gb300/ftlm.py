@@ -1,0 +1,323 @@
+"""Python binding of libftlm (include/ftlm.h): argument marshalling only.
+
+Every ftlm_* function here calls the C entry point of the same name; the compute
+runs in the CUDA kernels of libftlm.so.  torch supplies device memory and the
+current CUDA stream.  There is no fallback: if the library is missing, every call
+raises.
+
+Convenience layer (also marshalling only): ``Basis`` owns a sector handle,
+``lanczos``/``thermo`` allocate outputs and workspace with torch, and
+``run_ftlm`` queues a whole FTLM job (all S^z >= 0 sectors, R chains each, then the
+thermodynamic sums) through the same entry points.
+"""
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libftlm.so")
+
+FTLM_OK, FTLM_EINVAL, FTLM_ENOMEM, FTLM_EUNSUPPORTED, FTLM_ECUDA, FTLM_ETIMEOUT = range(6)
+RANK_AUTO, RANK_CLT, RANK_CR = 0, 1, 2
+F64, F32 = 0, 1
+GAUSS, RADEMACHER = 0, 1
+MAX_SITES, MAX_BONDS, MAX_LANCZOS, MAX_SECTORS = 36, 256, 1024, 64
+
+_lib = None
+
+
+class FtlmError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{_status_name(status)}: {message}")
+        self.status = status
+
+
+def _status_name(s):
+    return {0: "FTLM_OK", 1: "FTLM_EINVAL", 2: "FTLM_ENOMEM", 3: "FTLM_EUNSUPPORTED",
+            4: "FTLM_ECUDA", 5: "FTLM_ETIMEOUT"}.get(s, f"status {s}")
+
+
+def lib():
+    """The loaded libftlm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing; build it with __graft_entry__.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I, U64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_double
+    PU64 = ctypes.POINTER(ctypes.c_uint64)
+    PD = ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "ftlm_basis_create": [I, I, I, P, P, P, I, P, ctypes.POINTER(P)],
+        "ftlm_basis_dim": [P, PU64],
+        "ftlm_basis_bytes": [P, PU64],
+        "ftlm_basis_mode": [P, ctypes.POINTER(I)],
+        "ftlm_basis_updates": [P, PU64],
+        "ftlm_basis_labels": [P, U64, U64, P, P],
+        "ftlm_basis_rank": [P, U64, P, P, P],
+        "ftlm_basis_clt": [P, P, P, P],
+        "ftlm_hv": [P, I, P, P, P],
+        "ftlm_lanczos_workspace_bytes": [P, I, I, I, PU64],
+        "ftlm_lanczos": [P, I, I, U64, I, I, P, U64, P, P, P, P, P, P],
+        "ftlm_lanczos_from": [P, I, I, P, I, P, U64, P, P, P, P, P, P],
+        "ftlm_ritz": [I, I, P, P, P, P, P, P],
+        "ftlm_thermo": [I, P, P, I, I, P, P, P, I, D, D, I, P, P, P, P, P, P],
+        "ftlm_profile_enable": [I],
+        "ftlm_profile_read": [PU64, PD, PU64, PD],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.ftlm_basis_destroy.argtypes = [P]
+    L.ftlm_basis_destroy.restype = None
+    L.ftlm_status_string.argtypes = [ctypes.c_int]
+    L.ftlm_status_string.restype = ctypes.c_char_p
+    L.ftlm_last_error.argtypes = []
+    L.ftlm_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check(status):
+    if status != FTLM_OK:
+        raise FtlmError(status, lib().ftlm_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _dtype_code(dt):
+    if dt in (torch.float32, F32, "f32", "float32"):
+        return F32
+    if dt in (torch.float64, F64, "f64", "float64"):
+        return F64
+    raise ValueError(f"unsupported dtype {dt}")
+
+
+def torch_dtype(code):
+    return torch.float32 if _dtype_code(code) == F32 else torch.float64
+
+
+# ------------------------------------------------------------ raw entry points
+def ftlm_status_string(status):
+    return lib().ftlm_status_string(status).decode()
+
+
+def ftlm_last_error():
+    return lib().ftlm_last_error().decode()
+
+
+def ftlm_basis_create(N, two_sz, bi, bj, J, mode=RANK_AUTO, stream=None):
+    bi = np.ascontiguousarray(bi, dtype=np.int32)
+    bj = np.ascontiguousarray(bj, dtype=np.int32)
+    J = np.ascontiguousarray(J, dtype=np.float64)
+    if not (len(bi) == len(bj) == len(J)):
+        raise ValueError("bond arrays differ in length")
+    out = ctypes.c_void_p()
+    _check(lib().ftlm_basis_create(int(N), int(two_sz), len(J), bi.ctypes.data, bj.ctypes.data,
+                                   J.ctypes.data, int(mode), _stream(stream), ctypes.byref(out)))
+    return out
+
+
+def ftlm_basis_destroy(handle):
+    lib().ftlm_basis_destroy(handle)
+
+
+def _u64_query(fn, handle):
+    v = ctypes.c_uint64()
+    _check(fn(handle, ctypes.byref(v)))
+    return v.value
+
+
+def ftlm_basis_dim(handle):
+    return _u64_query(lib().ftlm_basis_dim, handle)
+
+
+def ftlm_basis_bytes(handle):
+    return _u64_query(lib().ftlm_basis_bytes, handle)
+
+
+def ftlm_basis_updates(handle):
+    return _u64_query(lib().ftlm_basis_updates, handle)
+
+
+def ftlm_basis_mode(handle):
+    v = ctypes.c_int()
+    _check(lib().ftlm_basis_mode(handle, ctypes.byref(v)))
+    return v.value
+
+
+def ftlm_basis_labels(handle, first, count, labels, stream=None):
+    """labels: int64 device tensor (labels < 2^36 fit), length >= count."""
+    _check(lib().ftlm_basis_labels(handle, int(first), int(count), _ptr(labels), _stream(stream)))
+
+
+def ftlm_basis_rank(handle, labels, index, stream=None):
+    """labels: int64 device tensor; index: int64 device tensor of the same length."""
+    _check(lib().ftlm_basis_rank(handle, labels.numel(), _ptr(labels), _ptr(index), _stream(stream)))
+
+
+def ftlm_basis_clt(handle, mask, prefix, stream=None):
+    _check(lib().ftlm_basis_clt(handle, _ptr(mask), _ptr(prefix), _stream(stream)))
+
+
+def ftlm_hv(handle, x, y, stream=None):
+    """y = H x; x, y contiguous device tensors of equal float dtype and length D."""
+    if x.dtype != y.dtype or not x.is_contiguous() or not y.is_contiguous():
+        raise ValueError("x and y must be contiguous and of one dtype")
+    _check(lib().ftlm_hv(handle, _dtype_code(x.dtype), _ptr(x), _ptr(y), _stream(stream)))
+
+
+def ftlm_lanczos_workspace_bytes(handle, R, M, dtype):
+    v = ctypes.c_uint64()
+    _check(lib().ftlm_lanczos_workspace_bytes(handle, int(R), int(M), _dtype_code(dtype), ctypes.byref(v)))
+    return v.value
+
+
+def ftlm_lanczos(handle, R, M, seed, dist, dtype, work, theta, weight, m_eff, alpha=None, beta=None,
+                 stream=None):
+    _check(lib().ftlm_lanczos(handle, int(R), int(M), int(seed) & (2**64 - 1), int(dist),
+                              _dtype_code(dtype), _ptr(work), work.numel() * work.element_size(),
+                              _ptr(theta), _ptr(weight), _ptr(m_eff), _ptr(alpha), _ptr(beta),
+                              _stream(stream)))
+
+
+def ftlm_lanczos_from(handle, R, M, start, dtype, work, theta, weight, m_eff, alpha=None, beta=None,
+                      stream=None):
+    if start.dtype != torch.float64 or not start.is_contiguous():
+        raise ValueError("start vectors must be a contiguous float64 tensor")
+    _check(lib().ftlm_lanczos_from(handle, int(R), int(M), _ptr(start), _dtype_code(dtype), _ptr(work),
+                                   work.numel() * work.element_size(), _ptr(theta), _ptr(weight),
+                                   _ptr(m_eff), _ptr(alpha), _ptr(beta), _stream(stream)))
+
+
+def ftlm_ritz(n, M, alpha, beta, m, theta, weight, stream=None):
+    _check(lib().ftlm_ritz(int(n), int(M), _ptr(alpha), _ptr(beta), _ptr(m), _ptr(theta),
+                           _ptr(weight), _stream(stream)))
+
+
+def ftlm_thermo(two_sz, dims, R, M, thetas, weights, m_effs, mirror_neg, g, h, T, E, C, chi, mag=None,
+                stream=None):
+    n = len(two_sz)
+    tz = (ctypes.c_int * n)(*[int(v) for v in two_sz])
+    dm = (ctypes.c_uint64 * n)(*[int(v) for v in dims])
+    th = (ctypes.c_void_p * n)(*[t.data_ptr() for t in thetas])
+    wt = (ctypes.c_void_p * n)(*[t.data_ptr() for t in weights])
+    me = (ctypes.c_void_p * n)(*[t.data_ptr() for t in m_effs])
+    _check(lib().ftlm_thermo(n, tz, dm, int(R), int(M), th, wt, me, int(bool(mirror_neg)), float(g),
+                             float(h), T.numel(), _ptr(T), _ptr(E), _ptr(C), _ptr(chi), _ptr(mag),
+                             _stream(stream)))
+
+
+def ftlm_profile_enable(on=True):
+    _check(lib().ftlm_profile_enable(int(bool(on))))
+
+
+def ftlm_profile_read():
+    """(hv_launches, hv_ms, update_launches, update_ms) since the last read."""
+    a, c = ctypes.c_uint64(), ctypes.c_uint64()
+    b, d = ctypes.c_double(), ctypes.c_double()
+    _check(lib().ftlm_profile_read(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
+    return a.value, b.value, c.value, d.value
+
+
+# --------------------------------------------------------------- convenience
+class Basis:
+    """One S^z sector of a cluster on the current CUDA device (owns the handle)."""
+
+    def __init__(self, N, two_sz, bonds, mode=RANK_AUTO, stream=None):
+        bi, bj, J = bonds
+        self.N, self.two_sz = int(N), int(two_sz)
+        self.K = (self.N + self.two_sz) // 2
+        self.handle = ftlm_basis_create(N, two_sz, bi, bj, J, mode, stream)
+        self.dim = ftlm_basis_dim(self.handle)
+        self.table_bytes = ftlm_basis_bytes(self.handle)
+        self.mode = ftlm_basis_mode(self.handle)
+        self.updates = ftlm_basis_updates(self.handle)
+
+    def close(self):
+        if self.handle is not None:
+            ftlm_basis_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lanczos(basis, R, M, seed=1, dist=GAUSS, dtype=torch.float32, start=None, work=None,
+            keep_coeffs=False, stream=None):
+    """Run R chains on one sector; returns dict of device tensors theta, weight
+    (R x M), m_eff (R), and alpha, beta when keep_coeffs."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    code = _dtype_code(dtype)
+    nbytes = ftlm_lanczos_workspace_bytes(basis.handle, R, M, code)
+    if work is None or work.numel() * work.element_size() < nbytes:
+        work = torch.empty((nbytes + 255) // 256 * 256, dtype=torch.uint8, device=dev)
+    out = {
+        "theta": torch.empty((R, M), dtype=torch.float64, device=dev),
+        "weight": torch.empty((R, M), dtype=torch.float64, device=dev),
+        "m_eff": torch.empty(R, dtype=torch.int32, device=dev),
+    }
+    if keep_coeffs:
+        out["alpha"] = torch.empty((R, M), dtype=torch.float64, device=dev)
+        out["beta"] = torch.empty((R, M), dtype=torch.float64, device=dev)
+    args = (work, out["theta"], out["weight"], out["m_eff"], out.get("alpha"), out.get("beta"))
+    if start is None:
+        ftlm_lanczos(basis.handle, R, M, seed, dist, code, *args, stream=stream)
+    else:
+        ftlm_lanczos_from(basis.handle, R, M, start, code, *args, stream=stream)
+    return out
+
+
+def thermo(sectors, T, R, M, g=2.0, h=0.0, mirror=True, stream=None):
+    """sectors: list of (two_sz, dim, result-dict-of-lanczos); T: device float64."""
+    dev = T.device
+    out = {k: torch.empty_like(T) for k in ("E", "C", "chi", "mag")}
+    ftlm_thermo([s[0] for s in sectors], [s[1] for s in sectors], R, M,
+                [s[2]["theta"] for s in sectors], [s[2]["weight"] for s in sectors],
+                [s[2]["m_eff"] for s in sectors], mirror, g, h, T, out["E"], out["C"], out["chi"],
+                out["mag"], stream=stream)
+    return out
+
+
+def computed_two_sz(N):
+    """2 S^z of the sectors with S^z >= 0."""
+    return [2 * K - N for K in range((N + 1) // 2, N + 1)]
+
+
+def run_ftlm(N, bonds, R, M, T, seed=1, dist=GAUSS, dtype=torch.float32, g=2.0, h=0.0,
+             sectors=None, mode=RANK_AUTO, keep_coeffs=False, stream=None):
+    """A whole FTLM job on the device: for each sector (default: every S^z >= 0,
+    mirrored), R chains of M steps, then E, C, chi, mag on the grid T."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if not torch.is_tensor(T):
+        T = torch.as_tensor(np.asarray(T, dtype=np.float64), device=dev)
+    two = computed_two_sz(N) if sectors is None else list(sectors)
+    res, work = [], None
+    for tz in two:
+        with Basis(N, tz, bonds, mode, stream) as b:
+            r = lanczos(b, R, M, seed, dist, dtype, work=work, keep_coeffs=keep_coeffs, stream=stream)
+            res.append((tz, b.dim, r))
+    obs = thermo(res, T, R, M, g, h, mirror=sectors is None, stream=stream)
+    obs["sectors"] = res
+    return obs

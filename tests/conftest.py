@@ -24,3 +24,15 @@ def golden(name):
             k, v = (s.strip() for s in line.split("=", 1))
             out[k] = v
     return out
+
+
+@pytest.fixture(scope="session")
+def cuda_dev():
+    """cuda:0 with libftlm built and loaded (gpu tests only)."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    return torch.device("cuda", 0)

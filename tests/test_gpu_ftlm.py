@@ -1,0 +1,140 @@
+"""Thermodynamic sums and whole FTLM jobs on the GPU vs the oracle.
+
+Tolerance form for an observable O(T) (a reading; the paper states absolute
+errors): relative rtol where |O| >= 1e-6 max_T |O|, absolute rtol * max_T |O| below
+it (C is exponentially small at the lowest T of a gapped cluster).  rtol = 1e-9
+with FP64 vectors and 1e-4 with FP32 vectors.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as o
+from paper_2605_26261_gb300 import ftlm, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def assert_obs_close(got, ref, rtol, what):
+    got, ref = np.asarray(got), np.asarray(ref)
+    scale = np.max(np.abs(ref))
+    big = np.abs(ref) >= 1e-6 * scale
+    err = np.abs(got - ref)
+    bad = np.where(big, err > rtol * np.abs(ref), err > rtol * scale)
+    assert not bad.any(), f"{what}: max rel {np.max(err / np.maximum(np.abs(ref), 1e-6 * scale)):.3e}"
+
+
+def random_ritz_sectors(rng, N, R, M):
+    secs = []
+    for K in o.computed_sectors(N):
+        D = o.sector_dim(N, K)
+        m = rng.integers(1, min(M, D) + 1, size=R)
+        th = np.zeros((R, M))
+        w = np.zeros((R, M))
+        for r in range(R):
+            th[r, :m[r]] = np.sort(rng.uniform(-0.5 * N, 0.3 * N, size=m[r]))
+            x = rng.random(m[r])
+            w[r, :m[r]] = x / x.sum()
+        secs.append((2 * K - N, D, th, w, m.astype(np.int32)))
+    return secs
+
+
+@pytest.mark.parametrize("h,mirror", [(0.0, True), (0.7, True), (0.0, False)])
+def test_thermo_kernel_matches_oracle_sums(cuda_dev, h, mirror):
+    rng = np.random.default_rng(11)
+    N, R, M = 11, 5, 30
+    secs = random_ritz_sectors(rng, N, R, M)
+    T = inputs.log_t_grid(200)
+    dev_res = [(tz, D, {"theta": torch.as_tensor(th, device=cuda_dev),
+                        "weight": torch.as_tensor(w, device=cuda_dev),
+                        "m_eff": torch.as_tensor(m, device=cuda_dev)}) for tz, D, th, w, m in secs]
+    got = ftlm.thermo(dev_res, torch.as_tensor(T, device=cuda_dev), R, M, g=2.0, h=h, mirror=mirror)
+    ref = o.thermo([{"two_sz": tz, "dim": D, "chains": [(th[r, :m[r]], w[r, :m[r]]) for r in range(R)]}
+                    for tz, D, th, w, m in secs], T, g=2.0, h=h, mirror=mirror)
+    for k in ("E", "C", "chi", "mag"):
+        if k == "mag" and h == 0.0 and mirror:
+            assert np.max(np.abs(got[k].cpu().numpy())) < 1e-12
+            continue
+        assert_obs_close(got[k].cpu().numpy(), ref[k], 1e-12, k)
+
+
+CONFIG1 = dict(N=16, bonds=inputs.ring(16), R=20, M=100, seed=1, dist=o.GAUSS)
+
+
+@pytest.fixture(scope="module")
+def config1_oracle():
+    c = CONFIG1
+    secs = o.run_ftlm(c["N"], c["bonds"], c["R"], c["M"], seed=c["seed"], dist=c["dist"])
+    return o.thermo(secs, inputs.log_t_grid(200))
+
+
+@pytest.mark.parametrize("dtype,rtol", [(torch.float64, 1e-9), (torch.float32, 1e-4)])
+@pytest.mark.parametrize("mode", [ftlm.RANK_CLT, ftlm.RANK_CR])
+def test_config1_ring16_matches_oracle(cuda_dev, config1_oracle, dtype, rtol, mode):
+    # Ring N = 16, J = 1, every S^z sector (9 computed, mirrored), R = 20 Gaussian
+    # vectors, M = 100, 200 temperatures in [0.01, 10].
+    c = CONFIG1
+    T = inputs.log_t_grid(200)
+    got = ftlm.run_ftlm(c["N"], c["bonds"], c["R"], c["M"], T, seed=c["seed"], dist=c["dist"],
+                        dtype=dtype, mode=mode)
+    for k in ("E", "C", "chi"):
+        assert_obs_close(got[k].cpu().numpy(), config1_oracle[k], rtol, k)
+
+
+def test_config1_fp32_error_below_stochastic_error(cuda_dev):
+    # |O_FP32 - O_FP64| must stay below 1% of the seed-to-seed spread sigma_emp
+    # (Eq. 22, 1/N_s normalization) of the FP64 estimate.
+    c = CONFIG1
+    T = inputs.log_t_grid(200)
+    f64 = [ftlm.run_ftlm(c["N"], c["bonds"], c["R"], c["M"], T, seed=s, dtype=torch.float64)
+           for s in range(1, 11)]
+    f32 = ftlm.run_ftlm(c["N"], c["bonds"], c["R"], c["M"], T, seed=1, dtype=torch.float32)
+    for k in ("C", "chi"):
+        v = np.stack([r[k].cpu().numpy() for r in f64])
+        sigma = v.std(axis=0)  # ddof = 0 as in Eq. 22
+        d = np.abs(f32[k].cpu().numpy() - v[0])
+        sel = sigma > 1e-6 * np.max(sigma)
+        assert np.all(d[sel] < 0.01 * sigma[sel]), k
+
+
+@pytest.mark.parametrize("N,bonds,h", [(8, inputs.ring(8), 0.0), (9, inputs.random_graph(9, seed=7), 0.0),
+                                       (8, inputs.ladder(8, 0.4, 1.1), 0.8)])
+def test_exact_trace_mode_matches_oracle(cuda_dev, N, bonds, h):
+    # R = D unit start vectors and M = D make the estimator the exact trace.
+    # ftlm_thermo takes one chain count Rc for all sectors and weighs each chain by
+    # D / Rc; sectors with D < Rc get zero-length padding chains and their weights
+    # scaled by Rc / D, which gives every unit vector weight one.
+    T = inputs.log_t_grid(60, 0.05, 20.0)
+    ref = o.thermo(o.run_ftlm(N, bonds, 0, 0, start="unit"), T, h=h)
+    Rc = max(o.sector_dim(N, K) for K in o.computed_sectors(N))
+    dev_res = []
+    for K in o.computed_sectors(N):
+        D = o.sector_dim(N, K)
+        with ftlm.Basis(N, 2 * K - N, bonds) as b:
+            r = ftlm.lanczos(b, D, D, dtype=torch.float64,
+                             start=torch.eye(D, dtype=torch.float64, device=cuda_dev))
+        th = torch.zeros((Rc, Rc), dtype=torch.float64, device=cuda_dev)
+        w = torch.zeros_like(th)
+        m = torch.zeros(Rc, dtype=torch.int32, device=cuda_dev)
+        th[:D, :D], w[:D, :D], m[:D] = r["theta"], r["weight"] * (Rc / D), r["m_eff"]
+        dev_res.append((2 * K - N, D, {"theta": th, "weight": w, "m_eff": m}))
+    got = ftlm.thermo(dev_res, torch.as_tensor(T, device=cuda_dev), Rc, Rc, h=h)
+    for k in ("E", "C", "chi"):
+        assert_obs_close(got[k].cpu().numpy(), ref[k], 1e-9, k)
+
+
+def test_config2_lattice_sectors_match_oracle(cuda_dev):
+    # 4 x 6 J1-J2 lattice, Rademacher vectors, M = 150: the sectors with S^z >= 5
+    # (D <= 346104) on the oracle, first 2 chains of each; the same chains on the GPU.
+    N, R, M = 24, 2, 150
+    bonds = inputs.square_j1j2()
+    Ks = list(range(17, 25))
+    T = inputs.log_t_grid(200)
+    ref = o.thermo(o.run_ftlm(N, bonds, R, M, seed=1, dist=o.RADEMACHER, Ks=Ks), T, mirror=True)
+    for dtype, rtol in ((torch.float64, 1e-9), (torch.float32, 1e-4)):
+        got = ftlm.run_ftlm(N, bonds, R, M, T, seed=1, dist=ftlm.RADEMACHER, dtype=dtype,
+                            sectors=[2 * K - N for K in Ks])
+        # run_ftlm with explicit sectors does not mirror; redo thermo with mirroring
+        obs = ftlm.thermo(got["sectors"], torch.as_tensor(T, device=cuda_dev), R, M, mirror=True)
+        for k in ("E", "C", "chi"):
+            assert_obs_close(obs[k].cpu().numpy(), ref[k], rtol, f"{k} {dtype}")

@@ -1,0 +1,160 @@
+"""Lanczos chains and the Ritz step on the GPU vs the oracle.
+
+FP64 chains fed the oracle's own start vectors must reproduce the oracle's
+Lanczos coefficients to 1e-10 relative before orthogonality is lost; seeded chains
+regenerate the same start vectors on the device (same counter-based generator,
+separately implemented).  FP32 storage agrees to 1e-4 over the first steps.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as o
+from paper_2605_26261_gb300 import ftlm, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def oracle_chain(bonds, N, K, start, M, u=o.U64):
+    b = o.basis(N, K)
+    return o.lanczos(bonds, b, start, M, o.breakdown_tol(bonds[2], u), o.full_lut(N, b))
+
+
+@pytest.mark.parametrize("mode", [ftlm.RANK_CLT, ftlm.RANK_CR])
+def test_fp64_coefficients_from_given_start(cuda_dev, mode):
+    N, K, M, R = 18, 9, 40, 3
+    bonds = inputs.random_graph(N, seed=5)
+    D = len(o.basis(N, K))
+    starts = np.stack([inputs.seeded_vector(D, 50 + r) for r in range(R)])
+    with ftlm.Basis(N, 0, bonds, mode) as b:
+        res = ftlm.lanczos(b, R, M, dtype=torch.float64, start=torch.as_tensor(starts, device=cuda_dev),
+                           keep_coeffs=True)
+        torch.cuda.synchronize()
+    for r in range(R):
+        a, bt, m = oracle_chain(bonds, N, K, starts[r], M)
+        assert int(res["m_eff"][r]) == m == M
+        # the first 15 steps precede any loss of orthogonality
+        np.testing.assert_allclose(res["alpha"][r, :15].cpu().numpy(), a[:15], rtol=1e-10, atol=1e-12)
+        np.testing.assert_allclose(res["beta"][r, :15].cpu().numpy(), bt[:15], rtol=1e-10)
+
+
+@pytest.mark.parametrize("dist", [ftlm.GAUSS, ftlm.RADEMACHER])
+def test_seeded_start_vectors_match_oracle_generator(cuda_dev, dist):
+    N, K, M, R, seed = 16, 8, 12, 4, 1234
+    bonds = inputs.ring(N)
+    with ftlm.Basis(N, 0, bonds) as b:
+        res = ftlm.lanczos(b, R, M, seed=seed, dist=dist, dtype=torch.float64, keep_coeffs=True)
+        torch.cuda.synchronize()
+    for r in range(R):
+        v = o.start_vector(seed, N, K, r, dist)
+        a, bt, m = oracle_chain(bonds, N, K, v, M)
+        np.testing.assert_allclose(res["alpha"][r, :m].cpu().numpy(), a, rtol=1e-10, atol=1e-12)
+        np.testing.assert_allclose(res["beta"][r, :m - 1].cpu().numpy(), bt, rtol=1e-10)
+
+
+@pytest.mark.parametrize("mode", [ftlm.RANK_CLT, ftlm.RANK_CR])
+def test_fp32_coefficients_close_to_fp64_oracle(cuda_dev, mode):
+    N, K, M, R = 20, 10, 20, 2
+    bonds = inputs.ladder(20, 0.6, 1.0)
+    with ftlm.Basis(N, 0, bonds, mode) as b:
+        res = ftlm.lanczos(b, R, M, seed=9, dtype=torch.float32, keep_coeffs=True)
+        torch.cuda.synchronize()
+    for r in range(R):
+        v = o.start_vector(9, N, K, r, o.GAUSS)
+        a, bt, m = oracle_chain(bonds, N, K, v, M, o.U32)
+        np.testing.assert_allclose(res["alpha"][r, :m].cpu().numpy(), a, rtol=1e-4, atol=1e-5)
+        np.testing.assert_allclose(res["beta"][r, :m - 1].cpu().numpy(), bt, rtol=1e-4)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_breakdown_at_krylov_dimension(cuda_dev, dtype):
+    # One down spin on a 12-ring: 7 distinct levels, the chain must stop after 7.
+    N = 12
+    bonds = inputs.ring(N)
+    with ftlm.Basis(N, N - 2, bonds) as b:
+        res = ftlm.lanczos(b, 3, 12, seed=5, dtype=dtype)
+        torch.cuda.synchronize()
+        assert res["m_eff"].tolist() == [7, 7, 7]
+        th = res["theta"][0, :7].cpu().numpy()
+        ev = np.unique(np.round(np.linalg.eigvalsh(o.dense_h(bonds, o.basis(N, N - 1))), 8))
+        np.testing.assert_allclose(np.sort(th), ev, atol=1e-9 if dtype == torch.float64 else 1e-5)
+        w = res["weight"].cpu().numpy()
+        np.testing.assert_allclose(w.sum(1), 1.0, atol=1e-12)
+        assert np.all(w[:, 7:] == 0) and np.all(res["theta"][:, 7:].cpu().numpy() == 0)
+
+
+def test_dimension_one_and_two_sectors(cuda_dev):
+    N = 10
+    bonds = inputs.random_graph(N, seed=3)
+    with ftlm.Basis(N, N, bonds) as b:  # all up: D = 1
+        res = ftlm.lanczos(b, 2, 50, dtype=torch.float64)
+        torch.cuda.synchronize()
+        assert res["m_eff"].tolist() == [1, 1]
+        np.testing.assert_allclose(res["theta"][:, 0].cpu().numpy(), bonds[2].sum() / 4, rtol=1e-14)
+        np.testing.assert_array_equal(res["weight"][:, 0].cpu().numpy(), 1.0)
+    with ftlm.Basis(2, 0, inputs.dimer(1.0)) as b:  # D = 2: singlet and triplet
+        res = ftlm.lanczos(b, 1, 10, dtype=torch.float64)
+        torch.cuda.synchronize()
+        assert int(res["m_eff"][0]) == 2
+        np.testing.assert_allclose(res["theta"][0, :2].cpu().numpy(), [-0.75, 0.25], atol=1e-14)
+
+
+def test_zero_start_vector_gives_empty_chain(cuda_dev):
+    with ftlm.Basis(8, 0, inputs.ring(8)) as b:
+        start = torch.zeros((2, b.dim), dtype=torch.float64, device=cuda_dev)
+        start[1, 3] = 2.0
+        res = ftlm.lanczos(b, 2, 10, dtype=torch.float64, start=start)
+        torch.cuda.synchronize()
+        assert int(res["m_eff"][0]) == 0 and int(res["m_eff"][1]) > 0
+        assert torch.all(res["weight"][0] == 0).item()
+
+
+def test_workspace_too_small_is_rejected(cuda_dev):
+    with ftlm.Basis(8, 0, inputs.ring(8)) as b:
+        need = ftlm.ftlm_lanczos_workspace_bytes(b.handle, 2, 10, torch.float64)
+        work = torch.empty(need - 256, dtype=torch.uint8, device=cuda_dev)
+        out = [torch.empty((2, 10), dtype=torch.float64, device=cuda_dev) for _ in range(2)]
+        me = torch.empty(2, dtype=torch.int32, device=cuda_dev)
+        with pytest.raises(ftlm.FtlmError) as e:
+            ftlm.ftlm_lanczos(b.handle, 2, 10, 1, 0, torch.float64, work, out[0], out[1], me)
+        assert e.value.status == ftlm.FTLM_ENOMEM
+
+
+def test_repeated_runs_are_bit_identical(cuda_dev):
+    with ftlm.Basis(16, 0, inputs.ring(16)) as b:
+        r1 = ftlm.lanczos(b, 2, 30, seed=4, dtype=torch.float32, keep_coeffs=True)
+        r2 = ftlm.lanczos(b, 2, 30, seed=4, dtype=torch.float32, keep_coeffs=True)
+        torch.cuda.synchronize()
+        for k in ("alpha", "beta", "theta", "weight"):
+            assert torch.equal(r1[k], r2[k])
+
+
+def random_tridiagonals(n, M, seed):
+    rng = np.random.default_rng(seed)
+    m = rng.integers(1, M + 1, size=n)
+    m[0], m[1] = M, 1
+    a = rng.normal(size=(n, M))
+    b = np.abs(rng.normal(size=(n, M))) + 0.1
+    return a, b, m.astype(np.int32)
+
+
+@pytest.mark.parametrize("M", [1, 2, 7, 100, 300])
+def test_ritz_matches_dense_eigh(cuda_dev, M):
+    n = 16
+    a, b, m = random_tridiagonals(n, M, M)
+    th = torch.empty((n, M), dtype=torch.float64, device=cuda_dev)
+    w = torch.empty_like(th)
+    ftlm.ftlm_ritz(n, M, torch.as_tensor(a, device=cuda_dev), torch.as_tensor(b, device=cuda_dev),
+                   torch.as_tensor(m, device=cuda_dev), th, w)
+    th, w = th.cpu().numpy(), w.cpu().numpy()
+    for c in range(n):
+        k = m[c]
+        T = np.diag(a[c, :k]) + np.diag(b[c, :k - 1], 1) + np.diag(b[c, :k - 1], -1)
+        ev, S = np.linalg.eigh(T)
+        np.testing.assert_allclose(th[c, :k], ev, atol=1e-12 * max(1, np.abs(ev).max()))
+        # weights through smooth spectral functions (insensitive to near-degenerate splits)
+        for beta in (0.3, 1.0):
+            np.testing.assert_allclose((w[c, :k] * np.exp(-beta * th[c, :k])).sum(),
+                                       (S[0] ** 2 * np.exp(-beta * ev)).sum(), rtol=1e-11)
+        assert abs(w[c, :k].sum() - 1) < 1e-12
+        assert np.all(th[c, k:] == 0) and np.all(w[c, k:] == 0)
