@@ -231,6 +231,8 @@ def thermo(sectors, T, g=2.0, h=0.0, mirror=True):
         chains  list of (theta, weight) arrays, one per random vector (R = len).
     Each sector with M > 0 also stands for -M when mirror is set (same Ritz data).
     Returns dict with E, C, chi, mag (= <S^z>), Z_shifted and E0, all FP64.
+    C = beta^2 Var(H) (Eq. 8 moments) and, in a field, chi = g^2 beta Var(S^z); both
+    variances are evaluated as central second moments <(X - <X>)^2>.
     """
     E_list, W_list, M_list = [], [], []
     for s in sectors:
@@ -254,12 +256,15 @@ def thermo(sectors, T, g=2.0, h=0.0, mirror=True):
         bw = W * np.exp(-beta * (E - E0))
         Z = np.sum(bw)
         e1 = np.sum(bw * (E - E0)) / Z
-        e2 = np.sum(bw * (E - E0) ** 2) / Z
         m1 = np.sum(bw * Mz) / Z
-        m2 = np.sum(bw * Mz**2) / Z
+        # variances as central second moments: <(X - <X>)^2>
+        varE = np.sum(bw * (E - E0 - e1) ** 2) / Z
         out["E"][n] = E0 + e1
-        out["C"][n] = beta**2 * (e2 - e1**2)
-        out["chi"][n] = g**2 * beta * (m2 if h == 0.0 else m2 - m1**2)
+        out["C"][n] = beta**2 * varE
+        if h == 0.0:
+            out["chi"][n] = g**2 * beta * np.sum(bw * Mz**2) / Z  # Eq. 9
+        else:
+            out["chi"][n] = g**2 * beta * np.sum(bw * (Mz - m1) ** 2) / Z
         out["mag"][n] = m1
         out["Z_shifted"][n] = Z
     out["E0"] = E0

@@ -6,7 +6,8 @@
 // With E0 the lowest energy, one block per temperature forms
 //   Z = sum b,  b = (D/R) w e^{-beta (E - E0)}       (Eq. 7, shifted by E0)
 //   <E - E0> = sum b (E - E0) / Z,  Var(H) = sum b (E - E0 - <E - E0>)^2 / Z
-//   <S^z> = sum b S^z / Z,  <(S^z)^2> = sum b (S^z)^2 / Z
+//   <S^z> = sum b S^z / Z,  <(S^z)^2> = sum b (S^z)^2 / Z,
+//   Var(S^z) = sum b (S^z - <S^z>)^2 / Z
 // and C = beta^2 Var(H) (Eq. 8 moments, central form), chi = g^2 beta <(S^z)^2>
 // at h = 0 (Eq. 9) and g^2 beta Var(S^z) otherwise.  The shift keeps e^{-beta E}
 // finite at T = 0.01 and cancels in every ratio; the central second moment avoids
@@ -93,7 +94,7 @@ thermo_kernel(const ThermoArgs a, const double *__restrict__ T, double *E, doubl
     const double M1 = bcast(block_sum<kThermoThreads>(m1)) / Z;
     const double M2 = bcast(block_sum<kThermoThreads>(m2)) / Z;
 
-    double s2 = 0.0;
+    double s2 = 0.0, v2 = 0.0;
     for (int i = threadIdx.x; i < n; i += kThermoThreads) {
         const int s = i / per_sector, rem = i - s * per_sector, r = rem / a.M, k = rem - r * a.M;
         if (k >= __ldg(a.meff[s] + r)) continue;
@@ -103,16 +104,18 @@ thermo_kernel(const ThermoArgs a, const double *__restrict__ T, double *E, doubl
             const double mz = im ? -a.sz[s] : a.sz[s];
             const double de = th - a.h * mz - E0;
             const double b = w * exp(-beta * de);
-            const double dc = de - e1;
+            const double dc = de - e1, dm = mz - M1;
             s2 += b * dc * dc;
+            v2 += b * dm * dm;
         }
     }
-    const double S2 = block_sum<kThermoThreads>(s2);
+    const double S2 = bcast(block_sum<kThermoThreads>(s2));
+    const double V2 = block_sum<kThermoThreads>(v2);
     if (threadIdx.x == 0) {
         const int t = blockIdx.x;
         E[t] = E0 + e1;
         C[t] = beta * beta * (S2 / Z);
-        chi[t] = a.g * a.g * beta * (a.h == 0.0 ? M2 : M2 - M1 * M1);
+        chi[t] = a.g * a.g * beta * (a.h == 0.0 ? M2 : V2 / Z);
         if (mag) mag[t] = M1;
     }
 }
