@@ -53,6 +53,8 @@ def parse_args():
     p.add_argument("--M", type=int, default=100)
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--hv-only", action="store_true",
+                   help="time plain ftlm_hv launches on the workload (kernel microbenchmark)")
     return p.parse_args()
 
 
@@ -157,6 +159,21 @@ class ClockSampler:
         load = [s for s in sm if smax and s > 0.3 * smax] or sm
         return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": smax,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def aggregate_over_ranks(updates, ms, device, world):
+    """Whole-job totals over replicas: updates summed over ranks, the timed region's
+    duration taken as the maximum over ranks."""
+    import torch
+    import torch.distributed as dist
+
+    if world <= 1:
+        return float(updates), float(ms)
+    u = torch.tensor([float(updates)], dtype=torch.float64, device=device)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return u.item(), t.item()
 
 
 # ---------------------------------------------------------------------- oracle
@@ -299,14 +316,7 @@ def run_ours(args):
     m_max = min(M, D)
     launches_step = (2 if mode_used == ftlm.RANK_CLT else 0) + R * (2 + 2 * m_max) + 2
 
-    tot = torch.tensor([updates_step * args.steps, total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        u = tot[:1].clone()
-        t = tot[1:].clone()
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot = torch.cat([u, t])
-    all_updates, max_ms = tot.tolist()
+    all_updates, max_ms = aggregate_over_ranks(updates_step * args.steps, total_ms, dev, world)
     value = all_updates / (max_ms / 1e3) / 1e9
 
     # end-to-end through the public API with host buffers (one job per step):
@@ -393,9 +403,47 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_hv_only(args):
+    """Kernel microbenchmark: W + K plain H.v launches on the workload's sector."""
+    import torch
+
+    import __graft_entry__
+    from paper_2605_26261_gb300 import ftlm, inputs
+
+    __graft_entry__.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    N = WORKLOADS[args.workload]["N"]
+    bonds = bonds_of(args.workload)
+    mode = {"auto": ftlm.RANK_AUTO, "clt": ftlm.RANK_CLT, "cr": ftlm.RANK_CR}[args.mode]
+    dt = torch.float32 if args.dtype == "f32" else torch.float64
+    with ftlm.Basis(N, 0, bonds, mode) as b:
+        x = inputs.hashed_vector_torch(b.dim, dt, dev)
+        y = torch.empty_like(x)
+        for _ in range(args.warmup):
+            ftlm.ftlm_hv(b.handle, x, y)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        ev[0].record()
+        for i in range(args.steps):
+            ftlm.ftlm_hv(b.handle, x, y)
+            ev[i + 1].record()
+        torch.cuda.synchronize()
+        ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+        clt = b.mode == ftlm.RANK_CLT
+        alg = sector_model_bytes(b.updates, b.dim, 4 if dt == torch.float32 else 8, clt, lanczos=False)
+        med = statistics.median(ms)
+        print(json.dumps({"hv_only": True, "workload": args.workload, "mode": "clt" if clt else "cr",
+                          "dtype": args.dtype, "ms": ms, "ms_median": med,
+                          "Gupdates_per_s": b.updates / med * 1e-6,
+                          "sector_model_GBps": alg / med * 1e-6, "D": b.dim, "updates": b.updates}))
+
+
 def main():
     args = parse_args()
-    if args.impl == "reference":
+    if args.hv_only:
+        run_hv_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

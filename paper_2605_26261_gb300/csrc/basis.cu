@@ -179,6 +179,7 @@ void free_tables(ftlm_basis *b)
     cudaFree(b->tlo);
     cudaFree(b->ulo);
     cudaFree(b->uoff);
+    cudaFree(b->bond_slots);
     cudaFree(b->basis);
     cudaFree(b->clt);
 }
@@ -273,42 +274,59 @@ extern "C" ftlm_status ftlm_basis_create(int N, int two_sz, int n_bonds, const i
         return cuda_fail(ce, "cudaGetDevice/cudaDeviceGetAttribute");
     }
 
-    // Bond tables: CLT keeps the caller's order; CR groups by low/high block.
+    // Bond lists: CLT keeps the caller's order; CR groups by low/high block.  Both
+    // are padded to whole chunks with dummy bonds (mask 0, coupling 0).
     const int L = b->L;
     double jsum4 = 0.0;
     for (int k = 0; k < n_bonds; ++k) jsum4 += J[k] / 4.0;
-    for (BondTable *t : {&b->bonds_cr, &b->bonds_clt}) {
-        std::memset(t, 0, sizeof(*t));
-        t->nb = n_bonds;
-        t->jsum4 = jsum4;
-        t->jsum4f = (float)jsum4;
+    auto round_up = [](int v) { return (v + kBondChunk - 1) / kBondChunk * kBondChunk; };
+    // host images of the four slot arrays
+    std::vector<uint4> slots(4 * (size_t)kMaxBondSlots, make_uint4(0u, 0u, 0u, 0u));
+    auto put = [&](int which, int pos, uint32_t mlo, uint32_t mhi, double jh) {
+        float f = (float)jh;
+        uint32_t fb;
+        std::memcpy(&fb, &f, 4);
+        uint64_t db;
+        std::memcpy(&db, &jh, 8);
+        slots[(size_t)(2 * which) * kMaxBondSlots + pos] = make_uint4(mlo, mhi, fb, 0u);
+        slots[(size_t)(2 * which + 1) * kMaxBondSlots + pos] =
+            make_uint4(mlo, mhi, (uint32_t)db, (uint32_t)(db >> 32));
+    };
+    {
+        BondList &c = b->bonds_cr;
+        std::vector<int> lo, hi, rest;
+        for (int k = 0; k < n_bonds; ++k) {
+            bool il = bi[k] < L, jl = bj[k] < L;
+            (il && jl ? lo : (!il && !jl) ? hi : rest).push_back(k);
+        }
+        const int nlo = (int)lo.size() / kBondChunk * kBondChunk;
+        const int nhi = (int)hi.size() / kBondChunk * kBondChunk;
+        std::vector<int> order(lo.begin(), lo.begin() + nlo);
+        order.insert(order.end(), hi.begin(), hi.begin() + nhi);
+        order.insert(order.end(), lo.begin() + nlo, lo.end());
+        order.insert(order.end(), hi.begin() + nhi, hi.end());
+        order.insert(order.end(), rest.begin(), rest.end());
+        for (int pos = 0; pos < (int)order.size(); ++pos) {
+            const int k = order[pos];
+            const uint64_t m = (1ull << bi[k]) | (1ull << bj[k]);
+            if (pos < nlo) put(0, pos, (uint32_t)m, 0u, J[k] / 2.0);
+            else if (pos < nlo + nhi) put(0, pos, 0u, (uint32_t)(m >> L), J[k] / 2.0);
+            else put(0, pos, (uint32_t)m, (uint32_t)(m >> 32), J[k] / 2.0);
+        }
+        c.n_lo = nlo;
+        c.n_hi = nhi;
+        c.nb = nlo + nhi + round_up(n_bonds - nlo - nhi);
+        c.jsum4 = jsum4;
     }
     {
-        BondTable &t = b->bonds_clt;
+        BondList &c = b->bonds_clt;
         for (int k = 0; k < n_bonds; ++k) {
-            uint64_t m = (1ull << bi[k]) | (1ull << bj[k]);
-            t.mlo[k] = (uint32_t)m;
-            t.mhi[k] = (uint32_t)(m >> 32);
-            t.jh[k] = J[k] / 2.0;
-            t.jhf[k] = (float)(J[k] / 2.0);
+            const uint64_t m = (1ull << bi[k]) | (1ull << bj[k]);
+            put(1, k, (uint32_t)m, (uint32_t)(m >> 32), J[k] / 2.0);
         }
-        BondTable &c = b->bonds_cr;
-        int pos = 0;
-        for (int group = 0; group < 3; ++group) {
-            for (int k = 0; k < n_bonds; ++k) {
-                bool il = bi[k] < L, jl = bj[k] < L;
-                int g = (il && jl) ? 0 : (!il && !jl) ? 1 : 2;
-                if (g != group) continue;
-                uint64_t m = (1ull << bi[k]) | (1ull << bj[k]);
-                c.mlo[pos] = (uint32_t)(m & ((1ull << L) - 1));
-                c.mhi[pos] = (uint32_t)(m >> L);
-                c.jh[pos] = J[k] / 2.0;
-                c.jhf[pos] = (float)(J[k] / 2.0);
-                ++pos;
-            }
-            if (group == 0) c.n_lo = pos;
-            if (group == 1) c.n_hi = pos - c.n_lo;
-        }
+        c.n_lo = c.n_hi = 0;
+        c.nb = round_up(n_bonds);
+        c.jsum4 = jsum4;
     }
 
     // Digit-block tables on the host.
@@ -338,11 +356,21 @@ extern "C" ftlm_status ftlm_basis_create(int N, int two_sz, int n_bonds, const i
         return cuda_fail(e, what);
     };
     cudaError_t e;
+    if ((e = cudaMalloc(&b->bond_slots, slots.size() * sizeof(uint4))) != cudaSuccess)
+        return bail(e, "cudaMalloc(bond slots)");
+    if ((e = cudaMemcpy(b->bond_slots, slots.data(), slots.size() * sizeof(uint4), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+        return bail(e, "cudaMemcpy(bond slots)");
+    b->bonds_cr.slots_f32 = b->bond_slots;
+    b->bonds_cr.slots_f64 = b->bond_slots + kMaxBondSlots;
+    b->bonds_clt.slots_f32 = b->bond_slots + 2 * kMaxBondSlots;
+    b->bonds_clt.slots_f64 = b->bond_slots + 3 * kMaxBondSlots;
     if ((e = cudaMalloc(&b->thi, b->H * sizeof(uint32_t))) != cudaSuccess) return bail(e, "cudaMalloc(thi)");
     if ((e = cudaMalloc(&b->tlo, nlo * sizeof(uint16_t))) != cudaSuccess) return bail(e, "cudaMalloc(tlo)");
     if ((e = cudaMalloc(&b->ulo, nlo * sizeof(uint16_t))) != cudaSuccess) return bail(e, "cudaMalloc(ulo)");
     if ((e = cudaMalloc(&b->uoff, sizeof(b->ulo_off))) != cudaSuccess) return bail(e, "cudaMalloc(uoff)");
-    b->table_bytes = b->H * sizeof(uint32_t) + 2ull * nlo * sizeof(uint16_t) + sizeof(b->ulo_off);
+    b->table_bytes = b->H * sizeof(uint32_t) + 2ull * nlo * sizeof(uint16_t) + sizeof(b->ulo_off) +
+                     slots.size() * sizeof(uint4);
     // Synchronous copies: the host vectors go out of scope on return.
     if ((e = cudaMemcpy(b->thi, thi.data(), b->H * sizeof(uint32_t), cudaMemcpyHostToDevice)) != cudaSuccess)
         return bail(e, "cudaMemcpy(thi)");

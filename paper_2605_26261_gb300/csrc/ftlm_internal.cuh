@@ -17,25 +17,30 @@ constexpr int kRowThreads = 256;
 // Upper bound on resident blocks per SM the reduction partials are sized for.
 constexpr int kMaxBlocksPerSm = 8;
 
-// Bond list as the kernels see it (passed by value as a kernel parameter, so every
-// lane of a warp reads the same entry through the constant bank).  For the CR
-// kernels the bonds are sorted into three groups by where their two sites fall
-// relative to the low digit block: [0, n_lo) both low, [n_lo, n_lo + n_hi) both
-// high, the rest one of each.  mlo/mhi are the site bits inside the low block and
-// the high block (shifted down by L).  For the CLT kernel mlo holds the whole
-// two-bit mask (N <= 32) and the list keeps the caller's order.
-struct BondTable {
-    int nb;
+// Bonds are processed in chunks of kBondChunk: a chunk first computes every rank,
+// then issues every gather, then accumulates, so each thread keeps kBondChunk
+// independent loads in flight.  Ranges are padded to whole chunks with dummy
+// bonds (mask 0: never antiparallel, coupling 0).
+constexpr int kBondChunk = 8;
+constexpr int kMaxBondSlots = FTLM_MAX_BONDS + 2 * kBondChunk;
+
+// Bond list as the kernels see it.  Each slot is one 16-byte entry
+// {mlo, mhi, J/2 (float, or the two halves of a double)} in device memory; a block
+// stages the list into shared memory once and every lane of a warp then reads the
+// same entry (a broadcast), so no per-bond constant-bank load is issued.
+//   CR:  [0, n_lo) both sites in the low digit block (mlo = their bits),
+//        [n_lo, n_lo + n_hi) both sites in the high block (mhi = their bits >> L),
+//        [n_lo + n_hi, nb) any bond (full two-bit mask = mlo | mhi << 32).
+//        n_lo and n_hi are whole chunks; bonds left over go to the last range.
+//   CLT: [0, nb) in the caller's order, full mask in mlo (N <= 32).
+struct BondList {
+    int nb;    // slots in use, a multiple of kBondChunk
     int n_lo;
     int n_hi;
     int pad;
     double jsum4;  // sum_b J_b / 4 : the diagonal when every bond is parallel
-    float jsum4f;
-    float padf;
-    uint32_t mlo[FTLM_MAX_BONDS];
-    uint32_t mhi[FTLM_MAX_BONDS];
-    double jh[FTLM_MAX_BONDS];  // J_b / 2, the ladder coefficient (Eq. 13-14 at s = 1/2)
-    float jhf[FTLM_MAX_BONDS];
+    const uint4 *slots_f32;  // J/2 as float in .z
+    const uint4 *slots_f64;  // J/2 as double in .z (low word), .w (high word)
 };
 
 // Scalars of one Lanczos chain, kept on the device between launches.  The stored
@@ -78,8 +83,9 @@ struct ftlm_basis {
     uint64_t table_bytes;
     double tau64, tau32;
     int device, num_sms;
-    ftlm::BondTable bonds_cr;
-    ftlm::BondTable bonds_clt;
+    ftlm::BondList bonds_cr;
+    ftlm::BondList bonds_clt;
+    uint4 *bond_slots;  // device: cr f32, cr f64, clt f32, clt f64 (kMaxBondSlots each)
     uint32_t ulo_off[ftlm::kLoBitsMax + 2];
     uint32_t *thi;
     uint16_t *tlo;

@@ -41,13 +41,6 @@ namespace ftlm {
 
 namespace {
 
-template <typename V> __device__ __forceinline__ V jh_of(const BondTable &bt, int b);
-template <> __device__ __forceinline__ float jh_of<float>(const BondTable &bt, int b) { return bt.jhf[b]; }
-template <> __device__ __forceinline__ double jh_of<double>(const BondTable &bt, int b) { return bt.jh[b]; }
-template <typename V> __device__ __forceinline__ V jsum4_of(const BondTable &bt);
-template <> __device__ __forceinline__ float jsum4_of<float>(const BondTable &bt) { return bt.jsum4f; }
-template <> __device__ __forceinline__ double jsum4_of<double>(const BondTable &bt) { return bt.jsum4; }
-
 struct EpiDev {
     ChainState *st;
     double *partials;
@@ -55,11 +48,126 @@ struct EpiDev {
     int has_prev;
 };
 
-template <typename V, bool CLT, bool LANCZOS>
+// J/2 of a bond slot in the vector type.
+template <typename V> __device__ __forceinline__ V slot_jh(const uint4 &e);
+template <> __device__ __forceinline__ float slot_jh<float>(const uint4 &e) { return __uint_as_float(e.z); }
+template <> __device__ __forceinline__ double slot_jh<double>(const uint4 &e)
+{
+    return __hiloint2double((int)e.w, (int)e.z);
+}
+
+template <typename Lbl>
+__device__ __forceinline__ Lbl slot_mask(const uint4 &e)
+{
+    if constexpr (sizeof(Lbl) == 8) return (Lbl)e.x | ((Lbl)e.y << 32);
+    else return e.x;
+}
+
+// Gather the chunk's antiparallel terms (predicated loads, all issued together).
+template <typename V>
+__device__ __forceinline__ void gather_accumulate(const V *__restrict__ x, const bool (&aa)[kBondChunk],
+                                                  const uint32_t (&kk)[kBondChunk],
+                                                  const V (&jh)[kBondChunk], V &acc, V &dsum)
+{
+    V xv[kBondChunk];
+#pragma unroll
+    for (int q = 0; q < kBondChunk; ++q) xv[q] = aa[q] ? __ldg(x + kk[q]) : (V)0;
+#pragma unroll
+    for (int q = 0; q < kBondChunk; ++q) {
+        acc = fma(jh[q], xv[q], acc);
+        if (aa[q]) dsum += jh[q];
+    }
+}
+
+// Row sums of one output row (CR): sum over antiparallel bonds of (J_b/2) x[k_b]
+// in acc, sum of their J_b/2 in dsum.
+template <typename V, typename Lbl>
+__device__ __forceinline__ void row_cr(const SectorTables &s, const BondList &bl, const uint4 *s_bond,
+                                       const uint16_t *s_tlo, const V *__restrict__ x, uint32_t t, V &acc,
+                                       V &dsum)
+{
+    // inverse map t -> (h, l): last h with thi[h] <= t, then ulo within its group
+    uint32_t lo = 0, hi = s.H;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(s.thi + mid) <= t) lo = mid;
+        else hi = mid;
+    }
+    const uint32_t h = lo, r_hi = __ldg(s.thi + h), r_lo = t - r_hi;
+    const uint32_t l = __ldg(s.ulo + __ldg(s.uoff + (s.K - __popc(h))) + r_lo);
+    bool aa[kBondChunk];
+    uint32_t kk[kBondChunk];
+    V jh[kBondChunk];
+    const int e_lo = bl.n_lo, e_hi = bl.n_lo + bl.n_hi;
+    for (int b0 = 0; b0 < e_lo; b0 += kBondChunk) {  // both sites in the low block
+#pragma unroll
+        for (int q = 0; q < kBondChunk; ++q) {
+            const uint4 e = s_bond[b0 + q];
+            const uint32_t m = e.x, xm = l & m;
+            aa[q] = (xm != 0u) & (xm != m);
+            kk[q] = r_hi + s_tlo[l ^ m];
+            jh[q] = slot_jh<V>(e);
+        }
+        gather_accumulate(x, aa, kk, jh, acc, dsum);
+    }
+    for (int b0 = e_lo; b0 < e_hi; b0 += kBondChunk) {  // both sites in the high block
+#pragma unroll
+        for (int q = 0; q < kBondChunk; ++q) {
+            const uint4 e = s_bond[b0 + q];
+            const uint32_t m = e.y, xm = h & m;
+            aa[q] = (xm != 0u) & (xm != m);
+            kk[q] = __ldg(s.thi + (h ^ m)) + r_lo;
+            jh[q] = slot_jh<V>(e);
+        }
+        gather_accumulate(x, aa, kk, jh, acc, dsum);
+    }
+    const Lbl n = ((Lbl)h << s.L) | l;
+    for (int b0 = e_hi; b0 < bl.nb; b0 += kBondChunk) {  // any bond
+#pragma unroll
+        for (int q = 0; q < kBondChunk; ++q) {
+            const uint4 e = s_bond[b0 + q];
+            const Lbl m = slot_mask<Lbl>(e), xm = n & m, nn = n ^ m;
+            aa[q] = (xm != 0) & (xm != m);
+            kk[q] = __ldg(s.thi + (uint32_t)(nn >> s.L)) + s_tlo[(uint32_t)nn & s.lomask];
+            jh[q] = slot_jh<V>(e);
+        }
+        gather_accumulate(x, aa, kk, jh, acc, dsum);
+    }
+}
+
+// Row sums of one output row (CLT, Algorithm 2 per exchanged label).
+template <typename V>
+__device__ __forceinline__ void row_clt(const SectorTables &s, const BondList &bl, const uint4 *s_bond,
+                                        const V *__restrict__ x, uint32_t t, V &acc, V &dsum)
+{
+    const uint32_t n = __ldcs(s.basis + t);
+    bool aa[kBondChunk];
+    uint32_t kk[kBondChunk], nn[kBondChunk];
+    uint2 e2[kBondChunk];
+    V jh[kBondChunk];
+    for (int b0 = 0; b0 < bl.nb; b0 += kBondChunk) {
+#pragma unroll
+        for (int q = 0; q < kBondChunk; ++q) {
+            const uint4 e = s_bond[b0 + q];
+            const uint32_t m = e.x, xm = n & m;
+            aa[q] = (xm != 0u) & (xm != m);
+            nn[q] = n ^ m;
+            jh[q] = slot_jh<V>(e);
+        }
+#pragma unroll
+        for (int q = 0; q < kBondChunk; ++q) e2[q] = aa[q] ? __ldg(s.clt + (nn[q] >> 5)) : make_uint2(0u, 0u);
+#pragma unroll
+        for (int q = 0; q < kBondChunk; ++q) kk[q] = e2[q].y + __popc(e2[q].x & ((1u << (nn[q] & 31u)) - 1u));
+        gather_accumulate(x, aa, kk, jh, acc, dsum);
+    }
+}
+
+template <typename V, typename Lbl, bool CLT, bool LANCZOS>
 __global__ void __launch_bounds__(kRowThreads)
-hv_kernel(const SectorTables s, const BondTable bt, const V *__restrict__ x, V *y, const EpiDev ep)
+hv_kernel(const SectorTables s, const BondList bl, const V *__restrict__ x, V *y, const EpiDev ep)
 {
     extern __shared__ uint16_t s_tlo[];
+    __shared__ uint4 s_bond[kMaxBondSlots];
     double inv_s = 1.0, c_prev = 0.0;
     if (LANCZOS) {
         const ChainState *st = ep.st;
@@ -67,71 +175,20 @@ hv_kernel(const SectorTables s, const BondTable bt, const V *__restrict__ x, V *
         inv_s = 1.0 / st->s_cur;
         if (ep.has_prev) c_prev = st->beta_prev / st->s_prev;
     }
-    if (!CLT) {
-        for (uint32_t i = threadIdx.x; i <= s.lomask; i += blockDim.x) s_tlo[i] = __ldg(s.tlo + i);
-        __syncthreads();
+    {
+        const uint4 *src = sizeof(V) == 4 ? bl.slots_f32 : bl.slots_f64;
+        for (int i = threadIdx.x; i < bl.nb; i += blockDim.x) s_bond[i] = src[i];
     }
-    const V inv_s_v = (V)inv_s, c_prev_v = (V)c_prev, jsum4 = jsum4_of<V>(bt);
+    if (!CLT)
+        for (uint32_t i = threadIdx.x; i <= s.lomask; i += blockDim.x) s_tlo[i] = __ldg(s.tlo + i);
+    __syncthreads();
+    const V inv_s_v = (V)inv_s, c_prev_v = (V)c_prev, jsum4 = (V)bl.jsum4;
     double apart = 0.0;
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < s.D; t += stride) {
         V acc = 0, dsum = 0;
-        if (CLT) {
-            const uint32_t n = __ldcs(s.basis + t);
-#pragma unroll 4
-            for (int b = 0; b < bt.nb; ++b) {
-                const uint32_t m = bt.mlo[b], xm = n & m;
-                if (xm != 0u && xm != m) {
-                    const uint32_t nn = n ^ m;
-                    const uint2 e = __ldg(s.clt + (nn >> 5));
-                    const uint32_t k = e.y + __popc(e.x & ((1u << (nn & 31u)) - 1u));
-                    const V jh = jh_of<V>(bt, b);
-                    acc = fma(jh, __ldg(x + k), acc);
-                    dsum += jh;
-                }
-            }
-        } else {
-            // inverse map t -> (h, l)
-            uint32_t lo = 0, hi = s.H;
-            while (hi - lo > 1) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (__ldg(s.thi + mid) <= t) lo = mid;
-                else hi = mid;
-            }
-            const uint32_t h = lo, r_hi = __ldg(s.thi + h), r_lo = t - r_hi;
-            const uint32_t l = __ldg(s.ulo + __ldg(s.uoff + (s.K - __popc(h))) + r_lo);
-            const int b1 = bt.n_lo, b2 = bt.n_lo + bt.n_hi;
-#pragma unroll 4
-            for (int b = 0; b < b1; ++b) {  // both sites in the low block
-                const uint32_t m = bt.mlo[b], xm = l & m;
-                if (xm != 0u && xm != m) {
-                    const uint32_t k = r_hi + s_tlo[l ^ m];
-                    const V jh = jh_of<V>(bt, b);
-                    acc = fma(jh, __ldg(x + k), acc);
-                    dsum += jh;
-                }
-            }
-#pragma unroll 4
-            for (int b = b1; b < b2; ++b) {  // both sites in the high block
-                const uint32_t m = bt.mhi[b], xm = h & m;
-                if (xm != 0u && xm != m) {
-                    const uint32_t k = __ldg(s.thi + (h ^ m)) + r_lo;
-                    const V jh = jh_of<V>(bt, b);
-                    acc = fma(jh, __ldg(x + k), acc);
-                    dsum += jh;
-                }
-            }
-#pragma unroll 4
-            for (int b = b2; b < bt.nb; ++b) {  // one site in each block
-                const uint32_t ml = bt.mlo[b], mh = bt.mhi[b];
-                if (((l & ml) != 0u) != ((h & mh) != 0u)) {
-                    const uint32_t k = __ldg(s.thi + (h ^ mh)) + s_tlo[l ^ ml];
-                    const V jh = jh_of<V>(bt, b);
-                    acc = fma(jh, __ldg(x + k), acc);
-                    dsum += jh;
-                }
-            }
-        }
+        if (CLT) row_clt<V>(s, bl, s_bond, x, t, acc, dsum);
+        else row_cr<V, Lbl>(s, bl, s_bond, s_tlo, x, t, acc, dsum);
         const V xt = __ldg(x + t);
         const V hv = fma(jsum4 - dsum, xt, acc);
         if (LANCZOS) {
@@ -156,12 +213,12 @@ hv_kernel(const SectorTables s, const BondTable bt, const V *__restrict__ x, V *
     }
 }
 
-template <typename V, bool CLT, bool LANCZOS>
+template <typename V, typename Lbl, bool CLT, bool LANCZOS>
 ftlm_status launch(const ftlm_basis *b, const V *x, V *y, const EpiDev &ep, cudaStream_t stream)
 {
     static int occ = -1;  // resident blocks per SM for this instantiation
     const size_t smem = CLT ? 0 : ((size_t)1 << b->L) * sizeof(uint16_t);
-    auto kern = hv_kernel<V, CLT, LANCZOS>;
+    auto kern = hv_kernel<V, Lbl, CLT, LANCZOS>;
     if (occ < 0) {
         const size_t smem_max = CLT ? 0 : ((size_t)1 << kLoBitsMax) * sizeof(uint16_t);
         FTLM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kRowThreads, smem_max));
@@ -174,22 +231,27 @@ ftlm_status launch(const ftlm_basis *b, const V *x, V *y, const EpiDev &ep, cuda
     return FTLM_OK;
 }
 
+template <typename V, bool LANCZOS>
+ftlm_status launch_mode(const ftlm_basis *b, const void *x, void *y, const EpiDev &ep, cudaStream_t stream)
+{
+    if (b->mode == FTLM_RANK_CLT) return launch<V, uint32_t, true, LANCZOS>(b, (const V *)x, (V *)y, ep, stream);
+    if (b->N <= 32) return launch<V, uint32_t, false, LANCZOS>(b, (const V *)x, (V *)y, ep, stream);
+    return launch<V, uint64_t, false, LANCZOS>(b, (const V *)x, (V *)y, ep, stream);
+}
+
 template <typename V>
 ftlm_status launch_typed(const ftlm_basis *b, const void *x, void *y, const LanczosHv *epi,
                          cudaStream_t stream)
 {
     EpiDev ep{};
-    const bool clt = b->mode == FTLM_RANK_CLT;
     if (epi) {
         ep.st = epi->st;
         ep.partials = epi->partials;
         ep.alpha_out = epi->alpha_out;
         ep.has_prev = epi->j > 1;
-        return clt ? launch<V, true, true>(b, (const V *)x, (V *)y, ep, stream)
-                   : launch<V, false, true>(b, (const V *)x, (V *)y, ep, stream);
+        return launch_mode<V, true>(b, x, y, ep, stream);
     }
-    return clt ? launch<V, true, false>(b, (const V *)x, (V *)y, ep, stream)
-               : launch<V, false, false>(b, (const V *)x, (V *)y, ep, stream);
+    return launch_mode<V, false>(b, x, y, ep, stream);
 }
 
 }  // namespace
