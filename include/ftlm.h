@@ -177,6 +177,31 @@ ftlm_status ftlm_lanczos_from(const ftlm_basis *basis, int R, int M, const doubl
                               double *theta_dev, double *weight_dev, int *m_eff_dev,
                               double *alpha_dev, double *beta_dev, void *stream);
 
+/* ftlm_lanczos_noalloc -- ftlm_lanczos without a caller workspace and without any
+ * device allocation.  The paper has no counterpart: this entry point exists for
+ * callers that cannot call cudaMalloc at all, or not at the time of the call, e.g.
+ * a host application that owns every device allocation and forbids new ones after
+ * start-up, or a caller that must not risk the implicit device synchronization
+ * that cudaMalloc/cudaFree can cause.
+ *   Scratch: a file-scope __device__ array of FTLM_NOALLOC_SCRATCH_BYTES inside the
+ *   library.  Every GPU that loads the library holds it until the process exits.
+ *   The first call on a device looks up the array's device address on the current
+ *   device (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   Limit: the workspace ftlm_lanczos_workspace_bytes() reports for (R, M, dtype)
+ *   must fit in the array, else FTLM_EUNSUPPORTED (two vectors of D elements plus
+ *   O(R M) coefficients: about D <= 2 million in FP64, 4 million in FP32).
+ *   Sharing: all calls on a device use the same array and it keeps the previous
+ *   call's contents; each call clears what must start at zero.  Calls whose work
+ *   overlaps on the GPU (different streams, or different host threads) race on the
+ *   array; serialize them.
+ *   Arguments and outputs as for ftlm_lanczos.  Allocates nothing: no cudaMalloc,
+ *   cudaFree or allocating library routine. */
+#define FTLM_NOALLOC_SCRATCH_BYTES (32ull << 20)
+ftlm_status ftlm_lanczos_noalloc(const ftlm_basis *basis, int R, int M, uint64_t seed,
+                                 ftlm_vec_dist dist, ftlm_dtype dtype, double *theta_dev,
+                                 double *weight_dev, int *m_eff_dev, double *alpha_dev,
+                                 double *beta_dev, void *stream);
+
 /* ftlm_ritz -- the Ritz step alone (a5): for each of n chains, the eigenvalues theta
  * and first-component weights w = s_{k,1}^2 of the tridiagonal matrix with diagonal
  * alpha_dev[c*M .. c*M+m-1] and off-diagonal beta_dev[c*M .. c*M+m-2], m = m_dev[c]

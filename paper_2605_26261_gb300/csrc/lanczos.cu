@@ -12,6 +12,7 @@
 // queues 2 launches per step, and a chain that breaks down (beta_j <= tau) turns
 // the rest of its launches into no-ops.
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "ftlm_internal.cuh"
@@ -363,11 +364,56 @@ ftlm_status lanczos_common(const ftlm_basis *b, int R, int M, uint64_t seed, int
                                     alpha_dev, beta_dev, (cudaStream_t)stream);
 }
 
+// Scratch of ftlm_lanczos_noalloc, for callers that cannot allocate device memory.
+// Host code sees only a host-side stand-in for this symbol; its device address is
+// looked up once per device with cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[FTLM_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device (looked up on first use).
+ftlm_status noalloc_scratch(void **out)
+{
+    int dev = 0;
+    FTLM_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(FTLM_EUNSUPPORTED, "device index beyond 64");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        FTLM_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return FTLM_OK;
+}
+
 }  // namespace
 
 }  // namespace ftlm
 
 using namespace ftlm;
+
+extern "C" ftlm_status ftlm_lanczos_noalloc(const ftlm_basis *b, int R, int M, uint64_t seed,
+                                            ftlm_vec_dist dist, ftlm_dtype dtype, double *theta_dev,
+                                            double *weight_dev, int *m_eff_dev, double *alpha_dev,
+                                            double *beta_dev, void *stream)
+{
+    if (!b) return fail(FTLM_EINVAL, "NULL basis");
+    if (R < 1 || M < 1 || M > FTLM_MAX_LANCZOS) return fail(FTLM_EINVAL, "R or M out of range");
+    if (dtype != FTLM_F32 && dtype != FTLM_F64) return fail(FTLM_EINVAL, "bad dtype");
+    const uint64_t need = layout(b, R, M, dtype).total;
+    if (need > FTLM_NOALLOC_SCRATCH_BYTES)
+        return fail(FTLM_EUNSUPPORTED, "workspace of " + std::to_string(need) +
+                                           " bytes exceeds the static scratch of FTLM_NOALLOC_SCRATCH_BYTES (" +
+                                           std::to_string(FTLM_NOALLOC_SCRATCH_BYTES) + " bytes)");
+    void *scratch = nullptr;
+    ftlm_status s = noalloc_scratch(&scratch);
+    if (s != FTLM_OK) return s;
+    return lanczos_common(b, R, M, seed, dist, nullptr, dtype, scratch, FTLM_NOALLOC_SCRATCH_BYTES,
+                          theta_dev, weight_dev, m_eff_dev, alpha_dev, beta_dev, stream);
+}
 
 extern "C" ftlm_status ftlm_lanczos_workspace_bytes(const ftlm_basis *b, int R, int M, ftlm_dtype dtype,
                                                     uint64_t *bytes)

@@ -63,6 +63,7 @@ def lib():
         "ftlm_lanczos_workspace_bytes": [P, I, I, I, PU64],
         "ftlm_lanczos": [P, I, I, U64, I, I, P, U64, P, P, P, P, P, P],
         "ftlm_lanczos_from": [P, I, I, P, I, P, U64, P, P, P, P, P, P],
+        "ftlm_lanczos_noalloc": [P, I, I, U64, I, I, P, P, P, P, P, P],
         "ftlm_ritz": [I, I, P, P, P, P, P, P],
         "ftlm_thermo": [I, P, P, I, I, P, P, P, I, D, D, I, P, P, P, P, P, P],
         "ftlm_profile_enable": [I],
@@ -200,6 +201,15 @@ def ftlm_lanczos_from(handle, R, M, start, dtype, work, theta, weight, m_eff, al
     _check(lib().ftlm_lanczos_from(handle, int(R), int(M), _ptr(start), _dtype_code(dtype), _ptr(work),
                                    work.numel() * work.element_size(), _ptr(theta), _ptr(weight),
                                    _ptr(m_eff), _ptr(alpha), _ptr(beta), _stream(stream)))
+
+
+def ftlm_lanczos_noalloc(handle, R, M, seed, dist, dtype, theta, weight, m_eff, alpha=None, beta=None,
+                         stream=None):
+    """ftlm_lanczos with the library's static scratch instead of a workspace (for
+    callers that cannot allocate device memory); outputs as for ftlm_lanczos."""
+    _check(lib().ftlm_lanczos_noalloc(handle, int(R), int(M), int(seed) & (2**64 - 1), int(dist),
+                                      _dtype_code(dtype), _ptr(theta), _ptr(weight), _ptr(m_eff),
+                                      _ptr(alpha), _ptr(beta), _stream(stream)))
 
 
 def ftlm_ritz(n, M, alpha, beta, m, theta, weight, stream=None):
