@@ -90,6 +90,23 @@ __device__ __forceinline__ uint64_t unrank_label(uint32_t t, const SectorTables 
     return ((uint64_t)lo << s.L) | l;
 }
 
+// hs[k] = high pattern of row min(k << kHsShift, D - 1).
+__global__ void hs_fill_kernel(SectorTables s, uint64_t n_hs, uint32_t *hs)
+{
+    for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < n_hs;
+         k += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t row = k << kHsShift;
+        const uint32_t t = (uint32_t)(row < s.D ? row : s.D - 1);
+        uint32_t lo = 0, hi = s.H;
+        while (hi - lo > 1) {
+            uint32_t mid = (lo + hi) >> 1;
+            if (__ldg(s.thi + mid) <= t) lo = mid;
+            else hi = mid;
+        }
+        hs[k] = lo;
+    }
+}
+
 __global__ void basis_fill_kernel(SectorTables s, uint32_t *basis)
 {
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < s.D;
@@ -179,6 +196,7 @@ void free_tables(ftlm_basis *b)
     cudaFree(b->tlo);
     cudaFree(b->ulo);
     cudaFree(b->uoff);
+    cudaFree(b->hs);
     cudaFree(b->bond_slots);
     cudaFree(b->basis);
     cudaFree(b->clt);
@@ -213,6 +231,7 @@ ftlm::SectorTables ftlm_basis::tables() const
     s.tlo = tlo;
     s.ulo = ulo;
     s.uoff = uoff;
+    s.hs = hs;
     s.basis = basis;
     s.clt = clt;
     return s;
@@ -380,6 +399,12 @@ extern "C" ftlm_status ftlm_basis_create(int N, int two_sz, int n_bonds, const i
         return bail(e, "cudaMemcpy(ulo)");
     if ((e = cudaMemcpy(b->uoff, b->ulo_off, sizeof(b->ulo_off), cudaMemcpyHostToDevice)) != cudaSuccess)
         return bail(e, "cudaMemcpy(uoff)");
+    b->n_hs = ((D - 1) >> kHsShift) + 2;
+    if ((e = cudaMalloc(&b->hs, b->n_hs * sizeof(uint32_t))) != cudaSuccess) return bail(e, "cudaMalloc(hs)");
+    b->table_bytes += b->n_hs * sizeof(uint32_t);
+    hs_fill_kernel<<<grid_for(b->n_hs, 256, b->num_sms), 256, 0, stream>>>(b->tables(), b->n_hs, b->hs);
+    if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "hs_fill_kernel");
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return bail(e, "hs_fill_kernel");
 
     if (mode == FTLM_RANK_CLT) {
         if ((e = cudaMalloc(&b->basis, D * sizeof(uint32_t))) != cudaSuccess) return bail(e, "cudaMalloc(basis)");

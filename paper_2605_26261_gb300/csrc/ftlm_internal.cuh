@@ -12,6 +12,9 @@ namespace ftlm {
 
 // Low digit block of the combinatorial rank: the L lowest label bits (L <= 14).
 constexpr int kLoBitsMax = 14;
+// Coarse row index: one high-block pattern per 2^kHsShift rows narrows the inverse
+// map's search to the few blocks between two consecutive entries.
+constexpr int kHsShift = 8;
 // Threads per block of the row-parallel kernels.
 constexpr int kRowThreads = 256;
 // Upper bound on resident blocks per SM the reduction partials are sized for.
@@ -66,6 +69,7 @@ struct SectorTables {
     const uint16_t *tlo; // [2^L] rank of a low pattern among patterns of its popcount
     const uint16_t *ulo; // [2^L] patterns grouped by popcount, ascending (inverse of tlo)
     const uint32_t *uoff; // [kLoBitsMax + 2] start of popcount group c in ulo
+    const uint32_t *hs;   // [(D-1) >> kHsShift + 2] high pattern of row min(k << kHsShift, D-1)
     const uint32_t *basis;  // CLT mode: sorted labels [D]
     const uint2 *clt;       // CLT mode: {M_b, C_b} per 32-label block
 };
@@ -91,6 +95,8 @@ struct ftlm_basis {
     uint16_t *tlo;
     uint16_t *ulo;
     uint32_t *uoff;
+    uint32_t *hs;
+    uint64_t n_hs;
     uint32_t *basis;
     uint2 *clt;
 

@@ -34,6 +34,8 @@
 //   y[t] = (H u_j)[t] / s_j - (beta_{j-1} / s_{j-1}) u_{j-1}[t]     (overwrites u_{j-1})
 //   alpha partial += q_j[t] y[t]                                    (FP64)
 // The last block adds the per-block partials in a fixed order and stores alpha_j.
+#include <cstdlib>
+
 #include "ftlm_internal.cuh"
 #include "reduce.cuh"
 
@@ -63,106 +65,162 @@ __device__ __forceinline__ Lbl slot_mask(const uint4 &e)
     else return e.x;
 }
 
-// Gather the chunk's antiparallel terms (predicated loads, all issued together).
+// Bond data of one chunk, read once and applied to every row of the thread.
 template <typename V>
-__device__ __forceinline__ void gather_accumulate(const V *__restrict__ x, const bool (&aa)[kBondChunk],
-                                                  const uint32_t (&kk)[kBondChunk],
-                                                  const V (&jh)[kBondChunk], V &acc, V &dsum)
+struct Chunk {
+    uint32_t mlo[kBondChunk], mhi[kBondChunk];
+    V jh[kBondChunk];
+};
+
+template <typename V>
+__device__ __forceinline__ void load_chunk(const uint4 *s_bond, int b0, Chunk<V> &c)
 {
-    V xv[kBondChunk];
-#pragma unroll
-    for (int q = 0; q < kBondChunk; ++q) xv[q] = aa[q] ? __ldg(x + kk[q]) : (V)0;
 #pragma unroll
     for (int q = 0; q < kBondChunk; ++q) {
-        acc = fma(jh[q], xv[q], acc);
-        if (aa[q]) dsum += jh[q];
+        const uint4 e = s_bond[b0 + q];  // same address in every lane: a broadcast
+        c.mlo[q] = e.x;
+        c.mhi[q] = e.y;
+        c.jh[q] = slot_jh<V>(e);
     }
 }
 
-// Row sums of one output row (CR): sum over antiparallel bonds of (J_b/2) x[k_b]
-// in acc, sum of their J_b/2 in dsum.
-template <typename V, typename Lbl>
-__device__ __forceinline__ void row_cr(const SectorTables &s, const BondList &bl, const uint4 *s_bond,
-                                       const uint16_t *s_tlo, const V *__restrict__ x, uint32_t t, V &acc,
-                                       V &dsum)
+// Gather the chunk's antiparallel terms of RT rows (predicated loads, all issued
+// before the first use) and accumulate them.
+template <typename V, int RT>
+__device__ __forceinline__ void gather_accumulate(const V *__restrict__ x, const Chunk<V> &c,
+                                                  const bool (&aa)[RT][kBondChunk],
+                                                  const uint32_t (&kk)[RT][kBondChunk], V (&acc)[RT],
+                                                  V (&dsum)[RT])
 {
-    // inverse map t -> (h, l): last h with thi[h] <= t, then ulo within its group
-    uint32_t lo = 0, hi = s.H;
+    V xv[RT][kBondChunk];
+#pragma unroll
+    for (int i = 0; i < RT; ++i)
+#pragma unroll
+        for (int q = 0; q < kBondChunk; ++q) xv[i][q] = aa[i][q] ? __ldg(x + kk[i][q]) : (V)0;
+#pragma unroll
+    for (int i = 0; i < RT; ++i)
+#pragma unroll
+        for (int q = 0; q < kBondChunk; ++q)
+            if (aa[i][q]) {
+                acc[i] = fma(c.jh[q], xv[i][q], acc[i]);
+                dsum[i] += c.jh[q];
+            }
+}
+
+// Inverse map t -> (h, l) through the digit-block tables: the coarse index bounds
+// h to [hs[t >> kHsShift], hs[(t >> kHsShift) + 1]]; a binary search of thi finds
+// the last h with thi[h] <= t; the low pattern is entry t - thi[h] of popcount
+// group K - popcount(h).
+__device__ __forceinline__ void unrank_hl(const SectorTables &s, uint32_t t, uint32_t &h, uint32_t &l,
+                                          uint32_t &r_hi, uint32_t &r_lo)
+{
+    const uint32_t kc = t >> kHsShift;
+    uint32_t lo = __ldg(s.hs + kc), hi = __ldg(s.hs + kc + 1) + 1;
     while (hi - lo > 1) {
         const uint32_t mid = (lo + hi) >> 1;
         if (__ldg(s.thi + mid) <= t) lo = mid;
         else hi = mid;
     }
-    const uint32_t h = lo, r_hi = __ldg(s.thi + h), r_lo = t - r_hi;
-    const uint32_t l = __ldg(s.ulo + __ldg(s.uoff + (s.K - __popc(h))) + r_lo);
-    bool aa[kBondChunk];
-    uint32_t kk[kBondChunk];
-    V jh[kBondChunk];
+    h = lo;
+    r_hi = __ldg(s.thi + h);
+    r_lo = t - r_hi;
+    l = __ldg(s.ulo + __ldg(s.uoff + (s.K - __popc(h))) + r_lo);
+}
+
+// Row sums of RT output rows (CR): sum over antiparallel bonds of (J_b/2) x[k_b] in
+// acc, sum of their J_b/2 in dsum.
+template <typename V, typename Lbl, int RT>
+__device__ __forceinline__ void rows_cr(const SectorTables &s, const BondList &bl, const uint4 *s_bond,
+                                        const uint16_t *s_tlo, const V *__restrict__ x,
+                                        const uint32_t (&t)[RT], V (&acc)[RT], V (&dsum)[RT])
+{
+    uint32_t h[RT], l[RT], r_hi[RT], r_lo[RT];
+#pragma unroll
+    for (int i = 0; i < RT; ++i) unrank_hl(s, t[i], h[i], l[i], r_hi[i], r_lo[i]);
+    Chunk<V> c;
+    bool aa[RT][kBondChunk];
+    uint32_t kk[RT][kBondChunk];
     const int e_lo = bl.n_lo, e_hi = bl.n_lo + bl.n_hi;
     for (int b0 = 0; b0 < e_lo; b0 += kBondChunk) {  // both sites in the low block
+        load_chunk(s_bond, b0, c);
 #pragma unroll
-        for (int q = 0; q < kBondChunk; ++q) {
-            const uint4 e = s_bond[b0 + q];
-            const uint32_t m = e.x, xm = l & m;
-            aa[q] = (xm != 0u) & (xm != m);
-            kk[q] = r_hi + s_tlo[l ^ m];
-            jh[q] = slot_jh<V>(e);
-        }
-        gather_accumulate(x, aa, kk, jh, acc, dsum);
+        for (int i = 0; i < RT; ++i)
+#pragma unroll
+            for (int q = 0; q < kBondChunk; ++q) {
+                const uint32_t m = c.mlo[q], xm = l[i] & m;
+                aa[i][q] = (xm != 0u) & (xm != m);
+                kk[i][q] = r_hi[i] + s_tlo[l[i] ^ m];
+            }
+        gather_accumulate<V, RT>(x, c, aa, kk, acc, dsum);
     }
     for (int b0 = e_lo; b0 < e_hi; b0 += kBondChunk) {  // both sites in the high block
+        load_chunk(s_bond, b0, c);
 #pragma unroll
-        for (int q = 0; q < kBondChunk; ++q) {
-            const uint4 e = s_bond[b0 + q];
-            const uint32_t m = e.y, xm = h & m;
-            aa[q] = (xm != 0u) & (xm != m);
-            kk[q] = __ldg(s.thi + (h ^ m)) + r_lo;
-            jh[q] = slot_jh<V>(e);
-        }
-        gather_accumulate(x, aa, kk, jh, acc, dsum);
+        for (int i = 0; i < RT; ++i)
+#pragma unroll
+            for (int q = 0; q < kBondChunk; ++q) {
+                const uint32_t m = c.mhi[q], xm = h[i] & m;
+                aa[i][q] = (xm != 0u) & (xm != m);
+                kk[i][q] = __ldg(s.thi + (h[i] ^ m)) + r_lo[i];
+            }
+        gather_accumulate<V, RT>(x, c, aa, kk, acc, dsum);
     }
-    const Lbl n = ((Lbl)h << s.L) | l;
     for (int b0 = e_hi; b0 < bl.nb; b0 += kBondChunk) {  // any bond
+        load_chunk(s_bond, b0, c);
 #pragma unroll
-        for (int q = 0; q < kBondChunk; ++q) {
-            const uint4 e = s_bond[b0 + q];
-            const Lbl m = slot_mask<Lbl>(e), xm = n & m, nn = n ^ m;
-            aa[q] = (xm != 0) & (xm != m);
-            kk[q] = __ldg(s.thi + (uint32_t)(nn >> s.L)) + s_tlo[(uint32_t)nn & s.lomask];
-            jh[q] = slot_jh<V>(e);
+        for (int i = 0; i < RT; ++i) {
+            const Lbl n = ((Lbl)h[i] << s.L) | l[i];
+#pragma unroll
+            for (int q = 0; q < kBondChunk; ++q) {
+                Lbl m = c.mlo[q];
+                if constexpr (sizeof(Lbl) == 8) m |= (Lbl)c.mhi[q] << 32;
+                const Lbl xm = n & m, nn = n ^ m;
+                aa[i][q] = (xm != 0) & (xm != m);
+                kk[i][q] = __ldg(s.thi + (uint32_t)(nn >> s.L)) + s_tlo[(uint32_t)nn & s.lomask];
+            }
         }
-        gather_accumulate(x, aa, kk, jh, acc, dsum);
+        gather_accumulate<V, RT>(x, c, aa, kk, acc, dsum);
     }
 }
 
-// Row sums of one output row (CLT, Algorithm 2 per exchanged label).
-template <typename V>
-__device__ __forceinline__ void row_clt(const SectorTables &s, const BondList &bl, const uint4 *s_bond,
-                                        const V *__restrict__ x, uint32_t t, V &acc, V &dsum)
+// Row sums of RT output rows (CLT, Algorithm 2 per exchanged label).
+template <typename V, int RT>
+__device__ __forceinline__ void rows_clt(const SectorTables &s, const BondList &bl, const uint4 *s_bond,
+                                         const V *__restrict__ x, const uint32_t (&t)[RT], V (&acc)[RT],
+                                         V (&dsum)[RT])
 {
-    const uint32_t n = __ldcs(s.basis + t);
-    bool aa[kBondChunk];
-    uint32_t kk[kBondChunk], nn[kBondChunk];
-    uint2 e2[kBondChunk];
-    V jh[kBondChunk];
+    uint32_t n[RT];
+#pragma unroll
+    for (int i = 0; i < RT; ++i) n[i] = __ldcs(s.basis + t[i]);
+    Chunk<V> c;
+    bool aa[RT][kBondChunk];
+    uint32_t kk[RT][kBondChunk];
     for (int b0 = 0; b0 < bl.nb; b0 += kBondChunk) {
+        load_chunk(s_bond, b0, c);
+        uint2 e2[RT][kBondChunk];
 #pragma unroll
-        for (int q = 0; q < kBondChunk; ++q) {
-            const uint4 e = s_bond[b0 + q];
-            const uint32_t m = e.x, xm = n & m;
-            aa[q] = (xm != 0u) & (xm != m);
-            nn[q] = n ^ m;
-            jh[q] = slot_jh<V>(e);
-        }
+        for (int i = 0; i < RT; ++i)
 #pragma unroll
-        for (int q = 0; q < kBondChunk; ++q) e2[q] = aa[q] ? __ldg(s.clt + (nn[q] >> 5)) : make_uint2(0u, 0u);
+            for (int q = 0; q < kBondChunk; ++q) {
+                const uint32_t m = c.mlo[q], xm = n[i] & m;
+                aa[i][q] = (xm != 0u) & (xm != m);
+                e2[i][q] = aa[i][q] ? __ldg(s.clt + ((n[i] ^ m) >> 5)) : make_uint2(0u, 0u);
+            }
 #pragma unroll
-        for (int q = 0; q < kBondChunk; ++q) kk[q] = e2[q].y + __popc(e2[q].x & ((1u << (nn[q] & 31u)) - 1u));
-        gather_accumulate(x, aa, kk, jh, acc, dsum);
+        for (int i = 0; i < RT; ++i)
+#pragma unroll
+            for (int q = 0; q < kBondChunk; ++q) {
+                const uint32_t nn = n[i] ^ c.mlo[q];
+                kk[i][q] = e2[i][q].y + __popc(e2[i][q].x & ((1u << (nn & 31u)) - 1u));
+            }
+        gather_accumulate<V, RT>(x, c, aa, kk, acc, dsum);
     }
 }
 
-template <typename V, typename Lbl, bool CLT, bool LANCZOS>
+// One warp owns a tile of 32 RT consecutive rows; lane l handles rows
+// tile_base + l + 32 i (i < RT).  Tiles are dealt to warps round-robin, so the
+// whole grid works on one contiguous window of rows at a time.
+template <typename V, typename Lbl, bool CLT, bool LANCZOS, int RT>
 __global__ void __launch_bounds__(kRowThreads)
 hv_kernel(const SectorTables s, const BondList bl, const V *__restrict__ x, V *y, const EpiDev ep)
 {
@@ -184,20 +242,38 @@ hv_kernel(const SectorTables s, const BondList bl, const V *__restrict__ x, V *y
     __syncthreads();
     const V inv_s_v = (V)inv_s, c_prev_v = (V)c_prev, jsum4 = (V)bl.jsum4;
     double apart = 0.0;
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < s.D; t += stride) {
-        V acc = 0, dsum = 0;
-        if (CLT) row_clt<V>(s, bl, s_bond, x, t, acc, dsum);
-        else row_cr<V, Lbl>(s, bl, s_bond, s_tlo, x, t, acc, dsum);
-        const V xt = __ldg(x + t);
-        const V hv = fma(jsum4 - dsum, xt, acc);
-        if (LANCZOS) {
-            const V up = ep.has_prev ? __ldcs(y + t) : (V)0;
-            const V yv = fma(-c_prev_v, up, hv * inv_s_v);
-            __stcs(y + t, yv);
-            apart += (double)(xt * inv_s_v) * (double)yv;
-        } else {
-            __stcs(y + t, hv);
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t tile_rows = 32u * RT;
+    const uint32_t ntiles = (uint32_t)(((uint64_t)s.D + tile_rows - 1) / tile_rows);
+    for (uint32_t tile = warp; tile < ntiles; tile += nwarps) {
+        uint32_t t[RT];
+        bool ok[RT];
+#pragma unroll
+        for (int i = 0; i < RT; ++i) {
+            const uint32_t tt = tile * tile_rows + 32u * i + lane;
+            ok[i] = tt < s.D;
+            t[i] = ok[i] ? tt : s.D - 1;  // rows past the end recompute the last row, unstored
+        }
+        V acc[RT], dsum[RT];
+#pragma unroll
+        for (int i = 0; i < RT; ++i) acc[i] = dsum[i] = (V)0;
+        if (CLT) rows_clt<V, RT>(s, bl, s_bond, x, t, acc, dsum);
+        else rows_cr<V, Lbl, RT>(s, bl, s_bond, s_tlo, x, t, acc, dsum);
+#pragma unroll
+        for (int i = 0; i < RT; ++i) {
+            if (!ok[i]) continue;
+            const V xt = __ldg(x + t[i]);
+            const V hv = fma(jsum4 - dsum[i], xt, acc[i]);
+            if (LANCZOS) {
+                const V up = ep.has_prev ? __ldcs(y + t[i]) : (V)0;
+                const V yv = fma(-c_prev_v, up, hv * inv_s_v);
+                __stcs(y + t[i], yv);
+                apart += (double)(xt * inv_s_v) * (double)yv;
+            } else {
+                __stcs(y + t[i], hv);
+            }
         }
     }
     if (LANCZOS) {
@@ -213,17 +289,31 @@ hv_kernel(const SectorTables s, const BondList bl, const V *__restrict__ x, V *y
     }
 }
 
-template <typename V, typename Lbl, bool CLT, bool LANCZOS>
+// Rows per thread (RT).  Measured on GB300 (icosidodecahedron, FP32): CR is fastest
+// with 2 rows per thread (its rank tables are L1/shared-memory resident and the
+// bond chunk is reused across rows), CLT with 1 (its two dependent gathers per bond
+// already fill the load queues).  FTLM_HV_ROWS = 1, 2 or 4 overrides both.
+int rows_per_thread(bool clt)
+{
+    static const int over = [] {
+        const char *e = getenv("FTLM_HV_ROWS");
+        const int v = e ? atoi(e) : 0;
+        return (v == 1 || v == 2 || v == 4) ? v : 0;
+    }();
+    return over ? over : (clt ? 1 : 2);
+}
+
+template <typename V, typename Lbl, bool CLT, bool LANCZOS, int RT>
 ftlm_status launch(const ftlm_basis *b, const V *x, V *y, const EpiDev &ep, cudaStream_t stream)
 {
     static int occ = -1;  // resident blocks per SM for this instantiation
     const size_t smem = CLT ? 0 : ((size_t)1 << b->L) * sizeof(uint16_t);
-    auto kern = hv_kernel<V, Lbl, CLT, LANCZOS>;
+    auto kern = hv_kernel<V, Lbl, CLT, LANCZOS, RT>;
     if (occ < 0) {
         const size_t smem_max = CLT ? 0 : ((size_t)1 << kLoBitsMax) * sizeof(uint16_t);
         FTLM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kRowThreads, smem_max));
     }
-    const int grid = row_grid(b, b->D, occ);
+    const int grid = row_grid(b, (b->D + RT - 1) / RT, occ);
     void *tok = profile_begin(kProfHv, stream);
     kern<<<grid, kRowThreads, smem, stream>>>(b->tables(), CLT ? b->bonds_clt : b->bonds_cr, x, y, ep);
     profile_end(tok, stream);
@@ -231,12 +321,22 @@ ftlm_status launch(const ftlm_basis *b, const V *x, V *y, const EpiDev &ep, cuda
     return FTLM_OK;
 }
 
+template <typename V, typename Lbl, bool CLT, bool LANCZOS>
+ftlm_status launch_rt(const ftlm_basis *b, const void *x, void *y, const EpiDev &ep, cudaStream_t stream)
+{
+    switch (rows_per_thread(CLT)) {
+    case 1: return launch<V, Lbl, CLT, LANCZOS, 1>(b, (const V *)x, (V *)y, ep, stream);
+    case 4: return launch<V, Lbl, CLT, LANCZOS, 4>(b, (const V *)x, (V *)y, ep, stream);
+    default: return launch<V, Lbl, CLT, LANCZOS, 2>(b, (const V *)x, (V *)y, ep, stream);
+    }
+}
+
 template <typename V, bool LANCZOS>
 ftlm_status launch_mode(const ftlm_basis *b, const void *x, void *y, const EpiDev &ep, cudaStream_t stream)
 {
-    if (b->mode == FTLM_RANK_CLT) return launch<V, uint32_t, true, LANCZOS>(b, (const V *)x, (V *)y, ep, stream);
-    if (b->N <= 32) return launch<V, uint32_t, false, LANCZOS>(b, (const V *)x, (V *)y, ep, stream);
-    return launch<V, uint64_t, false, LANCZOS>(b, (const V *)x, (V *)y, ep, stream);
+    if (b->mode == FTLM_RANK_CLT) return launch_rt<V, uint32_t, true, LANCZOS>(b, x, y, ep, stream);
+    if (b->N <= 32) return launch_rt<V, uint32_t, false, LANCZOS>(b, x, y, ep, stream);
+    return launch_rt<V, uint64_t, false, LANCZOS>(b, x, y, ep, stream);
 }
 
 template <typename V>
