@@ -55,6 +55,8 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--hv-only", action="store_true",
                    help="time plain ftlm_hv launches on the workload (kernel microbenchmark)")
+    p.add_argument("--block", type=int, default=1,
+                   help="with --hv-only: vectors per launch (ftlm_hv_block, 1/4/8/16)")
     return p.parse_args()
 
 
@@ -64,13 +66,15 @@ def bonds_of(name):
     return inputs.icosidodecahedron() if name == "icosidodecahedron" else inputs.ring(34)
 
 
-def sector_model_bytes(updates, D, dtype_bytes, clt, lanczos=True):
-    """Algorithmic bytes of one H.v launch under the sector model: one 32-byte
-    sector per gathered x element, the row streams x[t] and y[t] (and the u_{j-1}
-    read of the fused Lanczos epilogue), plus for CLT one 32-byte sector per
-    table lookup and the 4-byte basis[t] read."""
+def sector_model_bytes(updates, D, dtype_bytes, clt, lanczos=True, B=1):
+    """Algorithmic bytes of one H.v launch on B interleaved vectors under the
+    sector model: every gather of the B entries of a source row costs whole 32-byte
+    sectors (ceil(B * size / 32) of them), plus the row streams x[t] and y[t] (and
+    the u_{j-1} read of the fused Lanczos epilogue) for B vectors; CLT adds one
+    32-byte sector per table lookup and the 4-byte basis[t] read."""
     n_off = updates - D
-    b = 32 * n_off + (2 + (1 if lanczos else 0)) * dtype_bytes * D
+    sectors = -(-B * dtype_bytes // 32)
+    b = 32 * sectors * n_off + (2 + (1 if lanczos else 0)) * dtype_bytes * B * D
     if clt:
         b += 32 * n_off + 4 * D
     return b
@@ -310,11 +314,16 @@ def run_ours(args):
     torch.cuda.synchronize()
     step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     total_ms = sum(step_ms)
-    hv_n, hv_ms, up_n, up_ms = ftlm.ftlm_profile_read()
+    hv_n, hv_vec, hv_ms, up_n, up_ms = ftlm.ftlm_profile_read()
     chains_steps = int(m_eff.sum().item())
     updates_step = chains_steps * updates_hv
+    # kernels per step: H.v and update launches (counted), per chain block a start
+    # and an m_eff copy, the Ritz step, the thermodynamic sums, the coarse index
+    # build of the sector setup, and for CLT the basis and CLT builds
     m_max = min(M, D)
-    launches_step = (2 if mode_used == ftlm.RANK_CLT else 0) + R * (2 + 2 * m_max) + 2
+    blocks = hv_n // max(1, args.steps * m_max)
+    launches_step = ((hv_n + up_n) // args.steps + 2 * blocks + 2 + 1
+                     + (2 if mode_used == ftlm.RANK_CLT else 0))
 
     all_updates, max_ms = aggregate_over_ranks(updates_step * args.steps, total_ms, dev, world)
     value = all_updates / (max_ms / 1e3) / 1e9
@@ -357,8 +366,9 @@ def run_ours(args):
 
     peak, peak_src = peak_hbm()
     hv_avg_s = hv_ms / max(hv_n, 1) / 1e3
+    block = round(hv_vec / max(hv_n, 1))  # vectors per H.v launch (one block width per run)
     clt = mode_used == ftlm.RANK_CLT
-    alg_bytes = sector_model_bytes(updates_hv, D, 4 if dt == torch.float32 else 8, clt)
+    alg_bytes = sector_model_bytes(updates_hv, D, 4 if dt == torch.float32 else 8, clt, B=block)
     achieved = alg_bytes / hv_avg_s / 1e9 if hv_n else None
     mode_name = "clt" if clt else "cr"
     traffic = profiled_traffic(mode_name, args.dtype)
@@ -366,11 +376,11 @@ def run_ours(args):
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
         "frac": achieved / peak if achieved else None, "traffic": traffic,
         "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
-        "kernel": f"hv_kernel<{'float' if dt == torch.float32 else 'double'}, {mode_name.upper()}, lanczos>",
+        "kernel": f"hv_kernel<{'float' if dt == torch.float32 else 'double'}, {mode_name.upper()}, lanczos, B={block}>",
         "model": "sector model: 32 B per gathered x element + row streams",
         "algorithmic_bytes_per_launch": alg_bytes,
-        "hv_launches": hv_n, "hv_ms_avg": hv_avg_s * 1e3,
-        "hv_Gupdates_per_s": updates_hv / hv_avg_s / 1e9 if hv_n else None,
+        "hv_launches": hv_n, "vectors_per_launch": block, "hv_ms_avg": hv_avg_s * 1e3,
+        "hv_Gupdates_per_s": block * updates_hv / hv_avg_s / 1e9 if hv_n else None,
         "dram_frac": (traffic / hv_avg_s / 1e9 / peak) if (traffic and hv_n) else None,
         "update_ms_avg": up_ms / max(up_n, 1),
     }
@@ -417,26 +427,33 @@ def run_hv_only(args):
     bonds = bonds_of(args.workload)
     mode = {"auto": ftlm.RANK_AUTO, "clt": ftlm.RANK_CLT, "cr": ftlm.RANK_CR}[args.mode]
     dt = torch.float32 if args.dtype == "f32" else torch.float64
+    B = args.block
     with ftlm.Basis(N, 0, bonds, mode) as b:
-        x = inputs.hashed_vector_torch(b.dim, dt, dev)
+        x = inputs.hashed_vector_torch(b.dim * B, dt, dev)
         y = torch.empty_like(x)
+
+        def once():
+            if B == 1:
+                ftlm.ftlm_hv(b.handle, x, y)
+            else:
+                ftlm.ftlm_hv_block(b.handle, B, x, y)
+
         for _ in range(args.warmup):
-            ftlm.ftlm_hv(b.handle, x, y)
+            once()
         torch.cuda.synchronize()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
         ev[0].record()
         for i in range(args.steps):
-            ftlm.ftlm_hv(b.handle, x, y)
+            once()
             ev[i + 1].record()
         torch.cuda.synchronize()
         ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
         clt = b.mode == ftlm.RANK_CLT
-        alg = sector_model_bytes(b.updates, b.dim, 4 if dt == torch.float32 else 8, clt, lanczos=False)
         med = statistics.median(ms)
         print(json.dumps({"hv_only": True, "workload": args.workload, "mode": "clt" if clt else "cr",
-                          "dtype": args.dtype, "ms": ms, "ms_median": med,
-                          "Gupdates_per_s": b.updates / med * 1e-6,
-                          "sector_model_GBps": alg / med * 1e-6, "D": b.dim, "updates": b.updates}))
+                          "dtype": args.dtype, "block": B, "ms": ms, "ms_median": med,
+                          "Gupdates_per_s": B * b.updates / med * 1e-6, "D": b.dim,
+                          "updates_per_vector": b.updates}))
 
 
 def main():

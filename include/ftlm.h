@@ -53,7 +53,7 @@ typedef enum {
 } ftlm_status;
 
 typedef enum {
-    FTLM_RANK_AUTO = 0, /* pick CR (the faster one on this GPU)                         */
+    FTLM_RANK_AUTO = 0, /* CLT if N <= 32 and its tables fit in 1/4 of device memory, else CR */
     FTLM_RANK_CLT = 1,  /* compressed lookup table: basis array + {M_b, C_b} (Eq. 18-21) */
     FTLM_RANK_CR = 2    /* combinatorial ranking (Eq. 15-17), digit blocks via tables   */
 } ftlm_rank_mode;
@@ -132,10 +132,20 @@ ftlm_status ftlm_basis_clt(const ftlm_basis *basis, uint32_t *mask_dev, uint32_t
 ftlm_status ftlm_hv(const ftlm_basis *basis, ftlm_dtype dtype, const void *x_dev, void *y_dev,
                     void *stream);
 
+/* ftlm_hv_block -- Y = H X for a block of B vectors stored interleaved: entry
+ * (t, r) of vector r at X[t * B + r] (B in {1, 4, 8, 16}; x_dev, y_dev hold D * B
+ * elements of dtype).  Each row's rank work is shared by the B vectors (the batched
+ * scheme of Sec. 3.4); column r of Y is bit-identical to ftlm_hv on column r of X.
+ * EINVAL for another B. */
+ftlm_status ftlm_hv_block(const ftlm_basis *basis, ftlm_dtype dtype, int B, const void *x_dev,
+                          void *y_dev, void *stream);
+
 /* ---------------------------------------------------------------- Lanczos ---
  * Workspace bytes ftlm_lanczos / ftlm_lanczos_from need for R chains of at most M
- * steps: two vectors of D elements of dtype plus O(R M) coefficients.  EINVAL for
- * R < 1 or M outside 1..FTLM_MAX_LANCZOS. */
+ * steps: two blocks of D x B_w elements of dtype plus O(R M) coefficients, B_w the
+ * widest block of chains the call runs at once (chains go in blocks of 16, 8 or 4
+ * interleaved vectors, up to 8 in FP32 and 4 in FP64, then single chains).  EINVAL
+ * for R < 1 or M outside 1..FTLM_MAX_LANCZOS. */
 ftlm_status ftlm_lanczos_workspace_bytes(const ftlm_basis *basis, int R, int M, ftlm_dtype dtype,
                                          uint64_t *bytes);
 
@@ -155,6 +165,10 @@ ftlm_status ftlm_lanczos_workspace_bytes(const ftlm_basis *basis, int R, int M, 
  *   sum_b |J_b| (u = 2^-53 for F64, 2^-24 for F32).
  *   Ritz step (FP64 on the device): theta_k, w_k = s_{k,1}^2 of the m_eff x m_eff
  *   tridiagonal T, ascending in theta.
+ *   Chains run in blocks (see ftlm_lanczos_workspace_bytes) through ftlm_hv_block's
+ *   kernel; every chain's arithmetic is its own, so a chain's result does not
+ *   depend on the other chains of its block, up to the summation order of the
+ *   dot products.
  * Outputs (device, row r of chain r, each row M long, entries >= m_eff zero):
  *   theta_dev, weight_dev: double[R*M];  m_eff_dev: int[R];
  *   alpha_dev, beta_dev: double[R*M] or NULL (Lanczos coefficients; beta row r
@@ -234,13 +248,14 @@ ftlm_status ftlm_thermo(int n_sectors, const int *two_sz, const uint64_t *dims, 
 
 /* ------------------------------------------------------------- diagnostics ---
  * Kernel timing: while enabled, CUDA events are recorded on the launch stream
- * around every H.v launch (ftlm_hv and the Lanczos H.v step) and every Lanczos
- * vector-update launch.  ftlm_profile_read waits for those events, returns launch
- * counts and summed device milliseconds since the last read, and clears them.
- * Process-wide; thread-safe. */
+ * around every H.v launch (ftlm_hv, ftlm_hv_block and the Lanczos H.v step) and
+ * every Lanczos vector-update launch.  ftlm_profile_read waits for those events,
+ * returns launch counts, the number of vectors the H.v launches applied H to (a
+ * block launch counts B), and summed device milliseconds since the last read, and
+ * clears them.  Any output pointer may be NULL.  Process-wide; thread-safe. */
 ftlm_status ftlm_profile_enable(int on);
-ftlm_status ftlm_profile_read(uint64_t *hv_launches, double *hv_ms, uint64_t *update_launches,
-                              double *update_ms);
+ftlm_status ftlm_profile_read(uint64_t *hv_launches, uint64_t *hv_vectors, double *hv_ms,
+                              uint64_t *update_launches, double *update_ms);
 
 const char *ftlm_status_string(ftlm_status status);
 const char *ftlm_last_error(void); /* message of the last failure on this host thread */

@@ -13,6 +13,7 @@ thread_local std::string g_last_error;
 struct ProfRecord {
     cudaEvent_t start, stop;
     int kind;
+    int vectors;
 };
 std::mutex g_prof_mu;
 bool g_prof_on = false;
@@ -44,11 +45,11 @@ ftlm_status cuda_fail(cudaError_t e, const char *what)
     return FTLM_ECUDA;
 }
 
-void *profile_begin(int kind, cudaStream_t stream)
+void *profile_begin(int kind, cudaStream_t stream, int vectors)
 {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     if (!g_prof_on) return nullptr;
-    ProfRecord r{take_event(), take_event(), kind};
+    ProfRecord r{take_event(), take_event(), kind, vectors};
     if (!r.start || !r.stop) return nullptr;
     if (cudaEventRecord(r.start, stream) != cudaSuccess) return nullptr;
     g_records.push_back(r);
@@ -74,11 +75,11 @@ extern "C" ftlm_status ftlm_profile_enable(int on)
     return FTLM_OK;
 }
 
-extern "C" ftlm_status ftlm_profile_read(uint64_t *hv_launches, double *hv_ms, uint64_t *update_launches,
-                                         double *update_ms)
+extern "C" ftlm_status ftlm_profile_read(uint64_t *hv_launches, uint64_t *hv_vectors, double *hv_ms,
+                                         uint64_t *update_launches, double *update_ms)
 {
     std::lock_guard<std::mutex> lk(g_prof_mu);
-    uint64_t n[2] = {0, 0};
+    uint64_t n[2] = {0, 0}, vec = 0;
     double ms[2] = {0.0, 0.0};
     ftlm_status st = FTLM_OK;
     for (ProfRecord &r : g_records) {
@@ -88,11 +89,13 @@ extern "C" ftlm_status ftlm_profile_read(uint64_t *hv_launches, double *hv_ms, u
         if (e != cudaSuccess && st == FTLM_OK) st = cuda_fail(e, "cudaEventElapsedTime");
         n[r.kind] += 1;
         ms[r.kind] += t;
+        if (r.kind == kProfHv) vec += (uint64_t)r.vectors;
         g_event_pool.push_back(r.start);
         g_event_pool.push_back(r.stop);
     }
     g_records.clear();
     if (hv_launches) *hv_launches = n[kProfHv];
+    if (hv_vectors) *hv_vectors = vec;
     if (hv_ms) *hv_ms = ms[kProfHv];
     if (update_launches) *update_launches = n[kProfUpdate];
     if (update_ms) *update_ms = ms[kProfUpdate];

@@ -265,8 +265,18 @@ extern "C" ftlm_status ftlm_basis_create(int N, int two_sz, int n_bonds, const i
     init_binom();
     const int K = (N + two_sz) / 2;
     const uint64_t D = binom(N, K);
-    if (mode == FTLM_RANK_AUTO) mode = FTLM_RANK_CR;
     if (D >= (1ull << 32)) return fail(FTLM_EUNSUPPORTED, "sector dimension >= 2^32");
+    if (mode == FTLM_RANK_AUTO) {
+        // CLT when its tables (basis array + Eq. 21) fit in a quarter of the device
+        // memory: it is the faster map once chains run in blocks (measured on GB300);
+        // else combinatorial ranking, which stores almost nothing.
+        mode = FTLM_RANK_CR;
+        size_t free_b = 0, total_b = 0;
+        if (N <= 32 && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+            const uint64_t clt_bytes = 4 * D + 8 * (((1ull << N) + 31) / 32);
+            if (clt_bytes <= total_b / 4) mode = FTLM_RANK_CLT;
+        }
+    }
     if (mode == FTLM_RANK_CLT && N > 32) return fail(FTLM_EUNSUPPORTED, "CLT needs N <= 32");
 
     cudaStream_t stream = (cudaStream_t)stream_;

@@ -55,9 +55,13 @@ struct ChainState {
     double alpha;      // alpha_j of the step in flight
     int m_eff;         // steps completed when the chain ended
     int stopped;       // set once beta_j <= tau (or a zero start vector)
-    unsigned int counter;  // blocks finished in the current launch
-    int pad;
+    int pad[2];
 };
+
+// Block widths: chains run in blocks of B vectors stored interleaved, element
+// (t, r) of a block at t * B + r, so one rank computation serves B vectors and a
+// gather moves B contiguous values.
+constexpr int kMaxBlock = 16;
 
 // Device-side tables of one sector, in the form the kernels take them.
 struct SectorTables {
@@ -117,8 +121,9 @@ ftlm_status cuda_fail(cudaError_t e, const char *what);
 // ---- kernel timing (api.cu) ----------------------------------------------
 enum ProfileKind { kProfHv = 0, kProfUpdate = 1 };
 // Returns an opaque token (or nullptr when profiling is off) for a launch about to
-// be queued on `stream`; profile_end records the stop event.
-void *profile_begin(int kind, cudaStream_t stream);
+// be queued on `stream` that processes `vectors` vectors; profile_end records the
+// stop event.
+void *profile_begin(int kind, cudaStream_t stream, int vectors = 1);
 void profile_end(void *token, cudaStream_t stream);
 
 // ---- launch helpers --------------------------------------------------------
@@ -126,15 +131,19 @@ void profile_end(void *token, cudaStream_t stream);
 int row_grid(const ftlm_basis *b, uint64_t rows, int occupancy_blocks_per_sm);
 int max_row_grid(const ftlm_basis *b);
 
-// Lanczos epilogue of the H.v launch (hv.cu).
+// Lanczos epilogue of the H.v launch (hv.cu), for a block of B chains.
 struct LanczosHv {
-    const void *u_prev;  // = y buffer (in place)
-    ChainState *st;
-    double *partials;
-    double *alpha_out;   // alpha_j destination
+    ChainState *st;        // [B]
+    double *partials;      // [grid * B]
+    unsigned int *counter; // blocks finished in the current launch (zero between launches)
+    double *alpha_out;     // alpha_j of chain r goes to alpha_out[r * alpha_stride]
+    int alpha_stride;
     int j;
 };
-ftlm_status launch_hv(const ftlm_basis *b, ftlm_dtype dtype, const void *x, void *y,
+// y = H x for a block of B interleaved vectors (B in {1, 4, 8, 16}); with epi, the
+// Lanczos epilogue (y overwrites the u_{j-1} block in place).
+ftlm_status launch_hv(const ftlm_basis *b, ftlm_dtype dtype, int B, const void *x, void *y,
                       const LanczosHv *epi, cudaStream_t stream);
+bool valid_block(int B);
 
 }  // namespace ftlm

@@ -12,11 +12,13 @@
 // queues 2 launches per step, and a chain that breaks down (beta_j <= tau) turns
 // the rest of its launches into no-ops.
 #include <cmath>
+#include <cstdlib>
 #include <mutex>
 #include <vector>
 
 #include "ftlm_internal.cuh"
 #include "reduce.cuh"
+#include "vec.cuh"
 
 namespace ftlm {
 
@@ -51,104 +53,154 @@ __device__ __forceinline__ double start_value(uint64_t key, uint64_t t, int dist
     return sqrt(-2.0 * log(U1)) * cos(two_pi * U2);
 }
 
-// u = start vector (generated, or copied from src), and s_1 = ||u|| of the stored
-// (dtype-rounded) entries.
-template <typename V>
-__global__ void __launch_bounds__(kRowThreads)
-start_kernel(uint32_t D, uint64_t key, int dist, const double *__restrict__ src, V *__restrict__ u,
-             ChainState *st, double *partials)
+struct Keys {
+    uint64_t k[kMaxBlock];
+};
+
+// Finish a launch's per-chain reduction: every block stores its B partial sums;
+// the last block to arrive returns true (in every thread) and the caller's warp 0
+// adds the partials of chain r in block order with chain_total().
+template <int B>
+__device__ __forceinline__ bool publish_partials(const double (&part)[B], double *partials, unsigned int *counter)
 {
-    double part = 0.0;
+    __shared__ double s_part[B];
+    __shared__ bool s_last;
+#pragma unroll
+    for (int r = 0; r < B; ++r) {
+        const double v = block_sum<kRowThreads>(part[r]);
+        if (threadIdx.x == 0) s_part[r] = v;
+    }
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int r = 0; r < B; ++r) partials[(size_t)blockIdx.x * B + r] = s_part[r];
+        __threadfence();
+        s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    return s_last;
+}
+
+// Fixed-order total of chain r's partials; call from warp 0, valid in lane 0.
+template <int B>
+__device__ __forceinline__ double chain_total(const double *partials, int r)
+{
+    double v = 0.0;
+    for (int g = threadIdx.x; g < (int)gridDim.x; g += 32) v += __ldcg(partials + (size_t)g * B + r);
+    return warp_sum(v);
+}
+
+// Start vectors of a block of B chains (generated, or copied from src rows of
+// length D), interleaved, and s_1 = ||u|| of each chain's stored (dtype-rounded)
+// entries.
+template <typename V, int B>
+__global__ void __launch_bounds__(kRowThreads)
+start_kernel(uint32_t D, const Keys keys, int dist, const double *__restrict__ src, V *__restrict__ u,
+             ChainState *st, double *partials, unsigned int *counter)
+{
+    DotAcc<V> acc[B];
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < D; t += stride) {
-        const double v = src ? src[t] : start_value(key, t, dist);
-        const V vv = (V)v;
-        u[t] = vv;
-        part += (double)vv * (double)vv;
-    }
-    part = block_sum<kRowThreads>(part);
-    if (publish_partial(part, partials, &st->counter) && threadIdx.x < 32) {
-        const double nrm = sqrt(total_of_partials(partials, gridDim.x));
-        if (threadIdx.x == 0) {
-            st->s_cur = nrm;
-            st->s_prev = 1.0;
-            st->beta_prev = 0.0;
-            st->alpha = 0.0;
-            st->m_eff = 0;
-            st->stopped = (nrm > 0.0 && isfinite(nrm)) ? 0 : 1;
-            st->counter = 0;
+        V out[B];
+#pragma unroll
+        for (int r = 0; r < B; ++r) {
+            const double v = src ? src[(size_t)r * D + t] : start_value(keys.k[r], t, dist);
+            out[r] = (V)v;
+            acc[r].add(out[r], out[r]);
         }
+        st_vec<B>(u + (size_t)t * B, out);
     }
-}
-
-template <typename V> struct Vec2;
-template <> struct Vec2<float> { using T = float4; static constexpr int n = 4; };
-template <> struct Vec2<double> { using T = double2; static constexpr int n = 2; };
-
-__device__ __forceinline__ float4 upd(float4 y, float4 u, float a, double &part)
-{
-    float4 w;
-    w.x = fmaf(-a, u.x, y.x);
-    w.y = fmaf(-a, u.y, y.y);
-    w.z = fmaf(-a, u.z, y.z);
-    w.w = fmaf(-a, u.w, y.w);
-    part += (double)w.x * w.x + (double)w.y * w.y + ((double)w.z * w.z + (double)w.w * w.w);
-    return w;
-}
-__device__ __forceinline__ double2 upd(double2 y, double2 u, double a, double &part)
-{
-    double2 w;
-    w.x = fma(-a, u.x, y.x);
-    w.y = fma(-a, u.y, y.y);
-    part += w.x * w.x + w.y * w.y;
-    return w;
-}
-
-// w = y - alpha_j q_j (in place over y), beta_j = ||w||, breakdown test.
-template <typename V>
-__global__ void __launch_bounds__(kRowThreads)
-update_kernel(uint32_t D, V *__restrict__ y, const V *__restrict__ u, ChainState *st,
-              double *partials, int j, int m_max, double tau, double *beta_row)
-{
-    if (st->stopped) return;
-    const V a = (V)(st->alpha / st->s_cur);
-    using VT = typename Vec2<V>::T;
-    constexpr int W = Vec2<V>::n;
-    double part = 0.0;
-    const uint32_t nvec = D / W;
-    const uint32_t stride = gridDim.x * blockDim.x;
-    VT *yv = reinterpret_cast<VT *>(y);
-    const VT *uv = reinterpret_cast<const VT *>(u);
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nvec; i += stride)
-        __stcs(yv + i, upd(__ldcs(yv + i), __ldcs(uv + i), a, part));
-    for (uint32_t t = nvec * W + blockIdx.x * blockDim.x + threadIdx.x; t < D; t += stride) {
-        const V w = fma(-a, u[t], y[t]);
-        y[t] = w;
-        part += (double)w * (double)w;
-    }
-    part = block_sum<kRowThreads>(part);
-    if (publish_partial(part, partials, &st->counter) && threadIdx.x < 32) {
-        const double beta = sqrt(total_of_partials(partials, gridDim.x));
-        if (threadIdx.x == 0) {
-            if (j < m_max) {
-                if (beta <= tau) {
-                    st->stopped = 1;
-                    st->m_eff = j;
-                } else {
-                    beta_row[j - 1] = beta;
-                    st->s_prev = st->s_cur;
-                    st->s_cur = beta;
-                    st->beta_prev = beta;
-                }
-            } else {
-                st->m_eff = m_max;
+    double part[B];
+#pragma unroll
+    for (int r = 0; r < B; ++r) part[r] = acc[r].value();
+    if (publish_partials<B>(part, partials, counter) && threadIdx.x < 32) {
+        for (int r = 0; r < B; ++r) {
+            const double nrm = sqrt(chain_total<B>(partials, r));
+            if (threadIdx.x == 0) {
+                ChainState &c = st[r];
+                c.s_cur = nrm;
+                c.s_prev = 1.0;
+                c.beta_prev = 0.0;
+                c.alpha = 0.0;
+                c.m_eff = 0;
+                c.stopped = (nrm > 0.0 && isfinite(nrm)) ? 0 : 1;
             }
-            st->counter = 0;
         }
+        if (threadIdx.x == 0) *counter = 0;
     }
 }
 
-__global__ void copy_meff_kernel(const ChainState *st, int *dst) { *dst = st->m_eff; }
+// w = y - alpha_j q_j per chain (in place over y), beta_j = ||w||, breakdown test.
+// Columns of chains that have ended are set to zero.  The block is processed in
+// units of U = max(B, 16 bytes) values; entry e of a unit belongs to chain e % B.
+template <typename V, int B>
+__global__ void __launch_bounds__(kRowThreads)
+update_kernel(uint32_t D, V *__restrict__ y, const V *__restrict__ u, ChainState *st, double *partials,
+              unsigned int *counter, int j, int m_max, double tau, double *beta_out, int beta_stride)
+{
+    V a[B];
+    bool zero[B];
+    bool all_stopped = true;
+#pragma unroll
+    for (int r = 0; r < B; ++r) {
+        zero[r] = st[r].stopped != 0;
+        all_stopped &= zero[r];
+        a[r] = zero[r] ? (V)0 : (V)(st[r].alpha / st[r].s_cur);
+    }
+    if (all_stopped) return;
+    constexpr int W = 16 / (int)sizeof(V);
+    constexpr int U = B > W ? B : W;
+    DotAcc<V> acc[B];
+    const uint64_t total = (uint64_t)D * B, units = total / U;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < units; i += stride) {
+        V yv[U], uv[U], w[U];
+        ld_vec<U>(y + i * U, yv, true);
+        ld_vec<U>(u + i * U, uv, true);
+#pragma unroll
+        for (int e = 0; e < U; ++e) {
+            const int r = e % B;
+            w[e] = zero[r] ? (V)0 : fma(-a[r], uv[e], yv[e]);
+            acc[r].add(w[e], w[e]);
+        }
+        st_vec<U>(y + i * U, w);
+    }
+    for (uint64_t e = units * U + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < total; e += stride) {
+        // only reached with B = 1 (and D not a multiple of U)
+        const V w = zero[0] ? (V)0 : fma(-a[0], u[e], y[e]);
+        y[e] = w;
+        acc[0].add(w, w);
+    }
+    double part[B];
+#pragma unroll
+    for (int r = 0; r < B; ++r) part[r] = acc[r].value();
+    if (publish_partials<B>(part, partials, counter) && threadIdx.x < 32) {
+        for (int r = 0; r < B; ++r) {
+            const double beta = sqrt(chain_total<B>(partials, r));
+            if (threadIdx.x == 0 && !st[r].stopped) {
+                ChainState &c = st[r];
+                if (j < m_max) {
+                    if (beta <= tau) {
+                        c.stopped = 1;
+                        c.m_eff = j;
+                    } else {
+                        beta_out[(size_t)r * beta_stride + (j - 1)] = beta;
+                        c.s_prev = c.s_cur;
+                        c.s_cur = beta;
+                        c.beta_prev = beta;
+                    }
+                } else {
+                    c.m_eff = m_max;
+                }
+            }
+        }
+        if (threadIdx.x == 0) *counter = 0;
+    }
+}
+
+__global__ void copy_meff_kernel(const ChainState *st, int B, int *dst)
+{
+    if (threadIdx.x < B) dst[threadIdx.x] = st[threadIdx.x].m_eff;
+}
 
 // ---- Ritz step (a5) ---------------------------------------------------------
 // Implicit symmetric tridiagonal QR with Wilkinson shift (Golub & Van Loan,
@@ -261,29 +313,61 @@ ftlm_status launch_ritz(int n, int M, const double *alpha, const double *beta, c
     return FTLM_OK;
 }
 
-// ---- workspace -------------------------------------------------------------
+// ---- workspace and block plan -------------------------------------------
 uint64_t align256(uint64_t v) { return (v + 255) & ~255ull; }
 
+// Widest block of chains: 8 vectors (FP32) or 4 (FP64) unless FTLM_BLOCK (1, 4, 8
+// or 16) says otherwise.
+int max_block(ftlm_dtype dtype)
+{
+    static const int over = [] {
+        const char *e = getenv("FTLM_BLOCK");
+        const int v = e ? atoi(e) : 0;
+        return valid_block(v) ? v : 0;
+    }();
+    return over ? over : (dtype == FTLM_F32 ? 8 : 4);
+}
+
+// Split R chains into blocks: the widest allowed width in {16, 8, 4} that fits the
+// chains left, then single chains for fewer than 4.
+std::vector<int> block_plan(int R, ftlm_dtype dtype)
+{
+    const int bmax = max_block(dtype);
+    std::vector<int> plan;
+    int left = R;
+    for (int w : {16, 8, 4}) {
+        if (w > bmax) continue;
+        while (left >= w) {
+            plan.push_back(w);
+            left -= w;
+        }
+    }
+    while (left-- > 0) plan.push_back(1);
+    return plan;
+}
+
 struct Layout {
+    int bw;  // widest block
     uint64_t vec0, vec1, partials, state, alpha, beta, meff, total;
 };
 
 Layout layout(const ftlm_basis *b, int R, int M, ftlm_dtype dtype)
 {
     Layout l;
-    const uint64_t vb = align256(b->D * (dtype == FTLM_F32 ? 4ull : 8ull));
+    l.bw = 1;
+    for (int w : block_plan(R, dtype)) l.bw = w > l.bw ? w : l.bw;
+    const uint64_t vb = align256(b->D * (uint64_t)l.bw * (dtype == FTLM_F32 ? 4ull : 8ull));
     l.vec0 = 0;
     l.vec1 = vb;
     l.partials = 2 * vb;
-    l.state = l.partials + align256((uint64_t)max_row_grid(b) * sizeof(double));
-    l.alpha = l.state + align256(sizeof(ChainState));
+    l.state = l.partials + align256((uint64_t)max_row_grid(b) * l.bw * sizeof(double));
+    l.alpha = l.state + align256(l.bw * sizeof(ChainState) + 64);
     l.beta = l.alpha + align256((uint64_t)R * M * sizeof(double));
     l.meff = l.beta + align256((uint64_t)R * M * sizeof(double));
     l.total = l.meff + align256((uint64_t)R * sizeof(int));
     return l;
 }
 
-template <typename V>
 int occupancy_of(const void *kern)
 {
     int occ = 1;
@@ -291,48 +375,73 @@ int occupancy_of(const void *kern)
     return occ;
 }
 
-template <typename V>
-ftlm_status run_chains(const ftlm_basis *b, int R, int M, uint64_t seed, int dist, const double *src,
-                       ftlm_dtype dtype, char *ws, const Layout &lay, double *theta, double *weight,
-                       int *m_eff, double *alpha_dev, double *beta_dev, cudaStream_t stream)
+// One block of B chains: start vectors, then min(M, D) fused H.v + update launches.
+template <typename V, int B>
+ftlm_status run_block(const ftlm_basis *b, int M, int r0, uint64_t seed, int dist, const double *src,
+                      ftlm_dtype dtype, char *ws, const Layout &lay, cudaStream_t stream)
 {
     static int occ_start = -1, occ_upd = -1;
-    if (occ_start < 0) occ_start = occupancy_of<V>((const void *)start_kernel<V>);
-    if (occ_upd < 0) occ_upd = occupancy_of<V>((const void *)update_kernel<V>);
+    if (occ_start < 0) occ_start = occupancy_of((const void *)start_kernel<V, B>);
+    if (occ_upd < 0) occ_upd = occupancy_of((const void *)update_kernel<V, B>);
     V *vec[2] = {(V *)(ws + lay.vec0), (V *)(ws + lay.vec1)};
     double *partials = (double *)(ws + lay.partials);
     ChainState *st = (ChainState *)(ws + lay.state);
+    unsigned int *counter = (unsigned int *)(st + lay.bw);
     double *alpha_ws = (double *)(ws + lay.alpha);
     double *beta_ws = (double *)(ws + lay.beta);
     int *meff_ws = (int *)(ws + lay.meff);
     const uint32_t D = (uint32_t)b->D;
     const int m_max = (uint64_t)M < b->D ? M : (int)b->D;
     const double tau = dtype == FTLM_F32 ? b->tau32 : b->tau64;
+    constexpr int W = 16 / (int)sizeof(V);
+    constexpr int U = B > W ? B : W;
     const int g_start = row_grid(b, D, occ_start);
-    const int g_upd = row_grid(b, (D + Vec2<V>::n - 1) / Vec2<V>::n, occ_upd);
+    const int g_upd = row_grid(b, ((uint64_t)D * B + U - 1) / U, occ_upd);
 
-    FTLM_CUDA(cudaMemsetAsync(st, 0, sizeof(ChainState), stream));
+    FTLM_CUDA(cudaMemsetAsync(st, 0, lay.bw * sizeof(ChainState) + 64, stream));
+    Keys keys{};
+    for (int r = 0; r < B; ++r) keys.k[r] = chain_key(seed, b->N, b->K, (uint32_t)(r0 + r));
+    start_kernel<V, B><<<g_start, kRowThreads, 0, stream>>>(D, keys, dist, src ? src + (size_t)r0 * D : nullptr,
+                                                           vec[0], st, partials, counter);
+    FTLM_CUDA(cudaGetLastError());
+    int cur = 0;
+    for (int j = 1; j <= m_max; ++j) {
+        LanczosHv epi{st, partials, counter, alpha_ws + (size_t)r0 * M + (j - 1), M, j};
+        ftlm_status s = launch_hv(b, dtype, B, vec[cur], vec[1 - cur], &epi, stream);
+        if (s != FTLM_OK) return s;
+        void *tok = profile_begin(kProfUpdate, stream);
+        update_kernel<V, B><<<g_upd, kRowThreads, 0, stream>>>(D, vec[1 - cur], vec[cur], st, partials, counter, j,
+                                                               m_max, tau, beta_ws + (size_t)r0 * M, M);
+        profile_end(tok, stream);
+        FTLM_CUDA(cudaGetLastError());
+        cur = 1 - cur;
+    }
+    copy_meff_kernel<<<1, 32, 0, stream>>>(st, B, meff_ws + r0);
+    FTLM_CUDA(cudaGetLastError());
+    return FTLM_OK;
+}
+
+template <typename V>
+ftlm_status run_chains(const ftlm_basis *b, int R, int M, uint64_t seed, int dist, const double *src,
+                       ftlm_dtype dtype, char *ws, const Layout &lay, double *theta, double *weight,
+                       int *m_eff, double *alpha_dev, double *beta_dev, cudaStream_t stream)
+{
+    double *alpha_ws = (double *)(ws + lay.alpha);
+    double *beta_ws = (double *)(ws + lay.beta);
+    int *meff_ws = (int *)(ws + lay.meff);
     FTLM_CUDA(cudaMemsetAsync(alpha_ws, 0, (size_t)R * M * sizeof(double), stream));
     FTLM_CUDA(cudaMemsetAsync(beta_ws, 0, (size_t)R * M * sizeof(double), stream));
-    for (int r = 0; r < R; ++r) {
-        const uint64_t key = chain_key(seed, b->N, b->K, (uint32_t)r);
-        start_kernel<V><<<g_start, kRowThreads, 0, stream>>>(D, key, dist, src ? src + (size_t)r * D : nullptr,
-                                                             vec[0], st, partials);
-        FTLM_CUDA(cudaGetLastError());
-        int cur = 0;
-        for (int j = 1; j <= m_max; ++j) {
-            LanczosHv epi{vec[1 - cur], st, partials, alpha_ws + (size_t)r * M + (j - 1), j};
-            ftlm_status s = launch_hv(b, dtype, vec[cur], vec[1 - cur], &epi, stream);
-            if (s != FTLM_OK) return s;
-            void *tok = profile_begin(kProfUpdate, stream);
-            update_kernel<V><<<g_upd, kRowThreads, 0, stream>>>(D, vec[1 - cur], vec[cur], st, partials, j,
-                                                                m_max, tau, beta_ws + (size_t)r * M);
-            profile_end(tok, stream);
-            FTLM_CUDA(cudaGetLastError());
-            cur = 1 - cur;
+    int r0 = 0;
+    for (int B : block_plan(R, dtype)) {
+        ftlm_status s;
+        switch (B) {
+        case 16: s = run_block<V, 16>(b, M, r0, seed, dist, src, dtype, ws, lay, stream); break;
+        case 8: s = run_block<V, 8>(b, M, r0, seed, dist, src, dtype, ws, lay, stream); break;
+        case 4: s = run_block<V, 4>(b, M, r0, seed, dist, src, dtype, ws, lay, stream); break;
+        default: s = run_block<V, 1>(b, M, r0, seed, dist, src, dtype, ws, lay, stream); break;
         }
-        copy_meff_kernel<<<1, 1, 0, stream>>>(st, meff_ws + r);
-        FTLM_CUDA(cudaGetLastError());
+        if (s != FTLM_OK) return s;
+        r0 += B;
     }
     ftlm_status s = launch_ritz(R, M, alpha_ws, beta_ws, meff_ws, theta, weight, stream);
     if (s != FTLM_OK) return s;

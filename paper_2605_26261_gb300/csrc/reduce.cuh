@@ -61,3 +61,38 @@ __device__ __forceinline__ double total_of_partials(const double *partials, int 
 }
 
 }  // namespace ftlm
+
+namespace ftlm {
+
+// Per-thread accumulator of dot-product terms a * b.  For FP32 operands every
+// product is split exactly into p + e (p = fl(a b), e = fma(a, b, -p)) and added
+// to a two-float sum (hi, lo) with the error-free TwoSum of Knuth, so the running
+// sum keeps about 48 significant bits without touching the FP64 pipe, which is
+// narrow on GB300; value() hands the sum to the FP64 block and grid reductions.
+// FP64 operands accumulate in FP64 directly.
+template <typename V> struct DotAcc;
+
+template <> struct DotAcc<float> {
+    float hi = 0.f, lo = 0.f;
+    // The _rn intrinsics are never contracted into FMAs: TwoSum needs the rounded
+    // product p, not a fused hi + a * b.
+    __device__ __forceinline__ void add(float a, float b)
+    {
+        const float p = __fmul_rn(a, b);
+        const float e = fmaf(a, b, -p);
+        const float s = __fadd_rn(hi, p);
+        const float bv = __fsub_rn(s, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(p, bv));
+        hi = s;
+        lo = __fadd_rn(lo, __fadd_rn(err, e));
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+template <> struct DotAcc<double> {
+    double v = 0.0;
+    __device__ __forceinline__ void add(double a, double b) { v = fma(a, b, v); }
+    __device__ __forceinline__ double value() const { return v; }
+};
+
+}  // namespace ftlm

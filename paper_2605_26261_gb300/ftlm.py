@@ -60,6 +60,7 @@ def lib():
         "ftlm_basis_rank": [P, U64, P, P, P],
         "ftlm_basis_clt": [P, P, P, P],
         "ftlm_hv": [P, I, P, P, P],
+        "ftlm_hv_block": [P, I, I, P, P, P],
         "ftlm_lanczos_workspace_bytes": [P, I, I, I, PU64],
         "ftlm_lanczos": [P, I, I, U64, I, I, P, U64, P, P, P, P, P, P],
         "ftlm_lanczos_from": [P, I, I, P, I, P, U64, P, P, P, P, P, P],
@@ -67,7 +68,7 @@ def lib():
         "ftlm_ritz": [I, I, P, P, P, P, P, P],
         "ftlm_thermo": [I, P, P, I, I, P, P, P, I, D, D, I, P, P, P, P, P, P],
         "ftlm_profile_enable": [I],
-        "ftlm_profile_read": [PU64, PD, PU64, PD],
+        "ftlm_profile_read": [PU64, PU64, PD, PU64, PD],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -180,6 +181,14 @@ def ftlm_hv(handle, x, y, stream=None):
     _check(lib().ftlm_hv(handle, _dtype_code(x.dtype), _ptr(x), _ptr(y), _stream(stream)))
 
 
+def ftlm_hv_block(handle, B, x, y, stream=None):
+    """Y = H X for B interleaved vectors: x, y contiguous device tensors of D * B
+    elements (e.g. shape (D, B)), entry (t, r) at t * B + r."""
+    if x.dtype != y.dtype or not x.is_contiguous() or not y.is_contiguous():
+        raise ValueError("x and y must be contiguous and of one dtype")
+    _check(lib().ftlm_hv_block(handle, _dtype_code(x.dtype), int(B), _ptr(x), _ptr(y), _stream(stream)))
+
+
 def ftlm_lanczos_workspace_bytes(handle, R, M, dtype):
     v = ctypes.c_uint64()
     _check(lib().ftlm_lanczos_workspace_bytes(handle, int(R), int(M), _dtype_code(dtype), ctypes.byref(v)))
@@ -235,11 +244,12 @@ def ftlm_profile_enable(on=True):
 
 
 def ftlm_profile_read():
-    """(hv_launches, hv_ms, update_launches, update_ms) since the last read."""
-    a, c = ctypes.c_uint64(), ctypes.c_uint64()
+    """(hv_launches, hv_vectors, hv_ms, update_launches, update_ms) since the last read."""
+    a, v, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
     b, d = ctypes.c_double(), ctypes.c_double()
-    _check(lib().ftlm_profile_read(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
-    return a.value, b.value, c.value, d.value
+    _check(lib().ftlm_profile_read(ctypes.byref(a), ctypes.byref(v), ctypes.byref(b), ctypes.byref(c),
+                                   ctypes.byref(d)))
+    return a.value, v.value, b.value, c.value, d.value
 
 
 # --------------------------------------------------------------- convenience

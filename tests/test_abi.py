@@ -94,8 +94,9 @@ def test_null_handles_rejected(lib):
 
 def test_profile_toggle_without_gpu(lib):
     assert lib.ftlm_profile_enable(1) == 0
-    a, c = ctypes.c_uint64(), ctypes.c_uint64()
+    a, v, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
     b, d = ctypes.c_double(), ctypes.c_double()
-    assert lib.ftlm_profile_read(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)) == 0
-    assert a.value == 0 and c.value == 0
+    assert lib.ftlm_profile_read(ctypes.byref(a), ctypes.byref(v), ctypes.byref(b), ctypes.byref(c),
+                                 ctypes.byref(d)) == 0
+    assert a.value == 0 and v.value == 0 and c.value == 0
     assert lib.ftlm_profile_enable(0) == 0

@@ -95,4 +95,9 @@ def test_update_count_matches_eq10(cuda_dev, name, N, K, bonds):
     ref = o.basis(N, K)
     with ftlm.Basis(N, 2 * K - N, bonds) as b:
         assert b.updates == len(ref) + o.offdiag_terms(bonds, ref)
-        assert b.mode == ftlm.RANK_CR  # AUTO resolves to CR
+        assert b.mode == ftlm.RANK_CLT  # AUTO: small CLT tables fit
+
+
+def test_auto_mode_picks_cr_when_clt_cannot_be_built(cuda_dev):
+    with ftlm.Basis(34, 32, inputs.ring(34)) as b:  # N > 32: no CLT
+        assert b.mode == ftlm.RANK_CR

@@ -106,3 +106,30 @@ def test_hv_rejects_bad_vectors(cuda_dev):
             ftlm.ftlm_hv(b.handle, x, x)  # in place not allowed
         with pytest.raises(ftlm.FtlmError):
             ftlm.ftlm_hv(b.handle, x[1:], x[:-1].clone())  # misaligned input
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("mode", [ftlm.RANK_CLT, ftlm.RANK_CR])
+@pytest.mark.parametrize("B", [4, 8, 16])
+def test_block_hv_columns_equal_single_hv(cuda_dev, mode, dtype, B):
+    # Interleaved block of B vectors: each column is bit-identical to ftlm_hv.
+    N, K = 18, 8
+    bonds = inputs.random_graph(N, seed=21)
+    with ftlm.Basis(N, 2 * K - N, bonds, mode) as b:
+        g = torch.Generator(device="cpu").manual_seed(B)
+        X = torch.randn((b.dim, B), generator=g, dtype=torch.float64).to(dtype).to(cuda_dev)
+        Y = torch.full_like(X, float("nan"))
+        ftlm.ftlm_hv_block(b.handle, B, X, Y)
+        for r in range(B):
+            x = X[:, r].contiguous()
+            y = torch.empty_like(x)
+            ftlm.ftlm_hv(b.handle, x, y)
+            assert torch.equal(Y[:, r], y), r
+
+
+def test_block_hv_rejects_other_widths(cuda_dev):
+    with ftlm.Basis(8, 0, inputs.ring(8)) as b:
+        X = torch.ones((b.dim, 3), dtype=torch.float32, device=cuda_dev)
+        with pytest.raises(ftlm.FtlmError) as e:
+            ftlm.ftlm_hv_block(b.handle, 3, X, X.clone())
+        assert e.value.status == ftlm.FTLM_EINVAL

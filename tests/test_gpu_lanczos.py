@@ -38,9 +38,10 @@ def test_fp64_coefficients_from_given_start(cuda_dev, mode):
         np.testing.assert_allclose(res["beta"][r, :15].cpu().numpy(), bt[:15], rtol=1e-10)
 
 
+@pytest.mark.parametrize("R", [4, 8, 13])  # blocks of 4 / 8 / 8 + 4 + 1 chains
 @pytest.mark.parametrize("dist", [ftlm.GAUSS, ftlm.RADEMACHER])
-def test_seeded_start_vectors_match_oracle_generator(cuda_dev, dist):
-    N, K, M, R, seed = 16, 8, 12, 4, 1234
+def test_seeded_start_vectors_match_oracle_generator(cuda_dev, dist, R):
+    N, K, M, seed = 16, 8, 12, 1234
     bonds = inputs.ring(N)
     with ftlm.Basis(N, 0, bonds) as b:
         res = ftlm.lanczos(b, R, M, seed=seed, dist=dist, dtype=torch.float64, keep_coeffs=True)
@@ -52,9 +53,10 @@ def test_seeded_start_vectors_match_oracle_generator(cuda_dev, dist):
         np.testing.assert_allclose(res["beta"][r, :m - 1].cpu().numpy(), bt, rtol=1e-10)
 
 
+@pytest.mark.parametrize("R", [2, 8])  # single chains / one block of 8
 @pytest.mark.parametrize("mode", [ftlm.RANK_CLT, ftlm.RANK_CR])
-def test_fp32_coefficients_close_to_fp64_oracle(cuda_dev, mode):
-    N, K, M, R = 20, 10, 20, 2
+def test_fp32_coefficients_close_to_fp64_oracle(cuda_dev, mode, R):
+    N, K, M = 20, 10, 20
     bonds = inputs.ladder(20, 0.6, 1.0)
     with ftlm.Basis(N, 0, bonds, mode) as b:
         res = ftlm.lanczos(b, R, M, seed=9, dtype=torch.float32, keep_coeffs=True)
@@ -66,15 +68,16 @@ def test_fp32_coefficients_close_to_fp64_oracle(cuda_dev, mode):
         np.testing.assert_allclose(res["beta"][r, :m - 1].cpu().numpy(), bt, rtol=1e-4)
 
 
+@pytest.mark.parametrize("R", [3, 8])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-def test_breakdown_at_krylov_dimension(cuda_dev, dtype):
+def test_breakdown_at_krylov_dimension(cuda_dev, dtype, R):
     # One down spin on a 12-ring: 7 distinct levels, the chain must stop after 7.
     N = 12
     bonds = inputs.ring(N)
     with ftlm.Basis(N, N - 2, bonds) as b:
-        res = ftlm.lanczos(b, 3, 12, seed=5, dtype=dtype)
+        res = ftlm.lanczos(b, R, 12, seed=5, dtype=dtype)
         torch.cuda.synchronize()
-        assert res["m_eff"].tolist() == [7, 7, 7]
+        assert res["m_eff"].tolist() == [7] * R
         th = res["theta"][0, :7].cpu().numpy()
         ev = np.unique(np.round(np.linalg.eigvalsh(o.dense_h(bonds, o.basis(N, N - 1))), 8))
         np.testing.assert_allclose(np.sort(th), ev, atol=1e-9 if dtype == torch.float64 else 1e-5)
@@ -99,14 +102,26 @@ def test_dimension_one_and_two_sectors(cuda_dev):
         np.testing.assert_allclose(res["theta"][0, :2].cpu().numpy(), [-0.75, 0.25], atol=1e-14)
 
 
-def test_zero_start_vector_gives_empty_chain(cuda_dev):
-    with ftlm.Basis(8, 0, inputs.ring(8)) as b:
-        start = torch.zeros((2, b.dim), dtype=torch.float64, device=cuda_dev)
-        start[1, 3] = 2.0
-        res = ftlm.lanczos(b, 2, 10, dtype=torch.float64, start=start)
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("R", [2, 4, 8])
+def test_zero_start_vector_gives_empty_chain(cuda_dev, R, dtype):
+    # A zero start vector ends its chain at once without disturbing the other
+    # chains of its block.
+    N, K = 10, 5
+    bonds = inputs.ring(N)
+    with ftlm.Basis(N, 0, bonds) as b:
+        start = torch.as_tensor(np.stack([inputs.seeded_vector(b.dim, 70 + r) for r in range(R)]), device=cuda_dev)
+        start[0].zero_()
+        res = ftlm.lanczos(b, R, 10, dtype=dtype, start=start, keep_coeffs=True)
         torch.cuda.synchronize()
-        assert int(res["m_eff"][0]) == 0 and int(res["m_eff"][1]) > 0
+        assert int(res["m_eff"][0]) == 0
         assert torch.all(res["weight"][0] == 0).item()
+        for r in range(1, R):
+            a, bt, m = oracle_chain(bonds, N, K, start[r].cpu().numpy(), 10,
+                                    o.U64 if dtype == torch.float64 else o.U32)
+            assert int(res["m_eff"][r]) == m
+            rtol = 1e-10 if dtype == torch.float64 else 1e-4
+            np.testing.assert_allclose(res["alpha"][r, :m].cpu().numpy(), a, rtol=rtol, atol=10 * rtol)
 
 
 def test_workspace_too_small_is_rejected(cuda_dev):
@@ -158,3 +173,30 @@ def test_ritz_matches_dense_eigh(cuda_dev, M):
                                        (S[0] ** 2 * np.exp(-beta * ev)).sum(), rtol=1e-11)
         assert abs(w[c, :k].sum() - 1) < 1e-12
         assert np.all(th[c, k:] == 0) and np.all(w[c, k:] == 0)
+
+
+@pytest.mark.parametrize("R", [1, 8])
+def test_fp32_dot_products_accumulate_to_fp64_accuracy(cuda_dev, R):
+    # FP32 vectors, FP64-class reductions: with dyadic start entries and J = 1 the
+    # FP32 H.v is exact, so alpha_1 = sum_t q_t y_t can be rebuilt on the host from
+    # the same FP32 roundings (q = fl(x / s), y = fl((Hx) / s)) and summed in FP64.
+    # A plain FP32 accumulation over 184756 rows would miss it by ~1e-6 relative.
+    N, K = 20, 10
+    bonds = inputs.ring(N)
+    b_or = o.basis(N, K)
+    D = len(b_or)
+    xs = np.stack([inputs.hashed_value(np.arange(D) + 7919 * r) for r in range(R)])
+    with ftlm.Basis(N, 0, bonds) as b:
+        res = ftlm.lanczos(b, R, 1, dtype=torch.float32, start=torch.as_tensor(xs, device=cuda_dev),
+                           keep_coeffs=True)
+        torch.cuda.synchronize()
+    for r in range(R):
+        x = xs[r]
+        hx = o.hv(bonds, b_or, x)  # exact: dyadic entries, J = 1
+        s = np.sqrt(np.sum(x * x))
+        inv_s = np.float32(1.0 / s)
+        q = (x.astype(np.float32) * inv_s).astype(np.float64)
+        y = (hx.astype(np.float32) * inv_s).astype(np.float64)
+        ref = float(np.sum(q * y))
+        got = float(res["alpha"][r, 0])
+        assert abs(got - ref) <= 1e-12 * abs(ref), (got, ref)
