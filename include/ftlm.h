@@ -216,6 +216,47 @@ ftlm_status ftlm_lanczos_noalloc(const ftlm_basis *basis, int R, int M, uint64_t
                                  double *weight_dev, int *m_eff_dev, double *alpha_dev,
                                  double *beta_dev, void *stream);
 
+/* ------------------------------------------------------------- batches ---
+ * Many sectors (of one or many clusters) in one go: the batched form of
+ * ftlm_lanczos for workloads of many small sectors, where one launch sequence
+ * per sector would be launch-bound.
+ *
+ * ftlm_batch_item: chains r = 0 .. R-1 of `basis`, keyed as chains
+ *   first_chain + r under `seed` (the start-vector definition of ftlm_lanczos);
+ *   outputs theta_dev, weight_dev (double[R*M]) and m_eff_dev (int[R]) as for
+ *   ftlm_lanczos.  The basis and the outputs must outlive every run of the batch.
+ * ftlm_batch_create -- plan a batch: sectors with D <= 32768 are cut into units
+ *   of `block` chains (block = 1, 4, 8 or 16; 0 = 16 for FP32, 8 for FP64) that one
+ *   persistent kernel runs, one CTA per unit at a time, each unit's chains entirely
+ *   inside its CTA (vectors in a per-CTA workspace slot, CTA-local reductions);
+ *   larger sectors run through the launch sequence of ftlm_lanczos.  Uploads the
+ *   plan's descriptors (device memory owned by the batch; the only allocation).
+ *   `stream` is unused (reserved).  EINVAL for an empty batch or bad items.
+ * ftlm_batch_workspace_bytes -- scratch the plan needs (per-CTA vector slots,
+ *   O(chains M) coefficients, and the largest large-sector workspace).
+ * ftlm_batch_run -- queue the batch on `stream`: memsets and kernel launches only,
+ *   so a run can be captured into a CUDA graph and replayed.  Results match
+ *   ftlm_lanczos on each item up to the summation order of the dot products.
+ *   ENOMEM when the workspace is too small.  Runs of one batch must not overlap.
+ */
+typedef struct {
+    const ftlm_basis *basis;
+    int R;
+    int first_chain;
+    uint64_t seed;
+    double *theta_dev;
+    double *weight_dev;
+    int *m_eff_dev;
+} ftlm_batch_item;
+
+typedef struct ftlm_batch ftlm_batch;
+
+ftlm_status ftlm_batch_create(int n_items, const ftlm_batch_item *items, int M, ftlm_vec_dist dist,
+                              ftlm_dtype dtype, int block, void *stream, ftlm_batch **out);
+ftlm_status ftlm_batch_workspace_bytes(const ftlm_batch *batch, uint64_t *bytes);
+ftlm_status ftlm_batch_run(const ftlm_batch *batch, void *work_dev, uint64_t work_bytes, void *stream);
+void ftlm_batch_destroy(ftlm_batch *batch);
+
 /* ftlm_ritz -- the Ritz step alone (a5): for each of n chains, the eigenvalues theta
  * and first-component weights w = s_{k,1}^2 of the tridiagonal matrix with diagonal
  * alpha_dev[c*M .. c*M+m-1] and off-diagonal beta_dev[c*M .. c*M+m-2], m = m_dev[c]

@@ -1,0 +1,518 @@
+// Batched FTLM chains for many sectors at once (steps a2, a4, a5 over a batch).
+//
+// A batch lists sectors (of one or many clusters) with R chains each.  Sectors of
+// dimension above kSmallRows run through the grid-wide launch sequence of
+// ftlm_lanczos, one after the other.  All smaller sectors are cut into work units
+// of B chains and handed to ONE persistent launch: each CTA takes the next unit
+// from an atomic counter (no waiting on other CTAs) and runs the unit's whole
+// chains by itself -- start vectors, min(M, D) steps of fused H.v + Lanczos
+// update with CTA-local reductions, stop tests -- with the unit's two vector blocks
+// in a per-CTA slot of the workspace (L2-resident for small sectors).  One Ritz
+// launch then handles every chain of the small sectors, and a scatter copies the
+// results into each sector's outputs.  Units are sorted by dimension, largest
+// first, so the tail of the queue is short work.
+//
+// The plan (descriptors of sectors and units) is uploaded once by
+// ftlm_batch_create; ftlm_batch_run only issues memsets and kernel launches, so the
+// whole run can be captured in a CUDA graph and replayed.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ftlm_internal.cuh"
+#include "reduce.cuh"
+#include "rng.cuh"
+#include "rows.cuh"
+#include "vec.cuh"
+
+namespace ftlm {
+
+namespace {
+
+constexpr int kBatchThreads = 256;
+constexpr uint64_t kSmallRows = 1u << 15;  // sectors up to this dimension run inside one CTA
+
+struct BatchItemDev {
+    SectorTables s;
+    BondList bl;
+    uint64_t seed;
+    double tau;
+    int chain0;  // key index of the item's first chain
+    int m_max;
+    int N, K;
+    uint32_t chain_base;  // index of the item's chain 0 among the batch's small chains
+    int pad;
+};
+
+struct BatchUnitDev {
+    uint32_t item;  // index into the item descriptors
+    uint32_t r0;    // first chain of the unit within the item
+    uint32_t nact;  // chains of the unit (<= B); the other columns stay zero
+    uint32_t pad;
+};
+
+struct ScatterDev {
+    double *theta;  // row of the chain in the item's outputs
+    double *weight;
+    int *m_eff;
+};
+
+// Fixed-order CTA sum of B per-thread values; out[r] (shared) holds chain r's total.
+template <int B>
+__device__ __forceinline__ void cta_reduce(const double (&v)[B], double *s_warp, double *out)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int r = 0; r < B; ++r) {
+        const double x = warp_sum(v[r]);
+        if (lane == 0) s_warp[w * B + r] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < B) {
+        double t = 0.0;
+        for (int i = 0; i < kBatchThreads / 32; ++i) t += s_warp[i * B + threadIdx.x];
+        out[threadIdx.x] = t;
+    }
+    __syncthreads();
+}
+
+template <typename V, typename Lbl, bool CLT, int B, int C>
+__global__ void __launch_bounds__(kBatchThreads)
+batch_kernel(const BatchItemDev *__restrict__ items, const BatchUnitDev *__restrict__ units, uint32_t n_units,
+             unsigned int *queue, V *slots, uint64_t slot_elems, int M, int dist, double *alpha_all,
+             double *beta_all, int *meff_all)
+{
+    extern __shared__ uint16_t s_tlo[];
+    __shared__ uint4 s_bond[kMaxBondSlots];
+    __shared__ double s_warp[(kBatchThreads / 32) * B];
+    __shared__ double s_tot[B], s_cur[B], s_prev[B], s_bprev[B];
+    __shared__ V s_inv_s[B], s_cprev[B], s_a[B];
+    __shared__ int s_stop[B], s_meff[B];
+    __shared__ unsigned int s_unit;
+    __shared__ int s_all_stopped;
+    V *const u0 = slots + (size_t)blockIdx.x * 2 * slot_elems;
+    V *const u1 = u0 + slot_elems;
+
+    for (;;) {
+        if (threadIdx.x == 0) s_unit = atomicAdd(queue, 1u);
+        __syncthreads();
+        const unsigned int ui = s_unit;
+        if (ui >= n_units) break;  // CTA-uniform
+        const BatchUnitDev un = units[ui];
+        const SectorTables s = items[un.item].s;
+        const BondList bl = items[un.item].bl;
+        const BatchItemDev &it = items[un.item];
+        const uint32_t D = s.D;
+        const int m_max = it.m_max;
+        const double tau = it.tau;
+        const size_t cbase = (size_t)it.chain_base + un.r0;
+        {
+            const uint4 *src = sizeof(V) == 4 ? bl.slots_f32 : bl.slots_f64;
+            for (int i = threadIdx.x; i < bl.nb; i += kBatchThreads) s_bond[i] = src[i];
+            if (!CLT)
+                for (uint32_t i = threadIdx.x; i <= s.lomask; i += kBatchThreads) s_tlo[i] = __ldg(s.tlo + i);
+        }
+        // start vectors of the unit's chains (columns past nact stay zero)
+        {
+            uint64_t key[B];
+#pragma unroll
+            for (int r = 0; r < B; ++r) key[r] = chain_key(it.seed, it.N, it.K, (uint32_t)(it.chain0 + un.r0 + r));
+            DotAcc<V> acc[B];
+            for (uint32_t t = threadIdx.x; t < D; t += kBatchThreads) {
+                V out[B];
+#pragma unroll
+                for (int r = 0; r < B; ++r) {
+                    out[r] = r < (int)un.nact ? (V)start_value(key[r], t, dist) : (V)0;
+                    acc[r].add(out[r], out[r]);
+                }
+                st_vec<B>(u0 + (size_t)t * B, out);
+            }
+            double v[B];
+#pragma unroll
+            for (int r = 0; r < B; ++r) v[r] = acc[r].value();
+            cta_reduce<B>(v, s_warp, s_tot);
+            if (threadIdx.x < B) {
+                const int r = threadIdx.x;
+                const double nrm = sqrt(s_tot[r]);
+                s_cur[r] = nrm;
+                s_prev[r] = 1.0;
+                s_bprev[r] = 0.0;
+                s_stop[r] = (r < (int)un.nact && nrm > 0.0 && isfinite(nrm)) ? 0 : 1;
+                s_meff[r] = 0;
+            }
+            __syncthreads();
+        }
+        int cur = 0;
+        for (int j = 1; j <= m_max; ++j) {
+            if (threadIdx.x < B) {
+                const int r = threadIdx.x;
+                s_inv_s[r] = (V)(1.0 / s_cur[r]);
+                s_cprev[r] = j > 1 ? (V)(s_bprev[r] / s_prev[r]) : (V)0;
+            }
+            if (threadIdx.x == 0) {
+                int all = 1;
+                for (int r = 0; r < B; ++r) all &= s_stop[r];
+                s_all_stopped = all;
+            }
+            __syncthreads();
+            if (s_all_stopped) break;  // CTA-uniform
+            const V *x = cur ? u1 : u0;
+            V *y = cur ? u0 : u1;
+            // y = H q_j - beta_{j-1} q_{j-1} (over u_{j-1}), alpha partials
+            DotAcc<V> ap[B];
+            for (uint32_t t = threadIdx.x; t < D; t += kBatchThreads) {
+                const uint32_t tt[1] = {t};
+                V acc[1][B], dsum[1] = {(V)0};
+#pragma unroll
+                for (int r = 0; r < B; ++r) acc[0][r] = (V)0;
+                if (CLT) rows_clt<V, 1, B, C, false>(s, bl, s_bond, x, tt, acc, dsum);
+                else rows_cr<V, Lbl, 1, B, C, false>(s, bl, s_bond, s_tlo, x, tt, acc, dsum);
+                V xt[B], up[B], out[B];
+                ld_vec_coherent<B>(x + (size_t)t * B, xt);
+                if (j > 1) ld_vec_coherent<B>(y + (size_t)t * B, up);
+                const V diag = (V)bl.jsum4 - dsum[0];
+#pragma unroll
+                for (int r = 0; r < B; ++r) {
+                    const V hv = fma(diag, xt[r], acc[0][r]);
+                    out[r] = j > 1 ? fma(-s_cprev[r], up[r], hv * s_inv_s[r]) : hv * s_inv_s[r];
+                    ap[r].add(xt[r] * s_inv_s[r], out[r]);
+                }
+                st_vec<B>(y + (size_t)t * B, out);
+            }
+            {
+                double v[B];
+#pragma unroll
+                for (int r = 0; r < B; ++r) v[r] = ap[r].value();
+                cta_reduce<B>(v, s_warp, s_tot);
+            }
+            if (threadIdx.x < B) {
+                const int r = threadIdx.x;
+                if (!s_stop[r]) alpha_all[(cbase + r) * M + (j - 1)] = s_tot[r];
+                s_a[r] = s_stop[r] ? (V)0 : (V)(s_tot[r] / s_cur[r]);
+            }
+            __syncthreads();
+            // w = y - alpha_j q_j in place, beta_j = ||w||
+            DotAcc<V> bp[B];
+            for (uint32_t t = threadIdx.x; t < D; t += kBatchThreads) {
+                V yv[B], xv[B], w[B];
+                ld_vec_coherent<B>(y + (size_t)t * B, yv);
+                ld_vec_coherent<B>(x + (size_t)t * B, xv);
+#pragma unroll
+                for (int r = 0; r < B; ++r) {
+                    w[r] = s_stop[r] ? (V)0 : fma(-s_a[r], xv[r], yv[r]);
+                    bp[r].add(w[r], w[r]);
+                }
+                st_vec<B>(y + (size_t)t * B, w);
+            }
+            {
+                double v[B];
+#pragma unroll
+                for (int r = 0; r < B; ++r) v[r] = bp[r].value();
+                cta_reduce<B>(v, s_warp, s_tot);
+            }
+            if (threadIdx.x < B && !s_stop[threadIdx.x]) {
+                const int r = threadIdx.x;
+                const double beta = sqrt(s_tot[r]);
+                if (j < m_max) {
+                    if (beta <= tau) {
+                        s_stop[r] = 1;
+                        s_meff[r] = j;
+                    } else {
+                        beta_all[(cbase + r) * M + (j - 1)] = beta;
+                        s_prev[r] = s_cur[r];
+                        s_cur[r] = beta;
+                        s_bprev[r] = beta;
+                    }
+                } else {
+                    s_meff[r] = m_max;
+                }
+            }
+            __syncthreads();
+            cur ^= 1;
+        }
+        if (threadIdx.x < un.nact) meff_all[cbase + threadIdx.x] = s_meff[threadIdx.x];
+        __syncthreads();  // the next unit reuses shared memory and the slot
+    }
+}
+
+__global__ void scatter_kernel(int n, int M, const double *__restrict__ theta, const double *__restrict__ weight,
+                               const int *__restrict__ meff, const ScatterDev *__restrict__ dst)
+{
+    const int c = blockIdx.x;
+    if (c >= n) return;
+    const ScatterDev d = dst[c];
+    for (int k = threadIdx.x; k < M; k += blockDim.x) {
+        d.theta[k] = theta[(size_t)c * M + k];
+        d.weight[k] = weight[(size_t)c * M + k];
+    }
+    if (threadIdx.x == 0) *d.m_eff = meff[c];
+}
+
+uint64_t align256(uint64_t v) { return (v + 255) & ~255ull; }
+
+// Kernel variant of a group of units: rank mode and label width.
+enum Group { kCr32 = 0, kCr64 = 1, kClt = 2 };
+
+template <typename V, int B>
+void *batch_kernel_ptr(int group)
+{
+    constexpr int C = B >= 8 ? 4 : kBondChunk;
+    if (group == kClt) return (void *)batch_kernel<V, uint32_t, true, B, C>;
+    if (group == kCr64) return (void *)batch_kernel<V, uint64_t, false, B, C>;
+    return (void *)batch_kernel<V, uint32_t, false, B, C>;
+}
+
+void *kernel_for(ftlm_dtype dtype, int B, int group)
+{
+    if (dtype == FTLM_F32) {
+        switch (B) {
+        case 16: return batch_kernel_ptr<float, 16>(group);
+        case 8: return batch_kernel_ptr<float, 8>(group);
+        case 4: return batch_kernel_ptr<float, 4>(group);
+        default: return batch_kernel_ptr<float, 1>(group);
+        }
+    }
+    switch (B) {
+    case 16: return batch_kernel_ptr<double, 16>(group);
+    case 8: return batch_kernel_ptr<double, 8>(group);
+    case 4: return batch_kernel_ptr<double, 4>(group);
+    default: return batch_kernel_ptr<double, 1>(group);
+    }
+}
+
+}  // namespace
+
+}  // namespace ftlm
+
+using namespace ftlm;
+
+struct ftlm_batch {
+    int n, M, dist, B;
+    ftlm_dtype dtype;
+    std::vector<ftlm_batch_item> items;
+    std::vector<int> large;     // items run through the grid-wide path
+    uint32_t n_small_chains;
+    uint32_t group_units[3];    // units per kernel variant
+    uint32_t group_first[3];    // offset of the group in the unit array
+    int group_grid[3];
+    int n_slots;
+    uint64_t slot_elems;        // D_max * B of the small items
+    // device descriptors (owned)
+    BatchItemDev *d_items;
+    BatchUnitDev *d_units;
+    ScatterDev *d_scatter;
+    // workspace layout
+    uint64_t off_queue, off_slots, off_alpha, off_beta, off_meff, off_theta, off_weight, off_large, total;
+    uint64_t large_bytes;
+};
+
+extern "C" ftlm_status ftlm_batch_create(int n, const ftlm_batch_item *items, int M, ftlm_vec_dist dist,
+                                         ftlm_dtype dtype, int block, void *stream_, ftlm_batch **out)
+{
+    if (!out) return fail(FTLM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || !items) return fail(FTLM_EINVAL, "empty batch");
+    if (M < 1 || M > FTLM_MAX_LANCZOS) return fail(FTLM_EINVAL, "M out of range");
+    if (dtype != FTLM_F32 && dtype != FTLM_F64) return fail(FTLM_EINVAL, "bad dtype");
+    if (dist != FTLM_VEC_GAUSS && dist != FTLM_VEC_RADEMACHER) return fail(FTLM_EINVAL, "bad distribution");
+    if (block == 0) block = dtype == FTLM_F32 ? 16 : 8;
+    if (!valid_block(block)) return fail(FTLM_EINVAL, "block width must be 0, 1, 4, 8 or 16");
+    for (int i = 0; i < n; ++i) {
+        const ftlm_batch_item &it = items[i];
+        if (!it.basis || it.R < 1 || it.first_chain < 0) return fail(FTLM_EINVAL, "bad batch item");
+        if (!it.theta_dev || !it.weight_dev || !it.m_eff_dev) return fail(FTLM_EINVAL, "NULL output in batch item");
+    }
+    ftlm_batch *p = new (std::nothrow) ftlm_batch();
+    if (!p) return fail(FTLM_ENOMEM, "host allocation failed");
+    p->n = n;
+    p->M = M;
+    p->dist = dist;
+    p->B = block;
+    p->dtype = dtype;
+    p->items.assign(items, items + n);
+    const int B = block;
+
+    std::vector<BatchItemDev> hitems;
+    std::vector<std::vector<BatchUnitDev>> gunits(3);
+    std::vector<ScatterDev> scatter;
+    std::vector<uint64_t> unit_dim[3];
+    uint64_t dmax = 1, large_bytes = 0;
+    int num_sms = 0;
+    for (int i = 0; i < n; ++i) {
+        const ftlm_basis *b = items[i].basis;
+        num_sms = b->num_sms;
+        if (b->D > kSmallRows) {
+            p->large.push_back(i);
+            large_bytes = std::max<uint64_t>(large_bytes, lanczos_workspace(b, items[i].R, M, dtype));
+            continue;
+        }
+        BatchItemDev d{};
+        d.s = b->tables();
+        d.bl = b->mode == FTLM_RANK_CLT ? b->bonds_clt : b->bonds_cr;
+        d.seed = items[i].seed;
+        d.tau = dtype == FTLM_F32 ? b->tau32 : b->tau64;
+        d.chain0 = items[i].first_chain;
+        d.m_max = (uint64_t)M < b->D ? M : (int)b->D;
+        d.N = b->N;
+        d.K = b->K;
+        d.chain_base = p->n_small_chains;
+        const int group = b->mode == FTLM_RANK_CLT ? kClt : (b->N > 32 ? kCr64 : kCr32);
+        for (int r0 = 0; r0 < items[i].R; r0 += B) {
+            BatchUnitDev u{};
+            u.item = (uint32_t)hitems.size();
+            u.r0 = (uint32_t)r0;
+            u.nact = (uint32_t)std::min(B, items[i].R - r0);
+            gunits[group].push_back(u);
+        }
+        for (int r = 0; r < items[i].R; ++r)
+            scatter.push_back({items[i].theta_dev + (size_t)r * M, items[i].weight_dev + (size_t)r * M,
+                               items[i].m_eff_dev + r});
+        p->n_small_chains += (uint32_t)items[i].R;
+        dmax = std::max<uint64_t>(dmax, b->D);
+        hitems.push_back(d);
+    }
+    // largest sectors first within each group (the queue's tail is short work)
+    std::vector<BatchUnitDev> units;
+    for (int g = 0; g < 3; ++g) {
+        std::stable_sort(gunits[g].begin(), gunits[g].end(), [&](const BatchUnitDev &a, const BatchUnitDev &b) {
+            return hitems[a.item].s.D > hitems[b.item].s.D;
+        });
+        p->group_first[g] = (uint32_t)units.size();
+        p->group_units[g] = (uint32_t)gunits[g].size();
+        units.insert(units.end(), gunits[g].begin(), gunits[g].end());
+    }
+    // persistent grids: resident CTAs of each variant
+    p->n_slots = 1;
+    const size_t smem = ((size_t)1 << kLoBitsMax) * sizeof(uint16_t);
+    for (int g = 0; g < 3; ++g) {
+        p->group_grid[g] = 0;
+        if (!p->group_units[g]) continue;
+        void *kern = kernel_for(dtype, B, g);
+        int occ = 1;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBatchThreads, smem);
+        if (e != cudaSuccess) {
+            delete p;
+            return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(batch)");
+        }
+        occ = std::max(1, occ);
+        p->group_grid[g] = (int)std::min<uint64_t>(p->group_units[g], (uint64_t)num_sms * occ);
+        p->n_slots = std::max(p->n_slots, p->group_grid[g]);
+    }
+    // workspace layout
+    const uint64_t vsize = dtype == FTLM_F32 ? 4 : 8;
+    p->slot_elems = dmax * (uint64_t)B;
+    uint64_t off = 0;
+    p->off_queue = off;
+    off += 256;
+    p->off_slots = off;
+    off += align256((uint64_t)p->n_slots * 2 * p->slot_elems * vsize);
+    const uint64_t cm = (uint64_t)p->n_small_chains * M * sizeof(double);
+    p->off_alpha = off;
+    off += align256(cm);
+    p->off_beta = off;
+    off += align256(cm);
+    p->off_theta = off;
+    off += align256(cm);
+    p->off_weight = off;
+    off += align256(cm);
+    p->off_meff = off;
+    off += align256((uint64_t)p->n_small_chains * sizeof(int));
+    p->off_large = off;
+    off += align256(large_bytes);
+    p->large_bytes = large_bytes;
+    p->total = off;
+
+    // descriptors to the device
+    cudaStream_t stream = (cudaStream_t)stream_;
+    auto upload = [&](void **dst, const void *src, size_t bytes) -> cudaError_t {
+        if (bytes == 0) return cudaSuccess;
+        cudaError_t e = cudaMalloc(dst, bytes);
+        if (e == cudaSuccess) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+        return e;
+    };
+    cudaError_t e = upload((void **)&p->d_items, hitems.data(), hitems.size() * sizeof(BatchItemDev));
+    if (e == cudaSuccess) e = upload((void **)&p->d_units, units.data(), units.size() * sizeof(BatchUnitDev));
+    if (e == cudaSuccess) e = upload((void **)&p->d_scatter, scatter.data(), scatter.size() * sizeof(ScatterDev));
+    if (e == cudaSuccess) {
+        for (int g = 0; g < 3 && e == cudaSuccess; ++g)
+            if (p->group_units[g])
+                e = cudaFuncSetAttribute(kernel_for(dtype, B, g), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    }
+    (void)stream;
+    if (e != cudaSuccess) {
+        cudaFree(p->d_items);
+        cudaFree(p->d_units);
+        cudaFree(p->d_scatter);
+        delete p;
+        return cuda_fail(e, "batch descriptors");
+    }
+    *out = p;
+    return FTLM_OK;
+}
+
+extern "C" void ftlm_batch_destroy(ftlm_batch *p)
+{
+    if (!p) return;
+    cudaFree(p->d_items);
+    cudaFree(p->d_units);
+    cudaFree(p->d_scatter);
+    delete p;
+}
+
+extern "C" ftlm_status ftlm_batch_workspace_bytes(const ftlm_batch *p, uint64_t *bytes)
+{
+    if (!p || !bytes) return fail(FTLM_EINVAL, "NULL argument");
+    *bytes = p->total;
+    return FTLM_OK;
+}
+
+extern "C" ftlm_status ftlm_batch_run(const ftlm_batch *p, void *work_dev, uint64_t work_bytes, void *stream_)
+{
+    if (!p) return fail(FTLM_EINVAL, "NULL batch");
+    if (!work_dev || ((uintptr_t)work_dev & 255u)) return fail(FTLM_EINVAL, "workspace NULL or not 256-byte aligned");
+    if (work_bytes < p->total) return fail(FTLM_ENOMEM, "workspace smaller than ftlm_batch_workspace_bytes()");
+    cudaStream_t stream = (cudaStream_t)stream_;
+    char *ws = (char *)work_dev;
+    const int M = p->M;
+    unsigned int *queues = (unsigned int *)(ws + p->off_queue);
+    double *alpha = (double *)(ws + p->off_alpha), *beta = (double *)(ws + p->off_beta);
+    double *theta = (double *)(ws + p->off_theta), *weight = (double *)(ws + p->off_weight);
+    int *meff = (int *)(ws + p->off_meff);
+    if (p->n_small_chains) {
+        const size_t cm = (size_t)p->n_small_chains * M * sizeof(double);
+        FTLM_CUDA(cudaMemsetAsync(queues, 0, 3 * sizeof(unsigned int), stream));
+        FTLM_CUDA(cudaMemsetAsync(alpha, 0, cm, stream));
+        FTLM_CUDA(cudaMemsetAsync(beta, 0, cm, stream));
+        const size_t smem = ((size_t)1 << kLoBitsMax) * sizeof(uint16_t);
+        for (int g = 0; g < 3; ++g) {
+            if (!p->group_units[g]) continue;
+            void *kern = kernel_for(p->dtype, p->B, g);
+            const BatchItemDev *items = p->d_items;
+            const BatchUnitDev *units = p->d_units + p->group_first[g];
+            uint32_t n_units = p->group_units[g];
+            unsigned int *queue = queues + g;
+            void *slots = ws + p->off_slots;
+            uint64_t slot_elems = p->slot_elems;
+            int Mi = M, dist = p->dist;
+            void *args[] = {(void *)&items, (void *)&units, (void *)&n_units, (void *)&queue, (void *)&slots,
+                            (void *)&slot_elems, (void *)&Mi, (void *)&dist, (void *)&alpha, (void *)&beta,
+                            (void *)&meff};
+            FTLM_CUDA(cudaLaunchKernel(kern, dim3(p->group_grid[g]), dim3(kBatchThreads), args, smem, stream));
+        }
+        ftlm_status s = launch_ritz((int)p->n_small_chains, M, alpha, beta, meff, theta, weight, stream);
+        if (s != FTLM_OK) return s;
+        scatter_kernel<<<p->n_small_chains, 128, 0, stream>>>((int)p->n_small_chains, M, theta, weight, meff,
+                                                              p->d_scatter);
+        FTLM_CUDA(cudaGetLastError());
+    }
+    for (int i : p->large) {
+        const ftlm_batch_item &it = p->items[i];
+        ftlm_status s = lanczos_run(it.basis, it.R, M, it.first_chain, it.seed, p->dist, nullptr, p->dtype,
+                                    ws + p->off_large, p->large_bytes, it.theta_dev, it.weight_dev, it.m_eff_dev,
+                                    nullptr, nullptr, stream);
+        if (s != FTLM_OK) return s;
+    }
+    return FTLM_OK;
+}

@@ -146,4 +146,13 @@ ftlm_status launch_hv(const ftlm_basis *b, ftlm_dtype dtype, int B, const void *
                       const LanczosHv *epi, cudaStream_t stream);
 bool valid_block(int B);
 
+// Lanczos chains of one sector (lanczos.cu): chain r is keyed as chain chain0 + r.
+ftlm_status lanczos_run(const ftlm_basis *b, int R, int M, int chain0, uint64_t seed, int dist, const double *src,
+                        ftlm_dtype dtype, void *work, uint64_t work_bytes, double *theta, double *weight,
+                        int *m_eff, double *alpha_dev, double *beta_dev, cudaStream_t stream);
+uint64_t lanczos_workspace(const ftlm_basis *b, int R, int M, ftlm_dtype dtype);
+// Ritz step of n chains (alpha/beta rows of length M, m_eff per chain).
+ftlm_status launch_ritz(int n, int M, const double *alpha, const double *beta, const int *mv, double *theta,
+                        double *weight, cudaStream_t stream);
+
 }  // namespace ftlm

@@ -48,6 +48,7 @@
 #include "ftlm_internal.cuh"
 #include "reduce.cuh"
 #include "vec.cuh"
+#include "rows.cuh"
 
 namespace ftlm {
 
@@ -62,193 +63,19 @@ struct EpiDev {
     int has_prev;
 };
 
-// J/2 of a bond slot in the vector type.
-template <typename V> __device__ __forceinline__ V slot_jh(const uint4 &e);
-template <> __device__ __forceinline__ float slot_jh<float>(const uint4 &e) { return __uint_as_float(e.z); }
-template <> __device__ __forceinline__ double slot_jh<double>(const uint4 &e)
-{
-    return __hiloint2double((int)e.w, (int)e.z);
-}
-
-// Bonds per chunk: 8, or 4 when each gather brings 8 or more values.
-template <int B> __host__ __device__ constexpr int chunk_of() { return B >= 8 ? 4 : kBondChunk; }
-
-// Bond data of one chunk, read once and applied to every row of the thread.
-template <typename V, int C>
-struct Chunk {
-    uint32_t mlo[C], mhi[C];
-    V jh[C];
-};
-
-template <typename V, int C>
-__device__ __forceinline__ void load_chunk(const uint4 *s_bond, int b0, Chunk<V, C> &c)
-{
-#pragma unroll
-    for (int q = 0; q < C; ++q) {
-        const uint4 e = s_bond[b0 + q];  // same address in every lane: a broadcast
-        c.mlo[q] = e.x;
-        c.mhi[q] = e.y;
-        c.jh[q] = slot_jh<V>(e);
-    }
-}
-
-// Gather the chunk's antiparallel terms of RT rows (predicated loads, all issued
-// before the first use) and accumulate them into acc[row][vector].
-template <typename V, int RT, int B, int C>
-__device__ __forceinline__ void gather_accumulate(const V *__restrict__ x, const Chunk<V, C> &c,
-                                                  const bool (&aa)[RT][C], const uint32_t (&kk)[RT][C],
-                                                  V (&acc)[RT][B], V (&dsum)[RT])
-{
-    V xv[RT][C][B];
-#pragma unroll
-    for (int i = 0; i < RT; ++i)
-#pragma unroll
-        for (int q = 0; q < C; ++q) {
-            if (aa[i][q]) {
-                ld_vec<B>(x + (size_t)kk[i][q] * B, xv[i][q], false);
-            } else {
-#pragma unroll
-                for (int r = 0; r < B; ++r) xv[i][q][r] = (V)0;
-            }
-        }
-#pragma unroll
-    for (int i = 0; i < RT; ++i)
-#pragma unroll
-        for (int q = 0; q < C; ++q)
-            if (aa[i][q]) {
-#pragma unroll
-                for (int r = 0; r < B; ++r) acc[i][r] = fma(c.jh[q], xv[i][q][r], acc[i][r]);
-                dsum[i] += c.jh[q];
-            }
-}
-
-// Inverse map t -> (h, l) through the digit-block tables: the coarse index bounds
-// h to [hs[t >> kHsShift], hs[(t >> kHsShift) + 1]]; a binary search of thi finds
-// the last h with thi[h] <= t; the low pattern is entry t - thi[h] of popcount
-// group K - popcount(h).
-__device__ __forceinline__ void unrank_hl(const SectorTables &s, uint32_t t, uint32_t &h, uint32_t &l,
-                                          uint32_t &r_hi, uint32_t &r_lo)
-{
-    const uint32_t kc = t >> kHsShift;
-    uint32_t lo = __ldg(s.hs + kc), hi = __ldg(s.hs + kc + 1) + 1;
-    while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (__ldg(s.thi + mid) <= t) lo = mid;
-        else hi = mid;
-    }
-    h = lo;
-    r_hi = __ldg(s.thi + h);
-    r_lo = t - r_hi;
-    l = __ldg(s.ulo + __ldg(s.uoff + (s.K - __popc(h))) + r_lo);
-}
-
-// Row sums of RT output rows (CR): sum over antiparallel bonds of (J_b/2) x[k_b]
-// in acc, sum of their J_b/2 in dsum.
-template <typename V, typename Lbl, int RT, int B>
-__device__ __forceinline__ void rows_cr(const SectorTables &s, const BondList &bl, const uint4 *s_bond,
-                                        const uint16_t *s_tlo, const V *__restrict__ x,
-                                        const uint32_t (&t)[RT], V (&acc)[RT][B], V (&dsum)[RT])
-{
-    constexpr int C = chunk_of<B>();
-    uint32_t h[RT], l[RT], r_hi[RT], r_lo[RT];
-#pragma unroll
-    for (int i = 0; i < RT; ++i) unrank_hl(s, t[i], h[i], l[i], r_hi[i], r_lo[i]);
-    Chunk<V, C> c;
-    bool aa[RT][C];
-    uint32_t kk[RT][C];
-    const int e_lo = bl.n_lo, e_hi = bl.n_lo + bl.n_hi;
-    for (int b0 = 0; b0 < e_lo; b0 += C) {  // both sites in the low block
-        load_chunk(s_bond, b0, c);
-#pragma unroll
-        for (int i = 0; i < RT; ++i)
-#pragma unroll
-            for (int q = 0; q < C; ++q) {
-                const uint32_t m = c.mlo[q], xm = l[i] & m;
-                aa[i][q] = (xm != 0u) & (xm != m);
-                kk[i][q] = r_hi[i] + s_tlo[l[i] ^ m];
-            }
-        gather_accumulate<V, RT, B, C>(x, c, aa, kk, acc, dsum);
-    }
-    for (int b0 = e_lo; b0 < e_hi; b0 += C) {  // both sites in the high block
-        load_chunk(s_bond, b0, c);
-#pragma unroll
-        for (int i = 0; i < RT; ++i)
-#pragma unroll
-            for (int q = 0; q < C; ++q) {
-                const uint32_t m = c.mhi[q], xm = h[i] & m;
-                aa[i][q] = (xm != 0u) & (xm != m);
-                kk[i][q] = __ldg(s.thi + (h[i] ^ m)) + r_lo[i];
-            }
-        gather_accumulate<V, RT, B, C>(x, c, aa, kk, acc, dsum);
-    }
-    for (int b0 = e_hi; b0 < bl.nb; b0 += C) {  // any bond
-        load_chunk(s_bond, b0, c);
-#pragma unroll
-        for (int i = 0; i < RT; ++i) {
-            const Lbl n = ((Lbl)h[i] << s.L) | l[i];
-#pragma unroll
-            for (int q = 0; q < C; ++q) {
-                Lbl m = c.mlo[q];
-                if constexpr (sizeof(Lbl) == 8) m |= (Lbl)c.mhi[q] << 32;
-                const Lbl xm = n & m, nn = n ^ m;
-                aa[i][q] = (xm != 0) & (xm != m);
-                kk[i][q] = __ldg(s.thi + (uint32_t)(nn >> s.L)) + s_tlo[(uint32_t)nn & s.lomask];
-            }
-        }
-        gather_accumulate<V, RT, B, C>(x, c, aa, kk, acc, dsum);
-    }
-}
-
-// Row sums of RT output rows (CLT, Algorithm 2 per exchanged label).
-template <typename V, int RT, int B>
-__device__ __forceinline__ void rows_clt(const SectorTables &s, const BondList &bl, const uint4 *s_bond,
-                                         const V *__restrict__ x, const uint32_t (&t)[RT], V (&acc)[RT][B],
-                                         V (&dsum)[RT])
-{
-    constexpr int C = chunk_of<B>();
-    uint32_t n[RT];
-#pragma unroll
-    for (int i = 0; i < RT; ++i) n[i] = __ldcs(s.basis + t[i]);
-    Chunk<V, C> c;
-    bool aa[RT][C];
-    uint32_t kk[RT][C];
-    for (int b0 = 0; b0 < bl.nb; b0 += C) {
-        load_chunk(s_bond, b0, c);
-        uint2 e2[RT][C];
-#pragma unroll
-        for (int i = 0; i < RT; ++i)
-#pragma unroll
-            for (int q = 0; q < C; ++q) {
-                const uint32_t m = c.mlo[q], xm = n[i] & m;
-                aa[i][q] = (xm != 0u) & (xm != m);
-                e2[i][q] = aa[i][q] ? __ldg(s.clt + ((n[i] ^ m) >> 5)) : make_uint2(0u, 0u);
-            }
-#pragma unroll
-        for (int i = 0; i < RT; ++i)
-#pragma unroll
-            for (int q = 0; q < C; ++q) {
-                const uint32_t nn = n[i] ^ c.mlo[q];
-                kk[i][q] = e2[i][q].y + __popc(e2[i][q].x & ((1u << (nn & 31u)) - 1u));
-            }
-        gather_accumulate<V, RT, B, C>(x, c, aa, kk, acc, dsum);
-    }
-}
-
-// One warp owns a tile of 32 RT consecutive rows; lane l handles rows
-// tile_base + l + 32 i (i < RT).  Tiles are dealt to warps round-robin, so the
-// whole grid works on one contiguous window of rows at a time.
 // Resident CTAs per SM the compiler must allow for (register budget).  Single
 // vectors with up to 2 rows per thread keep a small register footprint (6 CTAs of
 // 256 threads, the shared-memory limit of the CR kernel); 4 rows per thread and
-// blocks of 4-8 vectors get at least 3 CTAs per SM (fewer starve the loads);
+// blocks of 4-8 vectors get at least 3 CTAs per SM (fewer starve the loads), 2 with
+// 8-bond chunks of 8-wide blocks (their 16 gathers per row in flight carry it);
 // 16-wide blocks keep all their registers (a cap spills).
-template <int RT, int B> __host__ __device__ constexpr int min_ctas()
+template <int RT, int B, int C> __host__ __device__ constexpr int min_ctas()
 {
-    return B >= 16 ? 1 : (B >= 4 || RT >= 4 ? 3 : 6);
+    return B >= 16 ? 1 : (B >= 8 && C >= 8 ? 2 : (B >= 4 || RT >= 4 ? 3 : 6));
 }
 
-template <typename V, typename Lbl, bool CLT, bool LANCZOS, int RT, int B>
-__global__ void __launch_bounds__(kRowThreads, min_ctas<RT, B>())
+template <typename V, typename Lbl, bool CLT, bool LANCZOS, int RT, int B, int C>
+__global__ void __launch_bounds__(kRowThreads, min_ctas<RT, B, C>())
 hv_kernel(const SectorTables s, const BondList bl, const V *__restrict__ x, V *y, const EpiDev ep)
 {
     extern __shared__ uint16_t s_tlo[];
@@ -295,8 +122,8 @@ hv_kernel(const SectorTables s, const BondList bl, const V *__restrict__ x, V *y
 #pragma unroll
             for (int r = 0; r < B; ++r) acc[i][r] = (V)0;
         }
-        if (CLT) rows_clt<V, RT, B>(s, bl, s_bond, x, t, acc, dsum);
-        else rows_cr<V, Lbl, RT, B>(s, bl, s_bond, s_tlo, x, t, acc, dsum);
+        if (CLT) rows_clt<V, RT, B, C>(s, bl, s_bond, x, t, acc, dsum);
+        else rows_cr<V, Lbl, RT, B, C>(s, bl, s_bond, s_tlo, x, t, acc, dsum);
 #pragma unroll
         for (int i = 0; i < RT; ++i) {
             if (!ok[i]) continue;
@@ -383,12 +210,12 @@ int hv_cta_cap()
     return cap;
 }
 
-template <typename V, typename Lbl, bool CLT, bool LANCZOS, int RT, int B>
+template <typename V, typename Lbl, bool CLT, bool LANCZOS, int RT, int B, int C>
 ftlm_status launch(const ftlm_basis *b, const V *x, V *y, const EpiDev &ep, cudaStream_t stream)
 {
     static int occ = -1;  // resident blocks per SM for this instantiation
     const size_t smem = CLT ? 0 : ((size_t)1 << b->L) * sizeof(uint16_t);
-    auto kern = hv_kernel<V, Lbl, CLT, LANCZOS, RT, B>;
+    auto kern = hv_kernel<V, Lbl, CLT, LANCZOS, RT, B, C>;
     if (occ < 0) {
         const size_t smem_max = CLT ? 0 : ((size_t)1 << kLoBitsMax) * sizeof(uint16_t);
         FTLM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kRowThreads, smem_max));
@@ -401,21 +228,35 @@ ftlm_status launch(const ftlm_basis *b, const V *x, V *y, const EpiDev &ep, cuda
     return FTLM_OK;
 }
 
+// Bonds per chunk for 8-wide blocks (FTLM_HV_CHUNK = 4 or 8 overrides the default
+// of 4): a larger chunk keeps more gathers in flight per row.
+int chunk8()
+{
+    static const int c = [] {
+        const char *e = getenv("FTLM_HV_CHUNK");
+        const int v = e ? atoi(e) : 0;
+        return v == 8 ? 8 : 4;
+    }();
+    return c;
+}
+
 template <typename V, typename Lbl, bool CLT, bool LANCZOS>
 ftlm_status launch_b(const ftlm_basis *b, int B, const void *x, void *y, const EpiDev &ep, cudaStream_t stream)
 {
     const V *xv = (const V *)x;
     V *yv = (V *)y;
     switch (B) {
-    case 4: return launch<V, Lbl, CLT, LANCZOS, 1, 4>(b, xv, yv, ep, stream);
-    case 8: return launch<V, Lbl, CLT, LANCZOS, 1, 8>(b, xv, yv, ep, stream);
-    case 16: return launch<V, Lbl, CLT, LANCZOS, 1, 16>(b, xv, yv, ep, stream);
+    case 4: return launch<V, Lbl, CLT, LANCZOS, 1, 4, 8>(b, xv, yv, ep, stream);
+    case 8:
+        return chunk8() == 8 ? launch<V, Lbl, CLT, LANCZOS, 1, 8, 8>(b, xv, yv, ep, stream)
+                             : launch<V, Lbl, CLT, LANCZOS, 1, 8, 4>(b, xv, yv, ep, stream);
+    case 16: return launch<V, Lbl, CLT, LANCZOS, 1, 16, 4>(b, xv, yv, ep, stream);
     default: break;
     }
     switch (rows_per_thread(CLT)) {
-    case 1: return launch<V, Lbl, CLT, LANCZOS, 1, 1>(b, xv, yv, ep, stream);
-    case 4: return launch<V, Lbl, CLT, LANCZOS, 4, 1>(b, xv, yv, ep, stream);
-    default: return launch<V, Lbl, CLT, LANCZOS, 2, 1>(b, xv, yv, ep, stream);
+    case 1: return launch<V, Lbl, CLT, LANCZOS, 1, 1, 8>(b, xv, yv, ep, stream);
+    case 4: return launch<V, Lbl, CLT, LANCZOS, 4, 1, 8>(b, xv, yv, ep, stream);
+    default: return launch<V, Lbl, CLT, LANCZOS, 2, 1, 8>(b, xv, yv, ep, stream);
     }
 }
 

@@ -19,39 +19,11 @@
 #include "ftlm_internal.cuh"
 #include "reduce.cuh"
 #include "vec.cuh"
+#include "rng.cuh"
 
 namespace ftlm {
 
 namespace {
-
-constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
-
-__host__ __device__ __forceinline__ uint64_t sm64_mix(uint64_t z)
-{
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
-uint64_t chain_key(uint64_t seed, int N, int K, uint32_t r)
-{
-    const uint64_t tag = ((uint64_t)N << 48) | ((uint64_t)K << 32) | (uint64_t)r;
-    return sm64_mix(sm64_mix(seed + kGamma) + tag + kGamma);
-}
-
-__device__ __forceinline__ double start_value(uint64_t key, uint64_t t, int dist)
-{
-    if (dist == FTLM_VEC_RADEMACHER) {
-        const uint64_t u = sm64_mix(key + (t + 1) * kGamma);
-        return (u >> 63) ? -1.0 : 1.0;
-    }
-    const uint64_t u1 = sm64_mix(key + (2 * t + 1) * kGamma);
-    const uint64_t u2 = sm64_mix(key + (2 * t + 2) * kGamma);
-    const double U1 = ((double)(u1 >> 11) + 1.0) * 0x1p-53;
-    const double U2 = (double)(u2 >> 11) * 0x1p-53;
-    const double two_pi = 2.0 * 3.14159265358979323846;
-    return sqrt(-2.0 * log(U1)) * cos(two_pi * U2);
-}
 
 struct Keys {
     uint64_t k[kMaxBlock];
@@ -207,29 +179,38 @@ __global__ void copy_meff_kernel(const ChainState *st, int B, int *dst)
 // "Matrix Computations", Sec. 8.3), deflating from the bottom.  Only the first
 // row z of the accumulated rotation matrix is kept: the eigenvector matrix of T is
 // the product of the rotations, so its first row gives s_{k,1}.
-__device__ void givens(double a, double b, double &c, double &s)
+//
+// GB300 has a narrow FP64 pipe, so FP64 square roots and divisions are long
+// dependent sequences; each rotation uses one reciprocal square root and no
+// division, and one thread runs one chain with many chains per CTA, so the
+// latency of many chains overlaps.  The arrays of the chains of a CTA are
+// interleaved in shared memory: element k of thread i at [k * T + i].
+struct Strided {
+    double *p;
+    int stride;
+    __device__ __forceinline__ double &operator[](int k) const { return p[k * stride]; }
+};
+
+// [c s; -s c]^T [a; b] = [r; 0] with r = sqrt(a^2 + b^2) >= 0.
+__device__ __forceinline__ void givens(double a, double b, double &c, double &s)
 {
-    // [c s; -s c]^T [a; b] = [r; 0]
-    if (b == 0.0) {
+    const double r2 = fma(a, a, b * b);
+    if (r2 == 0.0) {
         c = 1.0;
         s = 0.0;
-    } else if (fabs(b) > fabs(a)) {
-        const double tau = -a / b;
-        s = 1.0 / sqrt(1.0 + tau * tau);
-        c = s * tau;
-    } else {
-        const double tau = -b / a;
-        c = 1.0 / sqrt(1.0 + tau * tau);
-        s = c * tau;
+        return;
     }
+    const double ir = rsqrt(r2);
+    c = a * ir;
+    s = -b * ir;
 }
 
-__device__ bool negligible(double e, double d0, double d1)
+__device__ __forceinline__ bool negligible(double e, double d0, double d1)
 {
-    return fabs(e) <= 0x1p-52 * (fabs(d0) + fabs(d1)) || fabs(e) < 1e-290;
+    return fabs(e) <= 0x1p-52 * (fabs(d0) + fabs(d1)) || fabs(e) < 1e-150;
 }
 
-__device__ void tridiag_qr(double *d, double *e, double *z, int n)
+__device__ void tridiag_qr(Strided d, Strided e, Strided z, int n)
 {
     int hi = n - 1;
     const int max_sweeps = 64 * n;
@@ -245,7 +226,7 @@ __device__ void tridiag_qr(double *d, double *e, double *z, int n)
         ++sweep;
         const double dd = 0.5 * (d[hi - 1] - d[hi]);
         const double bb = e[hi - 1];
-        const double den = dd + (dd >= 0.0 ? 1.0 : -1.0) * hypot(dd, bb);
+        const double den = dd + (dd >= 0.0 ? 1.0 : -1.0) * sqrt(fma(dd, dd, bb * bb));
         const double mu = d[hi] - bb * (bb / den);
         double x = d[lo] - mu, zz = e[lo];
         for (int k = lo; k < hi; ++k) {
@@ -258,9 +239,10 @@ __device__ void tridiag_qr(double *d, double *e, double *z, int n)
             d[k + 1] = s2 * a + 2.0 * cs * b + c2 * cc;
             e[k] = cs * (a - cc) + (c2 - s2) * b;
             if (k < hi - 1) {
+                const double en = e[k + 1];
                 x = e[k];
-                zz = -s * e[k + 1];
-                e[k + 1] = c * e[k + 1];
+                zz = -s * en;
+                e[k + 1] = c * en;
             }
             const double z0 = z[k], z1 = z[k + 1];
             z[k] = c * z0 - s * z1;
@@ -269,49 +251,65 @@ __device__ void tridiag_qr(double *d, double *e, double *z, int n)
     }
 }
 
-__global__ void ritz_kernel(int M, const double *__restrict__ alpha, const double *__restrict__ beta,
+// One thread per chain; T chains per CTA.
+__global__ void ritz_kernel(int n, int M, const double *__restrict__ alpha, const double *__restrict__ beta,
                             const int *__restrict__ mv, double *theta, double *weight)
 {
     extern __shared__ double sh[];
-    double *d = sh, *e = sh + M, *z = sh + 2 * M;
-    const int c = blockIdx.x;
+    const int T = blockDim.x, i = threadIdx.x;
+    const int c = blockIdx.x * T + i;
+    if (c >= n) return;
+    Strided d{sh + i, T}, e{sh + (size_t)M * T + i, T}, z{sh + (size_t)2 * M * T + i, T};
     int m = mv[c];
     m = m < 0 ? 0 : (m > M ? M : m);
-    for (int i = threadIdx.x; i < M; i += blockDim.x) {
-        d[i] = i < m ? alpha[(size_t)c * M + i] : 0.0;
-        e[i] = i + 1 < m ? beta[(size_t)c * M + i] : 0.0;
-        z[i] = i == 0 ? 1.0 : 0.0;
+    for (int k = 0; k < m; ++k) {
+        d[k] = alpha[(size_t)c * M + k];
+        e[k] = k + 1 < m ? beta[(size_t)c * M + k] : 0.0;
+        z[k] = k == 0 ? 1.0 : 0.0;
     }
-    __syncthreads();
-    if (threadIdx.x == 0 && m > 1) {
+    if (m > 1) {
         tridiag_qr(d, e, z, m);
-        for (int i = 1; i < m; ++i) {  // ascending theta
-            const double dk = d[i], zk = z[i];
-            int k = i - 1;
-            while (k >= 0 && d[k] > dk) {
-                d[k + 1] = d[k];
-                z[k + 1] = z[k];
-                --k;
+        for (int k = 1; k < m; ++k) {  // ascending theta
+            const double dk = d[k], zk = z[k];
+            int j = k - 1;
+            while (j >= 0 && d[j] > dk) {
+                d[j + 1] = d[j];
+                z[j + 1] = z[j];
+                --j;
             }
-            d[k + 1] = dk;
-            z[k + 1] = zk;
+            d[j + 1] = dk;
+            z[j + 1] = zk;
         }
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < M; i += blockDim.x) {
-        theta[(size_t)c * M + i] = i < m ? d[i] : 0.0;
-        weight[(size_t)c * M + i] = i < m ? z[i] * z[i] : 0.0;
+    for (int k = 0; k < M; ++k) {
+        theta[(size_t)c * M + k] = k < m ? d[k] : 0.0;
+        weight[(size_t)c * M + k] = k < m ? z[k] * z[k] : 0.0;
     }
 }
+
+}  // namespace
 
 ftlm_status launch_ritz(int n, int M, const double *alpha, const double *beta, const int *mv,
                         double *theta, double *weight, cudaStream_t stream)
 {
     if (n == 0) return FTLM_OK;
-    ritz_kernel<<<n, 32, 3 * (size_t)M * sizeof(double), stream>>>(M, alpha, beta, mv, theta, weight);
+    constexpr size_t kSmemMax = 96 * 1024;
+    static bool attr_set = false;
+    if (!attr_set) {
+        FTLM_CUDA(cudaFuncSetAttribute(ritz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
+        attr_set = true;
+    }
+    const size_t per_chain = 3 * (size_t)M * sizeof(double);
+    int T = (int)(kSmemMax / per_chain);
+    T = T < 1 ? 1 : (T > 32 ? 32 : T);
+    if (T > n) T = n;
+    const int grid = (n + T - 1) / T;
+    ritz_kernel<<<grid, T, per_chain * T, stream>>>(n, M, alpha, beta, mv, theta, weight);
     FTLM_CUDA(cudaGetLastError());
     return FTLM_OK;
 }
+
+namespace {
 
 // ---- workspace and block plan -------------------------------------------
 uint64_t align256(uint64_t v) { return (v + 255) & ~255ull; }
@@ -377,7 +375,7 @@ int occupancy_of(const void *kern)
 
 // One block of B chains: start vectors, then min(M, D) fused H.v + update launches.
 template <typename V, int B>
-ftlm_status run_block(const ftlm_basis *b, int M, int r0, uint64_t seed, int dist, const double *src,
+ftlm_status run_block(const ftlm_basis *b, int M, int r0, int chain0, uint64_t seed, int dist, const double *src,
                       ftlm_dtype dtype, char *ws, const Layout &lay, cudaStream_t stream)
 {
     static int occ_start = -1, occ_upd = -1;
@@ -400,7 +398,7 @@ ftlm_status run_block(const ftlm_basis *b, int M, int r0, uint64_t seed, int dis
 
     FTLM_CUDA(cudaMemsetAsync(st, 0, lay.bw * sizeof(ChainState) + 64, stream));
     Keys keys{};
-    for (int r = 0; r < B; ++r) keys.k[r] = chain_key(seed, b->N, b->K, (uint32_t)(r0 + r));
+    for (int r = 0; r < B; ++r) keys.k[r] = chain_key(seed, b->N, b->K, (uint32_t)(chain0 + r0 + r));
     start_kernel<V, B><<<g_start, kRowThreads, 0, stream>>>(D, keys, dist, src ? src + (size_t)r0 * D : nullptr,
                                                            vec[0], st, partials, counter);
     FTLM_CUDA(cudaGetLastError());
@@ -422,7 +420,7 @@ ftlm_status run_block(const ftlm_basis *b, int M, int r0, uint64_t seed, int dis
 }
 
 template <typename V>
-ftlm_status run_chains(const ftlm_basis *b, int R, int M, uint64_t seed, int dist, const double *src,
+ftlm_status run_chains(const ftlm_basis *b, int R, int M, int chain0, uint64_t seed, int dist, const double *src,
                        ftlm_dtype dtype, char *ws, const Layout &lay, double *theta, double *weight,
                        int *m_eff, double *alpha_dev, double *beta_dev, cudaStream_t stream)
 {
@@ -435,10 +433,10 @@ ftlm_status run_chains(const ftlm_basis *b, int R, int M, uint64_t seed, int dis
     for (int B : block_plan(R, dtype)) {
         ftlm_status s;
         switch (B) {
-        case 16: s = run_block<V, 16>(b, M, r0, seed, dist, src, dtype, ws, lay, stream); break;
-        case 8: s = run_block<V, 8>(b, M, r0, seed, dist, src, dtype, ws, lay, stream); break;
-        case 4: s = run_block<V, 4>(b, M, r0, seed, dist, src, dtype, ws, lay, stream); break;
-        default: s = run_block<V, 1>(b, M, r0, seed, dist, src, dtype, ws, lay, stream); break;
+        case 16: s = run_block<V, 16>(b, M, r0, chain0, seed, dist, src, dtype, ws, lay, stream); break;
+        case 8: s = run_block<V, 8>(b, M, r0, chain0, seed, dist, src, dtype, ws, lay, stream); break;
+        case 4: s = run_block<V, 4>(b, M, r0, chain0, seed, dist, src, dtype, ws, lay, stream); break;
+        default: s = run_block<V, 1>(b, M, r0, chain0, seed, dist, src, dtype, ws, lay, stream); break;
         }
         if (s != FTLM_OK) return s;
         r0 += B;
@@ -453,9 +451,11 @@ ftlm_status run_chains(const ftlm_basis *b, int R, int M, uint64_t seed, int dis
     return FTLM_OK;
 }
 
-ftlm_status lanczos_common(const ftlm_basis *b, int R, int M, uint64_t seed, int dist, const double *src,
-                           ftlm_dtype dtype, void *work, uint64_t work_bytes, double *theta,
-                           double *weight, int *m_eff, double *alpha_dev, double *beta_dev, void *stream)
+}  // namespace
+
+ftlm_status lanczos_run(const ftlm_basis *b, int R, int M, int chain0, uint64_t seed, int dist, const double *src,
+                        ftlm_dtype dtype, void *work, uint64_t work_bytes, double *theta, double *weight,
+                        int *m_eff, double *alpha_dev, double *beta_dev, cudaStream_t stream)
 {
     if (!b) return fail(FTLM_EINVAL, "NULL basis");
     if (R < 1) return fail(FTLM_EINVAL, "R < 1");
@@ -467,11 +467,15 @@ ftlm_status lanczos_common(const ftlm_basis *b, int R, int M, uint64_t seed, int
     const Layout lay = layout(b, R, M, dtype);
     if (work_bytes < lay.total) return fail(FTLM_ENOMEM, "workspace smaller than ftlm_lanczos_workspace_bytes()");
     return dtype == FTLM_F32
-               ? run_chains<float>(b, R, M, seed, dist, src, dtype, (char *)work, lay, theta, weight, m_eff,
-                                   alpha_dev, beta_dev, (cudaStream_t)stream)
-               : run_chains<double>(b, R, M, seed, dist, src, dtype, (char *)work, lay, theta, weight, m_eff,
-                                    alpha_dev, beta_dev, (cudaStream_t)stream);
+               ? run_chains<float>(b, R, M, chain0, seed, dist, src, dtype, (char *)work, lay, theta, weight,
+                                   m_eff, alpha_dev, beta_dev, stream)
+               : run_chains<double>(b, R, M, chain0, seed, dist, src, dtype, (char *)work, lay, theta, weight,
+                                    m_eff, alpha_dev, beta_dev, stream);
 }
+
+uint64_t lanczos_workspace(const ftlm_basis *b, int R, int M, ftlm_dtype dtype) { return layout(b, R, M, dtype).total; }
+
+namespace {
 
 // Scratch of ftlm_lanczos_noalloc, for callers that cannot allocate device memory.
 // Host code sees only a host-side stand-in for this symbol; its device address is
@@ -520,8 +524,8 @@ extern "C" ftlm_status ftlm_lanczos_noalloc(const ftlm_basis *b, int R, int M, u
     void *scratch = nullptr;
     ftlm_status s = noalloc_scratch(&scratch);
     if (s != FTLM_OK) return s;
-    return lanczos_common(b, R, M, seed, dist, nullptr, dtype, scratch, FTLM_NOALLOC_SCRATCH_BYTES,
-                          theta_dev, weight_dev, m_eff_dev, alpha_dev, beta_dev, stream);
+    return lanczos_run(b, R, M, 0, seed, dist, nullptr, dtype, scratch, FTLM_NOALLOC_SCRATCH_BYTES, theta_dev,
+                       weight_dev, m_eff_dev, alpha_dev, beta_dev, (cudaStream_t)stream);
 }
 
 extern "C" ftlm_status ftlm_lanczos_workspace_bytes(const ftlm_basis *b, int R, int M, ftlm_dtype dtype,
@@ -539,8 +543,8 @@ extern "C" ftlm_status ftlm_lanczos(const ftlm_basis *b, int R, int M, uint64_t 
                                     double *weight_dev, int *m_eff_dev, double *alpha_dev, double *beta_dev,
                                     void *stream)
 {
-    return lanczos_common(b, R, M, seed, dist, nullptr, dtype, work_dev, work_bytes, theta_dev, weight_dev,
-                          m_eff_dev, alpha_dev, beta_dev, stream);
+    return lanczos_run(b, R, M, 0, seed, dist, nullptr, dtype, work_dev, work_bytes, theta_dev, weight_dev, m_eff_dev,
+                       alpha_dev, beta_dev, (cudaStream_t)stream);
 }
 
 extern "C" ftlm_status ftlm_lanczos_from(const ftlm_basis *b, int R, int M, const double *start_dev,
@@ -549,8 +553,8 @@ extern "C" ftlm_status ftlm_lanczos_from(const ftlm_basis *b, int R, int M, cons
                                          double *alpha_dev, double *beta_dev, void *stream)
 {
     if (!start_dev) return fail(FTLM_EINVAL, "start_dev is NULL");
-    return lanczos_common(b, R, M, 0, FTLM_VEC_GAUSS, start_dev, dtype, work_dev, work_bytes, theta_dev,
-                          weight_dev, m_eff_dev, alpha_dev, beta_dev, stream);
+    return lanczos_run(b, R, M, 0, 0, FTLM_VEC_GAUSS, start_dev, dtype, work_dev, work_bytes, theta_dev, weight_dev,
+                       m_eff_dev, alpha_dev, beta_dev, (cudaStream_t)stream);
 }
 
 extern "C" ftlm_status ftlm_ritz(int n, int M, const double *alpha_dev, const double *beta_dev,

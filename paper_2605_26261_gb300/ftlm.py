@@ -28,6 +28,13 @@ MAX_SITES, MAX_BONDS, MAX_LANCZOS, MAX_SECTORS = 36, 256, 1024, 64
 _lib = None
 
 
+class BatchItem(ctypes.Structure):
+    """ftlm_batch_item of include/ftlm.h."""
+    _fields_ = [("basis", ctypes.c_void_p), ("R", ctypes.c_int), ("first_chain", ctypes.c_int),
+                ("seed", ctypes.c_uint64), ("theta_dev", ctypes.c_void_p), ("weight_dev", ctypes.c_void_p),
+                ("m_eff_dev", ctypes.c_void_p)]
+
+
 class FtlmError(RuntimeError):
     def __init__(self, status, message):
         super().__init__(f"{_status_name(status)}: {message}")
@@ -67,6 +74,9 @@ def lib():
         "ftlm_lanczos_noalloc": [P, I, I, U64, I, I, P, P, P, P, P, P],
         "ftlm_ritz": [I, I, P, P, P, P, P, P],
         "ftlm_thermo": [I, P, P, I, I, P, P, P, I, D, D, I, P, P, P, P, P, P],
+        "ftlm_batch_create": [I, P, I, I, I, I, P, ctypes.POINTER(P)],
+        "ftlm_batch_workspace_bytes": [P, PU64],
+        "ftlm_batch_run": [P, P, U64, P],
         "ftlm_profile_enable": [I],
         "ftlm_profile_read": [PU64, PU64, PD, PU64, PD],
     }
@@ -76,6 +86,8 @@ def lib():
         f.restype = ctypes.c_int
     L.ftlm_basis_destroy.argtypes = [P]
     L.ftlm_basis_destroy.restype = None
+    L.ftlm_batch_destroy.argtypes = [P]
+    L.ftlm_batch_destroy.restype = None
     L.ftlm_status_string.argtypes = [ctypes.c_int]
     L.ftlm_status_string.restype = ctypes.c_char_p
     L.ftlm_last_error.argtypes = []
@@ -239,6 +251,27 @@ def ftlm_thermo(two_sz, dims, R, M, thetas, weights, m_effs, mirror_neg, g, h, T
                              _stream(stream)))
 
 
+def ftlm_batch_create(items, M, dist, dtype, block=0, stream=None):
+    """items: sequence of BatchItem; returns the batch handle."""
+    arr = (BatchItem * len(items))(*items)
+    out = ctypes.c_void_p()
+    _check(lib().ftlm_batch_create(len(items), arr, int(M), int(dist), _dtype_code(dtype), int(block),
+                                   _stream(stream), ctypes.byref(out)))
+    return out
+
+
+def ftlm_batch_workspace_bytes(handle):
+    return _u64_query(lib().ftlm_batch_workspace_bytes, handle)
+
+
+def ftlm_batch_run(handle, work, stream=None):
+    _check(lib().ftlm_batch_run(handle, _ptr(work), work.numel() * work.element_size(), _stream(stream)))
+
+
+def ftlm_batch_destroy(handle):
+    lib().ftlm_batch_destroy(handle)
+
+
 def ftlm_profile_enable(on=True):
     _check(lib().ftlm_profile_enable(int(bool(on))))
 
@@ -318,6 +351,49 @@ def thermo(sectors, T, R, M, g=2.0, h=0.0, mirror=True, stream=None):
                 [s[2]["m_eff"] for s in sectors], mirror, g, h, T, out["E"], out["C"], out["chi"],
                 out["mag"], stream=stream)
     return out
+
+
+class Batch:
+    """Many sectors in one batch (ftlm_batch_*): chains of every (basis, R, seed,
+    first_chain) entry; outputs per entry as device tensors theta, weight (R x M)
+    and m_eff (R)."""
+
+    def __init__(self, entries, M, dist=GAUSS, dtype=torch.float32, block=0, stream=None):
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.M = int(M)
+        self.results = []
+        items = []
+        for basis, R, seed, first_chain in entries:
+            out = {"theta": torch.zeros((R, M), dtype=torch.float64, device=dev),
+                   "weight": torch.zeros((R, M), dtype=torch.float64, device=dev),
+                   "m_eff": torch.zeros(R, dtype=torch.int32, device=dev)}
+            self.results.append(out)
+            items.append(BatchItem(basis.handle.value, int(R), int(first_chain), int(seed) & (2**64 - 1),
+                                   out["theta"].data_ptr(), out["weight"].data_ptr(), out["m_eff"].data_ptr()))
+        self.handle = ftlm_batch_create(items, M, dist, dtype, block, stream)
+        nbytes = ftlm_batch_workspace_bytes(self.handle)
+        self.work = torch.empty((nbytes + 255) // 256 * 256, dtype=torch.uint8, device=dev)
+
+    def run(self, stream=None):
+        ftlm_batch_run(self.handle, self.work, stream)
+        return self.results
+
+    def close(self):
+        if self.handle is not None:
+            ftlm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def computed_two_sz(N):

@@ -1,0 +1,127 @@
+"""Batched chains of many sectors (ftlm_batch_*) against per-sector ftlm_lanczos
+and against the oracle.
+
+Per-sector comparison: the same chains (same seed and chain indices), so Ritz data
+agree up to the summation order of the dot products; compared through spectral
+sums sum_k w_k exp(-b theta_k), which are insensitive to how near-degenerate
+(ghost) Ritz pairs split their weight: 1e-10 relative in FP64, 1e-5 in FP32.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as o
+from paper_2605_26261_gb300 import ftlm, inputs
+
+pytestmark = pytest.mark.gpu
+
+BETAS = (0.2, 1.0, 5.0)
+
+
+def spectral_sums(theta, weight, m):
+    th, w = theta.cpu().numpy(), weight.cpu().numpy()
+    out = []
+    for r in range(th.shape[0]):
+        k = int(m[r])
+        out.append([np.sum(w[r, :k] * np.exp(-b * (th[r, :k] - th[r, 0]))) for b in BETAS] + [th[r, 0]])
+    return np.array(out)
+
+
+def clusters():
+    return [(10, inputs.random_graph(10, seed=1)), (12, inputs.random_graph(12, seed=2)),
+            (13, inputs.random_graph(13, seed=3)), (16, inputs.ring(16))]
+
+
+@pytest.mark.parametrize("dtype,rtol", [(torch.float64, 1e-10), (torch.float32, 1e-5)])
+@pytest.mark.parametrize("block", [1, 4, 8, 16])
+def test_batch_matches_per_sector_lanczos(cuda_dev, dtype, rtol, block):
+    M, R, seed = 40, 6, 11
+    bases = []
+    for N, bonds in clusters():
+        for tz in ftlm.computed_two_sz(N):
+            bases.append(ftlm.Basis(N, tz, bonds, ftlm.RANK_CR if N % 2 else ftlm.RANK_CLT))
+    entries = [(b, R, seed + i, 3 * i) for i, b in enumerate(bases)]
+    with ftlm.Batch(entries, M, ftlm.GAUSS, dtype, block) as batch:
+        res = batch.run()
+        torch.cuda.synchronize()
+        for (b, R_, s, c0), got in zip(entries, res):
+            # reference: the same chains through ftlm_lanczos, one sector at a time
+            ref = ftlm.lanczos(b, R + c0, M, seed=s, dist=ftlm.GAUSS, dtype=dtype)
+            torch.cuda.synchronize()
+            m_ref = ref["m_eff"][c0:].cpu().numpy()
+            assert np.array_equal(got["m_eff"].cpu().numpy(), m_ref), (b.N, b.two_sz)
+            a = spectral_sums(got["theta"], got["weight"], m_ref)
+            e = spectral_sums(ref["theta"][c0:], ref["weight"][c0:], m_ref)
+            np.testing.assert_allclose(a, e, rtol=rtol, atol=rtol * 1e-3)
+    for b in bases:
+        b.close()
+
+
+def test_batch_mixes_small_and_large_sectors(cuda_dev):
+    # D = C(18, 9) = 48620 runs through the grid-wide path, the rest inside CTAs.
+    M, R = 30, 5
+    bonds = inputs.ring(18)
+    bases = [ftlm.Basis(18, tz, bonds) for tz in (0, 2, 10, 18)]
+    entries = [(b, R, 4, 0) for b in bases]
+    with ftlm.Batch(entries, M, ftlm.RADEMACHER, torch.float64) as batch:
+        res = batch.run()
+        torch.cuda.synchronize()
+        for b, got in zip(bases, res):
+            ref = ftlm.lanczos(b, R, M, seed=4, dist=ftlm.RADEMACHER, dtype=torch.float64)
+            torch.cuda.synchronize()
+            np.testing.assert_allclose(spectral_sums(got["theta"], got["weight"], got["m_eff"]),
+                                       spectral_sums(ref["theta"], ref["weight"], ref["m_eff"]), rtol=1e-10)
+    for b in bases:
+        b.close()
+
+
+def test_batch_run_captured_in_cuda_graph(cuda_dev):
+    M, R = 30, 8
+    bases = [ftlm.Basis(12, tz, inputs.random_graph(12, seed=9)) for tz in (0, 2, 4)]
+    entries = [(b, R, 1, 0) for b in bases]
+    with ftlm.Batch(entries, M, ftlm.GAUSS, torch.float32, 8) as batch:
+        direct = [{k: v.clone() for k, v in r.items()} for r in batch.run()]
+        torch.cuda.synchronize()
+        for r in batch.results:
+            for v in r.values():
+                v.zero_()
+        s = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            batch.run(stream=s)
+        g.replay()
+        g.replay()
+        torch.cuda.synchronize()
+        for a, b in zip(direct, batch.results):
+            for k in ("theta", "weight", "m_eff"):
+                assert torch.equal(a[k], b[k]), k
+    for b in bases:
+        b.close()
+
+
+def test_batch_ftlm_matches_oracle(cuda_dev):
+    # Two random clusters, every S^z >= 0 sector, FP64: thermodynamics vs the oracle.
+    M, R = 40, 5
+    T = inputs.log_t_grid(60, 0.05, 10.0)
+    for N, seed in ((11, 21), (12, 22)):
+        bonds = inputs.random_graph(N, seed=seed)
+        bases = [ftlm.Basis(N, tz, bonds) for tz in ftlm.computed_two_sz(N)]
+        with ftlm.Batch([(b, R, 7, 0) for b in bases], M, ftlm.GAUSS, torch.float64, 4) as batch:
+            res = batch.run()
+            obs = ftlm.thermo([(b.two_sz, b.dim, r) for b, r in zip(bases, res)],
+                              torch.as_tensor(T, device=cuda_dev), R, M)
+        ref = o.thermo(o.run_ftlm(N, bonds, R, M, seed=7), T)
+        for k in ("E", "C", "chi"):
+            got, want = obs[k].cpu().numpy(), ref[k]
+            scale = np.max(np.abs(want))
+            np.testing.assert_allclose(got, want, rtol=1e-9, atol=1e-12 * scale)
+        for b in bases:
+            b.close()
+
+
+def test_batch_rejects_bad_items(cuda_dev):
+    with ftlm.Basis(8, 0, inputs.ring(8)) as b:
+        with pytest.raises(ftlm.FtlmError):
+            ftlm.Batch([(b, 0, 1, 0)], 10)
+        with pytest.raises(ftlm.FtlmError):
+            ftlm.Batch([(b, 2, 1, 0)], 10, block=3)
