@@ -36,6 +36,14 @@ FALLBACK_HBM_GBS = 6800.0
 WORKLOADS = {
     "icosidodecahedron": dict(N=30, desc="icosidodecahedron N=30 S^z=0 (D=155117520, 60 bonds, J=1)"),
     "ring34": dict(N=34, desc="ring N=34 S^z=0 (D=2333606220, 34 bonds, J=1)"),
+    # a smaller sector of the same kind (4-regular-like random graph) for detailed
+    # counter captures that must stay within a few GB of device memory
+    "random28": dict(N=28, desc="random graph N=28 (degrees 3-5, J~U[0.5,1.5], seed 28) S^z=0 (D=40116600)"),
+    "serving": dict(N=26, desc="Poisson stream (200 jobs/s, seeded) of FTLM jobs: rings or 2-leg ladders, N uniform "
+                               "in {16,...,26} even, J~U[0.2,1.5], h~U[0,2], every S^z sector, R=8 Gaussian, M=80, "
+                               "f32 vectors"),
+    "clusters256": dict(N=22, desc="256 random clusters, N uniform in {18,20,22}, degrees 3-5, J~U[0.5,1.5], "
+                                   "every S^z >= 0 sector (mirrored), R=16 Rademacher, M=100, f32 vectors"),
 }
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "hv_kernel_icosidodecahedron.md")
 
@@ -52,18 +60,30 @@ def parse_args():
     p.add_argument("--R", type=int, default=8)
     p.add_argument("--M", type=int, default=100)
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--jobs", type=int, default=128, help="serving: requests in the timed stream")
+    p.add_argument("--slots", type=int, default=4, help="serving: concurrent groups (CUDA streams)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--hv-only", action="store_true",
                    help="time plain ftlm_hv launches on the workload (kernel microbenchmark)")
-    p.add_argument("--block", type=int, default=1,
-                   help="with --hv-only: vectors per launch (ftlm_hv_block, 1/4/8/16)")
+    p.add_argument("--block", type=int, default=0,
+                   help="with --hv-only: vectors per launch (ftlm_hv_block, 1/4/8/16); with clusters256: "
+                        "fixed block width instead of the autotuner")
     return p.parse_args()
 
 
 def bonds_of(name):
     from paper_2605_26261_gb300 import inputs
 
-    return inputs.icosidodecahedron() if name == "icosidodecahedron" else inputs.ring(34)
+    if name == "icosidodecahedron":
+        return inputs.icosidodecahedron()
+    if name == "random28":
+        return inputs.random_graph(28, seed=28)
+    if name == "clusters256":  # the CPU sample: the first N = 22 cluster of the set
+        return next(b for N, b in inputs.cluster_set(256, seed=256) if N == 22)
+    if name == "serving":  # the CPU sample: the first N = 26 request of the stream
+        reqs, _ = inputs.serving_requests(128, 200.0, seed=4)
+        return next(r["bonds"] for r in reqs if r["N"] == 26)
+    return inputs.ring(34)
 
 
 def sector_model_bytes(updates, D, dtype_bytes, clt, lanczos=True, B=1):
@@ -92,7 +112,7 @@ def peak_hbm():
 def kernel_fingerprint():
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2605_26261_gb300", "csrc")
-    for f in ("hv.cu", "reduce.cuh", "ftlm_internal.cuh"):
+    for f in ("hv.cu", "rows.cuh", "vec.cuh", "reduce.cuh", "ftlm_internal.cuh"):
         with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -200,18 +220,21 @@ class OracleSampler:
         self.upd_per_row = (self.D + 2 * len(self.bonds[2]) * math.comb(N - 2, N // 2 - 1)) / self.D
         self.x = np.random.default_rng(seed).standard_normal(self.D)
 
-    def _run(self, rows_per_chunk, offset):
+    def _run(self, rows_per_chunk, offset, passes=1):
         starts = (np.linspace(0, self.D - rows_per_chunk - 64, 64) + offset).astype(np.int64)
         out = np.empty(rows_per_chunk)
         t = time.perf_counter()
-        for s in starts:
-            self.o.hv_range(self.bonds, self.b, self.x, int(s), int(s) + rows_per_chunk, out=out)
-        return time.perf_counter() - t, 64 * rows_per_chunk
+        for _ in range(passes):
+            for s in starts:
+                self.o.hv_range(self.bonds, self.b, self.x, int(s), int(s) + rows_per_chunk, out=out)
+        return time.perf_counter() - t, passes * 64 * rows_per_chunk
 
     def sample(self, seconds, offset=0):
         t0, n0 = self._run(256, offset)
-        rows_chunk = max(256, int(seconds / (t0 / n0) / 64))
-        t1, n1 = self._run(rows_chunk, offset)
+        want = seconds / (t0 / n0)  # rows that take about `seconds`
+        rows_chunk = int(max(256, min(want / 64, (self.D - 128) // 64)))
+        passes = max(1, int(want / (64 * rows_chunk)))
+        t1, n1 = self._run(rows_chunk, offset, passes)
         return {"updates_per_s": n1 * self.upd_per_row / t1, "rows": n1, "seconds": t1,
                 "cores": self.o.num_threads(), "D": self.D}
 
@@ -302,6 +325,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     ftlm.ftlm_profile_enable(True)
+    launches0 = ftlm.ftlm_launch_count()
     with ClockSampler(local) as clocks:
         ev[0].record(stream)
         for i in range(args.steps):
@@ -309,6 +333,7 @@ def run_ours(args):
             ev[i + 1].record(stream)
         torch.cuda.synchronize()
     ftlm.ftlm_profile_enable(False)
+    launches_timed = ftlm.ftlm_launch_count() - launches0
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -317,13 +342,6 @@ def run_ours(args):
     hv_n, hv_vec, hv_ms, up_n, up_ms = ftlm.ftlm_profile_read()
     chains_steps = int(m_eff.sum().item())
     updates_step = chains_steps * updates_hv
-    # kernels per step: H.v and update launches (counted), per chain block a start
-    # and an m_eff copy, the Ritz step, the thermodynamic sums, the coarse index
-    # build of the sector setup, and for CLT the basis and CLT builds
-    m_max = min(M, D)
-    blocks = hv_n // max(1, args.steps * m_max)
-    launches_step = ((hv_n + up_n) // args.steps + 2 * blocks + 2 + 1
-                     + (2 if mode_used == ftlm.RANK_CLT else 0))
 
     all_updates, max_ms = aggregate_over_ranks(updates_step * args.steps, total_ms, dev, world)
     value = all_updates / (max_ms / 1e3) / 1e9
@@ -400,17 +418,293 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": value / PAPER_GUPS, "dtype": args.dtype, "data": "synthetic",
         "config": {"workload": wl["desc"] + f", R={R} Rademacher, M={M}, 200-point T grid",
                    "rank_mode": mode_name.upper(), "vectors": f"{args.dtype} storage, FP64 reductions",
-                   "l2": "inputs larger than L2 (two vectors of D elements, 620 MB each in f32)",
+                   "l2": f"inputs larger than L2 (two blocks of {R} vectors of D elements, "
+                         f"{2 * R * D * (4 if dt == torch.float32 else 8) / 1e9:.1f} GB)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "vs_baseline_ref": "paper GPU-CLT, 124 s for this job on RTX 4000 Ada (Table 3)"},
         "jobs_per_s": world * args.steps / (max_ms / 1e3),
         "p50_ms": srt[len(srt) // 2], "p99_ms": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": launches_step * args.steps, "clocks": clocks.summary(),
+        "gpu_launches": launches_timed, "clocks": clocks.summary(),
     }
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_clusters(args):
+    """Many small clusters in one batch: every sector of 256 clusters through one
+    ftlm_batch (persistent kernel for sectors up to 32768 states, side streams for
+    the rest), then the thermodynamic sums of each cluster, captured once as a CUDA
+    graph and replayed per step.  Block width and side-stream count come from
+    ftlm_batch_autotune on a 24-cluster subset."""
+    import torch
+
+    import __graft_entry__
+    from paper_2605_26261_gb300 import ftlm, inputs
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    R, M = 16, 100
+    dt = torch.float32
+    clusters = inputs.cluster_set(256, seed=256)
+    T_host = inputs.log_t_grid(200)
+    T = torch.as_tensor(T_host, device=dev)
+
+    def make_bases(cl):
+        return [[ftlm.Basis(N, tz, bonds) for tz in ftlm.computed_two_sz(N)] for N, bonds in cl]
+
+    def entries_of(bases_per_cluster, first=0):
+        return [(b, R, 1 + first + c, 0) for c, bs in enumerate(bases_per_cluster) for b in bs]
+
+    t_setup = time.perf_counter()
+    bases = make_bases(clusters)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t_setup
+    # autotune on 8 clusters of each size
+    sub = []
+    for n in (18, 20, 22):
+        sub += [c for c, (N, _) in enumerate(clusters) if N == n][:8]
+    t_tune = time.perf_counter()
+    if args.block:
+        block, streams, tune_times = (args.block if args.block > 1 else 16), 4, {}
+    else:
+        block, streams, tune_times = ftlm.autotune(entries_of([bases[c] for c in sub]), M, ftlm.RADEMACHER, dt)
+    tune_s = time.perf_counter() - t_tune
+    batch = ftlm.Batch(entries_of(bases), M, ftlm.RADEMACHER, dt, block, streams)
+    results = batch.results
+    outs = [{k: torch.empty_like(T) for k in ("E", "C", "chi", "mag")} for _ in clusters]
+    k0 = [0]
+    for bs in bases:
+        k0.append(k0[-1] + len(bs))
+
+    def step():
+        batch.run()
+        for c, bs in enumerate(bases):
+            res = results[k0[c]:k0[c + 1]]
+            o = outs[c]
+            ftlm.ftlm_thermo([b.two_sz for b in bs], [b.dim for b in bs], R, M, [r["theta"] for r in res],
+                             [r["weight"] for r in res], [r["m_eff"] for r in res], True, 2.0, 0.0, T,
+                             o["E"], o["C"], o["chi"], o["mag"])
+
+    # one eager run with kernel timing on, for the H.v launch statistics
+    ftlm.ftlm_profile_read()
+    ftlm.ftlm_profile_enable(True)
+    step()
+    torch.cuda.synchronize()
+    ftlm.ftlm_profile_enable(False)
+    hv_n, hv_vec, hv_ms, up_n, up_ms = ftlm.ftlm_profile_read()
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    launches0 = ftlm.ftlm_launch_count()
+    with torch.cuda.graph(graph, stream=side):
+        step()
+    launches_graph = ftlm.ftlm_launch_count() - launches0  # kernel nodes of one replay
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    with ClockSampler(local) as clocks:
+        ev[0].record(stream)
+        for i in range(args.steps):
+            graph.replay()
+            ev[i + 1].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    total_ms = sum(step_ms)
+
+    updates = 0
+    alg_bytes = 0
+    large_rows = small_rows = 0
+    for c, bs in enumerate(bases):
+        for b, r in zip(bs, results[k0[c]:k0[c + 1]]):
+            steps = int(r["m_eff"].sum().item())
+            updates += steps * b.updates
+            # sector model per chain step, block of `block` interleaved f32 vectors
+            alg_bytes += steps / block * sector_model_bytes(b.updates, b.dim, 4, b.mode == ftlm.RANK_CLT,
+                                                            B=block)
+            if b.dim > 32768:
+                large_rows += b.dim
+            else:
+                small_rows += b.dim
+    all_updates, max_ms = aggregate_over_ranks(updates * args.steps, total_ms, dev, world)
+    value = all_updates / (max_ms / 1e3) / 1e9
+
+    # end to end through the public API from host data: sector setup, plan, run,
+    # thermodynamic sums, results to pinned host memory, release
+    e2e = None
+    if rank == 0:
+        obs_host = torch.empty((len(clusters), 3, 200), dtype=torch.float64).pin_memory()
+        T_pin = torch.as_tensor(T_host).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        T.copy_(T_pin, non_blocking=True)
+        bases2 = make_bases(clusters)
+        with ftlm.Batch(entries_of(bases2), M, ftlm.RADEMACHER, dt, block, streams) as b2:
+            res2 = b2.run()
+            for c, bs in enumerate(bases2):
+                res = res2[k0[c]:k0[c + 1]]
+                o = outs[c]
+                ftlm.ftlm_thermo([b.two_sz for b in bs], [b.dim for b in bs], R, M, [r["theta"] for r in res],
+                                 [r["weight"] for r in res], [r["m_eff"] for r in res], True, 2.0, 0.0, T,
+                                 o["E"], o["C"], o["chi"], o["mag"])
+                for j, k in enumerate(("E", "C", "chi")):
+                    obs_host[c, j].copy_(o[k], non_blocking=True)
+            torch.cuda.synchronize()
+        for bs in bases2:
+            for b in bs:
+                b.close()
+        wall = time.perf_counter() - t0
+        h2d = sum(bonds[0].nbytes + bonds[1].nbytes + bonds[2].nbytes for _, bonds in clusters) + T_pin.numel() * 8
+        e2e = {"value": updates / wall / 1e9, "unit": "Gupdates/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(obs_host.numel() * 8), "ms_per_step": 1e3 * wall,
+               "clusters_per_s": len(clusters) / wall}
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    peak, peak_src = peak_hbm()
+    achieved = alg_bytes / (max_ms / args.steps / 1e3) / 1e9
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        res = OracleSampler(args.workload).sample(args.cpu_seconds)
+        cpu = {"value": res["updates_per_s"] / 1e9, "unit": "Gupdates/s", "cores": res["cores"], "kind": "oracle",
+               "sample": f"FP64 oracle H.v on {res['rows']} rows (64 evenly spread chunks) of the S^z=0 sector "
+                         f"(D={res['D']}) of the first N=22 cluster, {res['seconds']:.1f} s"}
+    srt = sorted(step_ms)
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gupdates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOADS["clusters256"]["desc"], "sectors": sum(len(bs) for bs in bases),
+                   "rows_small_sectors": small_rows, "rows_large_sectors": large_rows,
+                   "block": block, "side_streams": streams,
+                   "autotune": {f"B{k[0]}_s{k[1]}": round(v, 2) for k, v in tune_times.items()},
+                   "autotune_s": tune_s, "setup_s": setup_s,
+                   "graph": "one CUDA graph per step: batch run + 256 thermodynamic launches",
+                   "l2": "per-sector working sets are L2-sized (<= 90 MB); the whole step streams "
+                         f"{2 * 16 * 4 * (small_rows + large_rows) / 1e9:.1f} GB of vectors",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "clusters_per_s": world * len(clusters) * args.steps / (max_ms / 1e3),
+        "p50_ms": srt[len(srt) // 2], "p99_ms": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None,
+                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
+                     else "fallback",
+                     "kernel": "whole step (batch kernel + H.v launches of the large sectors)",
+                     "model": "sector model summed over every H.v of the step / step time; sectors are "
+                              "L2-resident, so the HBM model overstates the DRAM bytes",
+                     "hv_launches_large": hv_n, "hv_ms_large": hv_ms, "update_ms_large": up_ms},
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_graph * args.steps, "clocks": clocks.summary(),
+    }
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_serving(args):
+    """The request loop (serve.Engine) on a seeded Poisson stream of FTLM jobs: jobs/s
+    and p50/p99 latency from arrival to results on the host, beside the same jobs
+    run one at a time (one slot, one job per batch, all queued at once), and a
+    bit-for-bit comparison of every job's results in the two runs."""
+    import torch
+
+    import __graft_entry__
+    from paper_2605_26261_gb300 import ftlm, inputs, serve
+
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:  # replicas only: the request loop runs on rank 0's GPU
+        return
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    T = inputs.log_t_grid(200)
+    n_jobs = args.jobs
+    R, M = 8, 80
+
+    def engine(slots, max_group):
+        return serve.Engine(slots=slots, R=R, M=M, dtype=torch.float32, block=8, streams=2, T=T,
+                            dist=ftlm.GAUSS, max_group=max_group)
+
+    # warm-up: a few jobs of every size through a throwaway engine
+    warm, _ = serve.poisson_jobs(max(args.warmup, 6), 200.0, seed=99)
+    engine(args.slots, 8).run(warm)
+    torch.cuda.synchronize()
+
+    jobs, arrivals = serve.poisson_jobs(n_jobs, 200.0, seed=4)
+    launches0 = ftlm.ftlm_launch_count()
+    with ClockSampler(local) as clocks:
+        done = engine(args.slots, 8).run(jobs, arrivals)
+        torch.cuda.synchronize()
+    launches = ftlm.ftlm_launch_count() - launches0
+    lat = np.array([j.latency for j in done]) * 1e3
+    makespan = max(j.finish for j in done) - min(j.arrival for j in done)
+    served = {j.job_id: j for j in done}
+
+    alone_jobs, _ = serve.poisson_jobs(n_jobs, 200.0, seed=4)
+    t0 = time.perf_counter()
+    alone = engine(1, 1).run(alone_jobs)
+    torch.cuda.synchronize()
+    alone_s = time.perf_counter() - t0
+    same = sum(1 for j in alone if np.array_equal(j.result, served[j.job_id].result))
+    alone_lat = np.array([j.latency for j in alone]) * 1e3
+
+    updates = sum(j.updates for j in done)
+    value = len(done) / makespan
+    peak, peak_src = peak_hbm()
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        res = OracleSampler("serving").sample(args.cpu_seconds)
+        cpu = {"value": res["updates_per_s"] / 1e9, "unit": "Gupdates/s", "cores": res["cores"], "kind": "oracle",
+               "sample": f"FP64 oracle H.v on {res['rows']} rows of the S^z=0 sector (D={res['D']}) of the first "
+                         f"N=26 request, {res['seconds']:.1f} s (oracle Gupdates/s; GPU Gupdates/s of the served "
+                         f"run: {updates / makespan / 1e9:.1f})"}
+    h2d = sum(j.bonds[0].nbytes + j.bonds[1].nbytes + j.bonds[2].nbytes for j in jobs)
+    line = {
+        "metric": METRIC, "value": value, "unit": "jobs/s", "n_gpus": 1, "steps": n_jobs, "warmup": len(warm),
+        "ms_per_step": 1e3 * makespan / n_jobs, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOADS["serving"]["desc"], "jobs": n_jobs, "slots": args.slots,
+                   "max_group": 8, "block": 8, "side_streams": 2,
+                   "admission": "exact footprint (tables + workspace + outputs) within 80% of free HBM",
+                   "l2": "largest sectors (D=10400600, 8 f32 vectors) exceed L2",
+                   "parallelism": "single GPU"},
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "makespan_s": makespan, "Gupdates_per_s": updates / makespan / 1e9,
+        "one_at_a_time": {"jobs_per_s": n_jobs / alone_s, "p50_ms": float(np.percentile(alone_lat, 50)),
+                          "p99_ms": float(np.percentile(alone_lat, 99)),
+                          "note": "same jobs, one slot, one job per batch, all queued at t=0"},
+        "identical_alone_vs_mix": f"{same}/{n_jobs}",
+        "roofline": {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None, "traffic": None,
+                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+                     "note": "request-loop line: the H.v kernel roofline is reported by the default workload"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": value, "unit": "jobs/s", "h2d_bytes_per_step": int(h2d / n_jobs),
+                "d2h_bytes_per_step": int(4 * 200 * 8 + 4 * R * 14),
+                "note": "the request loop is end to end: bond lists from host memory, results to pinned host"},
+        "gpu_launches": launches, "clocks": clocks.summary(),
+    }
+    print(json.dumps(line))
 
 
 def run_hv_only(args):
@@ -427,7 +721,7 @@ def run_hv_only(args):
     bonds = bonds_of(args.workload)
     mode = {"auto": ftlm.RANK_AUTO, "clt": ftlm.RANK_CLT, "cr": ftlm.RANK_CR}[args.mode]
     dt = torch.float32 if args.dtype == "f32" else torch.float64
-    B = args.block
+    B = args.block or 1
     with ftlm.Basis(N, 0, bonds, mode) as b:
         x = inputs.hashed_vector_torch(b.dim * B, dt, dev)
         y = torch.empty_like(x)
@@ -460,6 +754,10 @@ def main():
     args = parse_args()
     if args.hv_only:
         run_hv_only(args)
+    elif args.workload == "clusters256" and args.impl == "ours":
+        run_clusters(args)
+    elif args.workload == "serving" and args.impl == "ours":
+        run_serving(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

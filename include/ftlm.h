@@ -19,7 +19,8 @@
  * Conventions for every call:
  *   - Pointers named *_dev are device pointers (cudaMalloc'd or from a caching
  *     allocator) owned by the caller; other pointers are host memory.  Device
- *     pointers of vectors must be 16-byte aligned.
+ *     pointers of vectors must be 16-byte aligned (32-byte for blocks whose rows
+ *     are 32 bytes or more, see ftlm_hv_block).
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is queued
  *     on it asynchronously; outputs are valid once the stream reaches that point.
  *   - Every call returns an ftlm_status; nothing aborts, throws or exits.  On a
@@ -79,9 +80,12 @@ typedef struct ftlm_basis ftlm_basis; /* one (cluster, N, S^z) sector; opaque */
  *   mode       rank strategy.  CLT needs N <= 32 and stores the sorted basis
  *              (4 D bytes) and the CLT (8 ceil(2^N/32) bytes, Eq. 21); CR stores
  *              only small digit-block tables (Eq. 15-16) and needs D < 2^32.
- *   stream     tables are built on it; the basis is usable by later work on any
- *              stream once this work has completed on `stream`.
- *   out        receives the handle; the library owns the device tables it holds.
+ *   stream     tables are built on it; create returns after that work has
+ *              completed on `stream` (no other stream is waited for), so the basis
+ *              is usable at once on any stream.
+ *   out        receives the handle; the library owns the device tables it holds:
+ *              one block from a per-device stream-ordered memory pool, so creating
+ *              and releasing sectors does not synchronize the device.
  * Errors: EINVAL (ranges, duplicate pair, i == j), EUNSUPPORTED (CLT with N > 32,
  * D >= 2^32), ENOMEM, ECUDA.
  */
@@ -89,9 +93,17 @@ ftlm_status ftlm_basis_create(int N, int two_sz, int n_bonds, const int *bi, con
                               const double *J, ftlm_rank_mode mode, void *stream,
                               ftlm_basis **out);
 
-/* Release the handle and its device tables (waits for nothing; do not destroy a
- * basis while work that uses it is still queued).  NULL is ignored. */
+/* Release the handle and its device tables.  Waits until the device has finished
+ * all queued work first (any stream may still read the tables).  NULL is ignored. */
 void ftlm_basis_destroy(ftlm_basis *basis);
+
+/* Release the handle at once and return its device tables to the pool in the order
+ * of `stream`, without waiting: every kernel that reads the tables must already be
+ * queued on `stream`, or be ordered before this point of `stream` by the caller
+ * (cudaStreamWaitEvent).  For request loops that retire jobs while others run.
+ * NULL is ignored (FTLM_OK).  ECUDA if the release cannot be queued (the handle is
+ * freed regardless). */
+ftlm_status ftlm_basis_destroy_async(ftlm_basis *basis, void *stream);
 
 /* Sector dimension D = C(N, K). */
 ftlm_status ftlm_basis_dim(const ftlm_basis *basis, uint64_t *dim);
@@ -134,9 +146,10 @@ ftlm_status ftlm_hv(const ftlm_basis *basis, ftlm_dtype dtype, const void *x_dev
 
 /* ftlm_hv_block -- Y = H X for a block of B vectors stored interleaved: entry
  * (t, r) of vector r at X[t * B + r] (B in {1, 4, 8, 16}; x_dev, y_dev hold D * B
- * elements of dtype).  Each row's rank work is shared by the B vectors (the batched
- * scheme of Sec. 3.4); column r of Y is bit-identical to ftlm_hv on column r of X.
- * EINVAL for another B. */
+ * elements of dtype, 32-byte aligned when a row of B entries is 32 bytes or
+ * more, else 16-byte aligned; EINVAL otherwise).  Each row's rank work is shared
+ * by the B vectors (the batched scheme of Sec. 3.4); column r of Y is
+ * bit-identical to ftlm_hv on column r of X.  EINVAL for another B. */
 ftlm_status ftlm_hv_block(const ftlm_basis *basis, ftlm_dtype dtype, int B, const void *x_dev,
                           void *y_dev, void *stream);
 
@@ -144,10 +157,18 @@ ftlm_status ftlm_hv_block(const ftlm_basis *basis, ftlm_dtype dtype, int B, cons
  * Workspace bytes ftlm_lanczos / ftlm_lanczos_from need for R chains of at most M
  * steps: two blocks of D x B_w elements of dtype plus O(R M) coefficients, B_w the
  * widest block of chains the call runs at once (chains go in blocks of 16, 8 or 4
- * interleaved vectors, up to 8 in FP32 and 4 in FP64, then single chains).  EINVAL
- * for R < 1 or M outside 1..FTLM_MAX_LANCZOS. */
+ * interleaved vectors, up to the width of ftlm_lanczos_set_block -- by default 8
+ * in FP32 and 4 in FP64 -- then single chains).  EINVAL for R < 1 or M outside
+ * 1..FTLM_MAX_LANCZOS. */
 ftlm_status ftlm_lanczos_workspace_bytes(const ftlm_basis *basis, int R, int M, ftlm_dtype dtype,
                                          uint64_t *bytes);
+
+/* ftlm_lanczos_set_block -- widest block of chains that later ftlm_lanczos,
+ * ftlm_lanczos_from and ftlm_lanczos_workspace_bytes calls use: 1 (every chain
+ * on its own, the plain one-vector path), 4, 8 or 16; 0 restores the default
+ * (FTLM_BLOCK from the environment, else 8 in FP32 and 4 in FP64).  Process-wide;
+ * size workspaces after setting it.  EINVAL for another width. */
+ftlm_status ftlm_lanczos_set_block(int width);
 
 /* ftlm_lanczos -- R Lanczos chains (steps a2, a4, a5) on one sector.
  *   Chain r starts from a counter-based random vector keyed by (seed, N, K, r):
@@ -229,15 +250,24 @@ ftlm_status ftlm_lanczos_noalloc(const ftlm_basis *basis, int R, int M, uint64_t
  *   of `block` chains (block = 1, 4, 8 or 16; 0 = 16 for FP32, 8 for FP64) that one
  *   persistent kernel runs, one CTA per unit at a time, each unit's chains entirely
  *   inside its CTA (vectors in a per-CTA workspace slot, CTA-local reductions);
- *   larger sectors run through the launch sequence of ftlm_lanczos.  Uploads the
- *   plan's descriptors (device memory owned by the batch; the only allocation).
- *   `stream` is unused (reserved).  EINVAL for an empty batch or bad items.
+ *   larger sectors run through the launch sequence of ftlm_lanczos with blocks of
+ *   up to `block` chains, spread over up to `streams` side streams (1..8; 0 =
+ *   FTLM_BATCH_STREAMS or 4) that each run forks from and joins back into the
+ *   caller's stream.  Uploads the plan's descriptors on
+ *   `stream` (one block from the library's device memory pool, owned by the
+ *   batch) and returns when they are in place.  EINVAL for an empty batch or bad
+ *   items.
  * ftlm_batch_workspace_bytes -- scratch the plan needs (per-CTA vector slots,
- *   O(chains M) coefficients, and the largest large-sector workspace).
- * ftlm_batch_run -- queue the batch on `stream`: memsets and kernel launches only,
- *   so a run can be captured into a CUDA graph and replayed.  Results match
- *   ftlm_lanczos on each item up to the summation order of the dot products.
- *   ENOMEM when the workspace is too small.  Runs of one batch must not overlap.
+ *   O(chains M) coefficients, one large-sector workspace per side stream).
+ * ftlm_batch_run -- queue the batch on `stream`: memsets, kernel launches and
+ *   event records/waits only, so a run can be captured into a CUDA graph (the side
+ *   streams join the capture) and replayed.  Results match ftlm_lanczos on each
+ *   item up to the summation order of the dot products, and do not depend on the
+ *   side-stream assignment.  ENOMEM when the workspace is too small.  Runs of one
+ *   batch must not overlap.
+ * ftlm_batch_destroy -- waits for the device to finish queued work, then releases.
+ * ftlm_batch_destroy_async -- releases without waiting; the descriptors return to
+ *   the pool in the order of `stream`, which every run of the batch must precede.
  */
 typedef struct {
     const ftlm_basis *basis;
@@ -252,10 +282,25 @@ typedef struct {
 typedef struct ftlm_batch ftlm_batch;
 
 ftlm_status ftlm_batch_create(int n_items, const ftlm_batch_item *items, int M, ftlm_vec_dist dist,
-                              ftlm_dtype dtype, int block, void *stream, ftlm_batch **out);
+                              ftlm_dtype dtype, int block, int streams, void *stream, ftlm_batch **out);
 ftlm_status ftlm_batch_workspace_bytes(const ftlm_batch *batch, uint64_t *bytes);
 ftlm_status ftlm_batch_run(const ftlm_batch *batch, void *work_dev, uint64_t work_bytes, void *stream);
 void ftlm_batch_destroy(ftlm_batch *batch);
+ftlm_status ftlm_batch_destroy_async(ftlm_batch *batch, void *stream);
+
+/* ftlm_batch_autotune -- pick the block width and side-stream count of a batch by
+ * timing it: for block in {4, 8, 16} and (when some item has D > 32768) streams in
+ * {1, 2, 4, 8}, plan the batch, run it once untimed and once between CUDA events on
+ * `stream`, and return the fastest pair in *block_out, *streams_out.  ms_out, if
+ * not NULL, receives the timed runs (float[12], index 4 * (0, 1, 2 for block 4, 8,
+ * 16) + (0..3 for streams 1, 2, 4, 8); entries not tried are left alone).  Blocks
+ * the host until the runs finish.  The items' outputs are overwritten.  Workspaces
+ * come from the library's pool and are released before return.  Tune on a
+ * representative subset of a large job: each candidate runs the whole list twice.
+ * Errors as ftlm_batch_create and ftlm_batch_run. */
+ftlm_status ftlm_batch_autotune(int n_items, const ftlm_batch_item *items, int M, ftlm_vec_dist dist,
+                                ftlm_dtype dtype, void *stream, int *block_out, int *streams_out,
+                                float *ms_out);
 
 /* ftlm_ritz -- the Ritz step alone (a5): for each of n chains, the eigenvalues theta
  * and first-component weights w = s_{k,1}^2 of the tridiagonal matrix with diagonal
@@ -286,6 +331,11 @@ ftlm_status ftlm_thermo(int n_sectors, const int *two_sz, const uint64_t *dims, 
                         const int *const *m_eff, int mirror_neg, double g, double h, int nT,
                         const double *T_dev, double *E_dev, double *C_dev, double *chi_dev,
                         double *mag_dev, void *stream);
+
+/* ftlm_launch_count -- kernels the library has queued in this process so far (every
+ * launch of every entry point, on any stream; a launch captured into a CUDA graph
+ * counts once, at capture, not at each replay). */
+ftlm_status ftlm_launch_count(uint64_t *count);
 
 /* ------------------------------------------------------------- diagnostics ---
  * Kernel timing: while enabled, CUDA events are recorded on the launch stream

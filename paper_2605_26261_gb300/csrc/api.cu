@@ -1,4 +1,5 @@
 // Error reporting and kernel timing shared by every entry point.
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -31,7 +32,36 @@ cudaEvent_t take_event()
     if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
     return e;
 }
+std::atomic<uint64_t> g_launches{0};
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[256] = {};
 }  // namespace
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+cudaError_t table_pool(int device, cudaMemPool_t *pool)
+{
+    if (device < 0 || device >= 256) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pools[device]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        cudaMemPool_t p = nullptr;
+        cudaError_t e = cudaMemPoolCreate(&p, &props);
+        if (e != cudaSuccess) return e;
+        uint64_t keep = kPoolKeepBytes;
+        e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(p);
+            return e;
+        }
+        g_pools[device] = p;
+    }
+    *pool = g_pools[device];
+    return cudaSuccess;
+}
 
 ftlm_status fail(ftlm_status s, const std::string &msg)
 {
@@ -100,6 +130,13 @@ extern "C" ftlm_status ftlm_profile_read(uint64_t *hv_launches, uint64_t *hv_vec
     if (update_launches) *update_launches = n[kProfUpdate];
     if (update_ms) *update_ms = ms[kProfUpdate];
     return st;
+}
+
+extern "C" ftlm_status ftlm_launch_count(uint64_t *count)
+{
+    if (!count) return fail(FTLM_EINVAL, "NULL argument");
+    *count = g_launches.load(std::memory_order_relaxed);
+    return FTLM_OK;
 }
 
 extern "C" const char *ftlm_status_string(ftlm_status s)

@@ -28,6 +28,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -38,15 +39,15 @@ namespace ftlm {
 namespace {
 
 uint64_t g_binom[65][65];
-bool g_binom_ready = false;
+std::once_flag g_binom_once;
 
 void init_binom()
 {
-    if (g_binom_ready) return;
-    for (int n = 0; n <= 64; ++n)
-        for (int k = 0; k <= 64; ++k)
-            g_binom[n][k] = (k == 0) ? 1 : (n == 0 ? 0 : g_binom[n - 1][k - 1] + g_binom[n - 1][k]);
-    g_binom_ready = true;
+    std::call_once(g_binom_once, [] {
+        for (int n = 0; n <= 64; ++n)
+            for (int k = 0; k <= 64; ++k)
+                g_binom[n][k] = (k == 0) ? 1 : (n == 0 ? 0 : g_binom[n - 1][k - 1] + g_binom[n - 1][k]);
+    });
 }
 
 uint64_t binom(int n, int k)
@@ -190,17 +191,7 @@ int grid_for(uint64_t n, int threads, int num_sms)
     return (int)std::max<uint64_t>(1, std::min(g, cap));
 }
 
-void free_tables(ftlm_basis *b)
-{
-    cudaFree(b->thi);
-    cudaFree(b->tlo);
-    cudaFree(b->ulo);
-    cudaFree(b->uoff);
-    cudaFree(b->hs);
-    cudaFree(b->bond_slots);
-    cudaFree(b->basis);
-    cudaFree(b->clt);
-}
+uint64_t align256(uint64_t v) { return (v + 255) & ~uint64_t(255); }
 
 }  // namespace
 
@@ -379,61 +370,90 @@ extern "C" ftlm_status ftlm_basis_create(int N, int two_sz, int n_bonds, const i
         for (uint64_t h = 0; h < b->H; ++h) thi[h] = (uint32_t)count_below(h << L, N, K);
     }
 
-    auto bail = [&](cudaError_t e, const char *what) {
-        free_tables(b);
-        delete b;
-        return cuda_fail(e, what);
+    // One stream-ordered allocation holds every table: the small ones first (bond
+    // slots, thi, tlo, ulo, uoff, and the binomials the CLT build reads), filled by
+    // one copy from a host image, then the coarse index and, for CLT, the basis
+    // array and the CLT entries, which kernels fill on the device.
+    b->n_hs = ((D - 1) >> kHsShift) + 2;
+    const bool clt = mode == FTLM_RANK_CLT;
+    uint64_t off = 0;
+    auto take = [&](uint64_t bytes) {
+        const uint64_t o = off;
+        off = align256(off + bytes);
+        return o;
     };
-    cudaError_t e;
-    if ((e = cudaMalloc(&b->bond_slots, slots.size() * sizeof(uint4))) != cudaSuccess)
-        return bail(e, "cudaMalloc(bond slots)");
-    if ((e = cudaMemcpy(b->bond_slots, slots.data(), slots.size() * sizeof(uint4), cudaMemcpyHostToDevice)) !=
-        cudaSuccess)
-        return bail(e, "cudaMemcpy(bond slots)");
+    const uint64_t o_slots = take(slots.size() * sizeof(uint4));
+    const uint64_t o_thi = take(b->H * sizeof(uint32_t));
+    const uint64_t o_tlo = take(nlo * sizeof(uint16_t));
+    const uint64_t o_ulo = take(nlo * sizeof(uint16_t));
+    const uint64_t o_uoff = take(sizeof(b->ulo_off));
+    const uint64_t o_binom = clt ? take(33 * 33 * sizeof(uint64_t)) : off;
+    const uint64_t small_bytes = off;
+    const uint64_t o_hs = take(b->n_hs * sizeof(uint32_t));
+    const uint64_t o_basis = clt ? take(D * sizeof(uint32_t)) : off;
+    const uint64_t o_clt = clt ? take(b->nblocks * sizeof(uint2)) : off;
+    b->table_bytes = off;
+
+    std::vector<unsigned char> image(small_bytes, 0);
+    std::memcpy(image.data() + o_slots, slots.data(), slots.size() * sizeof(uint4));
+    std::memcpy(image.data() + o_thi, thi.data(), b->H * sizeof(uint32_t));
+    std::memcpy(image.data() + o_tlo, tlo.data(), nlo * sizeof(uint16_t));
+    std::memcpy(image.data() + o_ulo, ulo.data(), nlo * sizeof(uint16_t));
+    std::memcpy(image.data() + o_uoff, b->ulo_off, sizeof(b->ulo_off));
+    if (clt) {
+        uint64_t *bh = reinterpret_cast<uint64_t *>(image.data() + o_binom);
+        for (int n = 0; n <= 32; ++n)
+            for (int k = 0; k <= 32; ++k) bh[n * 33 + k] = binom(n, k);
+    }
+
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = table_pool(b->device, &pool);
+    if (e != cudaSuccess) {
+        delete b;
+        return cuda_fail(e, "table memory pool");
+    }
+    e = cudaMallocFromPoolAsync(&b->block, b->table_bytes, pool, stream);
+    if (e != cudaSuccess) {
+        delete b;
+        return e == cudaErrorMemoryAllocation ? fail(FTLM_ENOMEM, "no device memory for the sector tables")
+                                              : cuda_fail(e, "cudaMallocFromPoolAsync(tables)");
+    }
+    char *base = static_cast<char *>(b->block);
+    b->bond_slots = reinterpret_cast<uint4 *>(base + o_slots);
+    b->thi = reinterpret_cast<uint32_t *>(base + o_thi);
+    b->tlo = reinterpret_cast<uint16_t *>(base + o_tlo);
+    b->ulo = reinterpret_cast<uint16_t *>(base + o_ulo);
+    b->uoff = reinterpret_cast<uint32_t *>(base + o_uoff);
+    b->hs = reinterpret_cast<uint32_t *>(base + o_hs);
+    b->basis = clt ? reinterpret_cast<uint32_t *>(base + o_basis) : nullptr;
+    b->clt = clt ? reinterpret_cast<uint2 *>(base + o_clt) : nullptr;
     b->bonds_cr.slots_f32 = b->bond_slots;
     b->bonds_cr.slots_f64 = b->bond_slots + kMaxBondSlots;
     b->bonds_clt.slots_f32 = b->bond_slots + 2 * kMaxBondSlots;
     b->bonds_clt.slots_f64 = b->bond_slots + 3 * kMaxBondSlots;
-    if ((e = cudaMalloc(&b->thi, b->H * sizeof(uint32_t))) != cudaSuccess) return bail(e, "cudaMalloc(thi)");
-    if ((e = cudaMalloc(&b->tlo, nlo * sizeof(uint16_t))) != cudaSuccess) return bail(e, "cudaMalloc(tlo)");
-    if ((e = cudaMalloc(&b->ulo, nlo * sizeof(uint16_t))) != cudaSuccess) return bail(e, "cudaMalloc(ulo)");
-    if ((e = cudaMalloc(&b->uoff, sizeof(b->ulo_off))) != cudaSuccess) return bail(e, "cudaMalloc(uoff)");
-    b->table_bytes = b->H * sizeof(uint32_t) + 2ull * nlo * sizeof(uint16_t) + sizeof(b->ulo_off) +
-                     slots.size() * sizeof(uint4);
-    // Synchronous copies: the host vectors go out of scope on return.
-    if ((e = cudaMemcpy(b->thi, thi.data(), b->H * sizeof(uint32_t), cudaMemcpyHostToDevice)) != cudaSuccess)
-        return bail(e, "cudaMemcpy(thi)");
-    if ((e = cudaMemcpy(b->tlo, tlo.data(), nlo * sizeof(uint16_t), cudaMemcpyHostToDevice)) != cudaSuccess)
-        return bail(e, "cudaMemcpy(tlo)");
-    if ((e = cudaMemcpy(b->ulo, ulo.data(), nlo * sizeof(uint16_t), cudaMemcpyHostToDevice)) != cudaSuccess)
-        return bail(e, "cudaMemcpy(ulo)");
-    if ((e = cudaMemcpy(b->uoff, b->ulo_off, sizeof(b->ulo_off), cudaMemcpyHostToDevice)) != cudaSuccess)
-        return bail(e, "cudaMemcpy(uoff)");
-    b->n_hs = ((D - 1) >> kHsShift) + 2;
-    if ((e = cudaMalloc(&b->hs, b->n_hs * sizeof(uint32_t))) != cudaSuccess) return bail(e, "cudaMalloc(hs)");
-    b->table_bytes += b->n_hs * sizeof(uint32_t);
-    hs_fill_kernel<<<grid_for(b->n_hs, 256, b->num_sms), 256, 0, stream>>>(b->tables(), b->n_hs, b->hs);
-    if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "hs_fill_kernel");
-    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return bail(e, "hs_fill_kernel");
 
-    if (mode == FTLM_RANK_CLT) {
-        if ((e = cudaMalloc(&b->basis, D * sizeof(uint32_t))) != cudaSuccess) return bail(e, "cudaMalloc(basis)");
-        if ((e = cudaMalloc(&b->clt, b->nblocks * sizeof(uint2))) != cudaSuccess) return bail(e, "cudaMalloc(clt)");
-        b->table_bytes += D * sizeof(uint32_t) + b->nblocks * sizeof(uint2);
-        uint64_t *binom_d = nullptr;
-        std::vector<uint64_t> bh(33 * 33);
-        for (int n = 0; n <= 32; ++n)
-            for (int k = 0; k <= 32; ++k) bh[n * 33 + k] = binom(n, k);
-        if ((e = cudaMalloc(&binom_d, bh.size() * sizeof(uint64_t))) != cudaSuccess) return bail(e, "cudaMalloc(binom)");
-        e = cudaMemcpy(binom_d, bh.data(), bh.size() * sizeof(uint64_t), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) {
+    // A copy from pageable memory returns once the image is staged, so `image`
+    // may go out of scope; the kernels below follow it in stream order.
+    e = cudaMemcpyAsync(base, image.data(), small_bytes, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) {
+        hs_fill_kernel<<<grid_for(b->n_hs, 256, b->num_sms), 256, 0, stream>>>(b->tables(), b->n_hs, b->hs);
+        note_launch();
+        if (clt) {
+            const uint64_t *binom_d = reinterpret_cast<const uint64_t *>(base + o_binom);
             basis_fill_kernel<<<grid_for(D, 256, b->num_sms), 256, 0, stream>>>(b->tables(), b->basis);
-            clt_fill_kernel<<<grid_for(b->nblocks, 256, b->num_sms), 256, 0, stream>>>(N, K, b->nblocks, binom_d, b->clt);
-            e = cudaGetLastError();
+            note_launch();
+            clt_fill_kernel<<<grid_for(b->nblocks, 256, b->num_sms), 256, 0, stream>>>(N, K, b->nblocks, binom_d,
+                                                                                        b->clt);
+            note_launch();
         }
-        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-        cudaFree(binom_d);
-        if (e != cudaSuccess) return bail(e, "CLT build kernels");
+        e = cudaGetLastError();
+    }
+    // The tables are complete when create returns (only this stream is waited for).
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(b->block, stream);
+        delete b;
+        return cuda_fail(e, "sector table build");
     }
     *out = b;
     return FTLM_OK;
@@ -442,8 +462,19 @@ extern "C" ftlm_status ftlm_basis_create(int N, int two_sz, int n_bonds, const i
 extern "C" void ftlm_basis_destroy(ftlm_basis *b)
 {
     if (!b) return;
-    free_tables(b);
+    // Wait for every queued kernel (any of them may read the tables), then return
+    // the block to the pool.
+    cudaDeviceSynchronize();
+    cudaFreeAsync(b->block, 0);
     delete b;
+}
+
+extern "C" ftlm_status ftlm_basis_destroy_async(ftlm_basis *b, void *stream)
+{
+    if (!b) return FTLM_OK;
+    const cudaError_t e = cudaFreeAsync(b->block, (cudaStream_t)stream);
+    delete b;
+    return e == cudaSuccess ? FTLM_OK : cuda_fail(e, "cudaFreeAsync(tables)");
 }
 
 extern "C" ftlm_status ftlm_basis_dim(const ftlm_basis *b, uint64_t *dim)
@@ -483,6 +514,7 @@ extern "C" ftlm_status ftlm_basis_labels(const ftlm_basis *b, uint64_t first, ui
     if (!labels_dev) return fail(FTLM_EINVAL, "labels_dev is NULL");
     labels_kernel<<<grid_for(count, 256, b->num_sms), 256, 0, (cudaStream_t)stream>>>(
         b->tables(), b->mode == FTLM_RANK_CLT, first, count, labels_dev);
+    note_launch();
     FTLM_CUDA(cudaGetLastError());
     return FTLM_OK;
 }
@@ -495,6 +527,7 @@ extern "C" ftlm_status ftlm_basis_rank(const ftlm_basis *b, uint64_t count, cons
     if (!labels_dev || !index_dev) return fail(FTLM_EINVAL, "NULL device pointer");
     rank_kernel<<<grid_for(count, 256, b->num_sms), 256, 0, (cudaStream_t)stream>>>(
         b->tables(), b->mode == FTLM_RANK_CLT, count, labels_dev, index_dev);
+    note_launch();
     FTLM_CUDA(cudaGetLastError());
     return FTLM_OK;
 }
@@ -507,6 +540,7 @@ extern "C" ftlm_status ftlm_basis_clt(const ftlm_basis *b, uint32_t *mask_dev, u
     if (!mask_dev || !prefix_dev) return fail(FTLM_EINVAL, "NULL device pointer");
     clt_split_kernel<<<grid_for(b->nblocks, 256, b->num_sms), 256, 0, (cudaStream_t)stream>>>(
         b->clt, b->nblocks, mask_dev, prefix_dev);
+    note_launch();
     FTLM_CUDA(cudaGetLastError());
     return FTLM_OK;
 }

@@ -2,7 +2,9 @@
 //
 // A batch lists sectors (of one or many clusters) with R chains each.  Sectors of
 // dimension above kSmallRows run through the grid-wide launch sequence of
-// ftlm_lanczos, one after the other.  All smaller sectors are cut into work units
+// ftlm_lanczos on up to kMaxSideStreams side streams forked from the caller's
+// stream (longest work first, each to the least-loaded stream), so mid-sized
+// sectors, whose launches fill only part of the GPU, overlap.  All smaller sectors are cut into work units
 // of B chains and handed to ONE persistent launch: each CTA takes the next unit
 // from an atomic counter (no waiting on other CTAs) and runs the unit's whole
 // chains by itself -- start vectors, min(M, D) steps of fused H.v + Lanczos
@@ -16,6 +18,7 @@
 // ftlm_batch_create; ftlm_batch_run only issues memsets and kernel launches, so the
 // whole run can be captured in a CUDA graph and replayed.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -32,6 +35,19 @@ namespace {
 
 constexpr int kBatchThreads = 256;
 constexpr uint64_t kSmallRows = 1u << 15;  // sectors up to this dimension run inside one CTA
+constexpr int kMaxSideStreams = 8;
+
+// Default number of side streams for the large items: FTLM_BATCH_STREAMS (1..8)
+// or 4.
+int side_streams()
+{
+    static const int n = [] {
+        const char *v = std::getenv("FTLM_BATCH_STREAMS");
+        const int k = v ? std::atoi(v) : 4;
+        return std::max(1, std::min(kMaxSideStreams, k));
+    }();
+    return n;
+}
 
 struct BatchItemDev {
     SectorTables s;
@@ -298,17 +314,39 @@ struct ftlm_batch {
     int group_grid[3];
     int n_slots;
     uint64_t slot_elems;        // D_max * B of the small items
-    // device descriptors (owned)
+    // device descriptors (owned): one pooled block holding the three arrays
+    void *desc_block;
     BatchItemDev *d_items;
     BatchUnitDev *d_units;
     ScatterDev *d_scatter;
     // workspace layout
     uint64_t off_queue, off_slots, off_alpha, off_beta, off_meff, off_theta, off_weight, off_large, total;
-    uint64_t large_bytes;
+    uint64_t large_bytes;       // workspace of one large item (the largest)
+    // large items run on side streams forked from the caller's stream, each with
+    // its own workspace region; large_side[k] is the side stream of large[k]
+    int n_side;
+    cudaStream_t side[kMaxSideStreams];
+    cudaEvent_t ev_fork, ev_join[kMaxSideStreams];
+    std::vector<int> large_side;
 };
 
+namespace {
+
+void release_host_objects(ftlm_batch *p)
+{
+    for (int k = 0; k < p->n_side; ++k) {
+        if (p->side[k]) cudaStreamDestroy(p->side[k]);
+        if (p->ev_join[k]) cudaEventDestroy(p->ev_join[k]);
+    }
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    delete p;
+}
+
+}  // namespace
+
 extern "C" ftlm_status ftlm_batch_create(int n, const ftlm_batch_item *items, int M, ftlm_vec_dist dist,
-                                         ftlm_dtype dtype, int block, void *stream_, ftlm_batch **out)
+                                         ftlm_dtype dtype, int block, int streams, void *stream_,
+                                         ftlm_batch **out)
 {
     if (!out) return fail(FTLM_EINVAL, "out is NULL");
     *out = nullptr;
@@ -318,6 +356,8 @@ extern "C" ftlm_status ftlm_batch_create(int n, const ftlm_batch_item *items, in
     if (dist != FTLM_VEC_GAUSS && dist != FTLM_VEC_RADEMACHER) return fail(FTLM_EINVAL, "bad distribution");
     if (block == 0) block = dtype == FTLM_F32 ? 16 : 8;
     if (!valid_block(block)) return fail(FTLM_EINVAL, "block width must be 0, 1, 4, 8 or 16");
+    if (streams < 0 || streams > kMaxSideStreams) return fail(FTLM_EINVAL, "streams must be 0..8");
+    if (streams == 0) streams = side_streams();
     for (int i = 0; i < n; ++i) {
         const ftlm_batch_item &it = items[i];
         if (!it.basis || it.R < 1 || it.first_chain < 0) return fail(FTLM_EINVAL, "bad batch item");
@@ -344,7 +384,7 @@ extern "C" ftlm_status ftlm_batch_create(int n, const ftlm_batch_item *items, in
         num_sms = b->num_sms;
         if (b->D > kSmallRows) {
             p->large.push_back(i);
-            large_bytes = std::max<uint64_t>(large_bytes, lanczos_workspace(b, items[i].R, M, dtype));
+            large_bytes = std::max<uint64_t>(large_bytes, lanczos_workspace(b, items[i].R, M, dtype, B));
             continue;
         }
         BatchItemDev d{};
@@ -418,35 +458,68 @@ extern "C" ftlm_status ftlm_batch_create(int n, const ftlm_batch_item *items, in
     off += align256(cm);
     p->off_meff = off;
     off += align256((uint64_t)p->n_small_chains * sizeof(int));
+    // Large items: longest-processing-time assignment to the side streams (the
+    // work of a sector's chains grows with D), so they overlap one another and the
+    // persistent kernel of the small items.
+    p->n_side = (int)std::min<size_t>(p->large.size(), (size_t)streams);
+    if (p->n_side) {
+        std::vector<int> order(p->large.size());
+        for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            return items[p->large[a]].basis->D * (uint64_t)items[p->large[a]].R >
+                   items[p->large[b]].basis->D * (uint64_t)items[p->large[b]].R;
+        });
+        std::vector<uint64_t> load(p->n_side, 0);
+        p->large_side.assign(p->large.size(), 0);
+        for (int k : order) {
+            const int sidx = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            p->large_side[k] = sidx;
+            load[sidx] += items[p->large[k]].basis->D * (uint64_t)items[p->large[k]].R;
+        }
+    }
+    large_bytes = align256(large_bytes);
     p->off_large = off;
-    off += align256(large_bytes);
+    off += large_bytes * (uint64_t)std::max(1, p->n_side);
     p->large_bytes = large_bytes;
     p->total = off;
 
-    // descriptors to the device
+    // descriptors to the device: one pooled block, one copy
     cudaStream_t stream = (cudaStream_t)stream_;
-    auto upload = [&](void **dst, const void *src, size_t bytes) -> cudaError_t {
-        if (bytes == 0) return cudaSuccess;
-        cudaError_t e = cudaMalloc(dst, bytes);
-        if (e == cudaSuccess) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
-        return e;
-    };
-    cudaError_t e = upload((void **)&p->d_items, hitems.data(), hitems.size() * sizeof(BatchItemDev));
-    if (e == cudaSuccess) e = upload((void **)&p->d_units, units.data(), units.size() * sizeof(BatchUnitDev));
-    if (e == cudaSuccess) e = upload((void **)&p->d_scatter, scatter.data(), scatter.size() * sizeof(ScatterDev));
+    const uint64_t o_items = 0;
+    const uint64_t o_units = align256(o_items + hitems.size() * sizeof(BatchItemDev));
+    const uint64_t o_scatter = align256(o_units + units.size() * sizeof(BatchUnitDev));
+    const uint64_t desc_bytes = std::max<uint64_t>(256, align256(o_scatter + scatter.size() * sizeof(ScatterDev)));
+    std::vector<unsigned char> image(desc_bytes, 0);
+    if (!hitems.empty()) std::memcpy(image.data() + o_items, hitems.data(), hitems.size() * sizeof(BatchItemDev));
+    if (!units.empty()) std::memcpy(image.data() + o_units, units.data(), units.size() * sizeof(BatchUnitDev));
+    if (!scatter.empty())
+        std::memcpy(image.data() + o_scatter, scatter.data(), scatter.size() * sizeof(ScatterDev));
+    int device = 0;
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = cudaGetDevice(&device);
+    if (e == cudaSuccess) e = table_pool(device, &pool);
+    if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&p->desc_block, desc_bytes, pool, stream);
     if (e == cudaSuccess) {
-        for (int g = 0; g < 3 && e == cudaSuccess; ++g)
-            if (p->group_units[g])
-                e = cudaFuncSetAttribute(kernel_for(dtype, B, g), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+        char *base = static_cast<char *>(p->desc_block);
+        p->d_items = reinterpret_cast<BatchItemDev *>(base + o_items);
+        p->d_units = reinterpret_cast<BatchUnitDev *>(base + o_units);
+        p->d_scatter = reinterpret_cast<ScatterDev *>(base + o_scatter);
+        e = cudaMemcpyAsync(base, image.data(), desc_bytes, cudaMemcpyHostToDevice, stream);
     }
-    (void)stream;
+    for (int g = 0; g < 3 && e == cudaSuccess; ++g)
+        if (p->group_units[g])
+            e = cudaFuncSetAttribute(kernel_for(dtype, B, g), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess && p->n_side) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+    for (int k = 0; k < p->n_side && e == cudaSuccess; ++k) {
+        e = cudaStreamCreateWithFlags(&p->side[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_join[k], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) {
-        cudaFree(p->d_items);
-        cudaFree(p->d_units);
-        cudaFree(p->d_scatter);
-        delete p;
-        return cuda_fail(e, "batch descriptors");
+        if (p->desc_block) cudaFreeAsync(p->desc_block, stream);
+        release_host_objects(p);
+        return e == cudaErrorMemoryAllocation ? fail(FTLM_ENOMEM, "no device memory for the batch descriptors")
+                                              : cuda_fail(e, "batch descriptors");
     }
     *out = p;
     return FTLM_OK;
@@ -455,10 +528,17 @@ extern "C" ftlm_status ftlm_batch_create(int n, const ftlm_batch_item *items, in
 extern "C" void ftlm_batch_destroy(ftlm_batch *p)
 {
     if (!p) return;
-    cudaFree(p->d_items);
-    cudaFree(p->d_units);
-    cudaFree(p->d_scatter);
-    delete p;
+    cudaDeviceSynchronize();
+    cudaFreeAsync(p->desc_block, 0);
+    release_host_objects(p);
+}
+
+extern "C" ftlm_status ftlm_batch_destroy_async(ftlm_batch *p, void *stream)
+{
+    if (!p) return FTLM_OK;
+    const cudaError_t e = cudaFreeAsync(p->desc_block, (cudaStream_t)stream);
+    release_host_objects(p);  // stream and event destruction waits for their work
+    return e == cudaSuccess ? FTLM_OK : cuda_fail(e, "cudaFreeAsync(batch descriptors)");
 }
 
 extern "C" ftlm_status ftlm_batch_workspace_bytes(const ftlm_batch *p, uint64_t *bytes)
@@ -500,19 +580,93 @@ extern "C" ftlm_status ftlm_batch_run(const ftlm_batch *p, void *work_dev, uint6
                             (void *)&slot_elems, (void *)&Mi, (void *)&dist, (void *)&alpha, (void *)&beta,
                             (void *)&meff};
             FTLM_CUDA(cudaLaunchKernel(kern, dim3(p->group_grid[g]), dim3(kBatchThreads), args, smem, stream));
+            note_launch();
         }
         ftlm_status s = launch_ritz((int)p->n_small_chains, M, alpha, beta, meff, theta, weight, stream);
         if (s != FTLM_OK) return s;
         scatter_kernel<<<p->n_small_chains, 128, 0, stream>>>((int)p->n_small_chains, M, theta, weight, meff,
                                                               p->d_scatter);
+        note_launch();
         FTLM_CUDA(cudaGetLastError());
     }
-    for (int i : p->large) {
-        const ftlm_batch_item &it = p->items[i];
-        ftlm_status s = lanczos_run(it.basis, it.R, M, it.first_chain, it.seed, p->dist, nullptr, p->dtype,
-                                    ws + p->off_large, p->large_bytes, it.theta_dev, it.weight_dev, it.m_eff_dev,
-                                    nullptr, nullptr, stream);
-        if (s != FTLM_OK) return s;
+    if (p->n_side) {
+        FTLM_CUDA(cudaEventRecord(p->ev_fork, stream));
+        for (int k = 0; k < p->n_side; ++k) FTLM_CUDA(cudaStreamWaitEvent(p->side[k], p->ev_fork, 0));
+        for (size_t k = 0; k < p->large.size(); ++k) {
+            const ftlm_batch_item &it = p->items[p->large[k]];
+            const int sidx = p->large_side[k];
+            ftlm_status s = lanczos_run(it.basis, it.R, M, it.first_chain, it.seed, p->dist, nullptr, p->dtype,
+                                        ws + p->off_large + (uint64_t)sidx * p->large_bytes, p->large_bytes,
+                                        it.theta_dev, it.weight_dev, it.m_eff_dev, nullptr, nullptr, p->side[sidx],
+                                        p->B);
+            if (s != FTLM_OK) return s;
+        }
+        for (int k = 0; k < p->n_side; ++k) {
+            FTLM_CUDA(cudaEventRecord(p->ev_join[k], p->side[k]));
+            FTLM_CUDA(cudaStreamWaitEvent(stream, p->ev_join[k], 0));
+        }
     }
+    return FTLM_OK;
+}
+
+extern "C" ftlm_status ftlm_batch_autotune(int n, const ftlm_batch_item *items, int M, ftlm_vec_dist dist,
+                                           ftlm_dtype dtype, void *stream_, int *block_out, int *streams_out,
+                                           float *ms_out)
+{
+    if (!block_out || !streams_out) return fail(FTLM_EINVAL, "NULL output");
+    cudaStream_t stream = (cudaStream_t)stream_;
+    bool any_large = false;
+    for (int i = 0; i < n && items; ++i)
+        if (items[i].basis && items[i].basis->D > kSmallRows) any_large = true;
+    int device = 0;
+    cudaMemPool_t pool = nullptr;
+    FTLM_CUDA(cudaGetDevice(&device));
+    FTLM_CUDA(table_pool(device, &pool));
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    FTLM_CUDA(cudaEventCreate(&ev[0]));
+    FTLM_CUDA(cudaEventCreate(&ev[1]));
+    float best = -1.f;
+    int best_b = 0, best_s = 0;
+    ftlm_status st = FTLM_OK;
+    const int blocks[3] = {4, 8, 16};
+    const int streams_try[4] = {1, 2, 4, 8};
+    for (int bi = 0; bi < 3 && st == FTLM_OK; ++bi) {
+        for (int si = 0; si < (any_large ? 4 : 1) && st == FTLM_OK; ++si) {
+            ftlm_batch *p = nullptr;
+            st = ftlm_batch_create(n, items, M, dist, dtype, blocks[bi], streams_try[si], stream, &p);
+            if (st != FTLM_OK) break;
+            void *work = nullptr;
+            cudaError_t e = cudaMallocFromPoolAsync(&work, p->total, pool, stream);
+            if (e != cudaSuccess) {
+                ftlm_batch_destroy_async(p, stream);
+                st = e == cudaErrorMemoryAllocation ? fail(FTLM_ENOMEM, "no device memory for a tuning run")
+                                                    : cuda_fail(e, "cudaMallocFromPoolAsync(tuning workspace)");
+                break;
+            }
+            // one untimed run, then one timed run
+            st = ftlm_batch_run(p, work, p->total, stream);
+            if (st == FTLM_OK && (e = cudaEventRecord(ev[0], stream)) != cudaSuccess) st = cuda_fail(e, "event");
+            if (st == FTLM_OK) st = ftlm_batch_run(p, work, p->total, stream);
+            if (st == FTLM_OK && (e = cudaEventRecord(ev[1], stream)) != cudaSuccess) st = cuda_fail(e, "event");
+            if (st == FTLM_OK && (e = cudaEventSynchronize(ev[1])) != cudaSuccess) st = cuda_fail(e, "tuning run");
+            float ms = 0.f;
+            if (st == FTLM_OK && (e = cudaEventElapsedTime(&ms, ev[0], ev[1])) != cudaSuccess)
+                st = cuda_fail(e, "cudaEventElapsedTime");
+            cudaFreeAsync(work, stream);
+            ftlm_batch_destroy_async(p, stream);
+            if (st != FTLM_OK) break;
+            if (ms_out) ms_out[bi * 4 + si] = ms;
+            if (best < 0.f || ms < best) {
+                best = ms;
+                best_b = blocks[bi];
+                best_s = streams_try[si];
+            }
+        }
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (st != FTLM_OK) return st;
+    *block_out = best_b;
+    *streams_out = best_s;
     return FTLM_OK;
 }

@@ -93,6 +93,7 @@ struct ftlm_basis {
     int device, num_sms;
     ftlm::BondList bonds_cr;
     ftlm::BondList bonds_clt;
+    void *block;        // one pooled device allocation holding every table below
     uint4 *bond_slots;  // device: cr f32, cr f64, clt f32, clt f64 (kMaxBondSlots each)
     uint32_t ulo_off[ftlm::kLoBitsMax + 2];
     uint32_t *thi;
@@ -117,6 +118,16 @@ ftlm_status cuda_fail(cudaError_t e, const char *what);
         cudaError_t e_ = (call);                          \
         if (e_ != cudaSuccess) return ftlm::cuda_fail(e_, #call); \
     } while (0)
+
+// ---- device memory for tables and descriptors (api.cu) ----------------------
+// A stream-ordered pool per device: creating and releasing sector tables and batch
+// descriptors then neither synchronizes the device nor returns memory to the
+// driver at every release (the pool keeps up to kPoolKeepBytes cached).
+constexpr uint64_t kPoolKeepBytes = 4ull << 30;
+cudaError_t table_pool(int device, cudaMemPool_t *pool);
+
+// ---- launch count (api.cu): every kernel the library queues calls this once ----
+void note_launch();
 
 // ---- kernel timing (api.cu) ----------------------------------------------
 enum ProfileKind { kProfHv = 0, kProfUpdate = 1 };
@@ -149,8 +160,9 @@ bool valid_block(int B);
 // Lanczos chains of one sector (lanczos.cu): chain r is keyed as chain chain0 + r.
 ftlm_status lanczos_run(const ftlm_basis *b, int R, int M, int chain0, uint64_t seed, int dist, const double *src,
                         ftlm_dtype dtype, void *work, uint64_t work_bytes, double *theta, double *weight,
-                        int *m_eff, double *alpha_dev, double *beta_dev, cudaStream_t stream);
-uint64_t lanczos_workspace(const ftlm_basis *b, int R, int M, ftlm_dtype dtype);
+                        int *m_eff, double *alpha_dev, double *beta_dev, cudaStream_t stream, int bmax = 0);
+// bmax: widest block of chains (0: the process-wide setting).
+uint64_t lanczos_workspace(const ftlm_basis *b, int R, int M, ftlm_dtype dtype, int bmax = 0);
 // Ritz step of n chains (alpha/beta rows of length M, m_eff per chain).
 ftlm_status launch_ritz(int n, int M, const double *alpha, const double *beta, const int *mv, double *theta,
                         double *weight, cudaStream_t stream);

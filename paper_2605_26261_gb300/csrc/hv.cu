@@ -69,9 +69,14 @@ struct EpiDev {
 // blocks of 4-8 vectors get at least 3 CTAs per SM (fewer starve the loads), 2 with
 // 8-bond chunks of 8-wide blocks (their 16 gathers per row in flight carry it);
 // 16-wide blocks keep all their registers (a cap spills).
+// Resident CTAs per SM the register budget is cut for (build option
+// FTLM_B8_MIN_CTAS for the 8-wide blocks with chunks of 4 bonds).
+#ifndef FTLM_B8_MIN_CTAS
+#define FTLM_B8_MIN_CTAS 3
+#endif
 template <int RT, int B, int C> __host__ __device__ constexpr int min_ctas()
 {
-    return B >= 16 ? 1 : (B >= 8 && C >= 8 ? 2 : (B >= 4 || RT >= 4 ? 3 : 6));
+    return B >= 16 ? 1 : (B >= 8 && C >= 8 ? 2 : (B >= 8 ? FTLM_B8_MIN_CTAS : (B >= 4 || RT >= 4 ? 3 : 6)));
 }
 
 template <typename V, typename Lbl, bool CLT, bool LANCZOS, int RT, int B, int C>
@@ -223,6 +228,7 @@ ftlm_status launch(const ftlm_basis *b, const V *x, V *y, const EpiDev &ep, cuda
     const int grid = row_grid(b, (b->D + RT - 1) / RT, std::min(occ, hv_cta_cap()));
     void *tok = profile_begin(kProfHv, stream, B);
     kern<<<grid, kRowThreads, smem, stream>>>(b->tables(), CLT ? b->bonds_clt : b->bonds_cr, x, y, ep);
+    note_launch();
     profile_end(tok, stream);
     FTLM_CUDA(cudaGetLastError());
     return FTLM_OK;
@@ -300,13 +306,18 @@ ftlm_status launch_hv(const ftlm_basis *b, ftlm_dtype dtype, int B, const void *
 }  // namespace ftlm
 
 namespace {
-ftlm_status check_hv_args(const ftlm_basis *b, ftlm_dtype dtype, const void *x_dev, void *y_dev)
+ftlm_status check_hv_args(const ftlm_basis *b, ftlm_dtype dtype, int B, const void *x_dev, void *y_dev)
 {
     if (!b) return ftlm::fail(FTLM_EINVAL, "NULL basis");
     if (dtype != FTLM_F32 && dtype != FTLM_F64) return ftlm::fail(FTLM_EINVAL, "bad dtype");
     if (!x_dev || !y_dev) return ftlm::fail(FTLM_EINVAL, "NULL vector");
     if (x_dev == y_dev) return ftlm::fail(FTLM_EINVAL, "x and y must not overlap");
-    if (((uintptr_t)x_dev | (uintptr_t)y_dev) & 15u) return ftlm::fail(FTLM_EINVAL, "vectors must be 16-byte aligned");
+    // rows of 32 bytes or more move as 32-byte transactions
+    const unsigned row = (unsigned)B * (dtype == FTLM_F32 ? 4u : 8u);
+    const uintptr_t mask = row >= 32 ? 31u : 15u;
+    if (((uintptr_t)x_dev | (uintptr_t)y_dev) & mask)
+        return ftlm::fail(FTLM_EINVAL, row >= 32 ? "vectors must be 32-byte aligned for rows of 32 bytes or more"
+                                                 : "vectors must be 16-byte aligned");
     return FTLM_OK;
 }
 }  // namespace
@@ -314,7 +325,7 @@ ftlm_status check_hv_args(const ftlm_basis *b, ftlm_dtype dtype, const void *x_d
 extern "C" ftlm_status ftlm_hv(const ftlm_basis *b, ftlm_dtype dtype, const void *x_dev, void *y_dev,
                                void *stream)
 {
-    ftlm_status s = check_hv_args(b, dtype, x_dev, y_dev);
+    ftlm_status s = check_hv_args(b, dtype, 1, x_dev, y_dev);
     if (s != FTLM_OK) return s;
     return ftlm::launch_hv(b, dtype, 1, x_dev, y_dev, nullptr, (cudaStream_t)stream);
 }
@@ -322,8 +333,8 @@ extern "C" ftlm_status ftlm_hv(const ftlm_basis *b, ftlm_dtype dtype, const void
 extern "C" ftlm_status ftlm_hv_block(const ftlm_basis *b, ftlm_dtype dtype, int B, const void *x_dev,
                                      void *y_dev, void *stream)
 {
-    ftlm_status s = check_hv_args(b, dtype, x_dev, y_dev);
-    if (s != FTLM_OK) return s;
     if (!ftlm::valid_block(B)) return ftlm::fail(FTLM_EINVAL, "block width must be 1, 4, 8 or 16");
+    ftlm_status s = check_hv_args(b, dtype, B, x_dev, y_dev);
+    if (s != FTLM_OK) return s;
     return ftlm::launch_hv(b, dtype, B, x_dev, y_dev, nullptr, (cudaStream_t)stream);
 }

@@ -13,6 +13,7 @@
 // the rest of its launches into no-ops.
 #include <cmath>
 #include <cstdlib>
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -305,6 +306,7 @@ ftlm_status launch_ritz(int n, int M, const double *alpha, const double *beta, c
     if (T > n) T = n;
     const int grid = (n + T - 1) / T;
     ritz_kernel<<<grid, T, per_chain * T, stream>>>(n, M, alpha, beta, mv, theta, weight);
+    note_launch();
     FTLM_CUDA(cudaGetLastError());
     return FTLM_OK;
 }
@@ -314,8 +316,10 @@ namespace {
 // ---- workspace and block plan -------------------------------------------
 uint64_t align256(uint64_t v) { return (v + 255) & ~255ull; }
 
-// Widest block of chains: 8 vectors (FP32) or 4 (FP64) unless FTLM_BLOCK (1, 4, 8
-// or 16) says otherwise.
+// Widest block of chains: the width set by ftlm_lanczos_set_block, else FTLM_BLOCK
+// (1, 4, 8 or 16), else 8 vectors (FP32) or 4 (FP64).
+std::atomic<int> g_block_width{0};
+
 int max_block(ftlm_dtype dtype)
 {
     static const int over = [] {
@@ -323,14 +327,16 @@ int max_block(ftlm_dtype dtype)
         const int v = e ? atoi(e) : 0;
         return valid_block(v) ? v : 0;
     }();
+    const int set = g_block_width.load(std::memory_order_relaxed);
+    if (set) return set;
     return over ? over : (dtype == FTLM_F32 ? 8 : 4);
 }
 
 // Split R chains into blocks: the widest allowed width in {16, 8, 4} that fits the
-// chains left, then single chains for fewer than 4.
-std::vector<int> block_plan(int R, ftlm_dtype dtype)
+// chains left, then single chains for fewer than 4.  bmax = 0: max_block(dtype).
+std::vector<int> block_plan(int R, ftlm_dtype dtype, int bmax)
 {
-    const int bmax = max_block(dtype);
+    if (!bmax) bmax = max_block(dtype);
     std::vector<int> plan;
     int left = R;
     for (int w : {16, 8, 4}) {
@@ -349,11 +355,11 @@ struct Layout {
     uint64_t vec0, vec1, partials, state, alpha, beta, meff, total;
 };
 
-Layout layout(const ftlm_basis *b, int R, int M, ftlm_dtype dtype)
+Layout layout(const ftlm_basis *b, int R, int M, ftlm_dtype dtype, int bmax = 0)
 {
     Layout l;
     l.bw = 1;
-    for (int w : block_plan(R, dtype)) l.bw = w > l.bw ? w : l.bw;
+    for (int w : block_plan(R, dtype, bmax)) l.bw = w > l.bw ? w : l.bw;
     const uint64_t vb = align256(b->D * (uint64_t)l.bw * (dtype == FTLM_F32 ? 4ull : 8ull));
     l.vec0 = 0;
     l.vec1 = vb;
@@ -401,6 +407,7 @@ ftlm_status run_block(const ftlm_basis *b, int M, int r0, int chain0, uint64_t s
     for (int r = 0; r < B; ++r) keys.k[r] = chain_key(seed, b->N, b->K, (uint32_t)(chain0 + r0 + r));
     start_kernel<V, B><<<g_start, kRowThreads, 0, stream>>>(D, keys, dist, src ? src + (size_t)r0 * D : nullptr,
                                                            vec[0], st, partials, counter);
+    note_launch();
     FTLM_CUDA(cudaGetLastError());
     int cur = 0;
     for (int j = 1; j <= m_max; ++j) {
@@ -410,18 +417,20 @@ ftlm_status run_block(const ftlm_basis *b, int M, int r0, int chain0, uint64_t s
         void *tok = profile_begin(kProfUpdate, stream);
         update_kernel<V, B><<<g_upd, kRowThreads, 0, stream>>>(D, vec[1 - cur], vec[cur], st, partials, counter, j,
                                                                m_max, tau, beta_ws + (size_t)r0 * M, M);
+        note_launch();
         profile_end(tok, stream);
         FTLM_CUDA(cudaGetLastError());
         cur = 1 - cur;
     }
     copy_meff_kernel<<<1, 32, 0, stream>>>(st, B, meff_ws + r0);
+    note_launch();
     FTLM_CUDA(cudaGetLastError());
     return FTLM_OK;
 }
 
 template <typename V>
 ftlm_status run_chains(const ftlm_basis *b, int R, int M, int chain0, uint64_t seed, int dist, const double *src,
-                       ftlm_dtype dtype, char *ws, const Layout &lay, double *theta, double *weight,
+                       ftlm_dtype dtype, int bmax, char *ws, const Layout &lay, double *theta, double *weight,
                        int *m_eff, double *alpha_dev, double *beta_dev, cudaStream_t stream)
 {
     double *alpha_ws = (double *)(ws + lay.alpha);
@@ -430,7 +439,7 @@ ftlm_status run_chains(const ftlm_basis *b, int R, int M, int chain0, uint64_t s
     FTLM_CUDA(cudaMemsetAsync(alpha_ws, 0, (size_t)R * M * sizeof(double), stream));
     FTLM_CUDA(cudaMemsetAsync(beta_ws, 0, (size_t)R * M * sizeof(double), stream));
     int r0 = 0;
-    for (int B : block_plan(R, dtype)) {
+    for (int B : block_plan(R, dtype, bmax)) {
         ftlm_status s;
         switch (B) {
         case 16: s = run_block<V, 16>(b, M, r0, chain0, seed, dist, src, dtype, ws, lay, stream); break;
@@ -455,25 +464,30 @@ ftlm_status run_chains(const ftlm_basis *b, int R, int M, int chain0, uint64_t s
 
 ftlm_status lanczos_run(const ftlm_basis *b, int R, int M, int chain0, uint64_t seed, int dist, const double *src,
                         ftlm_dtype dtype, void *work, uint64_t work_bytes, double *theta, double *weight,
-                        int *m_eff, double *alpha_dev, double *beta_dev, cudaStream_t stream)
+                        int *m_eff, double *alpha_dev, double *beta_dev, cudaStream_t stream, int bmax)
 {
     if (!b) return fail(FTLM_EINVAL, "NULL basis");
     if (R < 1) return fail(FTLM_EINVAL, "R < 1");
+    if (bmax && !valid_block(bmax)) return fail(FTLM_EINVAL, "block width must be 1, 4, 8 or 16");
+    if (!bmax) bmax = max_block(dtype);
     if (M < 1 || M > FTLM_MAX_LANCZOS) return fail(FTLM_EINVAL, "M out of range");
     if (dtype != FTLM_F32 && dtype != FTLM_F64) return fail(FTLM_EINVAL, "bad dtype");
     if (dist != FTLM_VEC_GAUSS && dist != FTLM_VEC_RADEMACHER) return fail(FTLM_EINVAL, "bad distribution");
     if (!theta || !weight || !m_eff) return fail(FTLM_EINVAL, "NULL output");
     if (!work || ((uintptr_t)work & 255u)) return fail(FTLM_EINVAL, "workspace NULL or not 256-byte aligned");
-    const Layout lay = layout(b, R, M, dtype);
+    const Layout lay = layout(b, R, M, dtype, bmax);
     if (work_bytes < lay.total) return fail(FTLM_ENOMEM, "workspace smaller than ftlm_lanczos_workspace_bytes()");
     return dtype == FTLM_F32
-               ? run_chains<float>(b, R, M, chain0, seed, dist, src, dtype, (char *)work, lay, theta, weight,
+               ? run_chains<float>(b, R, M, chain0, seed, dist, src, dtype, bmax, (char *)work, lay, theta, weight,
                                    m_eff, alpha_dev, beta_dev, stream)
-               : run_chains<double>(b, R, M, chain0, seed, dist, src, dtype, (char *)work, lay, theta, weight,
+               : run_chains<double>(b, R, M, chain0, seed, dist, src, dtype, bmax, (char *)work, lay, theta, weight,
                                     m_eff, alpha_dev, beta_dev, stream);
 }
 
-uint64_t lanczos_workspace(const ftlm_basis *b, int R, int M, ftlm_dtype dtype) { return layout(b, R, M, dtype).total; }
+uint64_t lanczos_workspace(const ftlm_basis *b, int R, int M, ftlm_dtype dtype, int bmax)
+{
+    return layout(b, R, M, dtype, bmax).total;
+}
 
 namespace {
 
@@ -526,6 +540,13 @@ extern "C" ftlm_status ftlm_lanczos_noalloc(const ftlm_basis *b, int R, int M, u
     if (s != FTLM_OK) return s;
     return lanczos_run(b, R, M, 0, seed, dist, nullptr, dtype, scratch, FTLM_NOALLOC_SCRATCH_BYTES, theta_dev,
                        weight_dev, m_eff_dev, alpha_dev, beta_dev, (cudaStream_t)stream);
+}
+
+extern "C" ftlm_status ftlm_lanczos_set_block(int width)
+{
+    if (width != 0 && !valid_block(width)) return fail(FTLM_EINVAL, "block width must be 0, 1, 4, 8 or 16");
+    g_block_width.store(width, std::memory_order_relaxed);
+    return FTLM_OK;
 }
 
 extern "C" ftlm_status ftlm_lanczos_workspace_bytes(const ftlm_basis *b, int R, int M, ftlm_dtype dtype,

@@ -156,6 +156,7 @@ extern "C" ftlm_status ftlm_thermo(int n_sectors, const int *two_sz, const uint6
     }
     if (nT == 0) return FTLM_OK;
     thermo_kernel<<<nT, kThermoThreads, 0, (cudaStream_t)stream>>>(a, T_dev, E_dev, C_dev, chi_dev, mag_dev);
+    note_launch();
     FTLM_CUDA(cudaGetLastError());
     return FTLM_OK;
 }

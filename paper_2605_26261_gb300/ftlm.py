@@ -74,10 +74,15 @@ def lib():
         "ftlm_lanczos_noalloc": [P, I, I, U64, I, I, P, P, P, P, P, P],
         "ftlm_ritz": [I, I, P, P, P, P, P, P],
         "ftlm_thermo": [I, P, P, I, I, P, P, P, I, D, D, I, P, P, P, P, P, P],
-        "ftlm_batch_create": [I, P, I, I, I, I, P, ctypes.POINTER(P)],
+        "ftlm_batch_create": [I, P, I, I, I, I, I, P, ctypes.POINTER(P)],
+        "ftlm_lanczos_set_block": [I],
+        "ftlm_batch_autotune": [I, P, I, I, I, P, ctypes.POINTER(I), ctypes.POINTER(I), P],
         "ftlm_batch_workspace_bytes": [P, PU64],
         "ftlm_batch_run": [P, P, U64, P],
+        "ftlm_basis_destroy_async": [P, P],
+        "ftlm_batch_destroy_async": [P, P],
         "ftlm_profile_enable": [I],
+        "ftlm_launch_count": [PU64],
         "ftlm_profile_read": [PU64, PU64, PD, PU64, PD],
     }
     for name, args in sig.items():
@@ -146,6 +151,10 @@ def ftlm_basis_create(N, two_sz, bi, bj, J, mode=RANK_AUTO, stream=None):
 
 def ftlm_basis_destroy(handle):
     lib().ftlm_basis_destroy(handle)
+
+
+def ftlm_basis_destroy_async(handle, stream=None):
+    _check(lib().ftlm_basis_destroy_async(handle, _stream(stream)))
 
 
 def _u64_query(fn, handle):
@@ -233,6 +242,10 @@ def ftlm_lanczos_noalloc(handle, R, M, seed, dist, dtype, theta, weight, m_eff, 
                                       _ptr(alpha), _ptr(beta), _stream(stream)))
 
 
+def ftlm_lanczos_set_block(width):
+    _check(lib().ftlm_lanczos_set_block(int(width)))
+
+
 def ftlm_ritz(n, M, alpha, beta, m, theta, weight, stream=None):
     _check(lib().ftlm_ritz(int(n), int(M), _ptr(alpha), _ptr(beta), _ptr(m), _ptr(theta),
                            _ptr(weight), _stream(stream)))
@@ -251,13 +264,26 @@ def ftlm_thermo(two_sz, dims, R, M, thetas, weights, m_effs, mirror_neg, g, h, T
                              _stream(stream)))
 
 
-def ftlm_batch_create(items, M, dist, dtype, block=0, stream=None):
+def ftlm_batch_create(items, M, dist, dtype, block=0, streams=0, stream=None):
     """items: sequence of BatchItem; returns the batch handle."""
     arr = (BatchItem * len(items))(*items)
     out = ctypes.c_void_p()
     _check(lib().ftlm_batch_create(len(items), arr, int(M), int(dist), _dtype_code(dtype), int(block),
-                                   _stream(stream), ctypes.byref(out)))
+                                   int(streams), _stream(stream), ctypes.byref(out)))
     return out
+
+
+def ftlm_batch_autotune(items, M, dist, dtype, stream=None):
+    """Returns (block, streams, times) with times[(block, streams)] = ms of the
+    timed run of each candidate."""
+    arr = (BatchItem * len(items))(*items)
+    b, s = ctypes.c_int(), ctypes.c_int()
+    ms = (ctypes.c_float * 12)(*([-1.0] * 12))
+    _check(lib().ftlm_batch_autotune(len(items), arr, int(M), int(dist), _dtype_code(dtype), _stream(stream),
+                                     ctypes.byref(b), ctypes.byref(s), ms))
+    times = {(blk, st): ms[i * 4 + j] for i, blk in enumerate((4, 8, 16)) for j, st in enumerate((1, 2, 4, 8))
+             if ms[i * 4 + j] >= 0}
+    return b.value, s.value, times
 
 
 def ftlm_batch_workspace_bytes(handle):
@@ -270,6 +296,14 @@ def ftlm_batch_run(handle, work, stream=None):
 
 def ftlm_batch_destroy(handle):
     lib().ftlm_batch_destroy(handle)
+
+
+def ftlm_batch_destroy_async(handle, stream=None):
+    _check(lib().ftlm_batch_destroy_async(handle, _stream(stream)))
+
+
+def ftlm_launch_count():
+    return _u64_query(lambda h, p: lib().ftlm_launch_count(p), None)
 
 
 def ftlm_profile_enable(on=True):
@@ -303,6 +337,13 @@ class Basis:
         if self.handle is not None:
             ftlm_basis_destroy(self.handle)
             self.handle = None
+
+    def release(self, stream=None):
+        """Release without waiting: the tables return to the library's pool in the
+        order of `stream` (all work that reads them must precede that point)."""
+        if self.handle is not None:
+            h, self.handle = self.handle, None
+            ftlm_basis_destroy_async(h, stream)
 
     def __enter__(self):
         return self
@@ -353,35 +394,63 @@ def thermo(sectors, T, R, M, g=2.0, h=0.0, mirror=True, stream=None):
     return out
 
 
+def _batch_items(entries, M, dev):
+    results, items = [], []
+    for basis, R, seed, first_chain in entries:
+        out = {"theta": torch.zeros((R, M), dtype=torch.float64, device=dev),
+               "weight": torch.zeros((R, M), dtype=torch.float64, device=dev),
+               "m_eff": torch.zeros(R, dtype=torch.int32, device=dev)}
+        results.append(out)
+        items.append(BatchItem(basis.handle.value, int(R), int(first_chain), int(seed) & (2**64 - 1),
+                               out["theta"].data_ptr(), out["weight"].data_ptr(), out["m_eff"].data_ptr()))
+    return results, items
+
+
+def autotune(entries, M, dist=GAUSS, dtype=torch.float32, stream=None):
+    """ftlm_batch_autotune on the (basis, R, seed, first_chain) entries (outputs in
+    scratch tensors); returns (block, streams, times)."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    results, items = _batch_items(entries, M, dev)
+    out = ftlm_batch_autotune(items, M, dist, dtype, stream)
+    del results
+    return out
+
+
 class Batch:
     """Many sectors in one batch (ftlm_batch_*): chains of every (basis, R, seed,
     first_chain) entry; outputs per entry as device tensors theta, weight (R x M)
     and m_eff (R)."""
 
-    def __init__(self, entries, M, dist=GAUSS, dtype=torch.float32, block=0, stream=None):
-        dev = torch.device("cuda", torch.cuda.current_device())
+    def __init__(self, entries, M, dist=GAUSS, dtype=torch.float32, block=0, streams=0, stream=None, lazy=False):
+        self.dev = torch.device("cuda", torch.cuda.current_device())
         self.M = int(M)
-        self.results = []
-        items = []
-        for basis, R, seed, first_chain in entries:
-            out = {"theta": torch.zeros((R, M), dtype=torch.float64, device=dev),
-                   "weight": torch.zeros((R, M), dtype=torch.float64, device=dev),
-                   "m_eff": torch.zeros(R, dtype=torch.int32, device=dev)}
-            self.results.append(out)
-            items.append(BatchItem(basis.handle.value, int(R), int(first_chain), int(seed) & (2**64 - 1),
-                                   out["theta"].data_ptr(), out["weight"].data_ptr(), out["m_eff"].data_ptr()))
-        self.handle = ftlm_batch_create(items, M, dist, dtype, block, stream)
-        nbytes = ftlm_batch_workspace_bytes(self.handle)
-        self.work = torch.empty((nbytes + 255) // 256 * 256, dtype=torch.uint8, device=dev)
+        self.results, items = _batch_items(entries, M, self.dev)
+        self.handle = ftlm_batch_create(items, M, dist, dtype, block, streams, stream)
+        self.workspace_bytes = (ftlm_batch_workspace_bytes(self.handle) + 255) // 256 * 256
+        self.work = None
+        if not lazy:
+            self.alloc()
+
+    def alloc(self):
+        """The workspace (torch memory on the current stream), allocated on first use."""
+        if self.work is None:
+            self.work = torch.empty(self.workspace_bytes, dtype=torch.uint8, device=self.dev)
+        return self.work
 
     def run(self, stream=None):
-        ftlm_batch_run(self.handle, self.work, stream)
+        ftlm_batch_run(self.handle, self.alloc(), stream)
         return self.results
 
     def close(self):
         if self.handle is not None:
             ftlm_batch_destroy(self.handle)
             self.handle = None
+
+    def release(self, stream=None):
+        """Release without waiting, in the order of `stream` (see Basis.release)."""
+        if self.handle is not None:
+            h, self.handle = self.handle, None
+            ftlm_batch_destroy_async(h, stream)
 
     def __enter__(self):
         return self

@@ -152,6 +152,34 @@ def random_graph(N, seed, dmin=3, dmax=5, Jlo=0.5, Jhi=1.5, max_tries=100000):
     raise RuntimeError("no graph found")
 
 
+def cluster_set(n=256, seed=256, sizes=(18, 20, 22)):
+    """n independent clusters: N drawn uniformly from `sizes`, each a random_graph
+    (degrees 3-5, J ~ U[0.5, 1.5]) with its own seed; returns [(N, bonds)]."""
+    rng = np.random.default_rng(seed)
+    Ns = rng.choice(np.asarray(sizes), size=n)
+    return [(int(N), random_graph(int(N), seed=seed * 100_003 + c)) for c, N in enumerate(Ns)]
+
+
+def serving_requests(n, rate, seed=4, sizes=(16, 18, 20, 22, 24, 26)):
+    """n FTLM requests arriving as a Poisson process of `rate` per second: each a
+    ring or a two-leg ladder (equal odds) with N uniform in `sizes`, couplings
+    U[0.2, 1.5] (one J for the ring; J_rung and J_leg for the ladder) and field
+    h ~ U[0, 2].  Returns ([{"N", "bonds", "h", "kind"}], arrival seconds from 0)."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, size=n)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    reqs = []
+    for _ in range(n):
+        N = int(rng.choice(np.asarray(sizes)))
+        if rng.random() < 0.5:
+            reqs.append({"N": N, "bonds": ring(N, J=float(rng.uniform(0.2, 1.5))), "kind": "ring"})
+        else:
+            reqs.append({"N": N, "bonds": ladder(N, J_rung=float(rng.uniform(0.2, 1.5)),
+                                                 J_leg=float(rng.uniform(0.2, 1.5))), "kind": "ladder"})
+        reqs[-1]["h"] = float(rng.uniform(0.0, 2.0))
+    return reqs, arrivals
+
+
 def log_t_grid(n=200, lo=0.01, hi=10.0):
     """n log-spaced temperatures T_i = lo (hi/lo)^(i/(n-1)), both ends included."""
     return np.logspace(math.log10(lo), math.log10(hi), n)

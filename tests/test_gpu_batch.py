@@ -125,3 +125,88 @@ def test_batch_rejects_bad_items(cuda_dev):
             ftlm.Batch([(b, 0, 1, 0)], 10)
         with pytest.raises(ftlm.FtlmError):
             ftlm.Batch([(b, 2, 1, 0)], 10, block=3)
+
+
+def _large_batch_bases():
+    # three sectors above 32768 states (ring 18: K = 9, 10; random N = 19: K = 10)
+    # and two small ones, so the batch forks side streams and runs its persistent kernel
+    b18 = inputs.ring(18)
+    b19 = inputs.random_graph(19, seed=31)
+    return [ftlm.Basis(18, 0, b18), ftlm.Basis(18, 2, b18), ftlm.Basis(19, 1, b19),
+            ftlm.Basis(18, 8, b18), ftlm.Basis(19, 11, b19)]
+
+
+@pytest.mark.parametrize("block", [4, 16])
+def test_side_streams_do_not_change_results(cuda_dev, block):
+    # Large items run ftlm_lanczos's launch sequence with blocks of `block` chains on
+    # side streams: bit-identical for any number of side streams, and equal to
+    # ftlm_lanczos with the same block width on the caller's stream.
+    M, R = 25, 16
+    bases = _large_batch_bases()
+    entries = [(b, R, 40 + i, 0) for i, b in enumerate(bases)]
+    runs = []
+    for streams in (1, 3, 8):
+        with ftlm.Batch(entries, M, ftlm.GAUSS, torch.float32, block, streams) as batch:
+            runs.append([{k: v.clone() for k, v in r.items()} for r in batch.run()])
+            torch.cuda.synchronize()
+    for other in runs[1:]:
+        for a, b in zip(runs[0], other):
+            for k in ("theta", "weight", "m_eff"):
+                assert torch.equal(a[k], b[k]), k
+    ftlm.ftlm_lanczos_set_block(block)
+    try:
+        for i, b in enumerate(bases[:3]):  # the large items
+            ref = ftlm.lanczos(b, R, M, seed=40 + i, dist=ftlm.GAUSS, dtype=torch.float32)
+            torch.cuda.synchronize()
+            for k in ("theta", "weight", "m_eff"):
+                assert torch.equal(ref[k], runs[0][i][k]), (i, k)
+    finally:
+        ftlm.ftlm_lanczos_set_block(0)
+    for b in bases:
+        b.close()
+
+
+def test_graph_capture_with_side_streams(cuda_dev):
+    M, R = 20, 8
+    bases = _large_batch_bases()
+    with ftlm.Batch([(b, R, 3, 0) for b in bases], M, ftlm.RADEMACHER, torch.float32, 8, 3) as batch:
+        direct = [{k: v.clone() for k, v in r.items()} for r in batch.run()]
+        torch.cuda.synchronize()
+        for r in batch.results:
+            for v in r.values():
+                v.zero_()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            batch.run(stream=s)
+        for _ in range(2):
+            g.replay()
+        torch.cuda.synchronize()
+        for a, b in zip(direct, batch.results):
+            for k in ("theta", "weight", "m_eff"):
+                assert torch.equal(a[k], b[k]), k
+    for b in bases:
+        b.close()
+
+
+def test_autotune_picks_a_timed_candidate(cuda_dev):
+    M, R = 15, 16
+    bases = _large_batch_bases()
+    entries = [(b, R, 1, 0) for b in bases]
+    block, streams, times = ftlm.autotune(entries, M, ftlm.GAUSS, torch.float32)
+    assert (block, streams) in times
+    assert len(times) == 12  # large items present: 3 widths x 4 stream counts
+    assert times[(block, streams)] == min(times.values())
+    # a plan with the tuned parameters runs and agrees with the default plan
+    with ftlm.Batch(entries, M, ftlm.GAUSS, torch.float32, block, streams) as tuned:
+        a = [{k: v.clone() for k, v in r.items()} for r in tuned.run()]
+    with ftlm.Batch(entries, M, ftlm.GAUSS, torch.float32, 16) as ref:
+        e = ref.run()
+        torch.cuda.synchronize()
+        for x, y in zip(a, e):
+            assert torch.equal(x["m_eff"], y["m_eff"])
+            np.testing.assert_allclose(spectral_sums(x["theta"], x["weight"], x["m_eff"]),
+                                       spectral_sums(y["theta"], y["weight"], y["m_eff"]), rtol=1e-5)
+    for b in bases:
+        b.close()
