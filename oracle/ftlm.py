@@ -62,6 +62,12 @@ def lib():
         L.or_lanczos.argtypes = [c_int, P, P, P, P, c_i64, P, P, c_int, c_dbl, P, P]
         L.or_num_threads.restype = c_int
         L.or_num_threads.argtypes = []
+        L.or_spin_basis_enumerate.restype = c_i64
+        L.or_spin_basis_enumerate.argtypes = [c_int, c_int, c_int, P, c_i64]
+        L.or_spin_hv_range.restype = None
+        L.or_spin_hv_range.argtypes = [c_int, c_int, c_int, P, P, P, P, c_i64, P, P, c_i64, c_i64]
+        L.or_spin_offdiag_terms.restype = c_i64
+        L.or_spin_offdiag_terms.argtypes = [c_int, c_int, c_int, P, P, P, c_i64]
         _lib = L
     return _lib
 

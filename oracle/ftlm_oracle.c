@@ -1,5 +1,6 @@
 /*
- * ftlm_oracle.c -- plain, slow, FP64 CPU oracle for the spin-1/2 FTLM hot path.
+ * ftlm_oracle.c -- plain, slow, FP64 CPU oracle for the FTLM hot path (spin 1/2,
+ * and general spin s in the or_spin_* routines at the end).
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or call
  * this file; only the test-suite, the smoke check and the benchmark's CPU
@@ -281,6 +282,96 @@ int or_lanczos(int nb, const int *bi, const int *bj, const double *J, const uint
     free(q);
     free(y);
     return m_eff;
+}
+
+/* ---- general local spin s (Sec. 2: Eq. 10-14 with d = 2s + 1 digits) -----------
+ * A label n = sum_k a_k d^k (Eq. 11) carries the shifted quantum numbers
+ * a_k = m_k + s in 0 .. 2s as base-d digits; the sector of total S^z = M holds
+ * the labels with digit sum A = N s + M (Eq. 17), in increasing label order.
+ * two_s = 2s >= 1; two_s = 1 is the spin-1/2 case above. */
+static uint64_t or_ipow(uint64_t d, int k)
+{
+    uint64_t p = 1;
+    for (int i = 0; i < k; ++i) p *= d;
+    return p;
+}
+
+/* k-th base-d digit of n: floor(n / d^k) mod d (Sec. 2, after Eq. 11). */
+static int or_spin_digit(uint64_t n, int d, int k) { return (int)((n / or_ipow((uint64_t)d, k)) % (uint64_t)d); }
+
+/* Sector basis for spin s: every label 0 <= n < d^N with digit sum A, ascending.
+ * Writes at most cap labels; returns the dimension. */
+int64_t or_spin_basis_enumerate(int N, int two_s, int A, uint64_t *out, int64_t cap)
+{
+    const int d = two_s + 1;
+    const uint64_t full = or_ipow((uint64_t)d, N);
+    int64_t D = 0;
+    for (uint64_t n = 0; n < full; ++n) {
+        int sum = 0;
+        for (int k = 0; k < N; ++k) sum += or_spin_digit(n, d, k);
+        if (sum != A) continue;
+        if (out && D < cap) out[D] = n;
+        ++D;
+    }
+    return D;
+}
+
+/* One row of Eq. 12 for spin s: diagonal sum_b J_b m_i m_j, plus for every bond
+ * the source with (m_i - 1, m_j + 1) weighted by Eq. 13 and the source with
+ * (m_i + 1, m_j - 1) weighted by Eq. 14 (m values of the row state), each present
+ * when the source quantum numbers stay within -s .. s.  Sources are located by
+ * binary search of the sorted basis. */
+static double or_spin_hv_row(int N, int two_s, int nb, const int *bi, const int *bj, const double *J,
+                             const uint64_t *basis, int64_t D, const double *x, int64_t t)
+{
+    const int d = two_s + 1;
+    const double s = 0.5 * two_s, ss1 = s * (s + 1.0);
+    const uint64_t n = basis[t];
+    double diag = 0.0, off = 0.0;
+    (void)N;
+    for (int b = 0; b < nb; ++b) {
+        const int i = bi[b], j = bj[b];
+        const double mi = (double)or_spin_digit(n, d, i) - s;
+        const double mj = (double)or_spin_digit(n, d, j) - s;
+        const uint64_t di = or_ipow((uint64_t)d, i), dj = or_ipow((uint64_t)d, j);
+        diag += J[b] * mi * mj;
+        if (mi - 1.0 >= -s && mj + 1.0 <= s) {
+            const double cp = 0.5 * J[b] * sqrt(ss1 - mi * (mi - 1.0)) * sqrt(ss1 - mj * (mj + 1.0));
+            const int64_t k = or_index_bsearch(basis, D, n - di + dj);
+            off += cp * x[k];
+        }
+        if (mi + 1.0 <= s && mj - 1.0 >= -s) {
+            const double cm = 0.5 * J[b] * sqrt(ss1 - mi * (mi + 1.0)) * sqrt(ss1 - mj * (mj - 1.0));
+            const int64_t k = or_index_bsearch(basis, D, n + di - dj);
+            off += cm * x[k];
+        }
+    }
+    return diag * x[t] + off;
+}
+
+void or_spin_hv_range(int N, int two_s, int nb, const int *bi, const int *bj, const double *J,
+                      const uint64_t *basis, int64_t D, const double *x, double *y, int64_t t0, int64_t t1)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t t = t0; t < t1; ++t)
+        y[t - t0] = or_spin_hv_row(N, two_s, nb, bi, bj, J, basis, D, x, t);
+}
+
+/* Nonzero off-diagonal terms of one spin-s H.v: every ladder move of Eq. 13 or
+ * Eq. 14 whose coefficient is nonzero (with the D diagonal entries, N_nz of Eq. 10). */
+int64_t or_spin_offdiag_terms(int N, int two_s, int nb, const int *bi, const int *bj, const uint64_t *basis,
+                              int64_t D)
+{
+    const int d = two_s + 1;
+    int64_t cnt = 0;
+    (void)N;
+#pragma omp parallel for schedule(static) reduction(+ : cnt)
+    for (int64_t t = 0; t < D; ++t)
+        for (int b = 0; b < nb; ++b) {
+            const int ai = or_spin_digit(basis[t], d, bi[b]), aj = or_spin_digit(basis[t], d, bj[b]);
+            cnt += (ai >= 1 && aj <= two_s - 1) + (ai <= two_s - 1 && aj >= 1);
+        }
+    return cnt;
 }
 
 /* Number of OpenMP threads the H.v loop uses (1 when built without OpenMP). */
