@@ -13,7 +13,10 @@ Parts:
                  for sectors too large to enumerate (sampled-row checks).
   spin.py        general local spin s: Eq. 15 dimensions, Eq. 10 N_nz, base-d
                  basis, H.v (Eq. 12-14), Lanczos and the FTLM driver.
+  diagnostics.py FP32 diagnostics: Cullum-Willoughby ghosts and clusters (Eq. 25),
+                 sigma_emp (Eq. 22), sigma_theo.
 """
 from .ftlm import *  # noqa: F401,F403
 from . import counting  # noqa: F401
 from . import spin  # noqa: F401
+from . import diagnostics  # noqa: F401
