@@ -93,6 +93,23 @@ ftlm_status ftlm_basis_create(int N, int two_sz, int n_bonds, const int *bi, con
                               const double *J, ftlm_rank_mode mode, void *stream,
                               ftlm_basis **out);
 
+/* ftlm_basis_create_spin -- the sector of total S^z = two_sz / 2 for local spin
+ * s = two_s / 2 (Sec. 2: labels with base-d digits a_k = m_k + s, d = 2s + 1,
+ * Eq. 11; digit sum A = N s + S^z, Eq. 17; H.v rows of Eq. 12 with the ladder
+ * coefficients of Eq. 13-14 for general s).
+ *   two_s = 1 is ftlm_basis_create with FTLM_RANK_AUTO.  For 2 <= two_s <= 7 the
+ *   rank is Algorithm 1 in base d with digit blocks (mode FTLM_RANK_CR): N <= 16,
+ *   d^(N - L) <= 2^27 high labels (L low digits with d^L <= 2^14), D < 2^32.
+ *   two_sz must have the parity of N two_s.  Bond arguments, stream and ownership
+ *   as for ftlm_basis_create.  The handle works with every entry point that takes
+ *   a basis (ftlm_basis_labels returns base-d labels sum_k a_k d^k; ftlm_basis_clt
+ *   is EUNSUPPORTED); ftlm_basis_updates is N_nz of Eq. 10.  Chain keys of
+ *   ftlm_lanczos use (N | two_s << 8, A) in place of (N, K).
+ * Errors: EINVAL (ranges, parity, duplicate pair, i == j), EUNSUPPORTED (two_s > 7,
+ * N > 16, table or dimension limits), ENOMEM, ECUDA. */
+ftlm_status ftlm_basis_create_spin(int N, int two_s, int two_sz, int n_bonds, const int *bi, const int *bj,
+                                   const double *J, void *stream, ftlm_basis **out);
+
 /* Release the handle and its device tables.  Waits until the device has finished
  * all queued work first (any stream may still read the tables).  NULL is ignored. */
 void ftlm_basis_destroy(ftlm_basis *basis);
@@ -249,21 +266,25 @@ ftlm_status ftlm_lanczos_noalloc(const ftlm_basis *basis, int R, int M, uint64_t
  * ftlm_batch_create -- plan a batch: sectors with D <= 32768 are cut into units
  *   of `block` chains (block = 1, 4, 8 or 16; 0 = 16 for FP32, 8 for FP64) that one
  *   persistent kernel runs, one CTA per unit at a time, each unit's chains entirely
- *   inside its CTA (vectors in a per-CTA workspace slot, CTA-local reductions);
- *   larger sectors run through the launch sequence of ftlm_lanczos with blocks of
- *   up to `block` chains, spread over up to `streams` side streams (1..8; 0 =
- *   FTLM_BATCH_STREAMS or 4) that each run forks from and joins back into the
- *   caller's stream.  Uploads the plan's descriptors on
+ *   inside its CTA (vectors in a per-CTA workspace slot, CTA-local reductions).
+ *   Larger spin-1/2 sectors (N <= 32) are cut into units of `block` chains that
+ *   advance together, all units of a wave per launch (two launches per Lanczos
+ *   step: H.v with alpha, update with beta; per-unit reductions over tiles of 2048
+ *   rows; waves of at most FTLM_MS_WAVE_MB = 8192 MB of vectors) on a stream
+ *   forked from the caller's.  General-spin sectors and N > 32 run the launch
+ *   sequence of ftlm_lanczos with blocks of up to `block` chains, spread over up to
+ *   `streams` side streams (1..8; 0 = FTLM_BATCH_STREAMS or 4).  Uploads the plan's descriptors on
  *   `stream` (one block from the library's device memory pool, owned by the
  *   batch) and returns when they are in place.  EINVAL for an empty batch or bad
  *   items.
  * ftlm_batch_workspace_bytes -- scratch the plan needs (per-CTA vector slots,
- *   O(chains M) coefficients, one large-sector workspace per side stream).
+ *   O(chains M) coefficients, the vectors of the largest wave, one sector
+ *   workspace per side stream).
  * ftlm_batch_run -- queue the batch on `stream`: memsets, kernel launches and
  *   event records/waits only, so a run can be captured into a CUDA graph (the side
  *   streams join the capture) and replayed.  Results match ftlm_lanczos on each
- *   item up to the summation order of the dot products, and do not depend on the
- *   side-stream assignment.  ENOMEM when the workspace is too small.  Runs of one
+ *   item up to the summation order of the dot products; a chain's results do not
+ *   depend on the other items of the batch nor on the side-stream assignment.  ENOMEM when the workspace is too small.  Runs of one
  *   batch must not overlap.
  * ftlm_batch_destroy -- waits for the device to finish queued work, then releases.
  * ftlm_batch_destroy_async -- releases without waiting; the descriptors return to
@@ -289,9 +310,10 @@ void ftlm_batch_destroy(ftlm_batch *batch);
 ftlm_status ftlm_batch_destroy_async(ftlm_batch *batch, void *stream);
 
 /* ftlm_batch_autotune -- pick the block width and side-stream count of a batch by
- * timing it: for block in {4, 8, 16} and (when some item has D > 32768) streams in
- * {1, 2, 4, 8}, plan the batch, run it once untimed and once between CUDA events on
- * `stream`, and return the fastest pair in *block_out, *streams_out.  ms_out, if
+ * timing it: for block in {4, 8, 16} and (when some item runs on the side
+ * streams) streams in {1, 2, 4, 8}, plan the batch, run it once untimed and once
+ * between CUDA events on `stream`, and return the fastest pair in *block_out,
+ * *streams_out (streams 1 when no item uses them).  ms_out, if
  * not NULL, receives the timed runs (float[12], index 4 * (0, 1, 2 for block 4, 8,
  * 16) + (0..3 for streams 1, 2, 4, 8); entries not tried are left alone).  Blocks
  * the host until the runs finish.  The items' outputs are overwritten.  Workspaces
@@ -331,6 +353,44 @@ ftlm_status ftlm_thermo(int n_sectors, const int *two_sz, const uint64_t *dims, 
                         const int *const *m_eff, int mirror_neg, double g, double h, int nT,
                         const double *T_dev, double *E_dev, double *C_dev, double *chi_dev,
                         double *mag_dev, void *stream);
+
+/* ftlm_partition -- the shifted partition function of the FTLM estimate on a T grid
+ * (Eq. 7 with every exponent shifted by E0, the lowest Ritz energy of the data):
+ *   Z_dev[t] = sum over sectors (and mirror images), chains and Ritz pairs of
+ *              (D / R) w_k exp(-(theta_k - h S^z - E0) / T[t]),   E0_dev[t] = E0,
+ * i.e. Z_eff = Tr exp(-beta (H - E0)) of Sec. 3.1, for sigma_theo = O / sqrt(Z_eff).
+ * Arguments as ftlm_thermo (E0_dev may be NULL). */
+ftlm_status ftlm_partition(int n_sectors, const int *two_sz, const uint64_t *dims, int R, int M,
+                           const double *const *theta, const double *const *weight, const int *const *m_eff,
+                           int mirror_neg, double h, int nT, const double *T_dev, double *Z_dev, double *E0_dev,
+                           void *stream);
+
+/* ------------------------------------------------------- FP32 diagnostics ---
+ * ftlm_ghosts -- Cullum-Willoughby ghost test (Sec. 3.2, Eq. 25) for n chains.
+ *   Inputs per chain c: alpha_dev/beta_dev rows of length M (as for ftlm_ritz),
+ *   m_dev[c], and its Ritz values theta_dev (ascending) and weights weight_dev
+ *   (the outputs of ftlm_ritz or ftlm_lanczos).
+ *   With T^(1) the tridiagonal matrix without its first row and column (eigen-
+ *   values theta^(1)_j, FP64 implicit QR), for k < m:
+ *     ell_dev[c*M+k]     l_k = min_j |theta_k - theta^(1)_j|   (+inf when m = 1)
+ *     flags_dev[c*M+k]   1 when l_k < tau = c_tau * u * (theta_max - theta_min)
+ *     cluster_dev[c*M+k] index of the first member of theta_k's cluster: ascending
+ *                        Ritz values closer than tau belong to one cluster
+ *     cweight_dev[c*M+k] total weight of that cluster
+ *   and count_dev[c] = number of ghosts; entries k >= m are 0 (cluster -1).  The
+ *   paper takes u = the FP32 unit roundoff for FP32 and FP64 runs alike, c_tau of
+ *   order one.  EINVAL for n < 0, M outside 1..FTLM_MAX_LANCZOS, negative c_tau
+ *   or u, or NULL pointers. */
+ftlm_status ftlm_ghosts(int n, int M, const double *alpha_dev, const double *beta_dev, const int *m_dev,
+                        const double *theta_dev, const double *weight_dev, double c_tau, double u, double *ell_dev,
+                        int *cluster_dev, double *cweight_dev, int *flags_dev, int *count_dev, void *stream);
+
+/* ftlm_sigma_emp -- Eq. 22 over N_s independent FTLM estimates: obs_dev holds
+ * ns rows of nT values (row s = the observable on the T grid from seed s);
+ * mean_dev[t] (may be NULL) = the average, sigma_dev[t] = sqrt(sum_s (O_s - mean)^2
+ * / ns) with the 1/N_s of Eq. 22.  EINVAL for ns < 1. */
+ftlm_status ftlm_sigma_emp(int ns, int nT, const double *obs_dev, double *mean_dev, double *sigma_dev,
+                           void *stream);
 
 /* ftlm_launch_count -- kernels the library has queued in this process so far (every
  * launch of every entry point, on any stream; a launch captured into a CUDA graph

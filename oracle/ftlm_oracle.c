@@ -305,13 +305,23 @@ int64_t or_spin_basis_enumerate(int N, int two_s, int A, uint64_t *out, int64_t 
 {
     const int d = two_s + 1;
     const uint64_t full = or_ipow((uint64_t)d, N);
+    int a[64] = {0}; /* digits of n, counted up like an odometer alongside n */
+    int sum = 0;
     int64_t D = 0;
     for (uint64_t n = 0; n < full; ++n) {
-        int sum = 0;
-        for (int k = 0; k < N; ++k) sum += or_spin_digit(n, d, k);
-        if (sum != A) continue;
-        if (out && D < cap) out[D] = n;
-        ++D;
+        if (sum == A) {
+            if (out && D < cap) out[D] = n;
+            ++D;
+        }
+        for (int k = 0; k < N; ++k) { /* n + 1 */
+            if (a[k] + 1 < d) {
+                ++a[k];
+                ++sum;
+                break;
+            }
+            sum -= a[k];
+            a[k] = 0;
+        }
     }
     return D;
 }

@@ -197,6 +197,12 @@ uint64_t align256(uint64_t v) { return (v + 255) & ~uint64_t(255); }
 
 int max_row_grid(const ftlm_basis *b) { return b->num_sms * kMaxBlocksPerSm; }
 
+void launch_hs_fill(const ftlm_basis *b, cudaStream_t stream)
+{
+    hs_fill_kernel<<<grid_for(b->n_hs, 256, b->num_sms), 256, 0, stream>>>(b->tables(), b->n_hs, b->hs);
+    note_launch();
+}
+
 int row_grid(const ftlm_basis *b, uint64_t rows, int occ)
 {
     occ = std::max(1, std::min(occ, kMaxBlocksPerSm));
@@ -216,7 +222,13 @@ ftlm::SectorTables ftlm_basis::tables() const
     s.N = N;
     s.K = K;
     s.L = L;
-    s.lomask = (1u << L) - 1u;
+    if (two_s > 1) {  // base-d digit blocks: lomask + 1 = d^L low labels
+        uint32_t nlo = 1;
+        for (int k = 0; k < L; ++k) nlo *= (uint32_t)(two_s + 1);
+        s.lomask = nlo - 1u;
+    } else {
+        s.lomask = (1u << L) - 1u;
+    }
     s.H = (uint32_t)H;
     s.thi = thi;
     s.tlo = tlo;
@@ -276,6 +288,8 @@ extern "C" ftlm_status ftlm_basis_create(int N, int two_sz, int n_bonds, const i
     b->N = N;
     b->K = K;
     b->two_sz = two_sz;
+    b->two_s = 1;
+    b->key_n = N;
     b->D = D;
     b->mode = mode;
     b->L = std::min(N, kLoBitsMax);
@@ -436,8 +450,7 @@ extern "C" ftlm_status ftlm_basis_create(int N, int two_sz, int n_bonds, const i
     // may go out of scope; the kernels below follow it in stream order.
     e = cudaMemcpyAsync(base, image.data(), small_bytes, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) {
-        hs_fill_kernel<<<grid_for(b->n_hs, 256, b->num_sms), 256, 0, stream>>>(b->tables(), b->n_hs, b->hs);
-        note_launch();
+        launch_hs_fill(b, stream);
         if (clt) {
             const uint64_t *binom_d = reinterpret_cast<const uint64_t *>(base + o_binom);
             basis_fill_kernel<<<grid_for(D, 256, b->num_sms), 256, 0, stream>>>(b->tables(), b->basis);
@@ -512,6 +525,7 @@ extern "C" ftlm_status ftlm_basis_labels(const ftlm_basis *b, uint64_t first, ui
     if (first > b->D || count > b->D - first) return fail(FTLM_EINVAL, "index range beyond D");
     if (count == 0) return FTLM_OK;
     if (!labels_dev) return fail(FTLM_EINVAL, "labels_dev is NULL");
+    if (b->two_s > 1) return launch_spin_labels(b, first, count, labels_dev, (cudaStream_t)stream);
     labels_kernel<<<grid_for(count, 256, b->num_sms), 256, 0, (cudaStream_t)stream>>>(
         b->tables(), b->mode == FTLM_RANK_CLT, first, count, labels_dev);
     note_launch();
@@ -525,6 +539,7 @@ extern "C" ftlm_status ftlm_basis_rank(const ftlm_basis *b, uint64_t count, cons
     if (!b) return fail(FTLM_EINVAL, "NULL basis");
     if (count == 0) return FTLM_OK;
     if (!labels_dev || !index_dev) return fail(FTLM_EINVAL, "NULL device pointer");
+    if (b->two_s > 1) return launch_spin_rank(b, count, labels_dev, index_dev, (cudaStream_t)stream);
     rank_kernel<<<grid_for(count, 256, b->num_sms), 256, 0, (cudaStream_t)stream>>>(
         b->tables(), b->mode == FTLM_RANK_CLT, count, labels_dev, index_dev);
     note_launch();

@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "ftlm_internal.cuh"
+#include "msv.cuh"
 #include "reduce.cuh"
 #include "rng.cuh"
 #include "rows.cuh"
@@ -36,6 +37,17 @@ namespace {
 constexpr int kBatchThreads = 256;
 constexpr uint64_t kSmallRows = 1u << 15;  // sectors up to this dimension run inside one CTA
 constexpr int kMaxSideStreams = 8;
+
+// Vector bytes of one wave of the multi-sector path: FTLM_MS_WAVE_MB or 8192 MB.
+uint64_t ms_wave_bytes()
+{
+    static const uint64_t v = [] {
+        const char *e = std::getenv("FTLM_MS_WAVE_MB");
+        const long long mb = e ? std::atoll(e) : 8192;
+        return (uint64_t)(mb > 0 ? mb : 8192) << 20;
+    }();
+    return v;
+}
 
 // Default number of side streams for the large items: FTLM_BATCH_STREAMS (1..8)
 // or 4.
@@ -307,8 +319,9 @@ struct ftlm_batch {
     int n, M, dist, B;
     ftlm_dtype dtype;
     std::vector<ftlm_batch_item> items;
-    std::vector<int> large;     // items run through the grid-wide path
+    std::vector<int> large;     // items run through the launch sequence of ftlm_lanczos
     uint32_t n_small_chains;
+    uint32_t n_chains;          // small chains, then the chains of the multi-sector path
     uint32_t group_units[3];    // units per kernel variant
     uint32_t group_first[3];    // offset of the group in the unit array
     int group_grid[3];
@@ -328,6 +341,15 @@ struct ftlm_batch {
     cudaStream_t side[kMaxSideStreams];
     cudaEvent_t ev_fork, ev_join[kMaxSideStreams];
     std::vector<int> large_side;
+    // multi-sector path (msv.cu): units of B chains of the mid-sized and large
+    // spin-1/2 sectors, run in waves on their own stream
+    std::vector<MsWave> waves;
+    MsUnit *d_ms_units;
+    uint32_t *d_tile_unit;
+    uint64_t off_ms;
+    int num_sms;
+    cudaStream_t ms_stream;
+    cudaEvent_t ev_ms_join;
 };
 
 namespace {
@@ -339,6 +361,8 @@ void release_host_objects(ftlm_batch *p)
         if (p->ev_join[k]) cudaEventDestroy(p->ev_join[k]);
     }
     if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    if (p->ms_stream) cudaStreamDestroy(p->ms_stream);
+    if (p->ev_ms_join) cudaEventDestroy(p->ev_ms_join);
     delete p;
 }
 
@@ -379,10 +403,15 @@ extern "C" ftlm_status ftlm_batch_create(int n, const ftlm_batch_item *items, in
     std::vector<uint64_t> unit_dim[3];
     uint64_t dmax = 1, large_bytes = 0;
     int num_sms = 0;
+    std::vector<int> ms_items;
     for (int i = 0; i < n; ++i) {
         const ftlm_basis *b = items[i].basis;
         num_sms = b->num_sms;
-        if (b->D > kSmallRows) {
+        if (b->two_s > 1 || (b->N <= 32 && b->D > kSmallRows)) {  // the multi-sector path
+            ms_items.push_back(i);
+            continue;
+        }
+        if (b->D > kSmallRows) {  // N > 32: the launch sequence of ftlm_lanczos
             p->large.push_back(i);
             large_bytes = std::max<uint64_t>(large_bytes, lanczos_workspace(b, items[i].R, M, dtype, B));
             continue;
@@ -439,15 +468,83 @@ extern "C" ftlm_status ftlm_batch_create(int n, const ftlm_batch_item *items, in
         p->group_grid[g] = (int)std::min<uint64_t>(p->group_units[g], (uint64_t)num_sms * occ);
         p->n_slots = std::max(p->n_slots, p->group_grid[g]);
     }
-    // workspace layout
+    // Multi-sector path: units of B chains, grouped by rank kind, cut into waves of
+    // at most ms_wave_bytes() of vectors; offsets within a wave are relative to the
+    // ms region of the workspace (each wave reuses it).
     const uint64_t vsize = dtype == FTLM_F32 ? 4 : 8;
+    std::vector<MsUnit> ms_units;
+    std::vector<uint32_t> tile_unit;
+    uint64_t ms_bytes = 0;
+    p->n_chains = p->n_small_chains;
+    auto kind_of = [](const ftlm_basis *b) {
+        return b->two_s > 1 ? kMsSpin : (b->mode == FTLM_RANK_CLT ? kMsClt : kMsCr);
+    };
+    for (int kind = 0; kind < 3; ++kind) {
+        MsWave w{};
+        uint64_t wbytes = 0;
+        auto close_wave = [&]() {
+            if (!w.n_units) return;
+            p->waves.push_back(w);
+            ms_bytes = std::max(ms_bytes, wbytes);
+            w = MsWave{};
+            wbytes = 0;
+        };
+        for (int i : ms_items) {
+            const ftlm_basis *b = items[i].basis;
+            if (kind_of(b) != kind) continue;
+            for (int r0 = 0; r0 < items[i].R; r0 += B) {
+                const uint64_t vb = align256(b->D * (uint64_t)B * vsize);
+                const uint32_t nt = (uint32_t)((b->D + kMsTileRows - 1) / kMsTileRows);
+                const uint64_t ub = 2 * vb + align256(kMaxBlock * sizeof(ChainState) + 64) +
+                                    align256((uint64_t)nt * B * sizeof(double));
+                if (w.n_units && wbytes + ub > ms_wave_bytes()) close_wave();
+                if (!w.n_units) {
+                    w.unit0 = (uint32_t)ms_units.size();
+                    w.tile_off = (uint32_t)tile_unit.size();
+                    w.kind = kind;
+                }
+                MsUnit u{};
+                u.s = b->tables();
+                u.bl = b->mode == FTLM_RANK_CLT ? b->bonds_clt : b->bonds_cr;
+                u.spin = b->spin;
+                u.off_v0 = wbytes;
+                u.off_v1 = wbytes + vb;
+                u.off_st = wbytes + 2 * vb;
+                u.off_part = u.off_st + align256(kMaxBlock * sizeof(ChainState) + 64);
+                u.seed = items[i].seed;
+                u.tau = dtype == FTLM_F32 ? b->tau32 : b->tau64;
+                u.tile0 = w.n_tiles;
+                u.n_tiles = nt;
+                u.chain_base = p->n_chains + (uint32_t)r0;
+                u.key_n = b->key_n;
+                u.K = b->K;
+                u.chain0 = items[i].first_chain + r0;
+                u.nact = std::min(B, items[i].R - r0);
+                u.m_max = (uint64_t)M < b->D ? M : (int)b->D;
+                for (uint32_t k = 0; k < nt; ++k) tile_unit.push_back(w.n_units);  // wave-local unit index
+                w.n_units += 1;
+                w.n_tiles += nt;
+                w.m_max = std::max(w.m_max, u.m_max);
+                wbytes += ub;
+                ms_units.push_back(u);
+            }
+            for (int r = 0; r < items[i].R; ++r)
+                scatter.push_back({items[i].theta_dev + (size_t)r * M, items[i].weight_dev + (size_t)r * M,
+                                   items[i].m_eff_dev + r});
+            p->n_chains += (uint32_t)items[i].R;
+        }
+        close_wave();
+    }
+    p->num_sms = num_sms;
+
+    // workspace layout
     p->slot_elems = dmax * (uint64_t)B;
     uint64_t off = 0;
     p->off_queue = off;
     off += 256;
     p->off_slots = off;
     off += align256((uint64_t)p->n_slots * 2 * p->slot_elems * vsize);
-    const uint64_t cm = (uint64_t)p->n_small_chains * M * sizeof(double);
+    const uint64_t cm = (uint64_t)p->n_chains * M * sizeof(double);
     p->off_alpha = off;
     off += align256(cm);
     p->off_beta = off;
@@ -457,7 +554,9 @@ extern "C" ftlm_status ftlm_batch_create(int n, const ftlm_batch_item *items, in
     p->off_weight = off;
     off += align256(cm);
     p->off_meff = off;
-    off += align256((uint64_t)p->n_small_chains * sizeof(int));
+    off += align256((uint64_t)p->n_chains * sizeof(int));
+    p->off_ms = off;
+    off += ms_bytes;
     // Large items: longest-processing-time assignment to the side streams (the
     // work of a sector's chains grows with D), so they overlap one another and the
     // persistent kernel of the small items.
@@ -488,12 +587,17 @@ extern "C" ftlm_status ftlm_batch_create(int n, const ftlm_batch_item *items, in
     const uint64_t o_items = 0;
     const uint64_t o_units = align256(o_items + hitems.size() * sizeof(BatchItemDev));
     const uint64_t o_scatter = align256(o_units + units.size() * sizeof(BatchUnitDev));
-    const uint64_t desc_bytes = std::max<uint64_t>(256, align256(o_scatter + scatter.size() * sizeof(ScatterDev)));
+    const uint64_t o_ms = align256(o_scatter + scatter.size() * sizeof(ScatterDev));
+    const uint64_t o_tiles = align256(o_ms + ms_units.size() * sizeof(MsUnit));
+    const uint64_t desc_bytes = std::max<uint64_t>(256, align256(o_tiles + tile_unit.size() * sizeof(uint32_t)));
     std::vector<unsigned char> image(desc_bytes, 0);
     if (!hitems.empty()) std::memcpy(image.data() + o_items, hitems.data(), hitems.size() * sizeof(BatchItemDev));
     if (!units.empty()) std::memcpy(image.data() + o_units, units.data(), units.size() * sizeof(BatchUnitDev));
     if (!scatter.empty())
         std::memcpy(image.data() + o_scatter, scatter.data(), scatter.size() * sizeof(ScatterDev));
+    if (!ms_units.empty()) std::memcpy(image.data() + o_ms, ms_units.data(), ms_units.size() * sizeof(MsUnit));
+    if (!tile_unit.empty())
+        std::memcpy(image.data() + o_tiles, tile_unit.data(), tile_unit.size() * sizeof(uint32_t));
     int device = 0;
     cudaMemPool_t pool = nullptr;
     cudaError_t e = cudaGetDevice(&device);
@@ -504,12 +608,19 @@ extern "C" ftlm_status ftlm_batch_create(int n, const ftlm_batch_item *items, in
         p->d_items = reinterpret_cast<BatchItemDev *>(base + o_items);
         p->d_units = reinterpret_cast<BatchUnitDev *>(base + o_units);
         p->d_scatter = reinterpret_cast<ScatterDev *>(base + o_scatter);
+        p->d_ms_units = reinterpret_cast<MsUnit *>(base + o_ms);
+        p->d_tile_unit = reinterpret_cast<uint32_t *>(base + o_tiles);
         e = cudaMemcpyAsync(base, image.data(), desc_bytes, cudaMemcpyHostToDevice, stream);
     }
     for (int g = 0; g < 3 && e == cudaSuccess; ++g)
         if (p->group_units[g])
             e = cudaFuncSetAttribute(kernel_for(dtype, B, g), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess && p->n_side) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess && (p->n_side || !p->waves.empty()))
+        e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess && !p->waves.empty()) {
+        e = cudaStreamCreateWithFlags(&p->ms_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_ms_join, cudaEventDisableTiming);
+    }
     for (int k = 0; k < p->n_side && e == cudaSuccess; ++k) {
         e = cudaStreamCreateWithFlags(&p->side[k], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_join[k], cudaEventDisableTiming);
@@ -560,11 +671,38 @@ extern "C" ftlm_status ftlm_batch_run(const ftlm_batch *p, void *work_dev, uint6
     double *alpha = (double *)(ws + p->off_alpha), *beta = (double *)(ws + p->off_beta);
     double *theta = (double *)(ws + p->off_theta), *weight = (double *)(ws + p->off_weight);
     int *meff = (int *)(ws + p->off_meff);
-    if (p->n_small_chains) {
-        const size_t cm = (size_t)p->n_small_chains * M * sizeof(double);
+    if (p->n_chains) {
+        const size_t cm = (size_t)p->n_chains * M * sizeof(double);
         FTLM_CUDA(cudaMemsetAsync(queues, 0, 3 * sizeof(unsigned int), stream));
         FTLM_CUDA(cudaMemsetAsync(alpha, 0, cm, stream));
         FTLM_CUDA(cudaMemsetAsync(beta, 0, cm, stream));
+    }
+    if (p->n_side || !p->waves.empty()) FTLM_CUDA(cudaEventRecord(p->ev_fork, stream));
+    // multi-sector path on its own stream, overlapping the persistent kernel
+    if (!p->waves.empty()) {
+        FTLM_CUDA(cudaStreamWaitEvent(p->ms_stream, p->ev_fork, 0));
+        for (const MsWave &w : p->waves) {
+            ftlm_status s = ms_run_wave(w, p->dtype, p->B, p->d_ms_units + w.unit0, p->d_tile_unit + w.tile_off, M,
+                                        p->dist, ws + p->off_ms, alpha, beta, meff, p->num_sms, p->ms_stream);
+            if (s != FTLM_OK) return s;
+        }
+        FTLM_CUDA(cudaEventRecord(p->ev_ms_join, p->ms_stream));
+    }
+    // general-spin and N > 32 sectors on the side streams
+    if (p->n_side) {
+        for (int k = 0; k < p->n_side; ++k) FTLM_CUDA(cudaStreamWaitEvent(p->side[k], p->ev_fork, 0));
+        for (size_t k = 0; k < p->large.size(); ++k) {
+            const ftlm_batch_item &it = p->items[p->large[k]];
+            const int sidx = p->large_side[k];
+            ftlm_status s = lanczos_run(it.basis, it.R, M, it.first_chain, it.seed, p->dist, nullptr, p->dtype,
+                                        ws + p->off_large + (uint64_t)sidx * p->large_bytes, p->large_bytes,
+                                        it.theta_dev, it.weight_dev, it.m_eff_dev, nullptr, nullptr, p->side[sidx],
+                                        p->B);
+            if (s != FTLM_OK) return s;
+        }
+    }
+    // small sectors: one persistent launch per kernel variant
+    if (p->n_small_chains) {
         const size_t smem = ((size_t)1 << kLoBitsMax) * sizeof(uint16_t);
         for (int g = 0; g < 3; ++g) {
             if (!p->group_units[g]) continue;
@@ -582,29 +720,19 @@ extern "C" ftlm_status ftlm_batch_run(const ftlm_batch *p, void *work_dev, uint6
             FTLM_CUDA(cudaLaunchKernel(kern, dim3(p->group_grid[g]), dim3(kBatchThreads), args, smem, stream));
             note_launch();
         }
-        ftlm_status s = launch_ritz((int)p->n_small_chains, M, alpha, beta, meff, theta, weight, stream);
+    }
+    // Ritz step of every chain of both paths, results to the items' outputs
+    if (!p->waves.empty()) FTLM_CUDA(cudaStreamWaitEvent(stream, p->ev_ms_join, 0));
+    if (p->n_chains) {
+        ftlm_status s = launch_ritz((int)p->n_chains, M, alpha, beta, meff, theta, weight, stream);
         if (s != FTLM_OK) return s;
-        scatter_kernel<<<p->n_small_chains, 128, 0, stream>>>((int)p->n_small_chains, M, theta, weight, meff,
-                                                              p->d_scatter);
+        scatter_kernel<<<p->n_chains, 128, 0, stream>>>((int)p->n_chains, M, theta, weight, meff, p->d_scatter);
         note_launch();
         FTLM_CUDA(cudaGetLastError());
     }
-    if (p->n_side) {
-        FTLM_CUDA(cudaEventRecord(p->ev_fork, stream));
-        for (int k = 0; k < p->n_side; ++k) FTLM_CUDA(cudaStreamWaitEvent(p->side[k], p->ev_fork, 0));
-        for (size_t k = 0; k < p->large.size(); ++k) {
-            const ftlm_batch_item &it = p->items[p->large[k]];
-            const int sidx = p->large_side[k];
-            ftlm_status s = lanczos_run(it.basis, it.R, M, it.first_chain, it.seed, p->dist, nullptr, p->dtype,
-                                        ws + p->off_large + (uint64_t)sidx * p->large_bytes, p->large_bytes,
-                                        it.theta_dev, it.weight_dev, it.m_eff_dev, nullptr, nullptr, p->side[sidx],
-                                        p->B);
-            if (s != FTLM_OK) return s;
-        }
-        for (int k = 0; k < p->n_side; ++k) {
-            FTLM_CUDA(cudaEventRecord(p->ev_join[k], p->side[k]));
-            FTLM_CUDA(cudaStreamWaitEvent(stream, p->ev_join[k], 0));
-        }
+    for (int k = 0; k < p->n_side; ++k) {
+        FTLM_CUDA(cudaEventRecord(p->ev_join[k], p->side[k]));
+        FTLM_CUDA(cudaStreamWaitEvent(stream, p->ev_join[k], 0));
     }
     return FTLM_OK;
 }
@@ -615,9 +743,12 @@ extern "C" ftlm_status ftlm_batch_autotune(int n, const ftlm_batch_item *items, 
 {
     if (!block_out || !streams_out) return fail(FTLM_EINVAL, "NULL output");
     cudaStream_t stream = (cudaStream_t)stream_;
+    // the stream count matters only for items on the side streams (general spin, N > 32)
     bool any_large = false;
-    for (int i = 0; i < n && items; ++i)
-        if (items[i].basis && items[i].basis->D > kSmallRows) any_large = true;
+    for (int i = 0; i < n && items; ++i) {
+        const ftlm_basis *b = items[i].basis;
+        if (b && b->two_s == 1 && b->N > 32 && b->D > kSmallRows) any_large = true;
+    }
     int device = 0;
     cudaMemPool_t pool = nullptr;
     FTLM_CUDA(cudaGetDevice(&device));

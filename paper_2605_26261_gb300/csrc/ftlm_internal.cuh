@@ -78,10 +78,28 @@ struct SectorTables {
     const uint2 *clt;       // CLT mode: {M_b, C_b} per 32-label block
 };
 
+// General local spin s = two_s / 2 >= 1 (spin.cu): labels n = sum_k a_k d^k with
+// base-d digits a_k = m_k + s, d = two_s + 1 (Eq. 11).  The digit-block tables of
+// SectorTables are used with base d: thi over the d^(N-L) high labels, tlo/ulo
+// over the d^L low labels grouped by digit sum (uoff: start of each group).
+struct SpinDev {
+    uint32_t d, two_s, A, nb;   // digit base, 2s, sector digit sum (Eq. 17), bonds
+    uint64_t magic;             // division by d: q = (n * magic) >> shift, n < 2^29
+    uint32_t shift, pad;
+    const uint4 *slots;         // per bond {i | j << 8 | hi_i << 16 | hi_j << 17, d^i', d^j', 0}
+                                // (d^k' = power of the site within its digit block)
+    const float *jf;            // J_b
+    const double *jd;
+    const float *upf;           // up[a] = sqrt(s(s+1) - m(m+1)), m = a - s, a = 0 .. 2s-1
+    const double *upd;
+};
+
 }  // namespace ftlm
 
 struct ftlm_basis {
-    int N, K, two_sz;
+    int N, K, two_sz;       // K: digit sum of the sector (up spins at s = 1/2)
+    int two_s;              // 2s: 1 for spin 1/2, >= 2 for the general-spin path
+    int key_n;              // N argument of the chain keys: N, or N | two_s << 8 for s > 1/2
     uint64_t D;
     ftlm_rank_mode mode;
     int L;
@@ -104,6 +122,7 @@ struct ftlm_basis {
     uint64_t n_hs;
     uint32_t *basis;
     uint2 *clt;
+    ftlm::SpinDev spin;     // two_s >= 2 only
 
     ftlm::SectorTables tables() const;
 };
@@ -151,6 +170,16 @@ struct LanczosHv {
     int alpha_stride;
     int j;
 };
+// General-spin counterparts (spin.cu) of the H.v launch and the label/rank kernels.
+ftlm_status launch_hv_spin(const ftlm_basis *b, ftlm_dtype dtype, int B, const void *x, void *y,
+                           const LanczosHv *epi, cudaStream_t stream);
+ftlm_status launch_spin_labels(const ftlm_basis *b, uint64_t first, uint64_t count, uint64_t *out,
+                               cudaStream_t stream);
+ftlm_status launch_spin_rank(const ftlm_basis *b, uint64_t count, const uint64_t *labels, int64_t *out,
+                             cudaStream_t stream);
+// Coarse row index of a basis whose thi table is in place (basis.cu).
+void launch_hs_fill(const ftlm_basis *b, cudaStream_t stream);
+
 // y = H x for a block of B interleaved vectors (B in {1, 4, 8, 16}); with epi, the
 // Lanczos epilogue (y overwrites the u_{j-1} block in place).
 ftlm_status launch_hv(const ftlm_basis *b, ftlm_dtype dtype, int B, const void *x, void *y,

@@ -34,17 +34,11 @@
 // (32 bytes, one DRAM sector, for B = 8 in FP32), so the index arithmetic and the
 // table lookups are shared by the B vectors -- the batched scheme of Sec. 3.4.
 //
-// Lanczos epilogue (Paige's ordering), per chain r of the block.  Per-thread
-// partial dot products use DotAcc (exact products, two-float compensated sums for
-// FP32 vectors); block and grid sums are FP64.  The stored vector
-// u_j is un-normalized, q_j = u_j / s_j.  With x = u_j and the in-place buffer
-// holding u_{j-1}:
-//   y[t] = (H u_j)[t] / s_j - (beta_{j-1} / s_{j-1}) u_{j-1}[t]     (overwrites u_{j-1})
-//   alpha partial += q_j[t] y[t]                                    (FP64)
-// The last block adds the per-block partials in a fixed order and stores alpha_j.
+// The Lanczos epilogue (Paige's ordering) runs in the same launch (epi.cuh).
 #include <algorithm>
 #include <cstdlib>
 
+#include "epi.cuh"
 #include "ftlm_internal.cuh"
 #include "reduce.cuh"
 #include "vec.cuh"
@@ -53,15 +47,6 @@
 namespace ftlm {
 
 namespace {
-
-struct EpiDev {
-    ChainState *st;
-    double *partials;
-    unsigned int *counter;
-    double *alpha_out;
-    int alpha_stride;
-    int has_prev;
-};
 
 // Resident CTAs per SM the compiler must allow for (register budget).  Single
 // vectors with up to 2 rows per thread keep a small register footprint (6 CTAs of
@@ -73,6 +58,11 @@ struct EpiDev {
 // FTLM_B8_MIN_CTAS for the 8-wide blocks with chunks of 4 bonds).
 #ifndef FTLM_B8_MIN_CTAS
 #define FTLM_B8_MIN_CTAS 3
+#endif
+// Build option: 1 issues the CLT lookups of the next bond chunk ahead of the
+// current chunk's accumulation (rows_clt_pipelined).
+#ifndef FTLM_CLT_PIPELINE
+#define FTLM_CLT_PIPELINE 0
 #endif
 template <int RT, int B, int C> __host__ __device__ constexpr int min_ctas()
 {
@@ -86,17 +76,7 @@ hv_kernel(const SectorTables s, const BondList bl, const V *__restrict__ x, V *y
     extern __shared__ uint16_t s_tlo[];
     __shared__ uint4 s_bond[kMaxBondSlots];
     __shared__ V s_inv_s[B], s_c_prev[B];  // per-chain scalars of the epilogue
-    if (LANCZOS) {
-        bool all_stopped = true;
-#pragma unroll
-        for (int r = 0; r < B; ++r) all_stopped &= ep.st[r].stopped != 0;
-        if (all_stopped) return;  // every chain of the block ended: grid-uniform
-        if (threadIdx.x < B) {
-            const ChainState &st = ep.st[threadIdx.x];
-            s_inv_s[threadIdx.x] = (V)(1.0 / st.s_cur);
-            s_c_prev[threadIdx.x] = ep.has_prev ? (V)(st.beta_prev / st.s_prev) : (V)0;
-        }
-    }
+    if (LANCZOS && epi_begin<V, B>(ep, s_inv_s, s_c_prev)) return;
     {
         const uint4 *src = sizeof(V) == 4 ? bl.slots_f32 : bl.slots_f64;
         for (int i = threadIdx.x; i < bl.nb; i += blockDim.x) s_bond[i] = src[i];
@@ -127,64 +107,16 @@ hv_kernel(const SectorTables s, const BondList bl, const V *__restrict__ x, V *y
 #pragma unroll
             for (int r = 0; r < B; ++r) acc[i][r] = (V)0;
         }
-        if (CLT) rows_clt<V, RT, B, C>(s, bl, s_bond, x, t, acc, dsum);
+        if (CLT) {
+            if (FTLM_CLT_PIPELINE) rows_clt_pipelined<V, RT, B, C>(s, bl, s_bond, x, t, acc, dsum);
+            else rows_clt<V, RT, B, C>(s, bl, s_bond, x, t, acc, dsum);
+        }
         else rows_cr<V, Lbl, RT, B, C>(s, bl, s_bond, s_tlo, x, t, acc, dsum);
 #pragma unroll
-        for (int i = 0; i < RT; ++i) {
-            if (!ok[i]) continue;
-            V xt[B], out[B];
-            ld_vec<B>(x + (size_t)t[i] * B, xt, false);
-            const V diag = jsum4 - dsum[i];
-            if (LANCZOS) {
-                V up[B];
-                if (ep.has_prev) ld_vec<B>(y + (size_t)t[i] * B, up, true);
-#pragma unroll
-                for (int r = 0; r < B; ++r) {
-                    const V inv_s = s_inv_s[r];
-                    const V hv = fma(diag, xt[r], acc[i][r]);
-                    out[r] = ep.has_prev ? fma(-s_c_prev[r], up[r], hv * inv_s) : hv * inv_s;
-                    apart[r].add(xt[r] * inv_s, out[r]);
-                }
-            } else {
-#pragma unroll
-                for (int r = 0; r < B; ++r) out[r] = fma(diag, xt[r], acc[i][r]);
-            }
-            st_vec<B>(y + (size_t)t[i] * B, out);
-        }
+        for (int i = 0; i < RT; ++i)
+            if (ok[i]) epi_row<V, B, LANCZOS>(ep, s_inv_s, s_c_prev, x, y, t[i], jsum4 - dsum[i], acc[i], apart);
     }
-    if (LANCZOS) {
-        __shared__ double s_part[B];
-#pragma unroll
-        for (int r = 0; r < B; ++r) {
-            const double part = block_sum<kRowThreads>(apart[r].value());
-            if (threadIdx.x == 0) s_part[r] = part;
-        }
-        __syncthreads();
-        bool last = false;
-        {
-            __shared__ bool s_last;
-            if (threadIdx.x == 0) {
-#pragma unroll
-                for (int r = 0; r < B; ++r) ep.partials[(size_t)blockIdx.x * B + r] = s_part[r];
-                __threadfence();
-                s_last = atomicAdd(ep.counter, 1u) == gridDim.x - 1;
-            }
-            __syncthreads();
-            last = s_last;
-        }
-        if (last && threadIdx.x < 32) {
-            for (int r = 0; r < B; ++r) {
-                double v = 0.0;
-                for (int g = threadIdx.x; g < (int)gridDim.x; g += 32) v += __ldcg(ep.partials + (size_t)g * B + r);
-                v = warp_sum(v);
-                if (threadIdx.x == 0 && !ep.st[r].stopped) {
-                    ep.st[r].alpha = v;
-                    ep.alpha_out[(size_t)r * ep.alpha_stride] = v;
-                }
-            }
-            if (threadIdx.x == 0) *ep.counter = 0;
-        }
-    }
+    if (LANCZOS) epi_end<V, B, kRowThreads>(ep, apart);
 }
 
 // Rows per thread (RT) for single vectors.  Measured on GB300 (icosidodecahedron,
@@ -279,16 +211,8 @@ template <typename V>
 ftlm_status launch_typed(const ftlm_basis *b, int B, const void *x, void *y, const LanczosHv *epi,
                          cudaStream_t stream)
 {
-    EpiDev ep{};
-    if (epi) {
-        ep.st = epi->st;
-        ep.partials = epi->partials;
-        ep.counter = epi->counter;
-        ep.alpha_out = epi->alpha_out;
-        ep.alpha_stride = epi->alpha_stride;
-        ep.has_prev = epi->j > 1;
-        return launch_mode<V, true>(b, B, x, y, ep, stream);
-    }
+    const EpiDev ep = epi_of(epi);
+    if (epi) return launch_mode<V, true>(b, B, x, y, ep, stream);
     return launch_mode<V, false>(b, B, x, y, ep, stream);
 }
 
@@ -299,6 +223,7 @@ bool valid_block(int B) { return B == 1 || B == 4 || B == 8 || B == 16; }
 ftlm_status launch_hv(const ftlm_basis *b, ftlm_dtype dtype, int B, const void *x, void *y,
                       const LanczosHv *epi, cudaStream_t stream)
 {
+    if (b->two_s > 1) return launch_hv_spin(b, dtype, B, x, y, epi, stream);
     return dtype == FTLM_F32 ? launch_typed<float>(b, B, x, y, epi, stream)
                              : launch_typed<double>(b, B, x, y, epi, stream);
 }

@@ -1,0 +1,416 @@
+// Lanczos chains of many sectors advanced together, one launch per step kind
+// (steps a2-a4 over a set of sectors).
+//
+// The units are blocks of B chains of mid-sized and large sectors.  Their rows are
+// cut into tiles of kMsTileRows; one launch walks the tiles of every unit of a
+// wave (a persistent grid, tiles dealt round-robin, so at any moment the GPU works
+// on a window of consecutive tiles -- one or two sectors -- whose vectors stay in
+// L2).  Per Lanczos step there are two launches for the whole wave: the fused
+// H.v + alpha epilogue and the w/beta update, each with per-unit reductions:
+// every tile stores its partial sums, and the CTA that finishes a unit's last tile
+// (an atomic ticket per unit, no waiting) adds the unit's partials in tile order.
+// A unit's arithmetic depends only on its own tiles, so its results are the same
+// whatever other units share the launch, and bit-reproducible.
+//
+// The recurrence, stop test and chain state follow ftlm_lanczos exactly (Paige's
+// ordering, 1/beta folded into the next H.v, columns of ended chains zeroed).
+#include "epi.cuh"
+#include "ftlm_internal.cuh"
+#include "msv.cuh"
+#include "reduce.cuh"
+#include "rng.cuh"
+#include "rows.cuh"
+#include "spin_rows.cuh"
+#include "vec.cuh"
+
+namespace ftlm {
+
+namespace {
+
+struct UnitView {
+    const MsUnit *u;
+    char *ws;
+    __device__ ChainState *st() const { return reinterpret_cast<ChainState *>(ws + u->off_st); }
+    __device__ unsigned int *counter() const
+    {
+        return reinterpret_cast<unsigned int *>(ws + u->off_st + (size_t)kMaxBlock * sizeof(ChainState));
+    }
+    __device__ double *partials() const { return reinterpret_cast<double *>(ws + u->off_part); }
+    template <typename V> __device__ V *vec(int which) const
+    {
+        return reinterpret_cast<V *>(ws + (which ? u->off_v1 : u->off_v0));
+    }
+};
+
+// Store this tile's B block sums at tile slot k of the unit; returns true (in every
+// thread) in the CTA that completes the unit.
+template <int B>
+__device__ __forceinline__ bool tile_publish(const double (&part)[B], double *partials, uint32_t k,
+                                             unsigned int *counter, uint32_t n_tiles)
+{
+    __shared__ double s_part[B];
+    __shared__ bool s_last;
+#pragma unroll
+    for (int r = 0; r < B; ++r) {
+        const double v = block_sum<kRowThreads>(part[r]);
+        if (threadIdx.x == 0) s_part[r] = v;
+    }
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int r = 0; r < B; ++r) partials[(size_t)k * B + r] = s_part[r];
+        __threadfence();
+        s_last = atomicAdd(counter, 1u) == n_tiles - 1;
+    }
+    __syncthreads();
+    return s_last;
+}
+
+// Fixed-order total of chain r over the unit's tiles; warp 0, valid in lane 0.
+template <int B>
+__device__ __forceinline__ double tile_total(const double *partials, uint32_t n_tiles, int r)
+{
+    double v = 0.0;
+    for (uint32_t k = threadIdx.x; k < n_tiles; k += 32) v += __ldcg(partials + (size_t)k * B + r);
+    return warp_sum(v);
+}
+
+template <typename V, int B>
+__global__ void __launch_bounds__(kRowThreads)
+ms_start_kernel(const MsUnit *__restrict__ units, const uint32_t *__restrict__ tile_unit, uint32_t n_tiles, int dist,
+                char *ws)
+{
+    for (uint32_t g = blockIdx.x; g < n_tiles; g += gridDim.x) {
+        const UnitView uv{units + tile_unit[g], ws};
+        const MsUnit &U = *uv.u;
+        const uint32_t k = g - U.tile0, D = U.s.D;
+        uint64_t key[B];
+#pragma unroll
+        for (int r = 0; r < B; ++r) key[r] = chain_key(U.seed, U.key_n, U.K, (uint32_t)(U.chain0 + r));
+        V *u0 = uv.vec<V>(0);
+        DotAcc<V> acc[B];
+        const uint32_t row1 = min(D, (k + 1) * kMsTileRows);
+        for (uint32_t t = k * kMsTileRows + threadIdx.x; t < row1; t += kRowThreads) {
+            V out[B];
+#pragma unroll
+            for (int r = 0; r < B; ++r) {
+                out[r] = r < U.nact ? (V)start_value(key[r], t, dist) : (V)0;
+                acc[r].add(out[r], out[r]);
+            }
+            st_vec<B>(u0 + (size_t)t * B, out);
+        }
+        double part[B];
+#pragma unroll
+        for (int r = 0; r < B; ++r) part[r] = acc[r].value();
+        if (tile_publish<B>(part, uv.partials(), k, uv.counter(), U.n_tiles) && threadIdx.x < 32) {
+            ChainState *st = uv.st();
+            for (int r = 0; r < B; ++r) {
+                const double nrm = sqrt(tile_total<B>(uv.partials(), U.n_tiles, r));
+                if (threadIdx.x == 0) {
+                    ChainState &c = st[r];
+                    c.s_cur = nrm;
+                    c.s_prev = 1.0;
+                    c.beta_prev = 0.0;
+                    c.alpha = 0.0;
+                    c.m_eff = 0;
+                    c.stopped = (r < U.nact && nrm > 0.0 && isfinite(nrm)) ? 0 : 1;
+                }
+            }
+            if (threadIdx.x == 0) *uv.counter() = 0;
+        }
+        __syncthreads();
+    }
+}
+
+// Step j: y = H q_j - beta_{j-1} q_{j-1} over the u_{j-1} block and alpha_j, for
+// every tile of every unit (x = u_j is block (j - 1) % 2, y block j % 2).
+template <typename V, int KIND, int B, int C>
+__global__ void __launch_bounds__(kRowThreads, B >= 16 ? 1 : 2)
+ms_hv_kernel(const MsUnit *__restrict__ units, const uint32_t *__restrict__ tile_unit, uint32_t n_tiles, int j,
+             int M, double *alpha, char *ws)
+{
+    constexpr bool CLT = KIND == kMsClt, SPIN = KIND == kMsSpin;
+    extern __shared__ uint16_t s_tlo[];
+    __shared__ uint4 s_bond[kMaxBondSlots];
+    __shared__ V s_J[SPIN ? kMaxBondSlots : 1];
+    __shared__ V s_up[kSpinMaxTwoS + 1];
+    __shared__ V s_inv_s[B], s_c_prev[B];
+    __shared__ int s_skip;
+    uint32_t loaded = 0xffffffffu;
+    EpiDev ep{};
+    ep.has_prev = j > 1;
+    for (uint32_t g = blockIdx.x; g < n_tiles; g += gridDim.x) {
+        const uint32_t ui = tile_unit[g];
+        const UnitView uv{units + ui, ws};
+        const MsUnit &U = *uv.u;
+        if (ui != loaded) {  // CTA-uniform: stage the unit's bonds, tlo and chain scalars
+            __syncthreads();  // every thread is past its last read of the previous unit's data
+            loaded = ui;
+            if (SPIN) {
+                for (uint32_t i = threadIdx.x; i < U.spin.nb; i += blockDim.x) {
+                    s_bond[i] = U.spin.slots[i];
+                    s_J[i] = spin_J<V>(U.spin)[i];
+                }
+                if (threadIdx.x < U.spin.two_s) s_up[threadIdx.x] = spin_up<V>(U.spin)[threadIdx.x];
+            } else {
+                const uint4 *src = sizeof(V) == 4 ? U.bl.slots_f32 : U.bl.slots_f64;
+                for (int i = threadIdx.x; i < U.bl.nb; i += blockDim.x) s_bond[i] = src[i];
+            }
+            if (!CLT)
+                for (uint32_t i = threadIdx.x; i <= U.s.lomask; i += blockDim.x) s_tlo[i] = __ldg(U.s.tlo + i);
+            if (threadIdx.x == 0) {
+                const ChainState *st = uv.st();
+                int all = 1;
+                for (int r = 0; r < B; ++r) all &= st[r].stopped;
+                s_skip = all || j > U.m_max;
+            }
+            if (threadIdx.x < B) {
+                const ChainState &c = uv.st()[threadIdx.x];
+                s_inv_s[threadIdx.x] = (V)(1.0 / c.s_cur);
+                s_c_prev[threadIdx.x] = j > 1 ? (V)(c.beta_prev / c.s_prev) : (V)0;
+            }
+            __syncthreads();
+        }
+        if (s_skip) continue;  // CTA-uniform
+        const uint32_t k = g - U.tile0, D = U.s.D;
+        const V *x = uv.vec<V>((j - 1) & 1);
+        V *y = uv.vec<V>(j & 1);
+        const V jsum4 = (V)U.bl.jsum4;
+        DotAcc<V> apart[B];
+        const uint32_t row0 = k * kMsTileRows;
+        for (uint32_t p = 0; p < kMsTileRows; p += kRowThreads) {
+            const uint32_t tt = row0 + p + threadIdx.x;
+            if (row0 + p >= D) break;  // CTA-uniform
+            const bool ok = tt < D;
+            const uint32_t t[1] = {ok ? tt : D - 1};  // rows past the end recompute the last row, unstored
+            if constexpr (SPIN) {
+                V acc[B], diag;
+                spin_row<V, B, C>(U.s, U.spin, s_tlo, s_bond, s_J, s_up, x, t[0], acc, diag);
+                if (ok) epi_row<V, B, true>(ep, s_inv_s, s_c_prev, x, y, t[0], diag, acc, apart);
+            } else {
+                V acc[1][B], dsum[1] = {(V)0};
+#pragma unroll
+                for (int r = 0; r < B; ++r) acc[0][r] = (V)0;
+                if (CLT) rows_clt<V, 1, B, C>(U.s, U.bl, s_bond, x, t, acc, dsum);
+                else rows_cr<V, uint32_t, 1, B, C>(U.s, U.bl, s_bond, s_tlo, x, t, acc, dsum);
+                if (ok) epi_row<V, B, true>(ep, s_inv_s, s_c_prev, x, y, t[0], jsum4 - dsum[0], acc[0], apart);
+            }
+        }
+        double part[B];
+#pragma unroll
+        for (int r = 0; r < B; ++r) part[r] = apart[r].value();
+        if (tile_publish<B>(part, uv.partials(), k, uv.counter(), U.n_tiles) && threadIdx.x < 32) {
+            ChainState *st = uv.st();
+            for (int r = 0; r < B; ++r) {
+                const double v = tile_total<B>(uv.partials(), U.n_tiles, r);
+                if (threadIdx.x == 0 && !st[r].stopped) {
+                    st[r].alpha = v;
+                    alpha[(size_t)(U.chain_base + r) * M + (j - 1)] = v;
+                }
+            }
+            if (threadIdx.x == 0) *uv.counter() = 0;
+        }
+        __syncthreads();
+    }
+}
+
+// Step j: w = y - alpha_j q_j in place, beta_j = ||w||, breakdown test (as
+// update_kernel of lanczos.cu, per unit).
+template <typename V, int B>
+__global__ void __launch_bounds__(kRowThreads)
+ms_update_kernel(const MsUnit *__restrict__ units, const uint32_t *__restrict__ tile_unit, uint32_t n_tiles, int j,
+                 int M, double *beta, char *ws)
+{
+    constexpr int W = 16 / (int)sizeof(V);
+    constexpr int U_ = B > W ? B : W;  // values per thread and pass
+    __shared__ V s_a[B];
+    __shared__ int s_zero[B];
+    __shared__ int s_skip;
+    uint32_t loaded = 0xffffffffu;
+    for (uint32_t g = blockIdx.x; g < n_tiles; g += gridDim.x) {
+        const uint32_t ui = tile_unit[g];
+        const UnitView uv{units + ui, ws};
+        const MsUnit &U = *uv.u;
+        if (ui != loaded) {
+            __syncthreads();
+            loaded = ui;
+            if (threadIdx.x == 0) {
+                const ChainState *st = uv.st();
+                int all = 1;
+                for (int r = 0; r < B; ++r) all &= st[r].stopped;
+                s_skip = all || j > U.m_max;
+            }
+            if (threadIdx.x < B) {
+                const ChainState &c = uv.st()[threadIdx.x];
+                s_zero[threadIdx.x] = c.stopped;
+                s_a[threadIdx.x] = c.stopped ? (V)0 : (V)(c.alpha / c.s_cur);
+            }
+            __syncthreads();
+        }
+        if (s_skip) continue;
+        const uint32_t k = g - U.tile0, D = U.s.D;
+        V *y = uv.vec<V>(j & 1);
+        const V *u = uv.vec<V>((j - 1) & 1);
+        V a[B];
+        bool zero[B];
+#pragma unroll
+        for (int r = 0; r < B; ++r) {
+            a[r] = s_a[r];
+            zero[r] = s_zero[r] != 0;
+        }
+        DotAcc<V> acc[B];
+        const uint64_t e0 = (uint64_t)k * kMsTileRows * B;
+        const uint64_t e1 = (uint64_t)min(D, (k + 1) * kMsTileRows) * B;
+        const uint64_t full = e0 + (e1 - e0) / U_ * U_;
+        for (uint64_t e = e0 + (uint64_t)threadIdx.x * U_; e < full; e += (uint64_t)kRowThreads * U_) {
+            V yv[U_], xv[U_], w[U_];
+            ld_vec<U_>(y + e, yv, true);
+            ld_vec<U_>(u + e, xv, true);
+#pragma unroll
+            for (int q = 0; q < U_; ++q) {
+                const int r = q % B;
+                w[q] = zero[r] ? (V)0 : fma(-a[r], xv[q], yv[q]);
+                acc[r].add(w[q], w[q]);
+            }
+            st_vec<U_>(y + e, w);
+        }
+        for (uint64_t e = full + threadIdx.x; e < e1; e += kRowThreads) {  // only with B = 1
+            const V w = zero[0] ? (V)0 : fma(-a[0], u[e], y[e]);
+            y[e] = w;
+            acc[0].add(w, w);
+        }
+        double part[B];
+#pragma unroll
+        for (int r = 0; r < B; ++r) part[r] = acc[r].value();
+        if (tile_publish<B>(part, uv.partials(), k, uv.counter(), U.n_tiles) && threadIdx.x < 32) {
+            ChainState *st = uv.st();
+            for (int r = 0; r < B; ++r) {
+                const double bt = sqrt(tile_total<B>(uv.partials(), U.n_tiles, r));
+                if (threadIdx.x == 0 && !st[r].stopped) {
+                    ChainState &c = st[r];
+                    if (j < U.m_max) {
+                        if (bt <= U.tau) {
+                            c.stopped = 1;
+                            c.m_eff = j;
+                        } else {
+                            beta[(size_t)(U.chain_base + r) * M + (j - 1)] = bt;
+                            c.s_prev = c.s_cur;
+                            c.s_cur = bt;
+                            c.beta_prev = bt;
+                        }
+                    } else {
+                        c.m_eff = U.m_max;
+                    }
+                }
+            }
+            if (threadIdx.x == 0) *uv.counter() = 0;
+        }
+        __syncthreads();
+    }
+}
+
+// Chain states and reduction counters of every unit of the wave to zero (the
+// counters must start at zero: the last tile of a unit is found by its ticket).
+__global__ void ms_reset_kernel(const MsUnit *__restrict__ units, uint32_t n_units, char *ws)
+{
+    constexpr uint32_t words = (kMaxBlock * sizeof(ChainState) + 64) / sizeof(uint32_t);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_units * words; i += gridDim.x * blockDim.x) {
+        uint32_t *p = reinterpret_cast<uint32_t *>(ws + units[i / words].off_st);
+        p[i % words] = 0u;
+    }
+}
+
+__global__ void ms_meff_kernel(const MsUnit *__restrict__ units, uint32_t n_units, int B, int *meff, char *ws)
+{
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_units * (uint32_t)B; i += gridDim.x * blockDim.x) {
+        const MsUnit &U = units[i / B];
+        const int r = (int)(i % B);
+        if (r < U.nact) meff[U.chain_base + r] = reinterpret_cast<const ChainState *>(ws + U.off_st)[r].m_eff;
+    }
+}
+
+template <int B> __host__ __device__ constexpr int ms_chunk() { return B >= 8 ? 4 : kBondChunk; }
+
+template <typename V, int B> void *ms_hv_ptr(int kind)
+{
+    if (kind == kMsSpin) return (void *)ms_hv_kernel<V, kMsSpin, B, spin_chunk<B>()>;
+    if (kind == kMsClt) return (void *)ms_hv_kernel<V, kMsClt, B, ms_chunk<B>()>;
+    return (void *)ms_hv_kernel<V, kMsCr, B, ms_chunk<B>()>;
+}
+
+int occupancy(const void *kern, size_t smem)
+{
+    int occ = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kRowThreads, smem);
+    return occ < 1 ? 1 : occ;
+}
+
+template <typename V, int B>
+ftlm_status ms_run_typed(const MsWave &w, const MsUnit *units, const uint32_t *tile_unit, int M, int dist,
+                         char *ws, double *alpha, double *beta, int *meff, int num_sms, cudaStream_t stream)
+{
+    const size_t smem = w.kind == kMsClt ? 0 : ((size_t)1 << kLoBitsMax) * sizeof(uint16_t);
+    void *hv = ms_hv_ptr<V, B>(w.kind);
+    static int occ_hv[3] = {0, 0, 0}, occ_start = 0, occ_upd = 0;
+    int &oh = occ_hv[w.kind];
+    if (!oh) {
+        if (smem) FTLM_CUDA(cudaFuncSetAttribute(hv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        oh = occupancy(hv, smem);
+        occ_start = occupancy((const void *)ms_start_kernel<V, B>, 0);
+        occ_upd = occupancy((const void *)ms_update_kernel<V, B>, 0);
+    }
+    auto grid = [&](int occ) { return (int)std::min<uint64_t>(w.n_tiles, (uint64_t)num_sms * occ); };
+    {
+        const uint32_t words = (kMaxBlock * sizeof(ChainState) + 64) / sizeof(uint32_t);
+        const int g = (int)std::min<uint64_t>(((uint64_t)w.n_units * words + 255) / 256, (uint64_t)num_sms * 4);
+        ms_reset_kernel<<<g, 256, 0, stream>>>(units, w.n_units, ws);
+        note_launch();
+    }
+    ms_start_kernel<V, B><<<grid(occ_start), kRowThreads, 0, stream>>>(units, tile_unit, w.n_tiles, dist, ws);
+    note_launch();
+    FTLM_CUDA(cudaGetLastError());
+    for (int j = 1; j <= w.m_max; ++j) {
+        void *tok = profile_begin(kProfHv, stream, B);
+        uint32_t nt = w.n_tiles;
+        int jj = j, MM = M;
+        void *args[] = {(void *)&units, (void *)&tile_unit, (void *)&nt, (void *)&jj, (void *)&MM, (void *)&alpha,
+                        (void *)&ws};
+        FTLM_CUDA(cudaLaunchKernel(hv, dim3(grid(oh)), dim3(kRowThreads), args, smem, stream));
+        note_launch();
+        profile_end(tok, stream);
+        tok = profile_begin(kProfUpdate, stream);
+        ms_update_kernel<V, B><<<grid(occ_upd), kRowThreads, 0, stream>>>(units, tile_unit, w.n_tiles, j, M, beta, ws);
+        note_launch();
+        profile_end(tok, stream);
+        FTLM_CUDA(cudaGetLastError());
+    }
+    ms_meff_kernel<<<(w.n_units * B + 255) / 256, 256, 0, stream>>>(units, w.n_units, B, meff, ws);
+    note_launch();
+    FTLM_CUDA(cudaGetLastError());
+    return FTLM_OK;
+}
+
+template <typename V>
+ftlm_status ms_run_v(const MsWave &w, int B, const MsUnit *units, const uint32_t *tile_unit, int M, int dist,
+                     char *ws, double *alpha, double *beta, int *meff, int num_sms, cudaStream_t stream)
+{
+    switch (B) {
+    case 16: return ms_run_typed<V, 16>(w, units, tile_unit, M, dist, ws, alpha, beta, meff, num_sms, stream);
+    case 8: return ms_run_typed<V, 8>(w, units, tile_unit, M, dist, ws, alpha, beta, meff, num_sms, stream);
+    case 4: return ms_run_typed<V, 4>(w, units, tile_unit, M, dist, ws, alpha, beta, meff, num_sms, stream);
+    default: return ms_run_typed<V, 1>(w, units, tile_unit, M, dist, ws, alpha, beta, meff, num_sms, stream);
+    }
+}
+
+}  // namespace
+
+ftlm_status ms_run_wave(const MsWave &w, ftlm_dtype dtype, int B, const MsUnit *units, const uint32_t *tile_unit,
+                        int M, int dist, char *ws, double *alpha, double *beta, int *meff, int num_sms,
+                        cudaStream_t stream)
+{
+    if (!w.n_tiles) return FTLM_OK;
+    return dtype == FTLM_F32
+               ? ms_run_v<float>(w, B, units, tile_unit, M, dist, ws, alpha, beta, meff, num_sms, stream)
+               : ms_run_v<double>(w, B, units, tile_unit, M, dist, ws, alpha, beta, meff, num_sms, stream);
+}
+
+}  // namespace ftlm

@@ -1,0 +1,46 @@
+// Descriptors of the multi-sector Lanczos path (msv.cu), planned by ftlm_batch.
+#pragma once
+
+#include "ftlm_internal.cuh"
+
+namespace ftlm {
+
+constexpr uint32_t kMsTileRows = 2048;  // rows per tile (a multiple of kRowThreads)
+
+// One block of B chains of one sector.  Offsets are into the run's workspace.
+struct MsUnit {
+    SectorTables s;
+    BondList bl;
+    uint64_t off_v0, off_v1;  // the two vector blocks, D x B each
+    uint64_t off_st;          // ChainState[kMaxBlock], then the unit's reduction counter
+    uint64_t off_part;        // per-tile partial sums [n_tiles][B]
+    uint64_t seed;
+    double tau;
+    uint32_t tile0, n_tiles;  // the unit's tiles within its wave
+    uint32_t chain_base;      // chain 0 of the unit in the batch's alpha/beta/meff arrays
+    int key_n, K, chain0;     // chain keys: chain r is keyed (seed, key_n, K, chain0 + r)
+    int nact;                 // chains of the unit (<= B); the other columns stay zero
+    int m_max;
+    int pad;
+    SpinDev spin;             // general-spin units (kMsSpin)
+};
+
+// Rank kinds of a wave (one kernel instantiation each).
+enum MsKind { kMsCr = 0, kMsClt = 1, kMsSpin = 2 };
+
+// Units run together (one rank kind), their tiles numbered 0 .. n_tiles-1.
+struct MsWave {
+    uint32_t unit0, n_units;  // units [unit0, unit0 + n_units) of the plan
+    uint32_t tile_off;        // offset of the wave's tile->unit map in the plan's map
+    uint32_t n_tiles;
+    int m_max;                // longest chain length of the wave
+    int kind;                 // MsKind
+};
+
+// Queue one wave: start vectors, m_max steps of (H.v + alpha, update + beta), and
+// the chain lengths into meff.  units and tile_unit point at the wave's own entries.
+ftlm_status ms_run_wave(const MsWave &w, ftlm_dtype dtype, int B, const MsUnit *units, const uint32_t *tile_unit,
+                        int M, int dist, char *ws, double *alpha, double *beta, int *meff, int num_sms,
+                        cudaStream_t stream);
+
+}  // namespace ftlm

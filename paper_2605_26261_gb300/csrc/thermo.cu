@@ -58,7 +58,7 @@ __device__ __forceinline__ double bcast(double v)
 
 __global__ void __launch_bounds__(kThermoThreads)
 thermo_kernel(const ThermoArgs a, const double *__restrict__ T, double *E, double *C, double *chi,
-              double *mag)
+              double *mag, double *Zs, double *E0s)
 {
     const int per_sector = a.R * a.M;
     const int n = a.ns * per_sector;
@@ -113,10 +113,12 @@ thermo_kernel(const ThermoArgs a, const double *__restrict__ T, double *E, doubl
     const double V2 = block_sum<kThermoThreads>(v2);
     if (threadIdx.x == 0) {
         const int t = blockIdx.x;
-        E[t] = E0 + e1;
-        C[t] = beta * beta * (S2 / Z);
-        chi[t] = a.g * a.g * beta * (a.h == 0.0 ? M2 : V2 / Z);
+        if (E) E[t] = E0 + e1;
+        if (C) C[t] = beta * beta * (S2 / Z);
+        if (chi) chi[t] = a.g * a.g * beta * (a.h == 0.0 ? M2 : V2 / Z);
         if (mag) mag[t] = M1;
+        if (Zs) Zs[t] = Z;
+        if (E0s) E0s[t] = E0;
     }
 }
 
@@ -155,7 +157,43 @@ extern "C" ftlm_status ftlm_thermo(int n_sectors, const int *two_sz, const uint6
         a.sz[s] = two_sz[s] / 2.0;
     }
     if (nT == 0) return FTLM_OK;
-    thermo_kernel<<<nT, kThermoThreads, 0, (cudaStream_t)stream>>>(a, T_dev, E_dev, C_dev, chi_dev, mag_dev);
+    thermo_kernel<<<nT, kThermoThreads, 0, (cudaStream_t)stream>>>(a, T_dev, E_dev, C_dev, chi_dev, mag_dev,
+                                                                    nullptr, nullptr);
+    note_launch();
+    FTLM_CUDA(cudaGetLastError());
+    return FTLM_OK;
+}
+
+extern "C" ftlm_status ftlm_partition(int n_sectors, const int *two_sz, const uint64_t *dims, int R, int M,
+                                      const double *const *theta, const double *const *weight,
+                                      const int *const *m_eff, int mirror_neg, double h, int nT, const double *T_dev,
+                                      double *Z_dev, double *E0_dev, void *stream)
+{
+    if (n_sectors < 1 || n_sectors > FTLM_MAX_SECTORS) return fail(FTLM_EINVAL, "n_sectors out of range");
+    if (R < 1 || M < 1 || M > FTLM_MAX_LANCZOS) return fail(FTLM_EINVAL, "R or M out of range");
+    if ((int64_t)n_sectors * R * M > (1ll << 31) - 1) return fail(FTLM_EUNSUPPORTED, "too many Ritz pairs");
+    if (nT < 0) return fail(FTLM_EINVAL, "nT < 0");
+    if (!two_sz || !dims || !theta || !weight || !m_eff) return fail(FTLM_EINVAL, "NULL host array");
+    if (nT > 0 && (!T_dev || !Z_dev)) return fail(FTLM_EINVAL, "NULL device output");
+    ThermoArgs a{};
+    a.ns = n_sectors;
+    a.R = R;
+    a.M = M;
+    a.mirror = mirror_neg != 0;
+    a.g = 0.0;
+    a.h = h;
+    for (int s = 0; s < n_sectors; ++s) {
+        if (!theta[s] || !weight[s] || !m_eff[s]) return fail(FTLM_EINVAL, "NULL sector pointer");
+        if (dims[s] == 0) return fail(FTLM_EINVAL, "zero sector dimension");
+        a.theta[s] = theta[s];
+        a.weight[s] = weight[s];
+        a.meff[s] = m_eff[s];
+        a.wscale[s] = (double)dims[s] / R;
+        a.sz[s] = two_sz[s] / 2.0;
+    }
+    if (nT == 0) return FTLM_OK;
+    thermo_kernel<<<nT, kThermoThreads, 0, (cudaStream_t)stream>>>(a, T_dev, nullptr, nullptr, nullptr, nullptr,
+                                                                    Z_dev, E0_dev);
     note_launch();
     FTLM_CUDA(cudaGetLastError());
     return FTLM_OK;

@@ -59,6 +59,7 @@ def lib():
     PD = ctypes.POINTER(ctypes.c_double)
     sig = {
         "ftlm_basis_create": [I, I, I, P, P, P, I, P, ctypes.POINTER(P)],
+        "ftlm_basis_create_spin": [I, I, I, I, P, P, P, P, ctypes.POINTER(P)],
         "ftlm_basis_dim": [P, PU64],
         "ftlm_basis_bytes": [P, PU64],
         "ftlm_basis_mode": [P, ctypes.POINTER(I)],
@@ -83,6 +84,9 @@ def lib():
         "ftlm_batch_destroy_async": [P, P],
         "ftlm_profile_enable": [I],
         "ftlm_launch_count": [PU64],
+        "ftlm_partition": [I, P, P, I, I, P, P, P, I, D, I, P, P, P, P],
+        "ftlm_ghosts": [I, I, P, P, P, P, P, D, D, P, P, P, P, P, P],
+        "ftlm_sigma_emp": [I, I, P, P, P, P],
         "ftlm_profile_read": [PU64, PU64, PD, PU64, PD],
     }
     for name, args in sig.items():
@@ -146,6 +150,18 @@ def ftlm_basis_create(N, two_sz, bi, bj, J, mode=RANK_AUTO, stream=None):
     out = ctypes.c_void_p()
     _check(lib().ftlm_basis_create(int(N), int(two_sz), len(J), bi.ctypes.data, bj.ctypes.data,
                                    J.ctypes.data, int(mode), _stream(stream), ctypes.byref(out)))
+    return out
+
+
+def ftlm_basis_create_spin(N, two_s, two_sz, bi, bj, J, stream=None):
+    bi = np.ascontiguousarray(bi, dtype=np.int32)
+    bj = np.ascontiguousarray(bj, dtype=np.int32)
+    J = np.ascontiguousarray(J, dtype=np.float64)
+    if not (len(bi) == len(bj) == len(J)):
+        raise ValueError("bond arrays differ in length")
+    out = ctypes.c_void_p()
+    _check(lib().ftlm_basis_create_spin(int(N), int(two_s), int(two_sz), len(J), bi.ctypes.data, bj.ctypes.data,
+                                        J.ctypes.data, _stream(stream), ctypes.byref(out)))
     return out
 
 
@@ -264,6 +280,44 @@ def ftlm_thermo(two_sz, dims, R, M, thetas, weights, m_effs, mirror_neg, g, h, T
                              _stream(stream)))
 
 
+def ftlm_partition(two_sz, dims, R, M, thetas, weights, m_effs, mirror_neg, h, T, Z, E0=None, stream=None):
+    n = len(two_sz)
+    tz = (ctypes.c_int * n)(*[int(v) for v in two_sz])
+    dm = (ctypes.c_uint64 * n)(*[int(v) for v in dims])
+    th = (ctypes.c_void_p * n)(*[t.data_ptr() for t in thetas])
+    wt = (ctypes.c_void_p * n)(*[t.data_ptr() for t in weights])
+    me = (ctypes.c_void_p * n)(*[t.data_ptr() for t in m_effs])
+    _check(lib().ftlm_partition(n, tz, dm, int(R), int(M), th, wt, me, int(bool(mirror_neg)), float(h), T.numel(),
+                                _ptr(T), _ptr(Z), _ptr(E0), _stream(stream)))
+
+
+def ftlm_ghosts(n, M, alpha, beta, m, theta, weight, c_tau, u, ell, cluster, cweight, flags, count, stream=None):
+    _check(lib().ftlm_ghosts(int(n), int(M), _ptr(alpha), _ptr(beta), _ptr(m), _ptr(theta), _ptr(weight),
+                             float(c_tau), float(u), _ptr(ell), _ptr(cluster), _ptr(cweight), _ptr(flags),
+                             _ptr(count), _stream(stream)))
+
+
+def ftlm_sigma_emp(obs, mean, sigma, stream=None):
+    """obs: (N_s, nT) contiguous float64 device tensor."""
+    _check(lib().ftlm_sigma_emp(int(obs.shape[0]), int(obs.shape[1]), _ptr(obs), _ptr(mean), _ptr(sigma),
+                                _stream(stream)))
+
+
+def ghosts(res, c_tau=1.0, u=2.0**-24, stream=None):
+    """Cullum-Willoughby diagnostic of the chains of a lanczos(..., keep_coeffs=True)
+    result: dict of device tensors ell, cluster, cweight, flags (R x M) and count (R)."""
+    R, M = res["alpha"].shape
+    dev = res["alpha"].device
+    out = {"ell": torch.empty((R, M), dtype=torch.float64, device=dev),
+           "cluster": torch.empty((R, M), dtype=torch.int32, device=dev),
+           "cweight": torch.empty((R, M), dtype=torch.float64, device=dev),
+           "flags": torch.empty((R, M), dtype=torch.int32, device=dev),
+           "count": torch.empty(R, dtype=torch.int32, device=dev)}
+    ftlm_ghosts(R, M, res["alpha"], res["beta"], res["m_eff"], res["theta"], res["weight"], c_tau, u,
+                out["ell"], out["cluster"], out["cweight"], out["flags"], out["count"], stream)
+    return out
+
+
 def ftlm_batch_create(items, M, dist, dtype, block=0, streams=0, stream=None):
     """items: sequence of BatchItem; returns the batch handle."""
     arr = (BatchItem * len(items))(*items)
@@ -323,11 +377,14 @@ def ftlm_profile_read():
 class Basis:
     """One S^z sector of a cluster on the current CUDA device (owns the handle)."""
 
-    def __init__(self, N, two_sz, bonds, mode=RANK_AUTO, stream=None):
+    def __init__(self, N, two_sz, bonds, mode=RANK_AUTO, stream=None, two_s=1):
         bi, bj, J = bonds
-        self.N, self.two_sz = int(N), int(two_sz)
-        self.K = (self.N + self.two_sz) // 2
-        self.handle = ftlm_basis_create(N, two_sz, bi, bj, J, mode, stream)
+        self.N, self.two_sz, self.two_s = int(N), int(two_sz), int(two_s)
+        self.K = (self.N * self.two_s + self.two_sz) // 2  # digit sum (up spins at s = 1/2)
+        if self.two_s == 1:
+            self.handle = ftlm_basis_create(N, two_sz, bi, bj, J, mode, stream)
+        else:
+            self.handle = ftlm_basis_create_spin(N, two_s, two_sz, bi, bj, J, stream)
         self.dim = ftlm_basis_dim(self.handle)
         self.table_bytes = ftlm_basis_bytes(self.handle)
         self.mode = ftlm_basis_mode(self.handle)
@@ -465,9 +522,10 @@ class Batch:
             pass
 
 
-def computed_two_sz(N):
-    """2 S^z of the sectors with S^z >= 0."""
-    return [2 * K - N for K in range((N + 1) // 2, N + 1)]
+def computed_two_sz(N, two_s=1):
+    """2 S^z of the sectors with S^z >= 0 (local spin two_s / 2)."""
+    top = N * two_s
+    return list(range(top % 2, top + 1, 2))
 
 
 def run_ftlm(N, bonds, R, M, T, seed=1, dist=GAUSS, dtype=torch.float32, g=2.0, h=0.0,

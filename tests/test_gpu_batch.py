@@ -127,22 +127,87 @@ def test_batch_rejects_bad_items(cuda_dev):
             ftlm.Batch([(b, 2, 1, 0)], 10, block=3)
 
 
-def _large_batch_bases():
-    # three sectors above 32768 states (ring 18: K = 9, 10; random N = 19: K = 10)
-    # and two small ones, so the batch forks side streams and runs its persistent kernel
+def _mid_sector_bases():
+    # three spin-1/2 sectors above 32768 states (ring 18: K = 9, 10; random N = 19:
+    # K = 10), run by the multi-sector path, and two small ones for the persistent
+    # kernel
     b18 = inputs.ring(18)
     b19 = inputs.random_graph(19, seed=31)
     return [ftlm.Basis(18, 0, b18), ftlm.Basis(18, 2, b18), ftlm.Basis(19, 1, b19),
             ftlm.Basis(18, 8, b18), ftlm.Basis(19, 11, b19)]
 
 
-@pytest.mark.parametrize("block", [4, 16])
+@pytest.mark.parametrize("dtype,rtol", [(torch.float64, 1e-10), (torch.float32, 1e-5)])
+@pytest.mark.parametrize("block", [1, 4, 16])
+def test_multi_sector_path_matches_per_sector_lanczos(cuda_dev, dtype, rtol, block):
+    # R = 6 leaves a partial last unit (nact < block) for block 4 and 16
+    M, R = 30, 6
+    bases = _mid_sector_bases()
+    entries = [(b, R, 40 + i, 2 * i) for i, b in enumerate(bases)]
+    with ftlm.Batch(entries, M, ftlm.GAUSS, dtype, block) as batch:
+        res = batch.run()
+        torch.cuda.synchronize()
+        for (b, _, s, c0), got in zip(entries, res):
+            ref = ftlm.lanczos(b, R + c0, M, seed=s, dist=ftlm.GAUSS, dtype=dtype)
+            torch.cuda.synchronize()
+            m_ref = ref["m_eff"][c0:].cpu().numpy()
+            assert np.array_equal(got["m_eff"].cpu().numpy(), m_ref), (b.N, b.two_sz)
+            np.testing.assert_allclose(spectral_sums(got["theta"], got["weight"], m_ref),
+                                       spectral_sums(ref["theta"][c0:], ref["weight"][c0:], m_ref),
+                                       rtol=rtol, atol=rtol * 1e-3)
+    for b in bases:
+        b.close()
+
+
+def test_multi_sector_results_independent_of_the_mix(cuda_dev):
+    # a unit's arithmetic depends only on its own tiles: bit-identical alone and
+    # together with other sectors
+    M, R = 25, 8
+    bases = _mid_sector_bases()
+    with ftlm.Batch([(bases[0], R, 5, 0)], M, ftlm.RADEMACHER, torch.float32, 8) as alone:
+        a = {k: v.clone() for k, v in alone.run()[0].items()}
+    with ftlm.Batch([(b, R, 5 if i == 0 else 9 + i, 0) for i, b in enumerate(bases)], M, ftlm.RADEMACHER,
+                    torch.float32, 8) as mix:
+        m = mix.run()[0]
+        torch.cuda.synchronize()
+        for k in ("theta", "weight", "m_eff"):
+            assert torch.equal(a[k], m[k]), k
+    for b in bases:
+        b.close()
+
+
+def test_multi_sector_path_matches_oracle(cuda_dev):
+    # every S^z >= 0 sector of a random N = 18 cluster (D up to 48620), FP64
+    N, M, R = 18, 30, 5
+    T = inputs.log_t_grid(50, 0.05, 10.0)
+    bonds = inputs.random_graph(N, seed=44)
+    bases = [ftlm.Basis(N, tz, bonds) for tz in ftlm.computed_two_sz(N)]
+    with ftlm.Batch([(b, R, 7, 0) for b in bases], M, ftlm.GAUSS, torch.float64, 4) as batch:
+        res = batch.run()
+        obs = ftlm.thermo([(b.two_sz, b.dim, r) for b, r in zip(bases, res)], torch.as_tensor(T, device=cuda_dev),
+                          R, M)
+    ref = o.thermo(o.run_ftlm(N, bonds, R, M, seed=7), T)
+    for k in ("E", "C", "chi"):
+        want = ref[k]
+        np.testing.assert_allclose(obs[k].cpu().numpy(), want, rtol=1e-9, atol=1e-12 * np.max(np.abs(want)))
+    for b in bases:
+        b.close()
+
+
+def _n33_bases():
+    # N = 33 ring sectors above 32768 states (K = 29: 40920, K = 28: 237336): the
+    # launch sequence of ftlm_lanczos on side streams; K = 30 (5456) is small
+    bonds = inputs.ring(33)
+    return [ftlm.Basis(33, 2 * K - 33, bonds) for K in (29, 28, 30)]
+
+
+@pytest.mark.parametrize("block", [4, 8])
 def test_side_streams_do_not_change_results(cuda_dev, block):
-    # Large items run ftlm_lanczos's launch sequence with blocks of `block` chains on
-    # side streams: bit-identical for any number of side streams, and equal to
-    # ftlm_lanczos with the same block width on the caller's stream.
-    M, R = 25, 16
-    bases = _large_batch_bases()
+    # Sectors with N > 32 run ftlm_lanczos's launch sequence with blocks of `block`
+    # chains on side streams: bit-identical for any number of side streams, and
+    # equal to ftlm_lanczos with the same block width on the caller's stream.
+    M, R = 25, 8
+    bases = _n33_bases()
     entries = [(b, R, 40 + i, 0) for i, b in enumerate(bases)]
     runs = []
     for streams in (1, 3, 8):
@@ -155,7 +220,7 @@ def test_side_streams_do_not_change_results(cuda_dev, block):
                 assert torch.equal(a[k], b[k]), k
     ftlm.ftlm_lanczos_set_block(block)
     try:
-        for i, b in enumerate(bases[:3]):  # the large items
+        for i, b in enumerate(bases[:2]):  # the side-stream sectors
             ref = ftlm.lanczos(b, R, M, seed=40 + i, dist=ftlm.GAUSS, dtype=torch.float32)
             torch.cuda.synchronize()
             for k in ("theta", "weight", "m_eff"):
@@ -166,9 +231,11 @@ def test_side_streams_do_not_change_results(cuda_dev, block):
         b.close()
 
 
-def test_graph_capture_with_side_streams(cuda_dev):
+def test_graph_capture_with_all_paths(cuda_dev):
+    # persistent kernel, multi-sector path (spin 1/2 and spin 1) and side streams in
+    # one captured run
     M, R = 20, 8
-    bases = _large_batch_bases()
+    bases = _mid_sector_bases() + [ftlm.Basis(8, 0, inputs.ring(8), two_s=2)] + _n33_bases()[:1]
     with ftlm.Batch([(b, R, 3, 0) for b in bases], M, ftlm.RADEMACHER, torch.float32, 8, 3) as batch:
         direct = [{k: v.clone() for k, v in r.items()} for r in batch.run()]
         torch.cuda.synchronize()
@@ -190,13 +257,16 @@ def test_graph_capture_with_side_streams(cuda_dev):
         b.close()
 
 
-def test_autotune_picks_a_timed_candidate(cuda_dev):
+@pytest.mark.parametrize("side_items", [False, True])
+def test_autotune_picks_a_timed_candidate(cuda_dev, side_items):
     M, R = 15, 16
-    bases = _large_batch_bases()
+    bases = _mid_sector_bases()
+    if side_items:
+        bases.append(_n33_bases()[0])
     entries = [(b, R, 1, 0) for b in bases]
     block, streams, times = ftlm.autotune(entries, M, ftlm.GAUSS, torch.float32)
     assert (block, streams) in times
-    assert len(times) == 12  # large items present: 3 widths x 4 stream counts
+    assert len(times) == (12 if side_items else 3)  # stream counts only with side-stream items
     assert times[(block, streams)] == min(times.values())
     # a plan with the tuned parameters runs and agrees with the default plan
     with ftlm.Batch(entries, M, ftlm.GAUSS, torch.float32, block, streams) as tuned:
