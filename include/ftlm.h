@@ -154,7 +154,9 @@ ftlm_status ftlm_basis_clt(const ftlm_basis *basis, uint32_t *mask_dev, uint32_t
 /* -------------------------------------------------------------------- H.v ---
  * ftlm_hv -- y = H x on the sector (step a3; Eq. 12 with Eq. 13-14 at s = 1/2):
  *   y[t] = (sum_b J_b m_i m_j) x[t] + sum_{b antiparallel in n_t} (J_b / 2) x[rank(n_t with
- *          spins i, j exchanged)].
+ *          spins i, j exchanged)];
+ * for a general-spin basis (ftlm_basis_create_spin) the two ladder terms of every
+ * bond with the coefficients of Eq. 13 and Eq. 14.
  * x_dev, y_dev: D elements of dtype (float or double), contiguous; x and y must not
  * overlap.  One thread per row, no atomics.  No scratch memory.
  */
@@ -270,7 +272,7 @@ ftlm_status ftlm_lanczos_noalloc(const ftlm_basis *basis, int R, int M, uint64_t
  *   Larger spin-1/2 sectors (N <= 32) are cut into units of `block` chains that
  *   advance together, all units of a wave per launch (two launches per Lanczos
  *   step: H.v with alpha, update with beta; per-unit reductions over tiles of 2048
- *   rows; waves of at most FTLM_MS_WAVE_MB = 8192 MB of vectors) on a stream
+ *   rows; waves of at most FTLM_MS_WAVE_MB = 256 MB of vectors) on a stream
  *   forked from the caller's.  General-spin sectors and N > 32 run the launch
  *   sequence of ftlm_lanczos with blocks of up to `block` chains, spread over up to
  *   `streams` side streams (1..8; 0 = FTLM_BATCH_STREAMS or 4).  Uploads the plan's descriptors on
@@ -327,9 +329,9 @@ ftlm_status ftlm_batch_autotune(int n_items, const ftlm_batch_item *items, int M
 /* ftlm_ritz -- the Ritz step alone (a5): for each of n chains, the eigenvalues theta
  * and first-component weights w = s_{k,1}^2 of the tridiagonal matrix with diagonal
  * alpha_dev[c*M .. c*M+m-1] and off-diagonal beta_dev[c*M .. c*M+m-2], m = m_dev[c]
- * (0 <= m <= M).  Implicit symmetric QR with Wilkinson shifts in FP64, one CUDA block
- * per chain; outputs ascending, zero past m.  EINVAL for n < 0 or M outside
- * 1..FTLM_MAX_LANCZOS. */
+ * (0 <= m <= M).  Implicit symmetric QR with Wilkinson shifts in FP64, one thread
+ * per chain (up to 32 chains per CTA); outputs ascending, zero past m.  EINVAL for
+ * n < 0 or M outside 1..FTLM_MAX_LANCZOS. */
 ftlm_status ftlm_ritz(int n, int M, const double *alpha_dev, const double *beta_dev,
                       const int *m_dev, double *theta_dev, double *weight_dev, void *stream);
 

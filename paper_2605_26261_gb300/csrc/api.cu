@@ -1,5 +1,6 @@
 // Error reporting and kernel timing shared by every entry point.
 #include <atomic>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -38,6 +39,40 @@ cudaMemPool_t g_pools[256] = {};
 }  // namespace
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+namespace {
+struct OccKey {
+    const void *kern;
+    int threads;
+    size_t smem;
+    bool operator<(const OccKey &o) const
+    {
+        return kern != o.kern ? kern < o.kern : (threads != o.threads ? threads < o.threads : smem < o.smem);
+    }
+};
+std::mutex g_occ_mu;
+std::map<OccKey, int> g_occ;
+}  // namespace
+
+cudaError_t kernel_occupancy(const void *kern, int threads, size_t smem, bool set_smem_attr, int *occ)
+{
+    std::lock_guard<std::mutex> lk(g_occ_mu);
+    const OccKey key{kern, threads, smem};
+    auto it = g_occ.find(key);
+    if (it != g_occ.end()) {
+        *occ = it->second;
+        return cudaSuccess;
+    }
+    cudaError_t e = cudaSuccess;
+    if (set_smem_attr) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int v = 1;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, threads, smem);
+    if (e != cudaSuccess) return e;
+    v = v < 1 ? 1 : v;
+    g_occ[key] = v;
+    *occ = v;
+    return cudaSuccess;
+}
 
 cudaError_t table_pool(int device, cudaMemPool_t *pool)
 {

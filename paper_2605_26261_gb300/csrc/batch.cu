@@ -38,13 +38,16 @@ constexpr int kBatchThreads = 256;
 constexpr uint64_t kSmallRows = 1u << 15;  // sectors up to this dimension run inside one CTA
 constexpr int kMaxSideStreams = 8;
 
-// Vector bytes of one wave of the multi-sector path: FTLM_MS_WAVE_MB or 8192 MB.
+// Vector bytes of one wave of the multi-sector path: FTLM_MS_WAVE_MB or 256 MB.
+// Small waves keep a wave's vectors near the L2 size (measured on GB300 with 256
+// clusters of 18-22 sites: 256 MB waves 9.6 s per run, 2 GB 11.0 s, 8 GB 11.9 s);
+// a unit larger than the budget forms a wave of its own.
 uint64_t ms_wave_bytes()
 {
     static const uint64_t v = [] {
         const char *e = std::getenv("FTLM_MS_WAVE_MB");
-        const long long mb = e ? std::atoll(e) : 8192;
-        return (uint64_t)(mb > 0 ? mb : 8192) << 20;
+        const long long mb = e ? std::atoll(e) : 256;
+        return (uint64_t)(mb > 0 ? mb : 256) << 20;
     }();
     return v;
 }

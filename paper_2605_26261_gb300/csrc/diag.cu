@@ -113,11 +113,8 @@ extern "C" ftlm_status ftlm_ghosts(int n, int M, const double *alpha_dev, const 
         !flags_dev || !count_dev)
         return fail(FTLM_EINVAL, "NULL device pointer");
     constexpr size_t kSmemMax = 96 * 1024;
-    static bool attr_set = false;
-    if (!attr_set) {
-        FTLM_CUDA(cudaFuncSetAttribute(ghost_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
-        attr_set = true;
-    }
+    int occ = 1;
+    FTLM_CUDA(kernel_occupancy((const void *)ghost_kernel, 32, kSmemMax, true, &occ));
     const size_t per_chain = 3 * (size_t)M * sizeof(double);
     int T = (int)(kSmemMax / per_chain);
     T = T < 1 ? 1 : (T > 32 ? 32 : T);

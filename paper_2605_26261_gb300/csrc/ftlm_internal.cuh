@@ -148,6 +148,13 @@ cudaError_t table_pool(int device, cudaMemPool_t *pool);
 // ---- launch count (api.cu): every kernel the library queues calls this once ----
 void note_launch();
 
+// ---- per-kernel launch configuration (api.cu) -------------------------------
+// Resident CTAs per SM of `kern` at `threads` threads and `smem` bytes of dynamic
+// shared memory (at least 1), computed once per (kernel, threads, smem) and cached
+// (thread-safe).  With set_smem_attr the kernel's dynamic shared memory limit is
+// raised to `smem` first.
+cudaError_t kernel_occupancy(const void *kern, int threads, size_t smem, bool set_smem_attr, int *occ);
+
 // ---- kernel timing (api.cu) ----------------------------------------------
 enum ProfileKind { kProfHv = 0, kProfUpdate = 1 };
 // Returns an opaque token (or nullptr when profiling is off) for a launch about to

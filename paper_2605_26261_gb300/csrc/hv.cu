@@ -59,14 +59,12 @@ namespace {
 #ifndef FTLM_B8_MIN_CTAS
 #define FTLM_B8_MIN_CTAS 3
 #endif
-// Build option: 1 issues the CLT lookups of the next bond chunk ahead of the
-// current chunk's accumulation (rows_clt_pipelined).
-#ifndef FTLM_CLT_PIPELINE
-#define FTLM_CLT_PIPELINE 0
-#endif
+
 template <int RT, int B, int C> __host__ __device__ constexpr int min_ctas()
 {
-    return B >= 16 ? 1 : (B >= 8 && C >= 8 ? 2 : (B >= 8 ? FTLM_B8_MIN_CTAS : (B >= 4 || RT >= 4 ? 3 : 6)));
+    return B >= 16 ? 1
+                   : (B >= 8 && C >= 8 ? 2
+                                       : (B >= 8 && C <= 2 ? 4 : (B >= 8 ? FTLM_B8_MIN_CTAS : (B >= 4 || RT >= 4 ? 3 : 6))));
 }
 
 template <typename V, typename Lbl, bool CLT, bool LANCZOS, int RT, int B, int C>
@@ -107,10 +105,7 @@ hv_kernel(const SectorTables s, const BondList bl, const V *__restrict__ x, V *y
 #pragma unroll
             for (int r = 0; r < B; ++r) acc[i][r] = (V)0;
         }
-        if (CLT) {
-            if (FTLM_CLT_PIPELINE) rows_clt_pipelined<V, RT, B, C>(s, bl, s_bond, x, t, acc, dsum);
-            else rows_clt<V, RT, B, C>(s, bl, s_bond, x, t, acc, dsum);
-        }
+        if (CLT) rows_clt<V, RT, B, C>(s, bl, s_bond, x, t, acc, dsum);
         else rows_cr<V, Lbl, RT, B, C>(s, bl, s_bond, s_tlo, x, t, acc, dsum);
 #pragma unroll
         for (int i = 0; i < RT; ++i)
@@ -150,13 +145,11 @@ int hv_cta_cap()
 template <typename V, typename Lbl, bool CLT, bool LANCZOS, int RT, int B, int C>
 ftlm_status launch(const ftlm_basis *b, const V *x, V *y, const EpiDev &ep, cudaStream_t stream)
 {
-    static int occ = -1;  // resident blocks per SM for this instantiation
     const size_t smem = CLT ? 0 : ((size_t)1 << b->L) * sizeof(uint16_t);
     auto kern = hv_kernel<V, Lbl, CLT, LANCZOS, RT, B, C>;
-    if (occ < 0) {
-        const size_t smem_max = CLT ? 0 : ((size_t)1 << kLoBitsMax) * sizeof(uint16_t);
-        FTLM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kRowThreads, smem_max));
-    }
+    int occ = 1;  // resident blocks per SM for this instantiation
+    const size_t smem_max = CLT ? 0 : ((size_t)1 << kLoBitsMax) * sizeof(uint16_t);
+    FTLM_CUDA(kernel_occupancy((const void *)kern, kRowThreads, smem_max, false, &occ));
     const int grid = row_grid(b, (b->D + RT - 1) / RT, std::min(occ, hv_cta_cap()));
     void *tok = profile_begin(kProfHv, stream, B);
     kern<<<grid, kRowThreads, smem, stream>>>(b->tables(), CLT ? b->bonds_clt : b->bonds_cr, x, y, ep);
@@ -166,14 +159,15 @@ ftlm_status launch(const ftlm_basis *b, const V *x, V *y, const EpiDev &ep, cuda
     return FTLM_OK;
 }
 
-// Bonds per chunk for 8-wide blocks (FTLM_HV_CHUNK = 4 or 8 overrides the default
-// of 4): a larger chunk keeps more gathers in flight per row.
+// Bonds per chunk for 8-wide blocks (FTLM_HV_CHUNK = 2, 4 or 8 overrides the
+// default of 4): a larger chunk keeps more gathers in flight per row, a smaller
+// one leaves registers for more resident warps.
 int chunk8()
 {
     static const int c = [] {
         const char *e = getenv("FTLM_HV_CHUNK");
         const int v = e ? atoi(e) : 0;
-        return v == 8 ? 8 : 4;
+        return (v == 8 || v == 2) ? v : 4;
     }();
     return c;
 }
@@ -186,8 +180,11 @@ ftlm_status launch_b(const ftlm_basis *b, int B, const void *x, void *y, const E
     switch (B) {
     case 4: return launch<V, Lbl, CLT, LANCZOS, 1, 4, 8>(b, xv, yv, ep, stream);
     case 8:
-        return chunk8() == 8 ? launch<V, Lbl, CLT, LANCZOS, 1, 8, 8>(b, xv, yv, ep, stream)
-                             : launch<V, Lbl, CLT, LANCZOS, 1, 8, 4>(b, xv, yv, ep, stream);
+        switch (chunk8()) {
+        case 8: return launch<V, Lbl, CLT, LANCZOS, 1, 8, 8>(b, xv, yv, ep, stream);
+        case 2: return launch<V, Lbl, CLT, LANCZOS, 1, 8, 2>(b, xv, yv, ep, stream);
+        default: return launch<V, Lbl, CLT, LANCZOS, 1, 8, 4>(b, xv, yv, ep, stream);
+        }
     case 16: return launch<V, Lbl, CLT, LANCZOS, 1, 16, 4>(b, xv, yv, ep, stream);
     default: break;
     }

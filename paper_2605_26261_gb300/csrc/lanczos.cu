@@ -209,11 +209,8 @@ ftlm_status launch_ritz(int n, int M, const double *alpha, const double *beta, c
 {
     if (n == 0) return FTLM_OK;
     constexpr size_t kSmemMax = 96 * 1024;
-    static bool attr_set = false;
-    if (!attr_set) {
-        FTLM_CUDA(cudaFuncSetAttribute(ritz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
-        attr_set = true;
-    }
+    int occ = 1;
+    FTLM_CUDA(kernel_occupancy((const void *)ritz_kernel, 32, kSmemMax, true, &occ));
     const size_t per_chain = 3 * (size_t)M * sizeof(double);
     int T = (int)(kSmemMax / per_chain);
     T = T < 1 ? 1 : (T > 32 ? 32 : T);
@@ -286,21 +283,14 @@ Layout layout(const ftlm_basis *b, int R, int M, ftlm_dtype dtype, int bmax = 0)
     return l;
 }
 
-int occupancy_of(const void *kern)
-{
-    int occ = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kRowThreads, 0);
-    return occ;
-}
-
 // One block of B chains: start vectors, then min(M, D) fused H.v + update launches.
 template <typename V, int B>
 ftlm_status run_block(const ftlm_basis *b, int M, int r0, int chain0, uint64_t seed, int dist, const double *src,
                       ftlm_dtype dtype, char *ws, const Layout &lay, cudaStream_t stream)
 {
-    static int occ_start = -1, occ_upd = -1;
-    if (occ_start < 0) occ_start = occupancy_of((const void *)start_kernel<V, B>);
-    if (occ_upd < 0) occ_upd = occupancy_of((const void *)update_kernel<V, B>);
+    int occ_start = 1, occ_upd = 1;
+    FTLM_CUDA(kernel_occupancy((const void *)start_kernel<V, B>, kRowThreads, 0, false, &occ_start));
+    FTLM_CUDA(kernel_occupancy((const void *)update_kernel<V, B>, kRowThreads, 0, false, &occ_upd));
     V *vec[2] = {(V *)(ws + lay.vec0), (V *)(ws + lay.vec1)};
     double *partials = (double *)(ws + lay.partials);
     ChainState *st = (ChainState *)(ws + lay.state);

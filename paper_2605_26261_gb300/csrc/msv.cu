@@ -337,27 +337,16 @@ template <typename V, int B> void *ms_hv_ptr(int kind)
     return (void *)ms_hv_kernel<V, kMsCr, B, ms_chunk<B>()>;
 }
 
-int occupancy(const void *kern, size_t smem)
-{
-    int occ = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kRowThreads, smem);
-    return occ < 1 ? 1 : occ;
-}
-
 template <typename V, int B>
 ftlm_status ms_run_typed(const MsWave &w, const MsUnit *units, const uint32_t *tile_unit, int M, int dist,
                          char *ws, double *alpha, double *beta, int *meff, int num_sms, cudaStream_t stream)
 {
     const size_t smem = w.kind == kMsClt ? 0 : ((size_t)1 << kLoBitsMax) * sizeof(uint16_t);
     void *hv = ms_hv_ptr<V, B>(w.kind);
-    static int occ_hv[3] = {0, 0, 0}, occ_start = 0, occ_upd = 0;
-    int &oh = occ_hv[w.kind];
-    if (!oh) {
-        if (smem) FTLM_CUDA(cudaFuncSetAttribute(hv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        oh = occupancy(hv, smem);
-        occ_start = occupancy((const void *)ms_start_kernel<V, B>, 0);
-        occ_upd = occupancy((const void *)ms_update_kernel<V, B>, 0);
-    }
+    int oh = 1, occ_start = 1, occ_upd = 1;
+    FTLM_CUDA(kernel_occupancy(hv, kRowThreads, smem, smem != 0, &oh));
+    FTLM_CUDA(kernel_occupancy((const void *)ms_start_kernel<V, B>, kRowThreads, 0, false, &occ_start));
+    FTLM_CUDA(kernel_occupancy((const void *)ms_update_kernel<V, B>, kRowThreads, 0, false, &occ_upd));
     auto grid = [&](int occ) { return (int)std::min<uint64_t>(w.n_tiles, (uint64_t)num_sms * occ); };
     {
         const uint32_t words = (kMaxBlock * sizeof(ChainState) + 64) / sizeof(uint32_t);

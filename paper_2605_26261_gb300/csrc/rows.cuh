@@ -180,87 +180,6 @@ __device__ __forceinline__ void rows_clt(const SectorTables &s, const BondList &
     }
 }
 
-// CLT lookups of one chunk: exchange flags and the {M_b, C_b} entries of the
-// exchanged labels (loads issued, not yet used).
-template <int RT, int C>
-__device__ __forceinline__ void clt_lookups(const SectorTables &s, const uint32_t (&n)[RT], const uint32_t (&mlo)[C],
-                                            bool (&aa)[RT][C], uint2 (&e2)[RT][C])
-{
-#pragma unroll
-    for (int i = 0; i < RT; ++i)
-#pragma unroll
-        for (int q = 0; q < C; ++q) {
-            const uint32_t m = mlo[q], xm = n[i] & m;
-            aa[i][q] = (xm != 0u) & (xm != m);
-            e2[i][q] = aa[i][q] ? __ldg(s.clt + ((n[i] ^ m) >> 5)) : make_uint2(0u, 0u);
-        }
-}
-
-// rows_clt with the CLT lookups of the next chunk issued before the current
-// chunk's gathers are consumed, so the two dependent loads of a term (CLT entry,
-// then x) of consecutive chunks overlap.
-template <typename V, int RT, int B, int C, bool NC = true>
-__device__ __forceinline__ void rows_clt_pipelined(const SectorTables &s, const BondList &bl, const uint4 *s_bond,
-                                                   const V *__restrict__ x, const uint32_t (&t)[RT],
-                                                   V (&acc)[RT][B], V (&dsum)[RT])
-{
-    uint32_t n[RT];
-#pragma unroll
-    for (int i = 0; i < RT; ++i) n[i] = __ldcs(s.basis + t[i]);
-    Chunk<V, C> c, cn;
-    bool aa[RT][C], an[RT][C];
-    uint2 e2[RT][C], en[RT][C];
-    load_chunk(s_bond, 0, c);
-    clt_lookups<RT, C>(s, n, c.mlo, aa, e2);
-    for (int b0 = 0; b0 < bl.nb; b0 += C) {
-        uint32_t kk[RT][C];
-#pragma unroll
-        for (int i = 0; i < RT; ++i)
-#pragma unroll
-            for (int q = 0; q < C; ++q) {
-                const uint32_t nn = n[i] ^ c.mlo[q];
-                kk[i][q] = e2[i][q].y + __popc(e2[i][q].x & ((1u << (nn & 31u)) - 1u));
-            }
-        V xv[RT][C][B];
-#pragma unroll
-        for (int i = 0; i < RT; ++i)
-#pragma unroll
-            for (int q = 0; q < C; ++q) {
-                if (aa[i][q]) {
-                    if constexpr (NC) ld_vec<B>(x + (size_t)kk[i][q] * B, xv[i][q], false);
-                    else ld_vec_coherent<B>(x + (size_t)kk[i][q] * B, xv[i][q]);
-                } else {
-#pragma unroll
-                    for (int r = 0; r < B; ++r) xv[i][q][r] = (V)0;
-                }
-            }
-        const bool more = b0 + C < bl.nb;  // warp-uniform
-        if (more) {
-            load_chunk(s_bond, b0 + C, cn);
-            clt_lookups<RT, C>(s, n, cn.mlo, an, en);
-        }
-#pragma unroll
-        for (int i = 0; i < RT; ++i)
-#pragma unroll
-            for (int q = 0; q < C; ++q)
-                if (aa[i][q]) {
-#pragma unroll
-                    for (int r = 0; r < B; ++r) acc[i][r] = fma(c.jh[q], xv[i][q][r], acc[i][r]);
-                    dsum[i] += c.jh[q];
-                }
-        if (more) {
-            c = cn;
-#pragma unroll
-            for (int i = 0; i < RT; ++i)
-#pragma unroll
-                for (int q = 0; q < C; ++q) {
-                    aa[i][q] = an[i][q];
-                    e2[i][q] = en[i][q];
-                }
-        }
-    }
-}
-
 // One warp owns a tile of 32 RT consecutive rows; lane l handles rows
 // tile_base + l + 32 i (i < RT).  Tiles are dealt to warps round-robin, so the
 // whole grid works on one contiguous window of rows at a time.

@@ -141,13 +141,10 @@ int grid_of(const ftlm_basis *b, uint64_t n)
 template <typename V, bool LANCZOS, int B>
 ftlm_status launch_spin(const ftlm_basis *b, const V *x, V *y, const EpiDev &ep, cudaStream_t stream)
 {
-    static int occ = -1;
     auto kern = hv_spin_kernel<V, LANCZOS, B>;
     const size_t smem_max = kSpinMaxLow * sizeof(uint16_t);
-    if (occ < 0) {
-        FTLM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
-        FTLM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kRowThreads, smem_max));
-    }
+    int occ = 1;
+    FTLM_CUDA(kernel_occupancy((const void *)kern, kRowThreads, smem_max, true, &occ));
     const size_t smem = (size_t)(b->tables().lomask + 1) * sizeof(uint16_t);
     const int grid = row_grid(b, b->D, occ);
     void *tok = profile_begin(kProfHv, stream, B);
