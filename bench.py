@@ -78,6 +78,7 @@ def parse_args():
     p.add_argument("--jobs", type=int, default=128, help="serving: requests in the timed stream")
     p.add_argument("--slots", type=int, default=4, help="serving: concurrent groups (CUDA streams)")
     p.add_argument("--seeds", type=int, default=8, help="precision: independent FTLM runs for sigma_emp")
+    p.add_argument("--clusters", type=int, default=256, help="clusters256: use the first n clusters (profiling)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--hv-only", action="store_true",
                    help="time plain ftlm_hv launches on the workload (kernel microbenchmark)")
@@ -547,7 +548,7 @@ def run_clusters(args):
     dev = torch.device("cuda", local)
     R, M = 16, 100
     dt = torch.float32
-    clusters = inputs.cluster_set(256, seed=256)
+    clusters = inputs.cluster_set(256, seed=256)[:args.clusters]
     T_host = inputs.log_t_grid(200)
     T = torch.as_tensor(T_host, device=dev)
 
@@ -685,7 +686,9 @@ def run_clusters(args):
         "metric": METRIC, "value": value, "unit": "Gupdates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOADS["clusters256"]["desc"], "sectors": sum(len(bs) for bs in bases),
+        "config": {"workload": WORKLOADS["clusters256"]["desc"] if len(clusters) == 256 else
+                   f"the first {len(clusters)} clusters of " + WORKLOADS["clusters256"]["desc"],
+                   "sectors": sum(len(bs) for bs in bases),
                    "rows_small_sectors": small_rows, "rows_large_sectors": large_rows,
                    "block": block, "side_streams": streams,
                    "autotune": {f"B{k[0]}_s{k[1]}": round(v, 2) for k, v in tune_times.items()},

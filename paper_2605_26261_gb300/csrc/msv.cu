@@ -44,23 +44,31 @@ struct UnitView {
 
 // Store this tile's B block sums at tile slot k of the unit; returns true (in every
 // thread) in the CTA that completes the unit.
+// The B sums share three barriers: warp trees for every chain, then thread r adds
+// chain r's warp sums in warp order (fixed order, reproducible).
 template <int B>
 __device__ __forceinline__ bool tile_publish(const double (&part)[B], double *partials, uint32_t k,
                                              unsigned int *counter, uint32_t n_tiles)
 {
-    __shared__ double s_part[B];
+    constexpr int kWarps = kRowThreads / 32;
+    __shared__ double s_w[kWarps][B];
     __shared__ bool s_last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int r = 0; r < B; ++r) {
-        const double v = block_sum<kRowThreads>(part[r]);
-        if (threadIdx.x == 0) s_part[r] = v;
+        const double v = warp_sum(part[r]);
+        if (lane == 0) s_w[wid][r] = v;
     }
-    if (threadIdx.x == 0) {
+    __syncthreads();
+    if (threadIdx.x < B) {
+        double t = 0.0;
 #pragma unroll
-        for (int r = 0; r < B; ++r) partials[(size_t)k * B + r] = s_part[r];
+        for (int i = 0; i < kWarps; ++i) t += s_w[i][threadIdx.x];
+        partials[(size_t)k * B + threadIdx.x] = t;
         __threadfence();
-        s_last = atomicAdd(counter, 1u) == n_tiles - 1;
     }
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(counter, 1u) == n_tiles - 1;
     __syncthreads();
     return s_last;
 }
@@ -123,8 +131,15 @@ ms_start_kernel(const MsUnit *__restrict__ units, const uint32_t *__restrict__ t
 
 // Step j: y = H q_j - beta_{j-1} q_{j-1} over the u_{j-1} block and alpha_j, for
 // every tile of every unit (x = u_j is block (j - 1) % 2, y block j % 2).
+// Resident CTAs per SM the registers are cut for: FP32 blocks up to 8 fit 3 CTAs
+// without spills (FP64 blocks of 4 and 8 need 2), single vectors 4.
+template <typename V, int B> __host__ __device__ constexpr int ms_min_ctas()
+{
+    return B >= 16 ? 1 : (sizeof(V) == 8 && B >= 4 ? 2 : (B >= 4 ? 3 : 4));
+}
+
 template <typename V, int KIND, int B, int C>
-__global__ void __launch_bounds__(kRowThreads, B >= 16 ? 1 : 2)
+__global__ void __launch_bounds__(kRowThreads, ms_min_ctas<V, B>())
 ms_hv_kernel(const MsUnit *__restrict__ units, const uint32_t *__restrict__ tile_unit, uint32_t n_tiles, int j,
              int M, double *alpha, char *ws)
 {

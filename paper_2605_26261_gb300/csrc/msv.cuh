@@ -5,7 +5,11 @@
 
 namespace ftlm {
 
-constexpr uint32_t kMsTileRows = 2048;  // rows per tile (a multiple of kRowThreads)
+// Rows per tile (a multiple of kRowThreads); build option FTLM_MS_TILE_ROWS.
+#ifndef FTLM_MS_TILE_ROWS
+#define FTLM_MS_TILE_ROWS 2048
+#endif
+constexpr uint32_t kMsTileRows = FTLM_MS_TILE_ROWS;
 
 // One block of B chains of one sector.  Offsets are into the run's workspace.
 struct MsUnit {

@@ -17,7 +17,9 @@ import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libftlm.so")
+# FTLM_LIBRARY selects another build of the library (e.g. one compiled with other
+# -D options); by default the in-tree libftlm.so next to this file.
+LIB_PATH = os.environ.get("FTLM_LIBRARY") or os.path.join(_HERE, "libftlm.so")
 
 FTLM_OK, FTLM_EINVAL, FTLM_ENOMEM, FTLM_EUNSUPPORTED, FTLM_ECUDA, FTLM_ETIMEOUT = range(6)
 RANK_AUTO, RANK_CLT, RANK_CR = 0, 1, 2

@@ -100,3 +100,57 @@ def test_profile_toggle_without_gpu(lib):
                                  ctypes.byref(d)) == 0
     assert a.value == 0 and v.value == 0 and c.value == 0
     assert lib.ftlm_profile_enable(0) == 0
+
+
+def _create_spin(lib, N, two_s, two_sz, bonds):
+    bi = np.ascontiguousarray([b[0] for b in bonds], dtype=np.int32)
+    bj = np.ascontiguousarray([b[1] for b in bonds], dtype=np.int32)
+    J = np.ascontiguousarray([b[2] for b in bonds], dtype=np.float64)
+    out = ctypes.c_void_p()
+    lib.ftlm_basis_create_spin.restype = ctypes.c_int
+    st = lib.ftlm_basis_create_spin(N, two_s, two_sz, len(J), ctypes.c_void_p(bi.ctypes.data),
+                                    ctypes.c_void_p(bj.ctypes.data), ctypes.c_void_p(J.ctypes.data), None,
+                                    ctypes.byref(out))
+    return st, out
+
+
+@pytest.mark.parametrize("N,two_s,two_sz,bonds,want", [
+    (6, 0, 0, [(0, 1, 1.0)], 1),                 # two_s < 1
+    (6, 2, 1, [(0, 1, 1.0)], 1),                 # parity of two_sz
+    (6, 2, 14, [(0, 1, 1.0)], 1),                # |two_sz| > N two_s
+    (6, 8, 0, [(0, 1, 1.0)], 3),                 # s = 4 > 7/2
+    (17, 2, 0, [(0, 1, 1.0)], 3),                # N > 16 at s > 1/2
+    (6, 2, 0, [(0, 0, 1.0)], 1),                 # self bond
+    (6, 2, 0, [(0, 1, 1.0), (1, 0, 1.0)], 1),    # duplicate pair
+    (6, 2, 0, [(0, 6, 1.0)], 1),                 # site out of range
+    (6, 1, 1, [(0, 1, 1.0)], 1),                 # two_s = 1: the spin-1/2 checks (parity)
+])
+def test_create_spin_rejects_bad_arguments(lib, N, two_s, two_sz, bonds, want):
+    st, out = _create_spin(lib, N, two_s, two_sz, bonds)
+    assert st == want and not out.value
+
+
+def test_new_entry_points_validate_without_a_device(lib):
+    P = ctypes.c_void_p
+    lib.ftlm_lanczos_set_block.restype = ctypes.c_int
+    assert lib.ftlm_lanczos_set_block(3) == 1
+    assert lib.ftlm_lanczos_set_block(0) == 0
+    assert lib.ftlm_launch_count(None) == 1
+    n = ctypes.c_uint64()
+    assert lib.ftlm_launch_count(ctypes.byref(n)) == 0
+    assert lib.ftlm_basis_destroy_async(None, None) == 0
+    assert lib.ftlm_batch_destroy_async(None, None) == 0
+    lib.ftlm_ghosts.argtypes = [ctypes.c_int, ctypes.c_int] + [P] * 5 + [ctypes.c_double] * 2 + [P] * 6
+    assert lib.ftlm_ghosts(-1, 10, *([None] * 5), 1.0, 1e-7, *([None] * 6)) == 1
+    assert lib.ftlm_ghosts(1, 0, *([None] * 5), 1.0, 1e-7, *([None] * 6)) == 1
+    assert lib.ftlm_ghosts(1, 10, *([None] * 5), -1.0, 1e-7, *([None] * 6)) == 1
+    assert lib.ftlm_ghosts(0, 10, *([None] * 5), 1.0, 1e-7, *([None] * 6)) == 0  # nothing to do
+    assert lib.ftlm_sigma_emp(0, 5, None, None, None, None) == 1
+    assert lib.ftlm_sigma_emp(2, 0, None, None, None, None) == 0
+    lib.ftlm_partition.argtypes = [ctypes.c_int, P, P, ctypes.c_int, ctypes.c_int, P, P, P, ctypes.c_int,
+                                   ctypes.c_double, ctypes.c_int, P, P, P, P]
+    assert lib.ftlm_partition(0, None, None, 1, 1, None, None, None, 1, 0.0, 1, None, None, None, None) == 1
+    lib.ftlm_batch_create.argtypes = [ctypes.c_int, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_int, P, ctypes.POINTER(P)]
+    out = P()
+    assert lib.ftlm_batch_create(0, None, 10, 0, 1, 0, 0, None, ctypes.byref(out)) == 1  # empty batch

@@ -200,3 +200,21 @@ def test_fp32_dot_products_accumulate_to_fp64_accuracy(cuda_dev, R):
         ref = float(np.sum(q * y))
         got = float(res["alpha"][r, 0])
         assert abs(got - ref) <= 1e-12 * abs(ref), (got, ref)
+
+
+@pytest.mark.parametrize("two_s", [1, 2])
+def test_no_bonds_gives_zero_hamiltonian(cuda_dev, two_s):
+    # H = 0: H.v is zero, every chain breaks down after one step with theta = 0
+    empty = (np.zeros(0, dtype=np.int32), np.zeros(0, dtype=np.int32), np.zeros(0))
+    N = 8
+    with ftlm.Basis(N, 0, empty, two_s=two_s) as b:
+        assert b.updates == b.dim
+        x = torch.ones(b.dim, dtype=torch.float64, device=cuda_dev)
+        y = torch.empty_like(x)
+        ftlm.ftlm_hv(b.handle, x, y)
+        assert torch.count_nonzero(y).item() == 0
+        res = ftlm.lanczos(b, 4, 10, dtype=torch.float32)
+        torch.cuda.synchronize()
+        assert res["m_eff"].tolist() == [1] * 4
+        assert torch.all(res["theta"] == 0).item()
+        assert torch.all(res["weight"][:, 0] == 1).item()
