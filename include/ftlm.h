@@ -48,7 +48,7 @@ typedef enum {
     FTLM_OK = 0,
     FTLM_EINVAL = 1,       /* an argument is out of range or inconsistent          */
     FTLM_ENOMEM = 2,       /* device allocation failed / workspace too small       */
-    FTLM_EUNSUPPORTED = 3, /* valid request outside what this build implements     */
+    FTLM_EUNSUPPORTED = 3, /* valid request outside what the library implements    */
     FTLM_ECUDA = 4,        /* a CUDA runtime call failed                           */
     FTLM_ETIMEOUT = 5      /* reserved: a bounded device wait expired              */
 } ftlm_status;

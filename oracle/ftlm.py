@@ -62,6 +62,8 @@ def lib():
         L.or_lanczos.argtypes = [c_int, P, P, P, P, c_i64, P, P, c_int, c_dbl, P, P]
         L.or_num_threads.restype = c_int
         L.or_num_threads.argtypes = []
+        L.or_set_num_threads.restype = None
+        L.or_set_num_threads.argtypes = [c_int]
         L.or_spin_basis_enumerate.restype = c_i64
         L.or_spin_basis_enumerate.argtypes = [c_int, c_int, c_int, P, c_i64]
         L.or_spin_hv_range.restype = None
@@ -86,6 +88,11 @@ def _bonds(bonds):
 
 def num_threads():
     return lib().or_num_threads()
+
+
+def set_num_threads(n):
+    """Threads of the oracle's OpenMP loops from now on (n >= 1)."""
+    lib().or_set_num_threads(int(n))
 
 
 # ---------------------------------------------------------------- sector tables

@@ -384,6 +384,17 @@ int64_t or_spin_offdiag_terms(int N, int two_s, int nb, const int *bi, const int
     return cnt;
 }
 
+/* Threads of the following OpenMP loops (ignored when built without OpenMP). */
+void or_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* Number of OpenMP threads the H.v loop uses (1 when built without OpenMP). */
 int or_num_threads(void)
 {

@@ -180,7 +180,7 @@ extern "C" const char *ftlm_status_string(ftlm_status s)
     case FTLM_OK: return "FTLM_OK";
     case FTLM_EINVAL: return "FTLM_EINVAL: invalid argument";
     case FTLM_ENOMEM: return "FTLM_ENOMEM: out of device memory or workspace too small";
-    case FTLM_EUNSUPPORTED: return "FTLM_EUNSUPPORTED: outside what this build implements";
+    case FTLM_EUNSUPPORTED: return "FTLM_EUNSUPPORTED: outside what the library implements";
     case FTLM_ECUDA: return "FTLM_ECUDA: CUDA runtime error";
     case FTLM_ETIMEOUT: return "FTLM_ETIMEOUT: device wait expired";
     }

@@ -9,7 +9,7 @@
 // from the bottom, at position p_k, contributes C(p_k, k).
 //
 // The paper's first GPU adaptation replaces the per-digit inner scan by one table
-// lookup per digit.  This build takes the same step for a whole block of digits:
+// lookup per digit.  The library takes the same step for a whole block of digits:
 // split the label n into a low block l (the L lowest bits) and a high block h.
 // The contributions of the low bits depend only on l (their k counts only bits
 // below them): tlo[l].  The contributions of the high bits depend on h and on the

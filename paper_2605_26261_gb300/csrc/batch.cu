@@ -349,6 +349,7 @@ struct ftlm_batch {
     std::vector<MsWave> waves;
     MsUnit *d_ms_units;
     uint32_t *d_tile_unit;
+    uint32_t *d_stile_unit;
     uint64_t off_ms;
     int num_sms;
     cudaStream_t ms_stream;
@@ -476,7 +477,7 @@ extern "C" ftlm_status ftlm_batch_create(int n, const ftlm_batch_item *items, in
     // ms region of the workspace (each wave reuses it).
     const uint64_t vsize = dtype == FTLM_F32 ? 4 : 8;
     std::vector<MsUnit> ms_units;
-    std::vector<uint32_t> tile_unit;
+    std::vector<uint32_t> tile_unit, stile_unit;
     uint64_t ms_bytes = 0;
     p->n_chains = p->n_small_chains;
     auto kind_of = [](const ftlm_basis *b) {
@@ -504,8 +505,10 @@ extern "C" ftlm_status ftlm_batch_create(int n, const ftlm_batch_item *items, in
                 if (!w.n_units) {
                     w.unit0 = (uint32_t)ms_units.size();
                     w.tile_off = (uint32_t)tile_unit.size();
+                    w.stile_off = (uint32_t)stile_unit.size();
                     w.kind = kind;
                 }
+                const uint32_t nst = (uint32_t)((b->D + kMsStreamRows - 1) / kMsStreamRows);
                 MsUnit u{};
                 u.s = b->tables();
                 u.bl = b->mode == FTLM_RANK_CLT ? b->bonds_clt : b->bonds_cr;
@@ -518,6 +521,8 @@ extern "C" ftlm_status ftlm_batch_create(int n, const ftlm_batch_item *items, in
                 u.tau = dtype == FTLM_F32 ? b->tau32 : b->tau64;
                 u.tile0 = w.n_tiles;
                 u.n_tiles = nt;
+                u.stile0 = w.n_stiles;
+                u.n_stiles = nst;
                 u.chain_base = p->n_chains + (uint32_t)r0;
                 u.key_n = b->key_n;
                 u.K = b->K;
@@ -525,8 +530,10 @@ extern "C" ftlm_status ftlm_batch_create(int n, const ftlm_batch_item *items, in
                 u.nact = std::min(B, items[i].R - r0);
                 u.m_max = (uint64_t)M < b->D ? M : (int)b->D;
                 for (uint32_t k = 0; k < nt; ++k) tile_unit.push_back(w.n_units);  // wave-local unit index
+                for (uint32_t k = 0; k < nst; ++k) stile_unit.push_back(w.n_units);
                 w.n_units += 1;
                 w.n_tiles += nt;
+                w.n_stiles += nst;
                 w.m_max = std::max(w.m_max, u.m_max);
                 wbytes += ub;
                 ms_units.push_back(u);
@@ -592,7 +599,8 @@ extern "C" ftlm_status ftlm_batch_create(int n, const ftlm_batch_item *items, in
     const uint64_t o_scatter = align256(o_units + units.size() * sizeof(BatchUnitDev));
     const uint64_t o_ms = align256(o_scatter + scatter.size() * sizeof(ScatterDev));
     const uint64_t o_tiles = align256(o_ms + ms_units.size() * sizeof(MsUnit));
-    const uint64_t desc_bytes = std::max<uint64_t>(256, align256(o_tiles + tile_unit.size() * sizeof(uint32_t)));
+    const uint64_t o_stiles = align256(o_tiles + tile_unit.size() * sizeof(uint32_t));
+    const uint64_t desc_bytes = std::max<uint64_t>(256, align256(o_stiles + stile_unit.size() * sizeof(uint32_t)));
     std::vector<unsigned char> image(desc_bytes, 0);
     if (!hitems.empty()) std::memcpy(image.data() + o_items, hitems.data(), hitems.size() * sizeof(BatchItemDev));
     if (!units.empty()) std::memcpy(image.data() + o_units, units.data(), units.size() * sizeof(BatchUnitDev));
@@ -601,6 +609,8 @@ extern "C" ftlm_status ftlm_batch_create(int n, const ftlm_batch_item *items, in
     if (!ms_units.empty()) std::memcpy(image.data() + o_ms, ms_units.data(), ms_units.size() * sizeof(MsUnit));
     if (!tile_unit.empty())
         std::memcpy(image.data() + o_tiles, tile_unit.data(), tile_unit.size() * sizeof(uint32_t));
+    if (!stile_unit.empty())
+        std::memcpy(image.data() + o_stiles, stile_unit.data(), stile_unit.size() * sizeof(uint32_t));
     int device = 0;
     cudaMemPool_t pool = nullptr;
     cudaError_t e = cudaGetDevice(&device);
@@ -613,6 +623,7 @@ extern "C" ftlm_status ftlm_batch_create(int n, const ftlm_batch_item *items, in
         p->d_scatter = reinterpret_cast<ScatterDev *>(base + o_scatter);
         p->d_ms_units = reinterpret_cast<MsUnit *>(base + o_ms);
         p->d_tile_unit = reinterpret_cast<uint32_t *>(base + o_tiles);
+        p->d_stile_unit = reinterpret_cast<uint32_t *>(base + o_stiles);
         e = cudaMemcpyAsync(base, image.data(), desc_bytes, cudaMemcpyHostToDevice, stream);
     }
     for (int g = 0; g < 3 && e == cudaSuccess; ++g)
@@ -685,8 +696,9 @@ extern "C" ftlm_status ftlm_batch_run(const ftlm_batch *p, void *work_dev, uint6
     if (!p->waves.empty()) {
         FTLM_CUDA(cudaStreamWaitEvent(p->ms_stream, p->ev_fork, 0));
         for (const MsWave &w : p->waves) {
-            ftlm_status s = ms_run_wave(w, p->dtype, p->B, p->d_ms_units + w.unit0, p->d_tile_unit + w.tile_off, M,
-                                        p->dist, ws + p->off_ms, alpha, beta, meff, p->num_sms, p->ms_stream);
+            ftlm_status s = ms_run_wave(w, p->dtype, p->B, p->d_ms_units + w.unit0, p->d_tile_unit + w.tile_off,
+                                        p->d_stile_unit + w.stile_off, M, p->dist, ws + p->off_ms, alpha, beta, meff,
+                                        p->num_sms, p->ms_stream);
             if (s != FTLM_OK) return s;
         }
         FTLM_CUDA(cudaEventRecord(p->ev_ms_join, p->ms_stream));

@@ -90,14 +90,14 @@ ms_start_kernel(const MsUnit *__restrict__ units, const uint32_t *__restrict__ t
     for (uint32_t g = blockIdx.x; g < n_tiles; g += gridDim.x) {
         const UnitView uv{units + tile_unit[g], ws};
         const MsUnit &U = *uv.u;
-        const uint32_t k = g - U.tile0, D = U.s.D;
+        const uint32_t k = g - U.stile0, D = U.s.D;
         uint64_t key[B];
 #pragma unroll
         for (int r = 0; r < B; ++r) key[r] = chain_key(U.seed, U.key_n, U.K, (uint32_t)(U.chain0 + r));
         V *u0 = uv.vec<V>(0);
         DotAcc<V> acc[B];
-        const uint32_t row1 = min(D, (k + 1) * kMsTileRows);
-        for (uint32_t t = k * kMsTileRows + threadIdx.x; t < row1; t += kRowThreads) {
+        const uint32_t row1 = min(D, (k + 1) * kMsStreamRows);
+        for (uint32_t t = k * kMsStreamRows + threadIdx.x; t < row1; t += kRowThreads) {
             V out[B];
 #pragma unroll
             for (int r = 0; r < B; ++r) {
@@ -109,10 +109,10 @@ ms_start_kernel(const MsUnit *__restrict__ units, const uint32_t *__restrict__ t
         double part[B];
 #pragma unroll
         for (int r = 0; r < B; ++r) part[r] = acc[r].value();
-        if (tile_publish<B>(part, uv.partials(), k, uv.counter(), U.n_tiles) && threadIdx.x < 32) {
+        if (tile_publish<B>(part, uv.partials(), k, uv.counter(), U.n_stiles) && threadIdx.x < 32) {
             ChainState *st = uv.st();
             for (int r = 0; r < B; ++r) {
-                const double nrm = sqrt(tile_total<B>(uv.partials(), U.n_tiles, r));
+                const double nrm = sqrt(tile_total<B>(uv.partials(), U.n_stiles, r));
                 if (threadIdx.x == 0) {
                     ChainState &c = st[r];
                     c.s_cur = nrm;
@@ -262,7 +262,7 @@ ms_update_kernel(const MsUnit *__restrict__ units, const uint32_t *__restrict__ 
             __syncthreads();
         }
         if (s_skip) continue;
-        const uint32_t k = g - U.tile0, D = U.s.D;
+        const uint32_t k = g - U.stile0, D = U.s.D;
         V *y = uv.vec<V>(j & 1);
         const V *u = uv.vec<V>((j - 1) & 1);
         V a[B];
@@ -273,8 +273,8 @@ ms_update_kernel(const MsUnit *__restrict__ units, const uint32_t *__restrict__ 
             zero[r] = s_zero[r] != 0;
         }
         DotAcc<V> acc[B];
-        const uint64_t e0 = (uint64_t)k * kMsTileRows * B;
-        const uint64_t e1 = (uint64_t)min(D, (k + 1) * kMsTileRows) * B;
+        const uint64_t e0 = (uint64_t)k * kMsStreamRows * B;
+        const uint64_t e1 = (uint64_t)min(D, (k + 1) * kMsStreamRows) * B;
         const uint64_t full = e0 + (e1 - e0) / U_ * U_;
         for (uint64_t e = e0 + (uint64_t)threadIdx.x * U_; e < full; e += (uint64_t)kRowThreads * U_) {
             V yv[U_], xv[U_], w[U_];
@@ -296,10 +296,10 @@ ms_update_kernel(const MsUnit *__restrict__ units, const uint32_t *__restrict__ 
         double part[B];
 #pragma unroll
         for (int r = 0; r < B; ++r) part[r] = acc[r].value();
-        if (tile_publish<B>(part, uv.partials(), k, uv.counter(), U.n_tiles) && threadIdx.x < 32) {
+        if (tile_publish<B>(part, uv.partials(), k, uv.counter(), U.n_stiles) && threadIdx.x < 32) {
             ChainState *st = uv.st();
             for (int r = 0; r < B; ++r) {
-                const double bt = sqrt(tile_total<B>(uv.partials(), U.n_tiles, r));
+                const double bt = sqrt(tile_total<B>(uv.partials(), U.n_stiles, r));
                 if (threadIdx.x == 0 && !st[r].stopped) {
                     ChainState &c = st[r];
                     if (j < U.m_max) {
@@ -353,8 +353,9 @@ template <typename V, int B> void *ms_hv_ptr(int kind)
 }
 
 template <typename V, int B>
-ftlm_status ms_run_typed(const MsWave &w, const MsUnit *units, const uint32_t *tile_unit, int M, int dist,
-                         char *ws, double *alpha, double *beta, int *meff, int num_sms, cudaStream_t stream)
+ftlm_status ms_run_typed(const MsWave &w, const MsUnit *units, const uint32_t *tile_unit,
+                         const uint32_t *stile_unit, int M, int dist, char *ws, double *alpha, double *beta,
+                         int *meff, int num_sms, cudaStream_t stream)
 {
     const size_t smem = w.kind == kMsClt ? 0 : ((size_t)1 << kLoBitsMax) * sizeof(uint16_t);
     void *hv = ms_hv_ptr<V, B>(w.kind);
@@ -363,13 +364,14 @@ ftlm_status ms_run_typed(const MsWave &w, const MsUnit *units, const uint32_t *t
     FTLM_CUDA(kernel_occupancy((const void *)ms_start_kernel<V, B>, kRowThreads, 0, false, &occ_start));
     FTLM_CUDA(kernel_occupancy((const void *)ms_update_kernel<V, B>, kRowThreads, 0, false, &occ_upd));
     auto grid = [&](int occ) { return (int)std::min<uint64_t>(w.n_tiles, (uint64_t)num_sms * occ); };
+    auto sgrid = [&](int occ) { return (int)std::min<uint64_t>(w.n_stiles, (uint64_t)num_sms * occ); };
     {
         const uint32_t words = (kMaxBlock * sizeof(ChainState) + 64) / sizeof(uint32_t);
         const int g = (int)std::min<uint64_t>(((uint64_t)w.n_units * words + 255) / 256, (uint64_t)num_sms * 4);
         ms_reset_kernel<<<g, 256, 0, stream>>>(units, w.n_units, ws);
         note_launch();
     }
-    ms_start_kernel<V, B><<<grid(occ_start), kRowThreads, 0, stream>>>(units, tile_unit, w.n_tiles, dist, ws);
+    ms_start_kernel<V, B><<<sgrid(occ_start), kRowThreads, 0, stream>>>(units, stile_unit, w.n_stiles, dist, ws);
     note_launch();
     FTLM_CUDA(cudaGetLastError());
     for (int j = 1; j <= w.m_max; ++j) {
@@ -382,7 +384,8 @@ ftlm_status ms_run_typed(const MsWave &w, const MsUnit *units, const uint32_t *t
         note_launch();
         profile_end(tok, stream);
         tok = profile_begin(kProfUpdate, stream);
-        ms_update_kernel<V, B><<<grid(occ_upd), kRowThreads, 0, stream>>>(units, tile_unit, w.n_tiles, j, M, beta, ws);
+        ms_update_kernel<V, B><<<sgrid(occ_upd), kRowThreads, 0, stream>>>(units, stile_unit, w.n_stiles, j, M,
+                                                                            beta, ws);
         note_launch();
         profile_end(tok, stream);
         FTLM_CUDA(cudaGetLastError());
@@ -394,27 +397,28 @@ ftlm_status ms_run_typed(const MsWave &w, const MsUnit *units, const uint32_t *t
 }
 
 template <typename V>
-ftlm_status ms_run_v(const MsWave &w, int B, const MsUnit *units, const uint32_t *tile_unit, int M, int dist,
-                     char *ws, double *alpha, double *beta, int *meff, int num_sms, cudaStream_t stream)
+ftlm_status ms_run_v(const MsWave &w, int B, const MsUnit *units, const uint32_t *tu, const uint32_t *su, int M,
+                     int dist, char *ws, double *alpha, double *beta, int *meff, int num_sms, cudaStream_t stream)
 {
     switch (B) {
-    case 16: return ms_run_typed<V, 16>(w, units, tile_unit, M, dist, ws, alpha, beta, meff, num_sms, stream);
-    case 8: return ms_run_typed<V, 8>(w, units, tile_unit, M, dist, ws, alpha, beta, meff, num_sms, stream);
-    case 4: return ms_run_typed<V, 4>(w, units, tile_unit, M, dist, ws, alpha, beta, meff, num_sms, stream);
-    default: return ms_run_typed<V, 1>(w, units, tile_unit, M, dist, ws, alpha, beta, meff, num_sms, stream);
+    case 16: return ms_run_typed<V, 16>(w, units, tu, su, M, dist, ws, alpha, beta, meff, num_sms, stream);
+    case 8: return ms_run_typed<V, 8>(w, units, tu, su, M, dist, ws, alpha, beta, meff, num_sms, stream);
+    case 4: return ms_run_typed<V, 4>(w, units, tu, su, M, dist, ws, alpha, beta, meff, num_sms, stream);
+    default: return ms_run_typed<V, 1>(w, units, tu, su, M, dist, ws, alpha, beta, meff, num_sms, stream);
     }
 }
 
 }  // namespace
 
 ftlm_status ms_run_wave(const MsWave &w, ftlm_dtype dtype, int B, const MsUnit *units, const uint32_t *tile_unit,
-                        int M, int dist, char *ws, double *alpha, double *beta, int *meff, int num_sms,
-                        cudaStream_t stream)
+                        const uint32_t *stile_unit, int M, int dist, char *ws, double *alpha, double *beta,
+                        int *meff, int num_sms, cudaStream_t stream)
 {
     if (!w.n_tiles) return FTLM_OK;
     return dtype == FTLM_F32
-               ? ms_run_v<float>(w, B, units, tile_unit, M, dist, ws, alpha, beta, meff, num_sms, stream)
-               : ms_run_v<double>(w, B, units, tile_unit, M, dist, ws, alpha, beta, meff, num_sms, stream);
+               ? ms_run_v<float>(w, B, units, tile_unit, stile_unit, M, dist, ws, alpha, beta, meff, num_sms, stream)
+               : ms_run_v<double>(w, B, units, tile_unit, stile_unit, M, dist, ws, alpha, beta, meff, num_sms,
+                                  stream);
 }
 
 }  // namespace ftlm

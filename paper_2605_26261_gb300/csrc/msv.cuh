@@ -10,6 +10,11 @@ namespace ftlm {
 #define FTLM_MS_TILE_ROWS 2048
 #endif
 constexpr uint32_t kMsTileRows = FTLM_MS_TILE_ROWS;
+// Rows per tile of the streaming kernels (start vectors, update): four H.v tiles.
+// The update's work per row is a few loads, so larger tiles amortize the per-tile
+// reduction (measured on the 256-cluster step: update 3.7 / 2.0 / 1.5 / 1.1 s per
+// step at 1024 / 2048 / 4096 / 8192 rows, H.v best at 2048).
+constexpr uint32_t kMsStreamRows = 4 * kMsTileRows;
 
 // One block of B chains of one sector.  Offsets are into the run's workspace.
 struct MsUnit {
@@ -20,7 +25,8 @@ struct MsUnit {
     uint64_t off_part;        // per-tile partial sums [n_tiles][B]
     uint64_t seed;
     double tau;
-    uint32_t tile0, n_tiles;  // the unit's tiles within its wave
+    uint32_t tile0, n_tiles;  // the unit's H.v tiles within its wave
+    uint32_t stile0, n_stiles;  // the unit's tiles of the streaming kernels
     uint32_t chain_base;      // chain 0 of the unit in the batch's alpha/beta/meff arrays
     int key_n, K, chain0;     // chain keys: chain r is keyed (seed, key_n, K, chain0 + r)
     int nact;                 // chains of the unit (<= B); the other columns stay zero
@@ -37,6 +43,8 @@ struct MsWave {
     uint32_t unit0, n_units;  // units [unit0, unit0 + n_units) of the plan
     uint32_t tile_off;        // offset of the wave's tile->unit map in the plan's map
     uint32_t n_tiles;
+    uint32_t stile_off;       // the same for the tiles of the streaming kernels
+    uint32_t n_stiles;
     int m_max;                // longest chain length of the wave
     int kind;                 // MsKind
 };
@@ -44,7 +52,7 @@ struct MsWave {
 // Queue one wave: start vectors, m_max steps of (H.v + alpha, update + beta), and
 // the chain lengths into meff.  units and tile_unit point at the wave's own entries.
 ftlm_status ms_run_wave(const MsWave &w, ftlm_dtype dtype, int B, const MsUnit *units, const uint32_t *tile_unit,
-                        int M, int dist, char *ws, double *alpha, double *beta, int *meff, int num_sms,
-                        cudaStream_t stream);
+                        const uint32_t *stile_unit, int M, int dist, char *ws, double *alpha, double *beta,
+                        int *meff, int num_sms, cudaStream_t stream);
 
 }  // namespace ftlm

@@ -58,33 +58,33 @@ def test_thermo_kernel_matches_oracle_sums(cuda_dev, h, mirror):
         assert_obs_close(got[k].cpu().numpy(), ref[k], 1e-12, k)
 
 
-CONFIG1 = dict(N=16, bonds=inputs.ring(16), R=20, M=100, seed=1, dist=o.GAUSS)
+RING16 = dict(N=16, bonds=inputs.ring(16), R=20, M=100, seed=1, dist=o.GAUSS)
 
 
 @pytest.fixture(scope="module")
-def config1_oracle():
-    c = CONFIG1
+def ring16_oracle():
+    c = RING16
     secs = o.run_ftlm(c["N"], c["bonds"], c["R"], c["M"], seed=c["seed"], dist=c["dist"])
     return o.thermo(secs, inputs.log_t_grid(200))
 
 
 @pytest.mark.parametrize("dtype,rtol", [(torch.float64, 1e-9), (torch.float32, 1e-4)])
 @pytest.mark.parametrize("mode", [ftlm.RANK_CLT, ftlm.RANK_CR])
-def test_config1_ring16_matches_oracle(cuda_dev, config1_oracle, dtype, rtol, mode):
+def test_ring16_all_sectors_matches_oracle(cuda_dev, ring16_oracle, dtype, rtol, mode):
     # Ring N = 16, J = 1, every S^z sector (9 computed, mirrored), R = 20 Gaussian
     # vectors, M = 100, 200 temperatures in [0.01, 10].
-    c = CONFIG1
+    c = RING16
     T = inputs.log_t_grid(200)
     got = ftlm.run_ftlm(c["N"], c["bonds"], c["R"], c["M"], T, seed=c["seed"], dist=c["dist"],
                         dtype=dtype, mode=mode)
     for k in ("E", "C", "chi"):
-        assert_obs_close(got[k].cpu().numpy(), config1_oracle[k], rtol, k)
+        assert_obs_close(got[k].cpu().numpy(), ring16_oracle[k], rtol, k)
 
 
-def test_config1_fp32_error_below_stochastic_error(cuda_dev):
+def test_ring16_fp32_error_below_stochastic_error(cuda_dev):
     # |O_FP32 - O_FP64| must stay below 1% of the seed-to-seed spread sigma_emp
     # (Eq. 22, 1/N_s normalization) of the FP64 estimate.
-    c = CONFIG1
+    c = RING16
     T = inputs.log_t_grid(200)
     f64 = [ftlm.run_ftlm(c["N"], c["bonds"], c["R"], c["M"], T, seed=s, dtype=torch.float64)
            for s in range(1, 11)]
@@ -123,7 +123,7 @@ def test_exact_trace_mode_matches_oracle(cuda_dev, N, bonds, h):
         assert_obs_close(got[k].cpu().numpy(), ref[k], 1e-9, k)
 
 
-def test_config2_lattice_sectors_match_oracle(cuda_dev):
+def test_j1j2_4x6_lattice_sectors_match_oracle(cuda_dev):
     # 4 x 6 J1-J2 lattice, Rademacher vectors, M = 150: the sectors with S^z >= 5
     # (D <= 346104) on the oracle, first 2 chains of each; the same chains on the GPU.
     N, R, M = 24, 2, 150
