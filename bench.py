@@ -130,24 +130,34 @@ def peak_hbm():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_fingerprint():
+# Device sources of each H.v kernel family: a committed ncu summary holds DRAM
+# traffic for the sources it was taken on.
+KERNEL_SOURCES = {
+    "hv": ("hv.cu", "epi.cuh", "rows.cuh", "vec.cuh", "reduce.cuh", "ftlm_internal.cuh"),
+    "spin": ("spin.cu", "spin_rows.cuh", "epi.cuh", "vec.cuh", "reduce.cuh", "ftlm_internal.cuh"),
+}
+
+
+def kernel_fingerprint(family="hv"):
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2605_26261_gb300", "csrc")
-    for f in ("hv.cu", "spin.cu", "epi.cuh", "rows.cuh", "vec.cuh", "reduce.cuh", "ftlm_internal.cuh"):
+    for f in KERNEL_SOURCES[family]:
         with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload, mode_name, dtype):
+def profiled_traffic(workload, mode_name, dtype, family="hv"):
     """DRAM bytes per H.v launch from a committed ncu summary (profiles/*.md) taken
-    on the current kernel sources for this workload, rank mode and dtype; else None."""
+    on the current sources of the kernel family for this workload, rank mode and
+    dtype; else None."""
     import glob
 
+    want = kernel_fingerprint(family)
     for path in sorted(glob.glob(os.path.join(PROFILES, "*.md"))):
         text = open(path).read()
-        fp = re.search(r"kernel_fingerprint:\s*(\w+)", text)
-        if not fp or fp.group(1) != kernel_fingerprint():
+        fp = re.search(rf"kernel_fingerprint\[{family}\]:\s*(\w+)", text)
+        if not fp or fp.group(1) != want:
             continue
         m = re.search(rf"dram_bytes_per_launch\[{re.escape(workload)},{mode_name},{dtype}\]:\s*([0-9.eE+]+)", text)
         if m:
@@ -498,7 +508,8 @@ def run_ours(args):
     D0, upd0, mode0 = info[sectors[0]]
     clt = mode0 == ftlm.RANK_CLT
     mode_name = "clt" if clt else "cr"
-    traffic = profiled_traffic(args.workload, mode_name, args.dtype) if len(sectors) == 1 else None
+    family = "spin" if two_s > 1 else "hv"
+    traffic = profiled_traffic(args.workload, mode_name, args.dtype, family) if len(sectors) == 1 else None
     hv_avg_s = hv_s / max(hv_n, 1)
     kname = "ms_hv_kernel" if len(sectors) > 1 else ("hv_kernel" if two_s == 1 else "hv_spin_kernel")
     roofline = {

@@ -199,7 +199,7 @@ ms_hv_kernel(const MsUnit *__restrict__ units, const uint32_t *__restrict__ tile
             const uint32_t t[1] = {ok ? tt : D - 1};  // rows past the end recompute the last row, unstored
             if constexpr (SPIN) {
                 V acc[B], diag;
-                spin_row<V, B, C>(U.s, U.spin, s_tlo, s_bond, s_J, s_up, x, t[0], acc, diag);
+                spin_row<V, B, C, false>(U.s, U.spin, s_tlo, nullptr, s_bond, s_J, s_up, x, t[0], acc, diag);
                 if (ok) epi_row<V, B, true>(ep, s_inv_s, s_c_prev, x, y, t[0], diag, acc, apart);
             } else {
                 V acc[1][B], dsum[1] = {(V)0};

@@ -63,12 +63,28 @@ struct Dims {
     uint64_t at(int m, int a) const { return (a < 0 || a > amax) ? 0 : v[(size_t)m * (amax + 1) + a]; }
 };
 
-template <typename V, bool LANCZOS, int B>
-__global__ void __launch_bounds__(kRowThreads, B >= 8 ? 2 : 3)
+// Resident CTAs per SM the registers are capped for; build option
+// FTLM_SPIN_B8_MIN_CTAS for B >= 8.
+#ifndef FTLM_SPIN_B8_MIN_CTAS
+#define FTLM_SPIN_B8_MIN_CTAS 2
+#endif
+
+// High-block rank tables up to this many entries (64 KB) are staged in shared
+// memory next to tlo, taking the lookup of the high half of a source rank off the
+// global load path; build option FTLM_SPIN_SMEM_HIGH (0: never).
+#ifndef FTLM_SPIN_SMEM_HIGH
+#define FTLM_SPIN_SMEM_HIGH 16384
+#endif
+constexpr uint64_t kSpinSmemHigh = FTLM_SPIN_SMEM_HIGH;
+
+template <typename V, bool LANCZOS, int B, bool TS>
+__global__ void __launch_bounds__(kRowThreads, B >= 8 ? FTLM_SPIN_B8_MIN_CTAS : 3)
 hv_spin_kernel(const SectorTables s, const SpinDev p, const V *__restrict__ x, V *y, const EpiDev ep)
 {
     constexpr int C = spin_chunk<B>();
     extern __shared__ uint16_t s_tlo[];
+    // thi after tlo, at a 16-byte boundary (tlo has at most 2^14 entries)
+    uint32_t *s_thi = reinterpret_cast<uint32_t *>(s_tlo + (((size_t)s.lomask + 8) & ~(size_t)7));
     __shared__ uint4 s_bond[kMaxBondSlots];
     __shared__ V s_J[kMaxBondSlots];
     __shared__ V s_up[kSpinMaxTwoS + 1];
@@ -80,6 +96,8 @@ hv_spin_kernel(const SectorTables s, const SpinDev p, const V *__restrict__ x, V
     }
     if (threadIdx.x < p.two_s) s_up[threadIdx.x] = spin_up<V>(p)[threadIdx.x];
     for (uint32_t i = threadIdx.x; i <= s.lomask; i += blockDim.x) s_tlo[i] = __ldg(s.tlo + i);
+    if (TS)
+        for (uint32_t i = threadIdx.x; i < s.H; i += blockDim.x) s_thi[i] = __ldg(s.thi + i);
     __syncthreads();
 
     DotAcc<V> apart[B];
@@ -92,7 +110,7 @@ hv_spin_kernel(const SectorTables s, const SpinDev p, const V *__restrict__ x, V
         const bool ok_row = tt < s.D;
         const uint32_t t = ok_row ? tt : s.D - 1;  // rows past the end recompute the last row, unstored
         V acc[B], diag;
-        spin_row<V, B, C>(s, p, s_tlo, s_bond, s_J, s_up, x, t, acc, diag);
+        spin_row<V, B, C, TS>(s, p, s_tlo, s_thi, s_bond, s_J, s_up, x, t, acc, diag);
         if (ok_row) epi_row<V, B, LANCZOS>(ep, s_inv_s, s_c_prev, x, y, t, diag, acc, apart);
     }
     if (LANCZOS) epi_end<V, B, kRowThreads>(ep, apart);
@@ -104,7 +122,7 @@ __global__ void spin_labels_kernel(SectorTables s, SpinDev p, uint64_t low_size,
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count;
          i += (uint64_t)gridDim.x * blockDim.x) {
         SpinRow w;
-        spin_unrank(s, p, (uint32_t)(first + i), w);
+        spin_unrank<false>(s, p, nullptr, (uint32_t)(first + i), w);
         out[i] = (uint64_t)w.hi * low_size + w.lo;
     }
 }
@@ -141,11 +159,13 @@ int grid_of(const ftlm_basis *b, uint64_t n)
 template <typename V, bool LANCZOS, int B>
 ftlm_status launch_spin(const ftlm_basis *b, const V *x, V *y, const EpiDev &ep, cudaStream_t stream)
 {
-    auto kern = hv_spin_kernel<V, LANCZOS, B>;
-    const size_t smem_max = kSpinMaxLow * sizeof(uint16_t);
+    const bool ts = b->H <= kSpinSmemHigh;
+    auto kern = ts ? hv_spin_kernel<V, LANCZOS, B, true> : hv_spin_kernel<V, LANCZOS, B, false>;
+    const size_t tlo_bytes = (((size_t)b->tables().lomask + 8) & ~(size_t)7) * sizeof(uint16_t);
+    const size_t smem_max = kSpinMaxLow * sizeof(uint16_t) + (ts ? kSpinSmemHigh * sizeof(uint32_t) : 0);
     int occ = 1;
     FTLM_CUDA(kernel_occupancy((const void *)kern, kRowThreads, smem_max, true, &occ));
-    const size_t smem = (size_t)(b->tables().lomask + 1) * sizeof(uint16_t);
+    const size_t smem = tlo_bytes + (ts ? (size_t)b->H * sizeof(uint32_t) : 0);
     const int grid = row_grid(b, b->D, occ);
     void *tok = profile_begin(kProfHv, stream, B);
     kern<<<grid, kRowThreads, smem, stream>>>(b->tables(), b->spin, x, y, ep);

@@ -20,23 +20,32 @@ __device__ __forceinline__ uint32_t div_d(const SpinDev &p, uint32_t n)
     return (uint32_t)(((uint64_t)n * p.magic) >> p.shift);
 }
 
+// thi[h]: from a shared-memory copy (TS) or through the read-only global path.
+template <bool TS> __device__ __forceinline__ uint32_t thi_at(const SectorTables &s, const uint32_t *s_thi, uint32_t h)
+{
+    if constexpr (TS) return s_thi[h];
+    else return __ldg(s.thi + h);
+}
+
 struct SpinRow {
     uint32_t lo, hi;      // low and high labels of the row
     uint32_t thi_h, r_lo; // the row's two halves of its rank
     uint64_t dig;         // digit k in bits 4k .. 4k+3
 };
 
-__device__ __forceinline__ void spin_unrank(const SectorTables &s, const SpinDev &p, uint32_t t, SpinRow &w)
+template <bool TS>
+__device__ __forceinline__ void spin_unrank(const SectorTables &s, const SpinDev &p, const uint32_t *s_thi, uint32_t t,
+                                            SpinRow &w)
 {
     const uint32_t kc = t >> kHsShift;
     uint32_t lo = __ldg(s.hs + kc), hi = __ldg(s.hs + kc + 1) + 1;
     while (hi - lo > 1) {
         const uint32_t mid = (lo + hi) >> 1;
-        if (__ldg(s.thi + mid) <= t) lo = mid;
+        if (thi_at<TS>(s, s_thi, mid) <= t) lo = mid;
         else hi = mid;
     }
     w.hi = lo;
-    w.thi_h = __ldg(s.thi + lo);
+    w.thi_h = thi_at<TS>(s, s_thi, lo);
     w.r_lo = t - w.thi_h;
     uint64_t dig = 0;
     uint32_t n = w.hi, sum = 0;
@@ -57,8 +66,9 @@ __device__ __forceinline__ void spin_unrank(const SectorTables &s, const SpinDev
 }
 
 // Rank of the row's label with digit i moved by di and digit j by dj (+-1).
-__device__ __forceinline__ uint32_t spin_rank(const SectorTables &s, const uint16_t *s_tlo, const SpinRow &w,
-                                              uint32_t flags, uint32_t pi, uint32_t pj, int di)
+template <bool TS>
+__device__ __forceinline__ uint32_t spin_rank(const SectorTables &s, const uint16_t *s_tlo, const uint32_t *s_thi,
+                                              const SpinRow &w, uint32_t flags, uint32_t pi, uint32_t pj, int di)
 {
     uint32_t lo = w.lo, hi = w.hi;
     const uint32_t ai = di > 0 ? pi : 0u - pi, aj = di > 0 ? 0u - pj : pj;
@@ -70,7 +80,7 @@ __device__ __forceinline__ uint32_t spin_rank(const SectorTables &s, const uint1
     // of a move that the caller discards
     lo = min(lo, s.lomask);
     hi = min(hi, s.H - 1u);
-    const uint32_t rh = hi == w.hi ? w.thi_h : __ldg(s.thi + hi);
+    const uint32_t rh = hi == w.hi ? w.thi_h : thi_at<TS>(s, s_thi, hi);
     const uint32_t rl = lo == w.lo ? w.r_lo : (uint32_t)s_tlo[lo];
     return rh + rl;
 }
@@ -82,18 +92,26 @@ template <typename V> __device__ __forceinline__ const V *spin_up(const SpinDev 
 template <> __device__ __forceinline__ const float *spin_up<float>(const SpinDev &p) { return p.upf; }
 template <> __device__ __forceinline__ const double *spin_up<double>(const SpinDev &p) { return p.upd; }
 
-template <int B> __host__ __device__ constexpr int spin_chunk() { return B >= 16 ? 1 : (B >= 8 ? 2 : 4); }
+// Bonds per chunk (two gathers each); build option FTLM_SPIN_CHUNK_B8 for B = 8.
+#ifndef FTLM_SPIN_CHUNK_B8
+#define FTLM_SPIN_CHUNK_B8 2
+#endif
+template <int B> __host__ __device__ constexpr int spin_chunk()
+{
+    return B >= 16 ? 1 : (B >= 8 ? FTLM_SPIN_CHUNK_B8 : 4);
+}
 
 // Row t: acc[r] = sum of the ladder terms of vector r, diag = sum_b J_b m_i m_j.
-template <typename V, int B, int C>
+// TS: thi is staged in shared memory at s_thi (else s_thi is unused).
+template <typename V, int B, int C, bool TS>
 __device__ __forceinline__ void spin_row(const SectorTables &s, const SpinDev &p, const uint16_t *s_tlo,
-                                         const uint4 *s_bond, const V *s_J, const V *s_up,
+                                         const uint32_t *s_thi, const uint4 *s_bond, const V *s_J, const V *s_up,
                                          const V *__restrict__ x, uint32_t t, V (&acc)[B], V &diag)
 {
     const V sv = (V)(0.5 * p.two_s);
     const uint32_t two_s = p.two_s;
     SpinRow w;
-    spin_unrank(s, p, t, w);
+    spin_unrank<TS>(s, p, s_thi, t, w);
     diag = (V)0;
 #pragma unroll
     for (int r = 0; r < B; ++r) acc[r] = (V)0;
@@ -117,11 +135,11 @@ __device__ __forceinline__ void spin_row(const SectorTables &s, const SpinDev &p
             // s_i^+ s_j^-: source digits (a_i - 1, a_j + 1), coefficient Eq. 13
             use[2 * q] = in && ai >= 1u && aj < two_s;
             c[2 * q] = use[2 * q] ? jh * s_up[im] * s_up[aj] : (V)0;
-            k[2 * q] = use[2 * q] ? spin_rank(s, s_tlo, w, flags, e.y, e.z, -1) : 0u;
+            k[2 * q] = use[2 * q] ? spin_rank<TS>(s, s_tlo, s_thi, w, flags, e.y, e.z, -1) : 0u;
             // s_i^- s_j^+: source digits (a_i + 1, a_j - 1), coefficient Eq. 14
             use[2 * q + 1] = in && ai < two_s && aj >= 1u;
             c[2 * q + 1] = use[2 * q + 1] ? jh * s_up[ai] * s_up[jm] : (V)0;
-            k[2 * q + 1] = use[2 * q + 1] ? spin_rank(s, s_tlo, w, flags, e.y, e.z, +1) : 0u;
+            k[2 * q + 1] = use[2 * q + 1] ? spin_rank<TS>(s, s_tlo, s_thi, w, flags, e.y, e.z, +1) : 0u;
         }
         V xv[2 * C][B];
 #pragma unroll

@@ -20,6 +20,9 @@ CASES = [  # (N, two_s, two_sz, bonds)
     (10, 2, 4, inputs.ladder(10, 0.7, 1.2)),
     (5, 5, -3, inputs.random_graph(5, seed=7, dmin=2, dmax=3)),
     (16, 2, 14, inputs.ring(16)),
+    (7, 7, 1, inputs.ring(7, J=1.1)),       # s = 7/2, the largest local spin
+    (4, 7, 26, inputs.ring(4)),             # one flipped quantum: D = 4
+    (4, 7, 28, inputs.ring(4)),             # fully polarized: D = 1, diagonal only
 ]
 
 
