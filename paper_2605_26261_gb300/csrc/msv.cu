@@ -132,14 +132,16 @@ ms_start_kernel(const MsUnit *__restrict__ units, const uint32_t *__restrict__ t
 // Step j: y = H q_j - beta_{j-1} q_{j-1} over the u_{j-1} block and alpha_j, for
 // every tile of every unit (x = u_j is block (j - 1) % 2, y block j % 2).
 // Resident CTAs per SM the registers are cut for: FP32 blocks up to 8 fit 3 CTAs
-// without spills (FP64 blocks of 4 and 8 need 2), single vectors 4.
-template <typename V, int B> __host__ __device__ constexpr int ms_min_ctas()
+// without spills (FP64 blocks of 4 and 8 need 2), single vectors 4 (3 for FP64
+// general-spin rows).
+template <typename V, int B, int KIND> __host__ __device__ constexpr int ms_min_ctas()
 {
-    return B >= 16 ? 1 : (sizeof(V) == 8 && B >= 4 ? 2 : (B >= 4 ? 3 : 4));
+    return B >= 16 ? 1
+                   : (sizeof(V) == 8 && B >= 4 ? 2 : (B >= 4 ? 3 : (sizeof(V) == 8 && KIND == kMsSpin ? 3 : 4)));
 }
 
 template <typename V, int KIND, int B, int C>
-__global__ void __launch_bounds__(kRowThreads, ms_min_ctas<V, B>())
+__global__ void __launch_bounds__(kRowThreads, ms_min_ctas<V, B, KIND>())
 ms_hv_kernel(const MsUnit *__restrict__ units, const uint32_t *__restrict__ tile_unit, uint32_t n_tiles, int j,
              int M, double *alpha, char *ws)
 {
@@ -147,7 +149,7 @@ ms_hv_kernel(const MsUnit *__restrict__ units, const uint32_t *__restrict__ tile
     extern __shared__ uint16_t s_tlo[];
     __shared__ uint4 s_bond[kMaxBondSlots];
     __shared__ V s_J[SPIN ? kMaxBondSlots : 1];
-    __shared__ V s_up[kSpinMaxTwoS + 1];
+    __shared__ V s_cf[SPIN ? kSpinCoef : 1];
     __shared__ V s_inv_s[B], s_c_prev[B];
     __shared__ int s_skip;
     uint32_t loaded = 0xffffffffu;
@@ -165,7 +167,7 @@ ms_hv_kernel(const MsUnit *__restrict__ units, const uint32_t *__restrict__ tile
                     s_bond[i] = U.spin.slots[i];
                     s_J[i] = spin_J<V>(U.spin)[i];
                 }
-                if (threadIdx.x < U.spin.two_s) s_up[threadIdx.x] = spin_up<V>(U.spin)[threadIdx.x];
+                spin_stage_coef<V>(U.spin, s_cf);
             } else {
                 const uint4 *src = sizeof(V) == 4 ? U.bl.slots_f32 : U.bl.slots_f64;
                 for (int i = threadIdx.x; i < U.bl.nb; i += blockDim.x) s_bond[i] = src[i];
@@ -199,7 +201,7 @@ ms_hv_kernel(const MsUnit *__restrict__ units, const uint32_t *__restrict__ tile
             const uint32_t t[1] = {ok ? tt : D - 1};  // rows past the end recompute the last row, unstored
             if constexpr (SPIN) {
                 V acc[B], diag;
-                spin_row<V, B, C, false>(U.s, U.spin, s_tlo, nullptr, s_bond, s_J, s_up, x, t[0], acc, diag);
+                spin_row<V, B, C, false>(U.s, U.spin, s_tlo, nullptr, s_bond, s_J, s_cf, x, t[0], acc, diag);
                 if (ok) epi_row<V, B, true>(ep, s_inv_s, s_c_prev, x, y, t[0], diag, acc, apart);
             } else {
                 V acc[1][B], dsum[1] = {(V)0};

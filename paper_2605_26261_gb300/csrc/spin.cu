@@ -64,7 +64,7 @@ struct Dims {
 };
 
 // Resident CTAs per SM the registers are capped for; build option
-// FTLM_SPIN_B8_MIN_CTAS for B >= 8.
+// FTLM_SPIN_B8_MIN_CTAS for B >= 8 (FP64 blocks of 4: 2, other blocks: 3).
 #ifndef FTLM_SPIN_B8_MIN_CTAS
 #define FTLM_SPIN_B8_MIN_CTAS 2
 #endif
@@ -78,7 +78,7 @@ struct Dims {
 constexpr uint64_t kSpinSmemHigh = FTLM_SPIN_SMEM_HIGH;
 
 template <typename V, bool LANCZOS, int B, bool TS>
-__global__ void __launch_bounds__(kRowThreads, B >= 8 ? FTLM_SPIN_B8_MIN_CTAS : 3)
+__global__ void __launch_bounds__(kRowThreads, B >= 8 ? FTLM_SPIN_B8_MIN_CTAS : (sizeof(V) == 8 && B >= 4 ? 2 : 3))
 hv_spin_kernel(const SectorTables s, const SpinDev p, const V *__restrict__ x, V *y, const EpiDev ep)
 {
     constexpr int C = spin_chunk<B>();
@@ -87,14 +87,14 @@ hv_spin_kernel(const SectorTables s, const SpinDev p, const V *__restrict__ x, V
     uint32_t *s_thi = reinterpret_cast<uint32_t *>(s_tlo + (((size_t)s.lomask + 8) & ~(size_t)7));
     __shared__ uint4 s_bond[kMaxBondSlots];
     __shared__ V s_J[kMaxBondSlots];
-    __shared__ V s_up[kSpinMaxTwoS + 1];
+    __shared__ V s_cf[kSpinCoef];
     __shared__ V s_inv_s[B], s_c_prev[B];
     if (LANCZOS && epi_begin<V, B>(ep, s_inv_s, s_c_prev)) return;
     for (uint32_t i = threadIdx.x; i < p.nb; i += blockDim.x) {
         s_bond[i] = p.slots[i];
         s_J[i] = spin_J<V>(p)[i];
     }
-    if (threadIdx.x < p.two_s) s_up[threadIdx.x] = spin_up<V>(p)[threadIdx.x];
+    spin_stage_coef<V>(p, s_cf);
     for (uint32_t i = threadIdx.x; i <= s.lomask; i += blockDim.x) s_tlo[i] = __ldg(s.tlo + i);
     if (TS)
         for (uint32_t i = threadIdx.x; i < s.H; i += blockDim.x) s_thi[i] = __ldg(s.thi + i);
@@ -110,7 +110,7 @@ hv_spin_kernel(const SectorTables s, const SpinDev p, const V *__restrict__ x, V
         const bool ok_row = tt < s.D;
         const uint32_t t = ok_row ? tt : s.D - 1;  // rows past the end recompute the last row, unstored
         V acc[B], diag;
-        spin_row<V, B, C, TS>(s, p, s_tlo, s_thi, s_bond, s_J, s_up, x, t, acc, diag);
+        spin_row<V, B, C, TS>(s, p, s_tlo, s_thi, s_bond, s_J, s_cf, x, t, acc, diag);
         if (ok_row) epi_row<V, B, LANCZOS>(ep, s_inv_s, s_c_prev, x, y, t, diag, acc, apart);
     }
     if (LANCZOS) epi_end<V, B, kRowThreads>(ep, apart);

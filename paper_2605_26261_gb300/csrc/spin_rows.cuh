@@ -92,9 +92,32 @@ template <typename V> __device__ __forceinline__ const V *spin_up(const SpinDev 
 template <> __device__ __forceinline__ const float *spin_up<float>(const SpinDev &p) { return p.upf; }
 template <> __device__ __forceinline__ const double *spin_up<double>(const SpinDev &p) { return p.upd; }
 
+// Per-bond factors of a row, indexed by the digit pair 8 a_i + a_j (digits <= 7):
+// [0, 64) the s_i^+ s_j^- factor of Eq. 13 and [64, 128) the s_i^- s_j^+ factor of
+// Eq. 14, both with the 1/2 of Eq. 12 and zero where the source digit leaves
+// 0 .. 2s; [128, 192) m_i m_j (exact: products of half-integers).
+constexpr int kSpinCoef = 3 * 64;
+
+template <typename V> __device__ __forceinline__ void spin_stage_coef(const SpinDev &p, V *s_cf)
+{
+    const V *up = spin_up<V>(p);
+    const uint32_t two_s = p.two_s;
+    const V sv = (V)(0.5 * p.two_s);
+    for (uint32_t idx = threadIdx.x; idx < (uint32_t)kSpinCoef; idx += blockDim.x) {
+        const uint32_t tab = idx >> 6, ai = (idx >> 3) & 7u, aj = idx & 7u;
+        V v = (V)0;
+        if (ai <= two_s && aj <= two_s) {
+            if (tab == 0u && ai >= 1u && aj < two_s) v = (V)0.5 * up[ai - 1] * up[aj];
+            else if (tab == 1u && ai < two_s && aj >= 1u) v = (V)0.5 * up[ai] * up[aj - 1];
+            else if (tab == 2u) v = ((V)ai - sv) * ((V)aj - sv);
+        }
+        s_cf[idx] = v;
+    }
+}
+
 // Bonds per chunk (two gathers each); build option FTLM_SPIN_CHUNK_B8 for B = 8.
 #ifndef FTLM_SPIN_CHUNK_B8
-#define FTLM_SPIN_CHUNK_B8 2
+#define FTLM_SPIN_CHUNK_B8 3
 #endif
 template <int B> __host__ __device__ constexpr int spin_chunk()
 {
@@ -105,11 +128,9 @@ template <int B> __host__ __device__ constexpr int spin_chunk()
 // TS: thi is staged in shared memory at s_thi (else s_thi is unused).
 template <typename V, int B, int C, bool TS>
 __device__ __forceinline__ void spin_row(const SectorTables &s, const SpinDev &p, const uint16_t *s_tlo,
-                                         const uint32_t *s_thi, const uint4 *s_bond, const V *s_J, const V *s_up,
+                                         const uint32_t *s_thi, const uint4 *s_bond, const V *s_J, const V *s_cf,
                                          const V *__restrict__ x, uint32_t t, V (&acc)[B], V &diag)
 {
-    const V sv = (V)(0.5 * p.two_s);
-    const uint32_t two_s = p.two_s;
     SpinRow w;
     spin_unrank<TS>(s, p, s_thi, t, w);
     diag = (V)0;
@@ -126,19 +147,19 @@ __device__ __forceinline__ void spin_row(const SectorTables &s, const SpinDev &p
             const uint4 e = s_bond[in ? b : 0];
             const uint32_t i = e.x & 255u, j = (e.x >> 8) & 255u, flags = e.x >> 16;
             const uint32_t ai = (uint32_t)(w.dig >> (4 * i)) & 15u, aj = (uint32_t)(w.dig >> (4 * j)) & 15u;
+            const uint32_t ij = ai * 8u + aj;
             const V J = in ? s_J[b] : (V)0;
-            diag = fma(J * ((V)ai - sv), (V)aj - sv, diag);
-            const V jh = J * (V)0.5;
-            // table indices are clamped into range; a term that does not exist is
-            // dropped by its flag
-            const uint32_t im = ai > 0u ? ai - 1u : 0u, jm = aj > 0u ? aj - 1u : 0u;
+            diag = fma(J, s_cf[128 + ij], diag);
+            // a term exists where its factor is nonzero; the clamps of spin_rank keep
+            // the table addresses of a dropped term in range
+            const V f0 = s_cf[ij], f1 = s_cf[64 + ij];
             // s_i^+ s_j^-: source digits (a_i - 1, a_j + 1), coefficient Eq. 13
-            use[2 * q] = in && ai >= 1u && aj < two_s;
-            c[2 * q] = use[2 * q] ? jh * s_up[im] * s_up[aj] : (V)0;
+            use[2 * q] = in && f0 != (V)0;
+            c[2 * q] = J * f0;
             k[2 * q] = use[2 * q] ? spin_rank<TS>(s, s_tlo, s_thi, w, flags, e.y, e.z, -1) : 0u;
             // s_i^- s_j^+: source digits (a_i + 1, a_j - 1), coefficient Eq. 14
-            use[2 * q + 1] = in && ai < two_s && aj >= 1u;
-            c[2 * q + 1] = use[2 * q + 1] ? jh * s_up[ai] * s_up[jm] : (V)0;
+            use[2 * q + 1] = in && f1 != (V)0;
+            c[2 * q + 1] = J * f1;
             k[2 * q + 1] = use[2 * q + 1] ? spin_rank<TS>(s, s_tlo, s_thi, w, flags, e.y, e.z, +1) : 0u;
         }
         V xv[2 * C][B];
