@@ -54,7 +54,7 @@ typedef enum {
 } ftlm_status;
 
 typedef enum {
-    FTLM_RANK_AUTO = 0, /* CLT if N <= 32 and its tables fit in 1/4 of device memory, else CR */
+    FTLM_RANK_AUTO = 0, /* CLT if N <= 32, D < 2^20 and its tables fit in 1/4 of device memory, else CR */
     FTLM_RANK_CLT = 1,  /* compressed lookup table: basis array + {M_b, C_b} (Eq. 18-21) */
     FTLM_RANK_CR = 2    /* combinatorial ranking (Eq. 15-17), digit blocks via tables   */
 } ftlm_rank_mode;

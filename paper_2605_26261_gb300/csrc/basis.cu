@@ -270,12 +270,15 @@ extern "C" ftlm_status ftlm_basis_create(int N, int two_sz, int n_bonds, const i
     const uint64_t D = binom(N, K);
     if (D >= (1ull << 32)) return fail(FTLM_EUNSUPPORTED, "sector dimension >= 2^32");
     if (mode == FTLM_RANK_AUTO) {
-        // CLT when its tables (basis array + Eq. 21) fit in a quarter of the device
-        // memory: it is the faster map once chains run in blocks (measured on GB300);
-        // else combinatorial ranking, which stores almost nothing.
+        // Measured on GB300 with blocks of chains: combinatorial ranking is the faster
+        // map from 2^20 rows up (its Lanczos H.v launches take rows in dynamic order,
+        // whose gathers share L2; 13 % faster on the N = 30 icosahedral sector), CLT
+        // below (many small sectors of a batch, where CR restages its rank table per
+        // sector).  CLT also needs its tables (basis array + Eq. 21) to fit in a
+        // quarter of the device memory.
         mode = FTLM_RANK_CR;
         size_t free_b = 0, total_b = 0;
-        if (N <= 32 && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+        if (N <= 32 && D < kAutoCrRows && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
             const uint64_t clt_bytes = 4 * D + 8 * (((1ull << N) + 31) / 32);
             if (clt_bytes <= total_b / 4) mode = FTLM_RANK_CLT;
         }

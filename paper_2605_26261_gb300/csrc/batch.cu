@@ -89,16 +89,14 @@ struct ScatterDev {
     int *m_eff;
 };
 
-// Fixed-order CTA sum of B per-thread values; out[r] (shared) holds chain r's total.
-template <int B>
-__device__ __forceinline__ void cta_reduce(const double (&v)[B], double *s_warp, double *out)
+// Fixed-order CTA sum of B per-thread accumulators (one transposed warp tree, then
+// the warp sums in warp order); out[r] (shared) holds chain r's total.
+template <typename V, int B>
+__device__ __forceinline__ void cta_reduce(DotAcc<V> (&v)[B], double *s_warp, double *out)
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-    for (int r = 0; r < B; ++r) {
-        const double x = warp_sum(v[r]);
-        if (lane == 0) s_warp[w * B + r] = x;
-    }
+    const DotAcc<V> t = warp_sum_multi<V, B>(v);
+    if (lane < B) s_warp[w * B + warp_multi_index<B>(lane)] = t.value();
     __syncthreads();
     if (threadIdx.x < B) {
         double t = 0.0;
@@ -159,10 +157,7 @@ batch_kernel(const BatchItemDev *__restrict__ items, const BatchUnitDev *__restr
                 }
                 st_vec<B>(u0 + (size_t)t * B, out);
             }
-            double v[B];
-#pragma unroll
-            for (int r = 0; r < B; ++r) v[r] = acc[r].value();
-            cta_reduce<B>(v, s_warp, s_tot);
+            cta_reduce<V, B>(acc, s_warp, s_tot);
             if (threadIdx.x < B) {
                 const int r = threadIdx.x;
                 const double nrm = sqrt(s_tot[r]);
@@ -211,12 +206,7 @@ batch_kernel(const BatchItemDev *__restrict__ items, const BatchUnitDev *__restr
                 }
                 st_vec<B>(y + (size_t)t * B, out);
             }
-            {
-                double v[B];
-#pragma unroll
-                for (int r = 0; r < B; ++r) v[r] = ap[r].value();
-                cta_reduce<B>(v, s_warp, s_tot);
-            }
+            cta_reduce<V, B>(ap, s_warp, s_tot);
             if (threadIdx.x < B) {
                 const int r = threadIdx.x;
                 if (!s_stop[r]) alpha_all[(cbase + r) * M + (j - 1)] = s_tot[r];
@@ -236,12 +226,7 @@ batch_kernel(const BatchItemDev *__restrict__ items, const BatchUnitDev *__restr
                 }
                 st_vec<B>(y + (size_t)t * B, w);
             }
-            {
-                double v[B];
-#pragma unroll
-                for (int r = 0; r < B; ++r) v[r] = bp[r].value();
-                cta_reduce<B>(v, s_warp, s_tot);
-            }
+            cta_reduce<V, B>(bp, s_warp, s_tot);
             if (threadIdx.x < B && !s_stop[threadIdx.x]) {
                 const int r = threadIdx.x;
                 const double beta = sqrt(s_tot[r]);

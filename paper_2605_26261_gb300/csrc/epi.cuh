@@ -7,8 +7,15 @@
 //   y[t] = (H u_j)[t] / s_j - (beta_{j-1} / s_{j-1}) u_{j-1}[t]     (overwrites u_{j-1})
 //   alpha partial += q_j[t] y[t]                                    (FP64-class)
 // Per-thread partial dot products use DotAcc (exact products, two-float
-// compensated sums for FP32 vectors); the block sum is an FP64 tree and the last
-// block to finish adds the per-block partials in a fixed order and stores alpha_j.
+// compensated sums for FP32 vectors).  Two ways to finish alpha_j:
+//  - static tile order (a warp takes every nwarps-th tile of rows): the block sum
+//    is an FP64 tree and the last block to finish adds the per-block partials in
+//    a fixed order and stores alpha_j (epi_end);
+//  - dynamic tile order (CR launches: tiles handed out by a counter, so that all
+//    warps work on one frontier of rows and the gathers of the rows in flight
+//    share L2): each tile's sums go through a fixed warp tree into a slot of their
+//    own (store_tile), and a second launch adds the slots in tile order.
+// Both orders are fixed for a given sector and grid: alpha_j is reproducible.
 #pragma once
 
 #include "ftlm_internal.cuh"
@@ -20,8 +27,9 @@ namespace ftlm {
 struct EpiDev {
     ChainState *st;
     double *partials;
-    unsigned int *counter;
+    unsigned int *counter;  // [0] block ticket; [1], [2] dynamic tile order
     double *alpha_out;
+    double *tile_part;      // per-tile sums of the dynamic tile order, [tile][B]
     int alpha_stride;
     int has_prev;
 };
@@ -34,6 +42,7 @@ inline EpiDev epi_of(const LanczosHv *epi)
         ep.partials = epi->partials;
         ep.counter = epi->counter;
         ep.alpha_out = epi->alpha_out;
+        ep.tile_part = epi->tile_part;
         ep.alpha_stride = epi->alpha_stride;
         ep.has_prev = epi->j > 1;
     }
@@ -119,6 +128,37 @@ __device__ __forceinline__ void epi_end(const EpiDev &ep, DotAcc<V> (&apart)[B])
         }
         if (threadIdx.x == 0) *ep.counter = 0;
     }
+}
+
+// Dynamic tile order: a warp's first tile is its index, later ones come from the
+// counter ep.counter[1]; ep.counter[2] counts the warps that ran out of tiles, and
+// the last of them zeroes both for the next launch (they start at zero).
+__device__ __forceinline__ uint32_t next_tile(const EpiDev &ep, uint32_t nwarps)
+{
+    uint32_t t = 0;
+    if ((threadIdx.x & 31u) == 0) t = atomicAdd(ep.counter + 1, 1u) + nwarps;
+    return __shfl_sync(0xffffffffu, t, 0);
+}
+
+__device__ __forceinline__ void tiles_done(const EpiDev &ep, uint32_t nwarps)
+{
+    if ((threadIdx.x & 31u) == 0) {
+        __threadfence();
+        if (atomicAdd(ep.counter + 2, 1u) == nwarps - 1) {
+            ep.counter[1] = 0;
+            ep.counter[2] = 0;
+        }
+    }
+}
+
+// The warp's alpha partial sums of one tile, through a fixed warp tree, into
+// ep.tile_part[tile * B + r].  Called by the whole warp.
+template <typename V, int B>
+__device__ __forceinline__ void store_tile(const EpiDev &ep, uint32_t tile, DotAcc<V> (&a)[B])
+{
+    const DotAcc<V> t = warp_sum_multi<V, B>(a);
+    const unsigned lane = threadIdx.x & 31u;
+    if (lane < B) ep.tile_part[(size_t)tile * B + warp_multi_index<B>(lane)] = t.value();
 }
 
 }  // namespace ftlm

@@ -176,6 +176,7 @@ struct LanczosHv {
     double *alpha_out;     // alpha_j of chain r goes to alpha_out[r * alpha_stride]
     int alpha_stride;
     int j;
+    double *tile_part;     // [hv_lanczos_tiles() * B]: per-tile sums of a dynamic tile order
 };
 // General-spin counterparts (spin.cu) of the H.v launch and the label/rank kernels.
 ftlm_status launch_hv_spin(const ftlm_basis *b, ftlm_dtype dtype, int B, const void *x, void *y,
@@ -192,6 +193,12 @@ void launch_hs_fill(const ftlm_basis *b, cudaStream_t stream);
 ftlm_status launch_hv(const ftlm_basis *b, ftlm_dtype dtype, int B, const void *x, void *y,
                       const LanczosHv *epi, cudaStream_t stream);
 bool valid_block(int B);
+// FTLM_RANK_AUTO picks CR for sectors of at least this many rows.
+constexpr uint64_t kAutoCrRows = 1ull << 20;
+// Tiles of a Lanczos H.v launch of B vectors that takes its tiles in dynamic order
+// and leaves alpha_j as per-tile sums in LanczosHv::tile_part (CR rank mode); 0 when
+// the launch finishes alpha_j itself.
+uint32_t hv_lanczos_tiles(const ftlm_basis *b, int B);
 
 // Lanczos chains of one sector (lanczos.cu): chain r is keyed as chain chain0 + r.
 ftlm_status lanczos_run(const ftlm_basis *b, int R, int M, int chain0, uint64_t seed, int dist, const double *src,

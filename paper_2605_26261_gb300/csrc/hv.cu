@@ -71,6 +71,9 @@ template <typename V, typename Lbl, bool CLT, bool LANCZOS, int RT, int B, int C
 __global__ void __launch_bounds__(kRowThreads, min_ctas<RT, B, C>())
 hv_kernel(const SectorTables s, const BondList bl, const V *__restrict__ x, V *y, const EpiDev ep)
 {
+    // CR Lanczos launches take their tiles in dynamic order (their gathers gain the
+    // most from a narrow frontier of rows) and store per-tile alpha sums
+    constexpr bool TILES = LANCZOS && !CLT;
     extern __shared__ uint16_t s_tlo[];
     __shared__ uint4 s_bond[kMaxBondSlots];
     __shared__ V s_inv_s[B], s_c_prev[B];  // per-chain scalars of the epilogue
@@ -89,7 +92,7 @@ hv_kernel(const SectorTables s, const BondList bl, const V *__restrict__ x, V *y
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t tile_rows = 32u * RT;
     const uint32_t ntiles = (uint32_t)(((uint64_t)s.D + tile_rows - 1) / tile_rows);
-    for (uint32_t tile = warp; tile < ntiles; tile += nwarps) {
+    for (uint32_t tile = warp; tile < ntiles; tile = TILES ? next_tile(ep, nwarps) : tile + nwarps) {
         uint32_t t[RT];
         bool ok[RT];
 #pragma unroll
@@ -107,11 +110,40 @@ hv_kernel(const SectorTables s, const BondList bl, const V *__restrict__ x, V *y
         }
         if (CLT) rows_clt<V, RT, B, C>(s, bl, s_bond, x, t, acc, dsum);
         else rows_cr<V, Lbl, RT, B, C>(s, bl, s_bond, s_tlo, x, t, acc, dsum);
+        if constexpr (TILES) {
+            DotAcc<V> tacc[B];
 #pragma unroll
-        for (int i = 0; i < RT; ++i)
-            if (ok[i]) epi_row<V, B, LANCZOS>(ep, s_inv_s, s_c_prev, x, y, t[i], jsum4 - dsum[i], acc[i], apart);
+            for (int i = 0; i < RT; ++i)
+                if (ok[i]) epi_row<V, B, true>(ep, s_inv_s, s_c_prev, x, y, t[i], jsum4 - dsum[i], acc[i], tacc);
+            store_tile<V, B>(ep, tile, tacc);
+        } else {
+#pragma unroll
+            for (int i = 0; i < RT; ++i)
+                if (ok[i]) epi_row<V, B, LANCZOS>(ep, s_inv_s, s_c_prev, x, y, t[i], jsum4 - dsum[i], acc[i], apart);
+        }
     }
-    if (LANCZOS) epi_end<V, B, kRowThreads>(ep, apart);
+    if (TILES) tiles_done(ep, nwarps);
+    else if (LANCZOS) epi_end<V, B, kRowThreads>(ep, apart);
+}
+
+// alpha_j of a dynamically ordered launch from its per-tile sums: block b adds a
+// fixed range of tiles (each thread its tiles in order), then the block trees and
+// the last block's sum over the blocks in order (epi_end).  The grid depends only
+// on the tile count, so alpha_j is reproducible.
+template <int B>
+__global__ void __launch_bounds__(kRowThreads) tile_alpha_kernel(const EpiDev ep, uint32_t ntiles)
+{
+    bool all_stopped = true;
+#pragma unroll
+    for (int r = 0; r < B; ++r) all_stopped &= ep.st[r].stopped != 0;
+    if (all_stopped) return;  // as the H.v launch: uniform over the grid
+    const uint32_t per = (ntiles + gridDim.x - 1) / gridDim.x;
+    const uint32_t t0 = min(ntiles, blockIdx.x * per), t1 = min(ntiles, t0 + per);
+    DotAcc<double> a[B];
+    for (uint32_t t = t0 + threadIdx.x; t < t1; t += blockDim.x)
+#pragma unroll
+        for (int r = 0; r < B; ++r) a[r].v += __ldcg(ep.tile_part + (size_t)t * B + r);
+    epi_end<double, B, kRowThreads>(ep, a);
 }
 
 // Rows per thread (RT) for single vectors.  Measured on GB300 (icosidodecahedron,
@@ -154,6 +186,13 @@ ftlm_status launch(const ftlm_basis *b, const V *x, V *y, const EpiDev &ep, cuda
     void *tok = profile_begin(kProfHv, stream, B);
     kern<<<grid, kRowThreads, smem, stream>>>(b->tables(), CLT ? b->bonds_clt : b->bonds_cr, x, y, ep);
     note_launch();
+    if (LANCZOS && !CLT) {  // alpha_j from the per-tile sums (timed with the H.v step)
+        const uint64_t rows = 32ull * RT;
+        const uint32_t ntiles = (uint32_t)((b->D + rows - 1) / rows);
+        const int ga = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)b->num_sms * 2, (ntiles + 2047) / 2048));
+        tile_alpha_kernel<B><<<ga, kRowThreads, 0, stream>>>(ep, ntiles);
+        note_launch();
+    }
     profile_end(tok, stream);
     FTLM_CUDA(cudaGetLastError());
     return FTLM_OK;
@@ -216,6 +255,13 @@ ftlm_status launch_typed(const ftlm_basis *b, int B, const void *x, void *y, con
 }  // namespace
 
 bool valid_block(int B) { return B == 1 || B == 4 || B == 8 || B == 16; }
+
+uint32_t hv_lanczos_tiles(const ftlm_basis *b, int B)
+{
+    if (b->two_s > 1 || b->mode == FTLM_RANK_CLT) return 0;
+    const uint64_t rows = 32ull * (B == 1 ? rows_per_thread(false) : 1);
+    return (uint32_t)((b->D + rows - 1) / rows);
+}
 
 ftlm_status launch_hv(const ftlm_basis *b, ftlm_dtype dtype, int B, const void *x, void *y,
                       const LanczosHv *epi, cudaStream_t stream)

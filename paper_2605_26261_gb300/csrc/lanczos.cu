@@ -263,7 +263,7 @@ std::vector<int> block_plan(int R, ftlm_dtype dtype, int bmax)
 
 struct Layout {
     int bw;  // widest block
-    uint64_t vec0, vec1, partials, state, alpha, beta, meff, total;
+    uint64_t vec0, vec1, partials, state, alpha, beta, meff, tiles, total;
 };
 
 Layout layout(const ftlm_basis *b, int R, int M, ftlm_dtype dtype, int bmax = 0)
@@ -279,7 +279,9 @@ Layout layout(const ftlm_basis *b, int R, int M, ftlm_dtype dtype, int bmax = 0)
     l.alpha = l.state + align256(l.bw * sizeof(ChainState) + 64);
     l.beta = l.alpha + align256((uint64_t)R * M * sizeof(double));
     l.meff = l.beta + align256((uint64_t)R * M * sizeof(double));
-    l.total = l.meff + align256((uint64_t)R * sizeof(int));
+    l.tiles = l.meff + align256((uint64_t)R * sizeof(int));
+    // per-tile alpha sums of dynamically ordered H.v launches (B >= 4 has the most tiles)
+    l.total = l.tiles + align256((uint64_t)hv_lanczos_tiles(b, 4) * l.bw * sizeof(double));
     return l;
 }
 
@@ -315,7 +317,7 @@ ftlm_status run_block(const ftlm_basis *b, int M, int r0, int chain0, uint64_t s
     FTLM_CUDA(cudaGetLastError());
     int cur = 0;
     for (int j = 1; j <= m_max; ++j) {
-        LanczosHv epi{st, partials, counter, alpha_ws + (size_t)r0 * M + (j - 1), M, j};
+        LanczosHv epi{st, partials, counter, alpha_ws + (size_t)r0 * M + (j - 1), M, j, (double *)(ws + lay.tiles)};
         ftlm_status s = launch_hv(b, dtype, B, vec[cur], vec[1 - cur], &epi, stream);
         if (s != FTLM_OK) return s;
         void *tok = profile_begin(kProfUpdate, stream);

@@ -25,6 +25,10 @@
 
 namespace ftlm {
 
+#ifndef FTLM_MS_DYN
+#define FTLM_MS_DYN 1
+#endif
+
 namespace {
 
 struct UnitView {
@@ -44,21 +48,18 @@ struct UnitView {
 
 // Store this tile's B block sums at tile slot k of the unit; returns true (in every
 // thread) in the CTA that completes the unit.
-// The B sums share three barriers: warp trees for every chain, then thread r adds
-// chain r's warp sums in warp order (fixed order, reproducible).
-template <int B>
-__device__ __forceinline__ bool tile_publish(const double (&part)[B], double *partials, uint32_t k,
+// The B sums share three barriers: one transposed warp tree for all chains, then
+// thread r adds chain r's warp sums in warp order (fixed order, reproducible).
+template <typename V, int B>
+__device__ __forceinline__ bool tile_publish(DotAcc<V> (&acc)[B], double *partials, uint32_t k,
                                              unsigned int *counter, uint32_t n_tiles)
 {
     constexpr int kWarps = kRowThreads / 32;
     __shared__ double s_w[kWarps][B];
     __shared__ bool s_last;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int r = 0; r < B; ++r) {
-        const double v = warp_sum(part[r]);
-        if (lane == 0) s_w[wid][r] = v;
-    }
+    const DotAcc<V> t = warp_sum_multi<V, B>(acc);
+    if (lane < B) s_w[wid][warp_multi_index<B>(lane)] = t.value();
     __syncthreads();
     if (threadIdx.x < B) {
         double t = 0.0;
@@ -106,10 +107,7 @@ ms_start_kernel(const MsUnit *__restrict__ units, const uint32_t *__restrict__ t
             }
             st_vec<B>(u0 + (size_t)t * B, out);
         }
-        double part[B];
-#pragma unroll
-        for (int r = 0; r < B; ++r) part[r] = acc[r].value();
-        if (tile_publish<B>(part, uv.partials(), k, uv.counter(), U.n_stiles) && threadIdx.x < 32) {
+        if (tile_publish<V, B>(acc, uv.partials(), k, uv.counter(), U.n_stiles) && threadIdx.x < 32) {
             ChainState *st = uv.st();
             for (int r = 0; r < B; ++r) {
                 const double nrm = sqrt(tile_total<B>(uv.partials(), U.n_stiles, r));
@@ -152,10 +150,14 @@ ms_hv_kernel(const MsUnit *__restrict__ units, const uint32_t *__restrict__ tile
     __shared__ V s_cf[SPIN ? kSpinCoef : 1];
     __shared__ V s_inv_s[B], s_c_prev[B];
     __shared__ int s_skip;
+    __shared__ uint32_t s_next;
     uint32_t loaded = 0xffffffffu;
     EpiDev ep{};
     ep.has_prev = j > 1;
-    for (uint32_t g = blockIdx.x; g < n_tiles; g += gridDim.x) {
+    // experimental (FTLM_MS_DYN): tiles after the first from a counter of the wave's
+    // first unit (its words 1 and 2: tiles handed out, CTAs done)
+    unsigned int *wctr = reinterpret_cast<unsigned int *>(ws + units[0].off_st + (size_t)kMaxBlock * sizeof(ChainState)) + 1;
+    for (uint32_t g = blockIdx.x; g < n_tiles;) {
         const uint32_t ui = tile_unit[g];
         const UnitView uv{units + ui, ws};
         const MsUnit &U = *uv.u;
@@ -187,7 +189,7 @@ ms_hv_kernel(const MsUnit *__restrict__ units, const uint32_t *__restrict__ tile
             }
             __syncthreads();
         }
-        if (s_skip) continue;  // CTA-uniform
+        if (!s_skip) {  // CTA-uniform
         const uint32_t k = g - U.tile0, D = U.s.D;
         const V *x = uv.vec<V>((j - 1) & 1);
         V *y = uv.vec<V>(j & 1);
@@ -212,10 +214,7 @@ ms_hv_kernel(const MsUnit *__restrict__ units, const uint32_t *__restrict__ tile
                 if (ok) epi_row<V, B, true>(ep, s_inv_s, s_c_prev, x, y, t[0], jsum4 - dsum[0], acc[0], apart);
             }
         }
-        double part[B];
-#pragma unroll
-        for (int r = 0; r < B; ++r) part[r] = apart[r].value();
-        if (tile_publish<B>(part, uv.partials(), k, uv.counter(), U.n_tiles) && threadIdx.x < 32) {
+        if (tile_publish<V, B>(apart, uv.partials(), k, uv.counter(), U.n_tiles) && threadIdx.x < 32) {
             ChainState *st = uv.st();
             for (int r = 0; r < B; ++r) {
                 const double v = tile_total<B>(uv.partials(), U.n_tiles, r);
@@ -227,6 +226,22 @@ ms_hv_kernel(const MsUnit *__restrict__ units, const uint32_t *__restrict__ tile
             if (threadIdx.x == 0) *uv.counter() = 0;
         }
         __syncthreads();
+        }
+        if (FTLM_MS_DYN) {
+            if (threadIdx.x == 0) s_next = atomicAdd(wctr, 1u) + gridDim.x;
+            __syncthreads();
+            g = s_next;
+            __syncthreads();
+        } else {
+            g += gridDim.x;
+        }
+    }
+    if (FTLM_MS_DYN && threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(wctr + 1, 1u) == gridDim.x - 1) {
+            wctr[0] = 0;
+            wctr[1] = 0;
+        }
     }
 }
 
@@ -295,10 +310,7 @@ ms_update_kernel(const MsUnit *__restrict__ units, const uint32_t *__restrict__ 
             y[e] = w;
             acc[0].add(w, w);
         }
-        double part[B];
-#pragma unroll
-        for (int r = 0; r < B; ++r) part[r] = acc[r].value();
-        if (tile_publish<B>(part, uv.partials(), k, uv.counter(), U.n_stiles) && threadIdx.x < 32) {
+        if (tile_publish<V, B>(acc, uv.partials(), k, uv.counter(), U.n_stiles) && threadIdx.x < 32) {
             ChainState *st = uv.st();
             for (int r = 0; r < B; ++r) {
                 const double bt = sqrt(tile_total<B>(uv.partials(), U.n_stiles, r));

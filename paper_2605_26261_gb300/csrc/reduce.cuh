@@ -86,13 +86,75 @@ template <> struct DotAcc<float> {
         hi = s;
         lo = __fadd_rn(lo, __fadd_rn(err, e));
     }
+    // Adds another accumulator: TwoSum of the high parts, low parts summed.  The
+    // TwoSum error is exact, so a.merge(b) and b.merge(a) give the same bits.
+    __device__ __forceinline__ void merge(const DotAcc &o)
+    {
+        const float s = __fadd_rn(hi, o.hi);
+        const float bv = __fsub_rn(s, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(o.hi, bv));
+        hi = s;
+        lo = __fadd_rn(__fadd_rn(lo, o.lo), err);
+    }
+    __device__ __forceinline__ DotAcc shfl_xor(int o) const
+    {
+        DotAcc r;
+        r.hi = __shfl_xor_sync(0xffffffffu, hi, o);
+        r.lo = __shfl_xor_sync(0xffffffffu, lo, o);
+        return r;
+    }
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
 template <> struct DotAcc<double> {
     double v = 0.0;
     __device__ __forceinline__ void add(double a, double b) { v = fma(a, b, v); }
+    __device__ __forceinline__ void merge(const DotAcc &o) { v += o.v; }
+    __device__ __forceinline__ DotAcc shfl_xor(int o) const
+    {
+        DotAcc r;
+        r.v = __shfl_xor_sync(0xffffffffu, v, o);
+        return r;
+    }
     __device__ __forceinline__ double value() const { return v; }
 };
+
+// Warp sums of B accumulators (B = 1, 2, 4, 8 or 16) by a transposed butterfly: at
+// each of the first log2(B) levels a lane keeps one half of its partial sums, sends
+// the other half to its partner and merges what it receives (B - 1 merges and
+// shuffles in all, instead of 5 B), then a plain butterfly over the remaining
+// lanes.  Lane l ends with the sum of accumulator warp_multi_index<B>(l): the bit
+// reversal of its low log2(B) bits, so lanes 0 .. B-1 hold the B sums.  The tree
+// is fixed: reproducible.
+template <typename V, int B>
+__device__ __forceinline__ DotAcc<V> warp_sum_multi(DotAcc<V> (&a)[B])
+{
+    static_assert(B == 1 || B == 2 || B == 4 || B == 8 || B == 16, "B must be a power of two <= 16");
+    const unsigned lane = threadIdx.x & 31u;
+#pragma unroll
+    for (int lvl = 0; (B >> lvl) > 1; ++lvl) {
+        const int h = (B >> lvl) / 2;
+        const bool upper = (lane >> lvl) & 1u;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            DotAcc<V> keep = upper ? a[i + h] : a[i];
+            const DotAcc<V> send = upper ? a[i] : a[i + h];
+            keep.merge(send.shfl_xor(1 << lvl));
+            a[i] = keep;
+        }
+    }
+    DotAcc<V> t = a[0];
+#pragma unroll
+    for (int o = B; o < 32; o <<= 1) t.merge(t.shfl_xor(o));
+    return t;
+}
+
+template <int B> __device__ __forceinline__ int warp_multi_index(unsigned lane)
+{
+    int r = 0;
+#pragma unroll
+    for (int lvl = 0; (B >> lvl) > 1; ++lvl) r += ((lane >> lvl) & 1u) ? (B >> (lvl + 1)) : 0;
+    return r;
+}
 
 }  // namespace ftlm

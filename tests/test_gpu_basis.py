@@ -95,7 +95,8 @@ def test_update_count_matches_eq10(cuda_dev, name, N, K, bonds):
     ref = o.basis(N, K)
     with ftlm.Basis(N, 2 * K - N, bonds) as b:
         assert b.updates == len(ref) + o.offdiag_terms(bonds, ref)
-        assert b.mode == ftlm.RANK_CLT  # AUTO: small CLT tables fit
+        # AUTO: CLT below 2^20 rows (its small tables fit), CR from there up
+        assert b.mode == (ftlm.RANK_CLT if len(ref) < 1 << 20 else ftlm.RANK_CR)
 
 
 def test_auto_mode_picks_cr_when_clt_cannot_be_built(cuda_dev):

@@ -62,7 +62,13 @@ def test_launch_counter(cuda_dev):
     ftlm.ftlm_hv(b.handle, x, y)
     assert ftlm.ftlm_launch_count() - c1 == 1
     c2 = ftlm.ftlm_launch_count()
-    ftlm.lanczos(b, R, M, dtype=torch.float32)  # one block of 8: start, M x (H.v + update), m_eff copy, Ritz
-    assert ftlm.ftlm_launch_count() - c2 == 1 + 2 * M + 1 + 1
+    # one block of 8: start, M x (H.v + tile alpha sums + update), m_eff copy, Ritz
+    ftlm.lanczos(b, R, M, dtype=torch.float32)
+    assert ftlm.ftlm_launch_count() - c2 == 1 + 3 * M + 1 + 1
     torch.cuda.synchronize()
     b.close()
+    with ftlm.Basis(N, 0, bonds, ftlm.RANK_CLT) as b:  # CLT: the H.v launch finishes alpha itself
+        c3 = ftlm.ftlm_launch_count()
+        ftlm.lanczos(b, R, M, dtype=torch.float32)
+        assert ftlm.ftlm_launch_count() - c3 == 1 + 2 * M + 1 + 1
+        torch.cuda.synchronize()
