@@ -3,9 +3,9 @@
 //
 // The units are blocks of B chains of mid-sized and large sectors.  Their rows are
 // cut into tiles of kMsTileRows; one launch walks the tiles of every unit of a
-// wave (a persistent grid, tiles dealt round-robin, so at any moment the GPU works
-// on a window of consecutive tiles -- one or two sectors -- whose vectors stay in
-// L2).  Per Lanczos step there are two launches for the whole wave: the fused
+// wave (a persistent grid; the H.v launch hands tiles out in order from a counter,
+// so at any moment the GPU works on a window of consecutive tiles -- one or two
+// sectors -- whose vectors stay in L2).  Per Lanczos step there are two launches for the whole wave: the fused
 // H.v + alpha epilogue and the w/beta update, each with per-unit reductions:
 // every tile stores its partial sums, and the CTA that finishes a unit's last tile
 // (an atomic ticket per unit, no waiting) adds the unit's partials in tile order.
@@ -24,10 +24,6 @@
 #include "vec.cuh"
 
 namespace ftlm {
-
-#ifndef FTLM_MS_DYN
-#define FTLM_MS_DYN 1
-#endif
 
 namespace {
 
@@ -154,8 +150,9 @@ ms_hv_kernel(const MsUnit *__restrict__ units, const uint32_t *__restrict__ tile
     uint32_t loaded = 0xffffffffu;
     EpiDev ep{};
     ep.has_prev = j > 1;
-    // experimental (FTLM_MS_DYN): tiles after the first from a counter of the wave's
-    // first unit (its words 1 and 2: tiles handed out, CTAs done)
+    // tiles after the first come from a counter in the wave's first unit (its words
+    // 1 and 2: tiles handed out, CTAs done; zeroed by ms_reset_kernel and again by
+    // the last CTA of each launch)
     unsigned int *wctr = reinterpret_cast<unsigned int *>(ws + units[0].off_st + (size_t)kMaxBlock * sizeof(ChainState)) + 1;
     for (uint32_t g = blockIdx.x; g < n_tiles;) {
         const uint32_t ui = tile_unit[g];
@@ -227,16 +224,12 @@ ms_hv_kernel(const MsUnit *__restrict__ units, const uint32_t *__restrict__ tile
         }
         __syncthreads();
         }
-        if (FTLM_MS_DYN) {
-            if (threadIdx.x == 0) s_next = atomicAdd(wctr, 1u) + gridDim.x;
-            __syncthreads();
-            g = s_next;
-            __syncthreads();
-        } else {
-            g += gridDim.x;
-        }
+        if (threadIdx.x == 0) s_next = atomicAdd(wctr, 1u) + gridDim.x;
+        __syncthreads();
+        g = s_next;
+        __syncthreads();  // every thread has read s_next before thread 0 writes it again
     }
-    if (FTLM_MS_DYN && threadIdx.x == 0) {
+    if (threadIdx.x == 0) {
         __threadfence();
         if (atomicAdd(wctr + 1, 1u) == gridDim.x - 1) {
             wctr[0] = 0;
