@@ -58,22 +58,25 @@ namespace {
 // 256 threads, the shared-memory limit of the CR kernel); 4 rows per thread and
 // blocks of 4-8 vectors get at least 3 CTAs per SM (fewer starve the loads), 2 with
 // 8-bond chunks of 8-wide blocks (their 16 gathers per row in flight carry it);
-// 16-wide blocks keep all their registers (a cap spills).
-// Resident CTAs per SM the register budget is cut for (build option
-// FTLM_B8_MIN_CTAS for the 8-wide blocks with chunks of 4 bonds).
+// 16-wide blocks keep all their registers (a cap spills).  FP64 vectors need about
+// twice the registers: 4 CTAs for single vectors (3 with 2 rows per thread, 2 with
+// 4), 2 for blocks of 4 and 1 for wider blocks, none of them spilling.
+// Build option FTLM_B8_MIN_CTAS: the FP32 cut for 8-wide blocks with chunks of 4.
 #ifndef FTLM_B8_MIN_CTAS
 #define FTLM_B8_MIN_CTAS 3
 #endif
 
-template <int RT, int B, int C> __host__ __device__ constexpr int min_ctas()
+template <typename V, int RT, int B, int C> __host__ __device__ constexpr int min_ctas()
 {
+    if (sizeof(V) == 8)  // FP64 accumulators and gathers take twice the registers
+        return B >= 8 ? 1 : (B >= 4 ? 2 : (RT >= 4 ? 2 : (RT >= 2 ? 3 : 4)));
     return B >= 16 ? 1
                    : (B >= 8 && C >= 8 ? 2
                                        : (B >= 8 && C <= 2 ? 4 : (B >= 8 ? FTLM_B8_MIN_CTAS : (B >= 4 || RT >= 4 ? 3 : 6))));
 }
 
 template <typename V, typename Lbl, bool CLT, bool LANCZOS, int RT, int B, int C>
-__global__ void __launch_bounds__(kRowThreads, min_ctas<RT, B, C>())
+__global__ void __launch_bounds__(kRowThreads, min_ctas<V, RT, B, C>())
 hv_kernel(const SectorTables s, const BondList bl, const V *__restrict__ x, V *y, const EpiDev ep)
 {
     // CR Lanczos launches take their tiles in dynamic order (their gathers gain the
