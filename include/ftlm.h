@@ -174,11 +174,12 @@ ftlm_status ftlm_hv_block(const ftlm_basis *basis, ftlm_dtype dtype, int B, cons
 
 /* ---------------------------------------------------------------- Lanczos ---
  * Workspace bytes ftlm_lanczos / ftlm_lanczos_from need for R chains of at most M
- * steps: two blocks of D x B_w elements of dtype plus O(R M) coefficients, B_w the
- * widest block of chains the call runs at once (chains go in blocks of 16, 8 or 4
- * interleaved vectors, up to the width of ftlm_lanczos_set_block -- by default 8
- * in FP32 and 4 in FP64 -- then single chains).  EINVAL for R < 1 or M outside
- * 1..FTLM_MAX_LANCZOS. */
+ * steps: two blocks of D x B_w elements of dtype plus O(R M) coefficients, and for
+ * CR spin-1/2 sectors ceil(D / 32) x B_w doubles of per-tile dot-product sums; B_w
+ * is the widest block of chains the call runs at once (chains go in blocks of 16,
+ * 8 or 4 interleaved vectors, up to the width of ftlm_lanczos_set_block -- by
+ * default 8 in FP32 and 4 in FP64 -- then single chains).  EINVAL for R < 1 or M
+ * outside 1..FTLM_MAX_LANCZOS. */
 ftlm_status ftlm_lanczos_workspace_bytes(const ftlm_basis *basis, int R, int M, ftlm_dtype dtype,
                                          uint64_t *bytes);
 
@@ -208,7 +209,9 @@ ftlm_status ftlm_lanczos_set_block(int width);
  *   Chains run in blocks (see ftlm_lanczos_workspace_bytes) through ftlm_hv_block's
  *   kernel; every chain's arithmetic is its own, so a chain's result does not
  *   depend on the other chains of its block, up to the summation order of the
- *   dot products.
+ *   dot products.  Every sum runs in a fixed order for a given sector, block width
+ *   and device, so repeated calls give bit-identical outputs (CR launches hand out
+ *   row tiles dynamically, but each tile's sums have a slot of their own).
  * Outputs (device, row r of chain r, each row M long, entries >= m_eff zero):
  *   theta_dev, weight_dev: double[R*M];  m_eff_dev: int[R];
  *   alpha_dev, beta_dev: double[R*M] or NULL (Lanczos coefficients; beta row r

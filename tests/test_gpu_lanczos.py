@@ -135,13 +135,21 @@ def test_workspace_too_small_is_rejected(cuda_dev):
         assert e.value.status == ftlm.FTLM_ENOMEM
 
 
-def test_repeated_runs_are_bit_identical(cuda_dev):
-    with ftlm.Basis(16, 0, inputs.ring(16)) as b:
-        r1 = ftlm.lanczos(b, 2, 30, seed=4, dtype=torch.float32, keep_coeffs=True)
-        r2 = ftlm.lanczos(b, 2, 30, seed=4, dtype=torch.float32, keep_coeffs=True)
+@pytest.mark.parametrize("N,bonds,mode,R,M", [
+    (16, inputs.ring(16), ftlm.RANK_AUTO, 2, 30),
+    # CR H.v launches take their 32-row tiles from a counter (2.7 M rows: far more
+    # tiles than warps, so which warp takes which tile varies from run to run);
+    # the per-tile alpha sums keep the coefficients bit-identical
+    (24, inputs.square_j1j2(), ftlm.RANK_CR, 9, 12),
+    (24, inputs.square_j1j2(), ftlm.RANK_CR, 1, 12),
+])
+def test_repeated_runs_are_bit_identical(cuda_dev, N, bonds, mode, R, M):
+    with ftlm.Basis(N, 0, bonds, mode) as b:
+        runs = [ftlm.lanczos(b, R, M, seed=4, dtype=torch.float32, keep_coeffs=True) for _ in range(3)]
         torch.cuda.synchronize()
-        for k in ("alpha", "beta", "theta", "weight"):
-            assert torch.equal(r1[k], r2[k])
+        for r in runs[1:]:
+            for k in ("alpha", "beta", "theta", "weight", "m_eff"):
+                assert torch.equal(runs[0][k], r[k]), k
 
 
 def random_tridiagonals(n, M, seed):
