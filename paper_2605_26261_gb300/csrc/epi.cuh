@@ -132,12 +132,17 @@ __device__ __forceinline__ void epi_end(const EpiDev &ep, DotAcc<V> (&apart)[B])
 
 // Dynamic tile order: a warp's first tile is its index, later ones come from the
 // counter ep.counter[1]; ep.counter[2] counts the warps that ran out of tiles, and
-// the last of them zeroes both for the next launch (they start at zero).
-__device__ __forceinline__ uint32_t next_tile(const EpiDev &ep, uint32_t nwarps)
+// the last of them zeroes both for the next launch (they start at zero).  A warp
+// claims its next tile when it starts a tile (claim_tile, lane 0) and reads the
+// claim when it finishes (claimed_tile), so the atomic's round trip is hidden.
+__device__ __forceinline__ uint32_t claim_tile(const EpiDev &ep)
 {
-    uint32_t t = 0;
-    if ((threadIdx.x & 31u) == 0) t = atomicAdd(ep.counter + 1, 1u) + nwarps;
-    return __shfl_sync(0xffffffffu, t, 0);
+    return (threadIdx.x & 31u) == 0 ? atomicAdd(ep.counter + 1, 1u) : 0u;
+}
+
+__device__ __forceinline__ uint32_t claimed_tile(uint32_t claim, uint32_t nwarps)
+{
+    return __shfl_sync(0xffffffffu, claim, 0) + nwarps;
 }
 
 __device__ __forceinline__ void tiles_done(const EpiDev &ep, uint32_t nwarps)

@@ -100,7 +100,9 @@ hv_kernel(const SectorTables s, const BondList bl, const V *__restrict__ x, V *y
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t tile_rows = 32u * RT;
     const uint32_t ntiles = (uint32_t)(((uint64_t)s.D + tile_rows - 1) / tile_rows);
-    for (uint32_t tile = warp; tile < ntiles; tile = TILES ? next_tile(ep, nwarps) : tile + nwarps) {
+    for (uint32_t tile = warp; tile < ntiles;) {
+        // claim the next tile now; its atomic completes while this tile's rows run
+        const uint32_t claim = TILES ? claim_tile(ep) : 0u;
         uint32_t t[RT];
         bool ok[RT];
 #pragma unroll
@@ -129,6 +131,7 @@ hv_kernel(const SectorTables s, const BondList bl, const V *__restrict__ x, V *y
             for (int i = 0; i < RT; ++i)
                 if (ok[i]) epi_row<V, B, LANCZOS>(ep, s_inv_s, s_c_prev, x, y, t[i], jsum4 - dsum[i], acc[i], apart);
         }
+        tile = TILES ? claimed_tile(claim, nwarps) : tile + nwarps;
     }
     if (TILES) tiles_done(ep, nwarps);
     else if (LANCZOS) epi_end<V, B, kRowThreads>(ep, apart);
