@@ -14,7 +14,7 @@ Parts:
   spin.py        general local spin s: Eq. 15 dimensions, Eq. 10 N_nz, base-d
                  basis, H.v (Eq. 12-14), Lanczos and the FTLM driver.
   diagnostics.py FP32 diagnostics: Cullum-Willoughby ghosts and clusters (Eq. 25),
-                 sigma_emp (Eq. 22), sigma_theo.
+                 sigma_emp (Eq. 22).
 """
 from .ftlm import *  # noqa: F401,F403
 from . import counting  # noqa: F401

@@ -8,7 +8,6 @@ Written from Sec. 3.1-3.2 of the paper:
                W_T = theta_max - theta_min; clusters join ascending Ritz values
                closer than tau (transitively), with their total weight.
   sigma_emp()  Eq. 22 with the printed 1/N_s.
-  sigma_theo() O / sqrt(Z_eff), Z_eff = Tr exp(-beta (H - E0)).
 """
 import numpy as np
 
@@ -50,6 +49,3 @@ def sigma_emp(obs):
     mean = obs.mean(axis=0)
     return mean, np.sqrt(np.sum((obs - mean) ** 2, axis=0) / obs.shape[0])
 
-
-def sigma_theo(O, Z_eff):
-    return np.abs(np.asarray(O)) / np.sqrt(np.asarray(Z_eff))
