@@ -10,11 +10,16 @@ namespace ftlm {
 #define FTLM_MS_TILE_ROWS 2048
 #endif
 constexpr uint32_t kMsTileRows = FTLM_MS_TILE_ROWS;
-// Rows per tile of the streaming kernels (start vectors, update): four H.v tiles.
+// Rows per tile of the streaming kernels (start vectors, update): eight H.v tiles.
 // The update's work per row is a few loads, so larger tiles amortize the per-tile
 // reduction (measured on the 256-cluster step: update 3.7 / 2.0 / 1.5 / 1.1 s per
-// step at 1024 / 2048 / 4096 / 8192 rows, H.v best at 2048).
-constexpr uint32_t kMsStreamRows = 4 * kMsTileRows;
+// step at 1024 / 2048 / 4096 / 8192 rows with one FP64 tree per chain; with the
+// transposed trees 1.35 / 1.18 / 1.67 s at 8192 / 16384 / 32768 rows; H.v best at
+// 2048).  Build option FTLM_MS_STREAM_ROWS.
+#ifndef FTLM_MS_STREAM_ROWS
+#define FTLM_MS_STREAM_ROWS (8 * FTLM_MS_TILE_ROWS)
+#endif
+constexpr uint32_t kMsStreamRows = FTLM_MS_STREAM_ROWS;
 
 // One block of B chains of one sector.  Offsets are into the run's workspace.
 struct MsUnit {
