@@ -272,13 +272,15 @@ ftlm_status ftlm_lanczos_noalloc(const ftlm_basis *basis, int R, int M, uint64_t
  *   of `block` chains (block = 1, 4, 8 or 16; 0 = 16 for FP32, 8 for FP64) that one
  *   persistent kernel runs, one CTA per unit at a time, each unit's chains entirely
  *   inside its CTA (vectors in a per-CTA workspace slot, CTA-local reductions).
- *   Larger spin-1/2 sectors (N <= 32) are cut into units of `block` chains that
- *   advance together, all units of a wave per launch (two launches per Lanczos
- *   step: H.v with alpha, update with beta; per-unit reductions over tiles of 2048
- *   rows; waves of at most FTLM_MS_WAVE_MB = 256 MB of vectors) on a stream
- *   forked from the caller's.  General-spin sectors and N > 32 run the launch
- *   sequence of ftlm_lanczos with blocks of up to `block` chains, spread over up to
- *   `streams` side streams (1..8; 0 = FTLM_BATCH_STREAMS or 4).  Uploads the plan's descriptors on
+ *   Larger spin-1/2 sectors with N <= 32, and every general-spin sector, are cut
+ *   into units of `block` chains that advance together, all units of a wave per
+ *   launch (two launches per Lanczos step: H.v with alpha, update with beta;
+ *   per-unit reductions over tiles of 2048 rows for H.v, handed out in order from
+ *   a counter, and 16384 rows for the update; waves of at most FTLM_MS_WAVE_MB =
+ *   256 MB of vectors) on a stream forked from the caller's.  Spin-1/2 sectors
+ *   with N > 32 run the launch sequence of ftlm_lanczos with blocks of up to
+ *   `block` chains, spread over up to `streams` side streams (1..8; 0 =
+ *   FTLM_BATCH_STREAMS or 4).  Uploads the plan's descriptors on
  *   `stream` (one block from the library's device memory pool, owned by the
  *   batch) and returns when they are in place.  EINVAL for an empty batch or bad
  *   items.
