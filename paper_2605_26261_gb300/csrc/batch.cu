@@ -1,11 +1,16 @@
 // Batched FTLM chains for many sectors at once (steps a2, a4, a5 over a batch).
 //
-// A batch lists sectors (of one or many clusters) with R chains each.  Sectors of
-// dimension above kSmallRows run through the grid-wide launch sequence of
-// ftlm_lanczos on up to kMaxSideStreams side streams forked from the caller's
-// stream (longest work first, each to the least-loaded stream), so mid-sized
-// sectors, whose launches fill only part of the GPU, overlap.  All smaller sectors are cut into work units
-// of B chains and handed to ONE persistent launch: each CTA takes the next unit
+// A batch lists sectors (of one or many clusters) with R chains each, routed by
+// size:
+//  - spin-1/2 sectors of dimension above kSmallRows with N <= 32, and every
+//    general-spin sector, run the multi-sector path (msv.cu): units of B chains
+//    of many sectors advance together, two launches per Lanczos step per wave, on
+//    a stream forked from the caller's;
+//  - spin-1/2 sectors above kSmallRows with N > 32 run the grid-wide launch
+//    sequence of ftlm_lanczos on up to kMaxSideStreams side streams (longest work
+//    first, each to the least-loaded stream);
+//  - all smaller sectors are cut into work units of B chains and handed to ONE
+//    persistent launch on the caller's stream: each CTA takes the next unit
 // from an atomic counter (no waiting on other CTAs) and runs the unit's whole
 // chains by itself -- start vectors, min(M, D) steps of fused H.v + Lanczos
 // update with CTA-local reductions, stop tests -- with the unit's two vector blocks
