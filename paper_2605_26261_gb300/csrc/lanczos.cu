@@ -9,8 +9,9 @@
 // and publishes beta_j.  The division by beta_j is folded into the next H.v (the
 // stored vectors stay un-normalized, q_j = u_j / s_j), so every step streams each
 // vector exactly once per launch.  All scalars stay on the device; the host only
-// queues 2 launches per step, and a chain that breaks down (beta_j <= tau) turns
-// the rest of its launches into no-ops.
+// queues 2 launches per step (3 for CR sectors, whose H.v launch leaves alpha_j
+// as per-tile sums for a short second launch), and a chain that breaks down
+// (beta_j <= tau) turns the rest of its launches into no-ops.
 #include <cmath>
 #include <cstdlib>
 #include <atomic>
