@@ -90,7 +90,7 @@ def kron_h(N, two_s, bonds):
     return H
 
 
-@pytest.mark.parametrize("N,two_s,seed", [(4, 2, 1), (3, 3, 2), (5, 2, 3), (3, 4, 4)])
+@pytest.mark.parametrize("N,two_s,seed", [(4, 2, 1), (3, 3, 2), (5, 2, 3), (3, 4, 4), (3, 5, 5), (3, 7, 6)])
 def test_sector_spectra_match_kronecker_ed(N, two_s, seed):
     rng = np.random.default_rng(seed)
     pairs = [(i, j) for i in range(N) for j in range(i + 1, N)]
@@ -107,7 +107,7 @@ def test_sector_spectra_match_kronecker_ed(N, two_s, seed):
         np.testing.assert_allclose(Hs, H[np.ix_(idx, idx)], atol=1e-12)
 
 
-@pytest.mark.parametrize("two_s", [2, 3, 4, 6])
+@pytest.mark.parametrize("two_s", [2, 3, 4, 5, 6, 7])
 def test_two_spin_closed_form(two_s):
     s, J = two_s / 2, 0.8
     bonds = (np.array([0], dtype=np.int32), np.array([1], dtype=np.int32), np.array([J]))
