@@ -183,6 +183,7 @@ extern "C" const char *ftlm_status_string(ftlm_status s)
     case FTLM_EUNSUPPORTED: return "FTLM_EUNSUPPORTED: outside what the library implements";
     case FTLM_ECUDA: return "FTLM_ECUDA: CUDA runtime error";
     case FTLM_ETIMEOUT: return "FTLM_ETIMEOUT: device wait expired";
+    case FTLM_ENOCONV: return "FTLM_ENOCONV: a tridiagonal eigenproblem did not converge";
     }
     return "unknown ftlm_status";
 }

@@ -18,10 +18,13 @@ namespace ftlm {
 
 namespace {
 
+// T^(1) problems that did not converge (read and cleared by ftlm_ritz_status).
+__device__ unsigned long long g_ghost_unconverged;
+
 __global__ void ghost_kernel(int n, int M, const double *__restrict__ alpha, const double *__restrict__ beta,
                              const int *__restrict__ mv, const double *__restrict__ theta,
                              const double *__restrict__ weight, double c_tau, double u, double *ell, int *cluster,
-                             double *cweight, int *flags, int *count)
+                             double *cweight, int *flags, int *count, int max_sweeps)
 {
     extern __shared__ double sh[];
     const int T = blockDim.x, i = threadIdx.x;
@@ -39,9 +42,11 @@ __global__ void ghost_kernel(int n, int M, const double *__restrict__ alpha, con
         e[k] = k + 1 < m1 ? beta[o + 1 + k] : 0.0;
         z[k] = 0.0;
     }
+    bool ok = true;
     if (m1 > 1) {
-        tridiag_qr(d, e, z, m1);
-        sort_ascending(d, z, m1);
+        ok = tridiag_qr(d, e, z, m1, max_sweeps);
+        if (ok) sort_ascending(d, z, m1);
+        else atomicAdd(&g_ghost_unconverged, 1ull);
     }
     const double tau = m > 0 ? c_tau * u * (th[m - 1] - th[0]) : 0.0;
     int ghosts = 0, j = 0, start = 0;
@@ -53,6 +58,7 @@ __global__ void ghost_kernel(int n, int M, const double *__restrict__ alpha, con
                 while (j + 1 < m1 && fabs(d[j + 1] - th[k]) <= fabs(d[j] - th[k])) ++j;
                 l = fabs(d[j] - th[k]);
             }
+            if (!ok) l = NAN;  // no spectrum of T^(1): no ghost test
             const bool ghost = l < tau;
             ghosts += ghost;
             ell[o + k] = l;
@@ -97,6 +103,16 @@ __global__ void sigma_kernel(int ns, int nT, const double *__restrict__ obs, dou
 
 }  // namespace
 
+ftlm_status ghost_unconverged_take(cudaStream_t stream, uint64_t *count)
+{
+    unsigned long long v = 0, zero = 0;
+    FTLM_CUDA(cudaMemcpyFromSymbolAsync(&v, g_ghost_unconverged, sizeof(v), 0, cudaMemcpyDeviceToHost, stream));
+    FTLM_CUDA(cudaMemcpyToSymbolAsync(g_ghost_unconverged, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, stream));
+    FTLM_CUDA(cudaStreamSynchronize(stream));
+    *count = v;
+    return FTLM_OK;
+}
+
 }  // namespace ftlm
 
 using namespace ftlm;
@@ -121,7 +137,7 @@ extern "C" ftlm_status ftlm_ghosts(int n, int M, const double *alpha_dev, const 
     if (T > n) T = n;
     ghost_kernel<<<(n + T - 1) / T, T, per_chain * T, (cudaStream_t)stream>>>(
         n, M, alpha_dev, beta_dev, m_dev, theta_dev, weight_dev, c_tau, u, ell_dev, cluster_dev, cweight_dev,
-        flags_dev, count_dev);
+        flags_dev, count_dev, ritz_max_sweeps());
     note_launch();
     FTLM_CUDA(cudaGetLastError());
     return FTLM_OK;

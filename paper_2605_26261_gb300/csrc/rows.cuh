@@ -181,7 +181,8 @@ __device__ __forceinline__ void rows_clt(const SectorTables &s, const BondList &
 }
 
 // One warp owns a tile of 32 RT consecutive rows; lane l handles rows
-// tile_base + l + 32 i (i < RT).  Tiles are dealt to warps round-robin, so the
-// whole grid works on one contiguous window of rows at a time.
+// tile_base + l + 32 i (i < RT).  The launches hand the tiles out in row order --
+// round-robin over the warps (plain H.v, CLT) or from a counter (CR Lanczos) --
+// so the whole grid works on one contiguous window of rows at a time.
 
 }  // namespace ftlm

@@ -41,10 +41,13 @@ __device__ __forceinline__ bool negligible(double e, double d0, double d1)
     return fabs(e) <= 0x1p-52 * (fabs(d0) + fabs(d1)) || fabs(e) < 1e-150;
 }
 
-static __device__ void tridiag_qr(Strided d, Strided e, Strided z, int n)
+// Returns false when the bottom-up deflation has not reached the top after
+// max_sweeps QR sweeps (0: 64 n, far more than the few sweeps per eigenvalue that
+// the Wilkinson shift needs); d and z then hold no eigendecomposition.
+static __device__ bool tridiag_qr(Strided d, Strided e, Strided z, int n, int max_sweeps = 0)
 {
     int hi = n - 1;
-    const int max_sweeps = 64 * n;
+    if (max_sweeps <= 0) max_sweeps = 64 * n;
     for (int sweep = 0; hi > 0 && sweep < max_sweeps;) {
         if (negligible(e[hi - 1], d[hi - 1], d[hi])) {
             e[hi - 1] = 0.0;
@@ -80,6 +83,13 @@ static __device__ void tridiag_qr(Strided d, Strided e, Strided z, int n)
             z[k + 1] = s * z0 + c * z1;
         }
     }
+    // converged when every remaining off-diagonal entry is negligible (the last
+    // permitted sweep may have finished the job)
+    for (int k = hi - 1; k >= 0; --k) {
+        if (!negligible(e[k], d[k], d[k + 1])) return false;
+        e[k] = 0.0;
+    }
+    return true;
 }
 
 // Ascending order of d (and z with it), insertion sort (n <= FTLM_MAX_LANCZOS).

@@ -183,6 +183,35 @@ def test_ritz_matches_dense_eigh(cuda_dev, M):
         assert np.all(th[c, k:] == 0) and np.all(w[c, k:] == 0)
 
 
+def test_ritz_reports_non_convergence(cuda_dev):
+    """A sweep limit far below what implicit QR needs leaves every chain with m > 1
+    unconverged: its theta and weight rows are NaN, ftlm_ritz_status counts it and
+    returns FTLM_ENOCONV; with the default limit the same input converges."""
+    n, M = 6, 40
+    a, b, _ = random_tridiagonals(n, M, M)
+    m = np.array([1, 40, 40, 30, 20, 10], dtype=np.int32)  # a 1 x 1 problem needs no sweep
+    args = [torch.as_tensor(v, device=cuda_dev) for v in (a, b, m)]
+    th = torch.empty((n, M), dtype=torch.float64, device=cuda_dev)
+    w = torch.empty_like(th)
+    ftlm.ftlm_ritz_status()  # start from a clear count
+    try:
+        ftlm.ftlm_ritz_set_max_sweeps(1)
+        ftlm.ftlm_ritz(n, M, *args, th, w)
+        with pytest.raises(ftlm.FtlmError) as e:
+            ftlm.ftlm_ritz_status()
+        assert e.value.status == ftlm.FTLM_ENOCONV and e.value.unconverged == n - 1
+    finally:
+        ftlm.ftlm_ritz_set_max_sweeps(0)
+    th_h, w_h = th.cpu().numpy(), w.cpu().numpy()
+    assert np.isfinite(th_h[0, 0]) and th_h[0, 0] == a[0, 0] and w_h[0, 0] == 1.0
+    for c in range(1, n):
+        assert np.all(np.isnan(th_h[c, :m[c]])) and np.all(np.isnan(w_h[c, :m[c]]))
+        assert np.all(th_h[c, m[c]:] == 0)
+    ftlm.ftlm_ritz(n, M, *args, th, w)
+    assert ftlm.ftlm_ritz_status() == 0
+    assert np.all(np.isfinite(th.cpu().numpy()))
+
+
 @pytest.mark.parametrize("R", [1, 8])
 def test_fp32_dot_products_accumulate_to_fp64_accuracy(cuda_dev, R):
     # FP32 vectors, FP64-class reductions: with dyadic start entries and J = 1 the
