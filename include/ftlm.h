@@ -50,7 +50,8 @@ typedef enum {
     FTLM_ENOMEM = 2,       /* device allocation failed / workspace too small       */
     FTLM_EUNSUPPORTED = 3, /* valid request outside what the library implements    */
     FTLM_ECUDA = 4,        /* a CUDA runtime call failed                           */
-    FTLM_ETIMEOUT = 5      /* reserved: a bounded device wait expired              */
+    FTLM_ETIMEOUT = 5,     /* reserved: a bounded device wait expired              */
+    FTLM_ENOCONV = 6       /* a tridiagonal eigenproblem did not converge          */
 } ftlm_status;
 
 typedef enum {
@@ -121,6 +122,34 @@ void ftlm_basis_destroy(ftlm_basis *basis);
  * NULL is ignored (FTLM_OK).  ECUDA if the release cannot be queued (the handle is
  * freed regardless). */
 ftlm_status ftlm_basis_destroy_async(ftlm_basis *basis, void *stream);
+
+/* ftlm_basis_set_schedule -- how the Lanczos H.v launches of this sector walk the
+ * rows (CR rank mode at s = 1/2; other sectors ignore it).  Eq. 12 is evaluated
+ * row by row in either case; only the order of the work and the launches differ.
+ *   FTLM_HV_ONE_WALK  one launch over the rows in sector (label) order.
+ *   FTLM_HV_SPLIT     two launches: the rows in label order with the bonds that
+ *                     touch the low digit block, then the rows in the transposed
+ *                     order (low-block rank fixed per lane, high patterns in turn)
+ *                     with the bonds inside the high block, which adds its terms
+ *                     to the first launch's output and finishes alpha_j.  A bond
+ *                     inside the high block moves a row by thi[h ^ m] - thi[h],
+ *                     far beyond L2 for the top sites in label order, but within
+ *                     the same 32 columns in the transposed order.
+ *   FTLM_HV_AUTO      (default) SPLIT when one block of B vectors of the call
+ *                     holds at least 64 MB, else ONE_WALK.
+ *   rows_per_tile: high patterns per tile of the transposed walk, 1..32, or 0 for
+ *   the default (8).  SPLIT needs 1..64 bonds inside the high block (the N - L
+ *   highest sites, L = min(N, 14)); otherwise the sector runs one walk.  Results
+ *   agree with ONE_WALK up to the summation order of each row (FP rounding).
+ *   Not thread-safe against Lanczos calls on the same basis.  EINVAL for a bad
+ *   schedule or rows_per_tile. */
+typedef enum { FTLM_HV_AUTO = 0, FTLM_HV_ONE_WALK = 1, FTLM_HV_SPLIT = 2 } ftlm_hv_schedule;
+ftlm_status ftlm_basis_set_schedule(ftlm_basis *basis, ftlm_hv_schedule schedule, int rows_per_tile);
+
+/* The walks (FTLM_HV_ONE_WALK or FTLM_HV_SPLIT) that Lanczos calls on this basis
+ * with blocks of B vectors of dtype use under its current schedule.  EINVAL for a
+ * bad B or dtype. */
+ftlm_status ftlm_basis_hv_schedule(const ftlm_basis *basis, int B, ftlm_dtype dtype, ftlm_hv_schedule *used);
 
 /* Sector dimension D = C(N, K). */
 ftlm_status ftlm_basis_dim(const ftlm_basis *basis, uint64_t *dim);
@@ -243,10 +272,20 @@ ftlm_status ftlm_lanczos_from(const ftlm_basis *basis, int R, int M, const doubl
  *   Scratch: a file-scope __device__ array of FTLM_NOALLOC_SCRATCH_BYTES inside the
  *   library.  Every GPU that loads the library holds it until the process exits.
  *   The first call on a device looks up the array's device address on the current
- *   device (cudaGetSymbolAddress); make that first call before any stream capture.
- *   Limit: the workspace ftlm_lanczos_workspace_bytes() reports for (R, M, dtype)
- *   must fit in the array, else FTLM_EUNSUPPORTED (two vectors of D elements plus
- *   O(R M) coefficients: about D <= 2 million in FP64, 4 million in FP32).
+ *   device (cudaGetSymbolAddress) and caches it with the id of the current
+ *   context; make that first call before any stream capture.  A device reset
+ *   (cudaDeviceReset) loads the library's device code again at a new address: the
+ *   next call sees the new context and looks the address up again, so after a
+ *   reset, too, the first call should come before any stream capture.
+ *   Limit: the call is accepted when ftlm_lanczos_workspace_bytes() for the same
+ *   (basis, R, M, dtype) is at most FTLM_NOALLOC_SCRATCH_BYTES (the exact test),
+ *   else FTLM_EUNSUPPORTED.  That workspace is about 2 B_w D s + D B_w / 4 bytes
+ *   plus O(R M) coefficients, with s = 8 (FP64) or 4 (FP32) bytes and B_w the widest
+ *   block of chains of the call: the largest of 16, 8, 4 not above both R and the
+ *   block width of ftlm_lanczos_set_block (default 4 in FP64, 8 in FP32), else 1.
+ *   With the 32 MiB array that admits about D <= 2.0 million (R < 4) and 0.5
+ *   million (R >= 4) in FP64; 4.0 million (R < 4), 1.0 million (4 <= R < 8) and
+ *   0.5 million (R >= 8) in FP32.
  *   Sharing: all calls on a device use the same array and it keeps the previous
  *   call's contents; each call clears what must start at zero.  Calls whose work
  *   overlaps on the GPU (different streams, or different host threads) race on the
@@ -339,6 +378,23 @@ ftlm_status ftlm_batch_autotune(int n_items, const ftlm_batch_item *items, int M
  * n < 0 or M outside 1..FTLM_MAX_LANCZOS. */
 ftlm_status ftlm_ritz(int n, int M, const double *alpha_dev, const double *beta_dev,
                       const int *m_dev, double *theta_dev, double *weight_dev, void *stream);
+
+/* Non-convergence of the tridiagonal eigenproblems.  The implicit QR of the Ritz
+ * step (ftlm_ritz, ftlm_lanczos*, ftlm_batch_run) and of the T^(1) spectra of
+ * ftlm_ghosts stops after a sweep limit (default 64 m sweeps for an m x m matrix;
+ * the Wilkinson shift converges in a few sweeps per eigenvalue).  A chain that
+ * reaches the limit gets NaN in its theta and weight rows (ftlm_ghosts: NaN ell,
+ * no ghost flags), so its NaN propagates into ftlm_thermo's observables, and the
+ * device counts it.  Those calls only queue work, so they cannot return the
+ * failure themselves:
+ * ftlm_ritz_status -- waits for `stream`, then returns the number of problems on
+ *   the current device that did not converge since the previous ftlm_ritz_status
+ *   (work of other streams counts once it has run) in *unconverged (may be NULL),
+ *   clears the count, and returns FTLM_ENOCONV when it is not zero.
+ * ftlm_ritz_set_max_sweeps -- process-wide sweep limit per problem for later
+ *   launches, 0 restores the default (for tests of this path).  EINVAL for < 0. */
+ftlm_status ftlm_ritz_status(void *stream, uint64_t *unconverged);
+ftlm_status ftlm_ritz_set_max_sweeps(int sweeps);
 
 /* ------------------------------------------------------------------ thermo ---
  * ftlm_thermo -- FTLM observables on a temperature grid (step a6, Eq. 6-9).

@@ -197,6 +197,40 @@ uint64_t align256(uint64_t v) { return (v + 255) & ~uint64_t(255); }
 
 int max_row_grid(const ftlm_basis *b) { return b->num_sms * kMaxBlocksPerSm; }
 
+bool build_hi_walk(const ftlm_basis *b, int rh, HiWalk *w)
+{
+    if (b->two_s != 1 || b->mode != FTLM_RANK_CR || !b->uhi) return false;
+    if (b->N <= b->L || b->n_hi_bonds < 1 || b->n_hi_bonds > kMaxHiBonds) return false;
+    if (rh < 1 || rh > 32) return false;
+    init_binom();
+    const int nhb = b->N - b->L;
+    HiWalk h{};
+    h.nbonds = b->n_hi_bonds;
+    h.rh = rh;
+    h.jsum4 = b->jsum4_hi;
+    h.uhi = b->uhi;
+    h.bonds = b->bond_slots + 6 * kMaxBondSlots;
+    uint64_t tiles = 0;
+    for (int q = 0; q <= b->L; ++q) {
+        const int p = b->K - q;
+        if (p < 0 || p > nhb) continue;
+        const uint64_t nl = binom(b->L, q), nh = binom(nhb, p);
+        if (!nl || !nh) continue;
+        const int g = h.ngroups++;
+        h.tile0[g] = (uint32_t)tiles;
+        h.nl[g] = (uint32_t)nl;
+        h.nh[g] = (uint32_t)nh;
+        h.hoff[g] = b->uhi_off[p];
+        h.nr[g] = (uint32_t)((nh + rh - 1) / rh);
+        tiles += ((nl + 31) / 32) * h.nr[g];
+    }
+    if (tiles >= (1ull << 32)) return false;
+    h.tile0[h.ngroups] = (uint32_t)tiles;
+    h.ntiles = (uint32_t)tiles;
+    *w = h;
+    return true;
+}
+
 void launch_hs_fill(const ftlm_basis *b, cudaStream_t stream)
 {
     hs_fill_kernel<<<grid_for(b->n_hs, 256, b->num_sms), 256, 0, stream>>>(b->tables(), b->n_hs, b->hs);
@@ -317,8 +351,8 @@ extern "C" ftlm_status ftlm_basis_create(int N, int two_sz, int n_bonds, const i
     double jsum4 = 0.0;
     for (int k = 0; k < n_bonds; ++k) jsum4 += J[k] / 4.0;
     auto round_up = [](int v) { return (v + kBondChunk - 1) / kBondChunk * kBondChunk; };
-    // host images of the four slot arrays
-    std::vector<uint4> slots(4 * (size_t)kMaxBondSlots, make_uint4(0u, 0u, 0u, 0u));
+    // host images of the slot arrays: CR, CLT and walk A (FP32 and FP64 each), walk B
+    std::vector<uint4> slots(7 * (size_t)kMaxBondSlots, make_uint4(0u, 0u, 0u, 0u));
     auto put = [&](int which, int pos, uint32_t mlo, uint32_t mhi, double jh) {
         float f = (float)jh;
         uint32_t fb;
@@ -356,6 +390,47 @@ extern "C" ftlm_status ftlm_basis_create(int N, int two_sz, int n_bonds, const i
         c.jsum4 = jsum4;
     }
     {
+        // split H.v: walk A takes the lo-lo bonds (whole chunks first) and the cross
+        // bonds, walk B the high-high bonds as one compact list
+        BondList &c = b->bonds_walk_a;
+        std::vector<int> lo, hi, rest;
+        for (int k = 0; k < n_bonds; ++k) {
+            bool il = bi[k] < L, jl = bj[k] < L;
+            (il && jl ? lo : (!il && !jl) ? hi : rest).push_back(k);
+        }
+        const int nlo = (int)lo.size() / kBondChunk * kBondChunk;
+        std::vector<int> order(lo.begin(), lo.begin() + nlo);
+        order.insert(order.end(), lo.begin() + nlo, lo.end());
+        order.insert(order.end(), rest.begin(), rest.end());
+        double j4 = 0.0;
+        for (int pos = 0; pos < (int)order.size(); ++pos) {
+            const int k = order[pos];
+            const uint64_t m = (1ull << bi[k]) | (1ull << bj[k]);
+            if (pos < nlo) put(2, pos, (uint32_t)m, 0u, J[k] / 2.0);
+            else put(2, pos, (uint32_t)m, (uint32_t)(m >> 32), J[k] / 2.0);
+            j4 += J[k] / 4.0;
+        }
+        c.n_lo = nlo;
+        c.n_hi = 0;
+        c.nb = nlo + round_up((int)order.size() - nlo);
+        c.jsum4 = j4;
+        b->n_hi_bonds = (int)hi.size();
+        double jh4 = 0.0;
+        for (int pos = 0; pos < (int)hi.size() && pos < kMaxBondSlots; ++pos) {
+            const int k = hi[pos];
+            const double jh = J[k] / 2.0;
+            const float f = (float)jh;
+            uint32_t fb;
+            std::memcpy(&fb, &f, 4);
+            uint64_t db;
+            std::memcpy(&db, &jh, 8);
+            const uint64_t m = ((1ull << bi[k]) | (1ull << bj[k])) >> L;
+            slots[(size_t)6 * kMaxBondSlots + pos] = make_uint4((uint32_t)m, fb, (uint32_t)db, (uint32_t)(db >> 32));
+            jh4 += J[k] / 4.0;
+        }
+        b->jsum4_hi = jh4;
+    }
+    {
         BondList &c = b->bonds_clt;
         for (int k = 0; k < n_bonds; ++k) {
             const uint64_t m = (1ull << bi[k]) | (1ull << bj[k]);
@@ -386,6 +461,18 @@ extern "C" ftlm_status ftlm_basis_create(int N, int two_sz, int n_bonds, const i
         }
         for (uint64_t h = 0; h < b->H; ++h) thi[h] = (uint32_t)count_below(h << L, N, K);
     }
+    // High patterns grouped by popcount, ascending (walk B of the split H.v).
+    std::vector<uint32_t> uhi(b->H);
+    {
+        const int nh = N - L;
+        uint32_t off = 0;
+        for (int p = 0; p <= kMaxHighBits + 1; ++p) {
+            b->uhi_off[p] = off;
+            if (p <= nh) off += (uint32_t)binom(nh, p);
+        }
+        std::vector<uint32_t> fill(b->uhi_off, b->uhi_off + kMaxHighBits + 2);
+        for (uint64_t h = 0; h < b->H; ++h) uhi[fill[popc64(h)]++] = (uint32_t)h;
+    }
 
     // One stream-ordered allocation holds every table: the small ones first (bond
     // slots, thi, tlo, ulo, uoff, and the binomials the CLT build reads), filled by
@@ -404,6 +491,7 @@ extern "C" ftlm_status ftlm_basis_create(int N, int two_sz, int n_bonds, const i
     const uint64_t o_tlo = take(nlo * sizeof(uint16_t));
     const uint64_t o_ulo = take(nlo * sizeof(uint16_t));
     const uint64_t o_uoff = take(sizeof(b->ulo_off));
+    const uint64_t o_uhi = take(b->H * sizeof(uint32_t));
     const uint64_t o_binom = clt ? take(33 * 33 * sizeof(uint64_t)) : off;
     const uint64_t small_bytes = off;
     const uint64_t o_hs = take(b->n_hs * sizeof(uint32_t));
@@ -417,6 +505,7 @@ extern "C" ftlm_status ftlm_basis_create(int N, int two_sz, int n_bonds, const i
     std::memcpy(image.data() + o_tlo, tlo.data(), nlo * sizeof(uint16_t));
     std::memcpy(image.data() + o_ulo, ulo.data(), nlo * sizeof(uint16_t));
     std::memcpy(image.data() + o_uoff, b->ulo_off, sizeof(b->ulo_off));
+    std::memcpy(image.data() + o_uhi, uhi.data(), b->H * sizeof(uint32_t));
     if (clt) {
         uint64_t *bh = reinterpret_cast<uint64_t *>(image.data() + o_binom);
         for (int n = 0; n <= 32; ++n)
@@ -441,6 +530,7 @@ extern "C" ftlm_status ftlm_basis_create(int N, int two_sz, int n_bonds, const i
     b->tlo = reinterpret_cast<uint16_t *>(base + o_tlo);
     b->ulo = reinterpret_cast<uint16_t *>(base + o_ulo);
     b->uoff = reinterpret_cast<uint32_t *>(base + o_uoff);
+    b->uhi = reinterpret_cast<uint32_t *>(base + o_uhi);
     b->hs = reinterpret_cast<uint32_t *>(base + o_hs);
     b->basis = clt ? reinterpret_cast<uint32_t *>(base + o_basis) : nullptr;
     b->clt = clt ? reinterpret_cast<uint2 *>(base + o_clt) : nullptr;
@@ -448,6 +538,8 @@ extern "C" ftlm_status ftlm_basis_create(int N, int two_sz, int n_bonds, const i
     b->bonds_cr.slots_f64 = b->bond_slots + kMaxBondSlots;
     b->bonds_clt.slots_f32 = b->bond_slots + 2 * kMaxBondSlots;
     b->bonds_clt.slots_f64 = b->bond_slots + 3 * kMaxBondSlots;
+    b->bonds_walk_a.slots_f32 = b->bond_slots + 4 * kMaxBondSlots;
+    b->bonds_walk_a.slots_f64 = b->bond_slots + 5 * kMaxBondSlots;
 
     // A copy from pageable memory returns once the image is staged, so `image`
     // may go out of scope; the kernels below follow it in stream order.
@@ -491,6 +583,17 @@ extern "C" ftlm_status ftlm_basis_destroy_async(ftlm_basis *b, void *stream)
     const cudaError_t e = cudaFreeAsync(b->block, (cudaStream_t)stream);
     delete b;
     return e == cudaSuccess ? FTLM_OK : cuda_fail(e, "cudaFreeAsync(tables)");
+}
+
+extern "C" ftlm_status ftlm_basis_set_schedule(ftlm_basis *b, ftlm_hv_schedule schedule, int rows_per_tile)
+{
+    if (!b) return fail(FTLM_EINVAL, "NULL basis");
+    if (schedule != FTLM_HV_AUTO && schedule != FTLM_HV_ONE_WALK && schedule != FTLM_HV_SPLIT)
+        return fail(FTLM_EINVAL, "bad H.v schedule");
+    if (rows_per_tile < 0 || rows_per_tile > 32) return fail(FTLM_EINVAL, "rows_per_tile must be 0..32");
+    b->hv_schedule = schedule;
+    b->walk_rh = rows_per_tile;
+    return FTLM_OK;
 }
 
 extern "C" ftlm_status ftlm_basis_dim(const ftlm_basis *b, uint64_t *dim)

@@ -32,6 +32,7 @@ struct EpiDev {
     double *tile_part;      // per-tile sums of the dynamic tile order, [tile][B]
     int alpha_stride;
     int has_prev;
+    unsigned int cta_tiles;  // > 1: tiles are claimed per CTA in runs of this many
 };
 
 inline EpiDev epi_of(const LanczosHv *epi)
@@ -88,6 +89,25 @@ __device__ __forceinline__ void epi_row(const EpiDev &ep, const V *s_inv_s, cons
     } else {
 #pragma unroll
         for (int r = 0; r < B; ++r) out[r] = fma(diag, xt[r], acc[r]);
+    }
+    st_vec<B>(y + (size_t)t * B, out);
+}
+
+// Output row t of walk A of a split H.v (CR): the Lanczos output of the bonds of
+// walk A, y = (H_A u_j)[t] / s_j - (beta_{j-1} / s_{j-1}) u_{j-1}[t], with no alpha
+// partial (walk B adds the rest of the row and finishes alpha).
+template <typename V, int B>
+__device__ __forceinline__ void epi_row_walk_a(const EpiDev &ep, const V *s_inv_s, const V *s_c_prev,
+                                               const V *__restrict__ x, V *y, uint32_t t, V diag,
+                                               const V (&acc)[B])
+{
+    V xt[B], out[B], up[B];
+    ld_vec<B>(x + (size_t)t * B, xt, false);
+    if (ep.has_prev) ld_vec<B>(y + (size_t)t * B, up, true);
+#pragma unroll
+    for (int r = 0; r < B; ++r) {
+        const V hv = fma(diag, xt[r], acc[r]);
+        out[r] = ep.has_prev ? fma(-s_c_prev[r], up[r], hv * s_inv_s[r]) : hv * s_inv_s[r];
     }
     st_vec<B>(y + (size_t)t * B, out);
 }

@@ -78,6 +78,41 @@ struct SectorTables {
     const uint2 *clt;       // CLT mode: {M_b, C_b} per 32-label block
 };
 
+// Split Lanczos H.v (CR, spin 1/2).  Rows t = (h, l) are stored in label order:
+// high pattern h major, low pattern l minor.  A bond with both sites in the high
+// block maps row (h, l) to (h ^ m, l), a jump of thi[h ^ m] - thi[h] rows that for
+// the top sites spans a large part of the sector, so in a walk over the rows in
+// label order those gathers miss L2.  The split runs two walks per Lanczos step:
+//   walk A  rows in label order, bonds with a site in the low block (lo-lo and
+//           cross bonds: their jumps stay near the row);
+//   walk B  the transposed order -- a warp fixes 32 consecutive low ranks r_lo
+//           (one per lane) and steps through the high patterns h of the matching
+//           popcount -- with the high-high bonds, whose sources (h ^ m, r_lo) lie
+//           in the same 32 columns: every gather is one contiguous run of 32 rows,
+//           and the columns' vector data (32 x C(N - L, K - q) rows) stays in L2.
+// Walk B adds its terms to walk A's output in place and finishes the Lanczos
+// epilogue.  HiWalk describes walk B's tiles: tile (g, c, r) = columns
+// 32c .. 32c + 31 of low popcount group g, high patterns rh r .. rh r + rh - 1 of
+// group K - q; tiles of a group are numbered column-major (all h of one column
+// chunk before the next), so the warps of a launch share one chunk's data.
+constexpr int kMaxHiBonds = 64;
+constexpr int kMaxHighBits = FTLM_MAX_SITES - kLoBitsMax;
+constexpr int kMaxHiGroups = kLoBitsMax + 1;
+struct HiWalk {
+    int ngroups;                      // low popcount groups with a non-empty high group
+    int nbonds;                       // high-high bonds, <= kMaxHiBonds
+    int rh;                           // high patterns per tile
+    uint32_t ntiles;
+    double jsum4;                     // sum of J_b / 4 over the high-high bonds
+    uint32_t tile0[kMaxHiGroups + 1]; // first tile of each group (tile0[ngroups] = ntiles)
+    uint32_t nl[kMaxHiGroups];        // low ranks (columns) of the group, C(L, q)
+    uint32_t nh[kMaxHiGroups];        // high patterns of the group, C(N - L, K - q)
+    uint32_t hoff[kMaxHiGroups];      // start of the group's high patterns in uhi
+    uint32_t nr[kMaxHiGroups];        // tiles per column chunk, ceil(nh / rh)
+    const uint32_t *uhi;              // high patterns grouped by popcount, ascending
+    const uint4 *bonds;               // {m >> L, J/2 as float, J/2 as double (lo, hi)}
+};
+
 // General local spin s = two_s / 2 >= 1 (spin.cu): labels n = sum_k a_k d^k with
 // base-d digits a_k = m_k + s, d = two_s + 1 (Eq. 11).  The digit-block tables of
 // SectorTables are used with base d: thi over the d^(N-L) high labels, tlo/ulo
@@ -111,8 +146,16 @@ struct ftlm_basis {
     int device, num_sms;
     ftlm::BondList bonds_cr;
     ftlm::BondList bonds_clt;
+    ftlm::BondList bonds_walk_a;   // split H.v, walk A: lo-lo and cross bonds (CR)
+    int n_hi_bonds;                // high-high bonds (walk B of the split H.v)
+    double jsum4_hi;               // their sum of J_b / 4
     void *block;        // one pooled device allocation holding every table below
-    uint4 *bond_slots;  // device: cr f32, cr f64, clt f32, clt f64 (kMaxBondSlots each)
+    uint4 *bond_slots;  // device: cr f32, cr f64, clt f32, clt f64, walk-A f32, walk-A f64,
+                        // walk-B bonds (kMaxBondSlots each)
+    uint32_t *uhi;      // CR: high patterns grouped by popcount, ascending (walk B)
+    ftlm_hv_schedule hv_schedule;  // Lanczos H.v walks (ftlm_basis_set_schedule)
+    int walk_rh;        // high patterns per walk-B tile (0: the default)
+    uint32_t uhi_off[ftlm::kMaxHighBits + 2];  // start of popcount group p in uhi
     uint32_t ulo_off[ftlm::kLoBitsMax + 2];
     uint32_t *thi;
     uint16_t *tlo;
@@ -195,10 +238,24 @@ ftlm_status launch_hv(const ftlm_basis *b, ftlm_dtype dtype, int B, const void *
 bool valid_block(int B);
 // FTLM_RANK_AUTO picks CR for sectors of at least this many rows.
 constexpr uint64_t kAutoCrRows = 1ull << 20;
-// Tiles of a Lanczos H.v launch of B vectors that takes its tiles in dynamic order
-// and leaves alpha_j as per-tile sums in LanczosHv::tile_part (CR rank mode); 0 when
-// the launch finishes alpha_j itself.
+// Upper bound on the tiles of a Lanczos H.v launch of B vectors that takes its tiles
+// in dynamic order and leaves alpha_j as per-tile sums in LanczosHv::tile_part (CR
+// rank mode, one walk or split); 0 when the launch finishes alpha_j itself.
 uint32_t hv_lanczos_tiles(const ftlm_basis *b, int B);
+
+// ---- split Lanczos H.v (basis.cu, walkb.cu, hv.cu) -------------------------
+// Walk B's tile layout for rh high patterns per tile (1 <= rh <= 32); false when
+// the sector has no split (not CR spin 1/2, no high block, no high-high bond, or
+// more than kMaxHiBonds of them).
+bool build_hi_walk(const ftlm_basis *b, int rh, HiWalk *w);
+struct EpiDev;
+// Walk A of a split Lanczos step with each block of rows staged in shared memory
+// (walka.cu; L < N <= 32).
+ftlm_status launch_walk_a_staged(const ftlm_basis *b, ftlm_dtype dtype, int B, const void *x, void *y,
+                                 const EpiDev &ep, cudaStream_t stream);
+// Walk B of a split Lanczos step (the epilogue's alpha as per-tile sums).
+ftlm_status launch_walk_b(const ftlm_basis *b, const HiWalk &w, ftlm_dtype dtype, int B, const void *x, void *y,
+                          const EpiDev &ep, cudaStream_t stream);
 
 // Lanczos chains of one sector (lanczos.cu): chain r is keyed as chain chain0 + r.
 ftlm_status lanczos_run(const ftlm_basis *b, int R, int M, int chain0, uint64_t seed, int dist, const double *src,
@@ -206,6 +263,11 @@ ftlm_status lanczos_run(const ftlm_basis *b, int R, int M, int chain0, uint64_t 
                         int *m_eff, double *alpha_dev, double *beta_dev, cudaStream_t stream, int bmax = 0);
 // bmax: widest block of chains (0: the process-wide setting).
 uint64_t lanczos_workspace(const ftlm_basis *b, int R, int M, ftlm_dtype dtype, int bmax = 0);
+// Sweep limit of the tridiagonal QR (ftlm_ritz_set_max_sweeps; 0: 64 n), and the
+// per-device counts of problems that did not converge (read and cleared).
+int ritz_max_sweeps();
+ftlm_status ritz_unconverged_take(cudaStream_t stream, uint64_t *count);
+ftlm_status ghost_unconverged_take(cudaStream_t stream, uint64_t *count);
 // Ritz step of n chains (alpha/beta rows of length M, m_eff per chain).
 ftlm_status launch_ritz(int n, int M, const double *alpha, const double *beta, const int *mv, double *theta,
                         double *weight, cudaStream_t stream);

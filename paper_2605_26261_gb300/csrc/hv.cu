@@ -8,9 +8,9 @@
 // so it is accumulated alongside the gathers.  Each thread writes one y[t]; there
 // are no atomics.
 //
-// Bonds are warp-uniform (a kernel parameter read through the constant bank), and
-// the 32 rows of a warp are 32 consecutive sector indices, i.e. 32 consecutive
-// labels in increasing order that differ only in their lowest bits.  For a bond
+// Bonds are warp-uniform (staged once per CTA in shared memory and read as
+// broadcasts), and the 32 rows of a warp are 32 consecutive sector indices, i.e.
+// 32 consecutive labels in increasing order that differ only in their lowest bits.  For a bond
 // on high sites the exchange therefore shifts all 32 ranks by the same amount and
 // the warp's gather is one contiguous 128-byte line; bonds on low sites land within
 // a few lines of the warp's own rows.  The grid is persistent (a multiple of the
@@ -75,10 +75,15 @@ template <typename V, int RT, int B, int C> __host__ __device__ constexpr int mi
                                        : (B >= 8 && C <= 2 ? 4 : (B >= 8 ? FTLM_B8_MIN_CTAS : (B >= 4 || RT >= 4 ? 3 : 6))));
 }
 
-template <typename V, typename Lbl, bool CLT, bool LANCZOS, int RT, int B, int C>
+// EPI: kPlain (y = H x), kLanczos (fused Lanczos epilogue with alpha), kWalkA
+// (walk A of a split H.v: the epilogue without alpha, see ftlm_internal.cuh).
+enum { kPlain = 0, kLanczos = 1, kWalkA = 2 };
+
+template <typename V, typename Lbl, bool CLT, int EPI, int RT, int B, int C>
 __global__ void __launch_bounds__(kRowThreads, min_ctas<V, RT, B, C>())
 hv_kernel(const SectorTables s, const BondList bl, const V *__restrict__ x, V *y, const EpiDev ep)
 {
+    constexpr bool LANCZOS = EPI != kPlain;
     // CR Lanczos launches take their tiles in dynamic order (their gathers gain the
     // most from a narrow frontier of rows) and store per-tile alpha sums
     constexpr bool TILES = LANCZOS && !CLT;
@@ -100,9 +105,8 @@ hv_kernel(const SectorTables s, const BondList bl, const V *__restrict__ x, V *y
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t tile_rows = 32u * RT;
     const uint32_t ntiles = (uint32_t)(((uint64_t)s.D + tile_rows - 1) / tile_rows);
-    for (uint32_t tile = warp; tile < ntiles;) {
-        // claim the next tile now; its atomic completes while this tile's rows run
-        const uint32_t claim = TILES ? claim_tile(ep) : 0u;
+    // the rows of one tile: rank work, gathers and the epilogue of the mode
+    auto do_tile = [&](uint32_t tile) {
         uint32_t t[RT];
         bool ok[RT];
 #pragma unroll
@@ -120,7 +124,11 @@ hv_kernel(const SectorTables s, const BondList bl, const V *__restrict__ x, V *y
         }
         if (CLT) rows_clt<V, RT, B, C>(s, bl, s_bond, x, t, acc, dsum);
         else rows_cr<V, Lbl, RT, B, C>(s, bl, s_bond, s_tlo, x, t, acc, dsum);
-        if constexpr (TILES) {
+        if constexpr (EPI == kWalkA) {
+#pragma unroll
+            for (int i = 0; i < RT; ++i)
+                if (ok[i]) epi_row_walk_a<V, B>(ep, s_inv_s, s_c_prev, x, y, t[i], jsum4 - dsum[i], acc[i]);
+        } else if constexpr (TILES) {
             DotAcc<V> tacc[B];
 #pragma unroll
             for (int i = 0; i < RT; ++i)
@@ -131,6 +139,40 @@ hv_kernel(const SectorTables s, const BondList bl, const V *__restrict__ x, V *y
             for (int i = 0; i < RT; ++i)
                 if (ok[i]) epi_row<V, B, LANCZOS>(ep, s_inv_s, s_c_prev, x, y, t[i], jsum4 - dsum[i], acc[i], apart);
         }
+    };
+    if (TILES && ep.cta_tiles > 1) {
+        // CTA-level order: a CTA claims runs of cta_tiles consecutive tiles from the
+        // counter and its warps share them, so a run's rows -- and the sources of
+        // their low-block exchanges, which stay inside the row's high-pattern group --
+        // meet in one SM's L1
+        __shared__ uint32_t s_next;
+        const uint32_t per = ep.cta_tiles;
+        const uint32_t nsup = (ntiles + per - 1) / per;
+        const uint32_t wic = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+        for (uint32_t st = blockIdx.x; st < nsup;) {
+            if (threadIdx.x == 0) s_next = atomicAdd(ep.counter + 1, 1u) + gridDim.x;
+            for (uint32_t sub = wic; sub < per; sub += wpc) {
+                const uint32_t tile = st * per + sub;
+                if (tile >= ntiles) break;
+                do_tile(tile);
+            }
+            __syncthreads();
+            st = s_next;
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (atomicAdd(ep.counter + 2, 1u) == gridDim.x - 1) {
+                ep.counter[1] = 0;
+                ep.counter[2] = 0;
+            }
+        }
+        return;
+    }
+    for (uint32_t tile = warp; tile < ntiles;) {
+        // claim the next tile now; its atomic completes while this tile's rows run
+        const uint32_t claim = TILES ? claim_tile(ep) : 0u;
+        do_tile(tile);
         tile = TILES ? claimed_tile(claim, nwarps) : tile + nwarps;
     }
     if (TILES) tiles_done(ep, nwarps);
@@ -172,6 +214,28 @@ int rows_per_thread(bool clt)
     return over ? over : (clt ? 1 : 2);
 }
 
+// Walk A of the split H.v with staged row blocks (FTLM_WALK_A_STAGED = 1 turns it on).
+bool walk_a_staged()
+{
+    static const bool on = [] {
+        const char *e = getenv("FTLM_WALK_A_STAGED");
+        return e && atoi(e) == 1;
+    }();
+    return on;
+}
+
+// Tiles per CTA-level claim of the dynamically ordered launches (FTLM_HV_CTA_TILES;
+// default 0: every warp claims its own tiles).
+uint32_t hv_cta_tiles()
+{
+    static const uint32_t v = [] {
+        const char *e = getenv("FTLM_HV_CTA_TILES");
+        const int n = e ? atoi(e) : 0;
+        return n > 1 ? (uint32_t)n : 0u;
+    }();
+    return v;
+}
+
 // Cap on resident CTAs per SM used for the H.v grid (FTLM_HV_CTAS, default: no cap).
 // Fewer CTAs shrink the window of rows in flight and with it the L2 working set of
 // the gather streams.
@@ -185,26 +249,76 @@ int hv_cta_cap()
     return cap;
 }
 
-template <typename V, typename Lbl, bool CLT, bool LANCZOS, int RT, int B, int C>
-ftlm_status launch(const ftlm_basis *b, const V *x, V *y, const EpiDev &ep, cudaStream_t stream)
+// Split Lanczos H.v (see HiWalk): used when the basis asks for it, or under
+// FTLM_HV_AUTO when one block of vectors is at least kSplitMinBytes -- below that
+// the sector's vectors stay in L2 and the one walk already hits there.
+constexpr uint64_t kSplitMinBytes = 64ull << 20;
+constexpr int kDefaultWalkRh = 8;
+
+bool split_walks(const ftlm_basis *b, int B, size_t vsize, HiWalk *w)
+{
+    if (b->hv_schedule == FTLM_HV_ONE_WALK) return false;
+    if (b->hv_schedule == FTLM_HV_AUTO && b->D * (uint64_t)B * vsize < kSplitMinBytes) return false;
+    return build_hi_walk(b, b->walk_rh ? b->walk_rh : kDefaultWalkRh, w);
+}
+
+// One hv_kernel launch over every row.
+template <typename V, typename Lbl, bool CLT, int EPI, int RT, int B, int C>
+ftlm_status launch_rows(const ftlm_basis *b, const BondList &bl, const V *x, V *y, const EpiDev &ep,
+                        cudaStream_t stream)
 {
     const size_t smem = CLT ? 0 : ((size_t)1 << b->L) * sizeof(uint16_t);
-    auto kern = hv_kernel<V, Lbl, CLT, LANCZOS, RT, B, C>;
+    auto kern = hv_kernel<V, Lbl, CLT, EPI, RT, B, C>;
     int occ = 1;  // resident blocks per SM for this instantiation
     const size_t smem_max = CLT ? 0 : ((size_t)1 << kLoBitsMax) * sizeof(uint16_t);
     FTLM_CUDA(kernel_occupancy((const void *)kern, kRowThreads, smem_max, false, &occ));
     const int grid = row_grid(b, (b->D + RT - 1) / RT, std::min(occ, hv_cta_cap()));
-    void *tok = profile_begin(kProfHv, stream, B);
-    kern<<<grid, kRowThreads, smem, stream>>>(b->tables(), CLT ? b->bonds_clt : b->bonds_cr, x, y, ep);
+    EpiDev e = ep;
+    e.cta_tiles = (EPI != kPlain && !CLT) ? hv_cta_tiles() : 0u;
+    kern<<<grid, kRowThreads, smem, stream>>>(b->tables(), bl, x, y, e);
     note_launch();
-    if (LANCZOS && !CLT) {  // alpha_j from the per-tile sums (timed with the H.v step)
-        const uint64_t rows = 32ull * RT;
-        const uint32_t ntiles = (uint32_t)((b->D + rows - 1) / rows);
-        const int ga = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)b->num_sms * 2, (ntiles + 2047) / 2048));
-        tile_alpha_kernel<B><<<ga, kRowThreads, 0, stream>>>(ep, ntiles);
-        note_launch();
+    return FTLM_OK;
+}
+
+// alpha_j from the per-tile sums of a dynamically ordered launch.
+template <int B>
+void launch_tile_alpha(const ftlm_basis *b, const EpiDev &ep, uint32_t ntiles, cudaStream_t stream)
+{
+    const int ga = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)b->num_sms * 2, (ntiles + 2047) / 2048));
+    tile_alpha_kernel<B><<<ga, kRowThreads, 0, stream>>>(ep, ntiles);
+    note_launch();
+}
+
+template <typename V, typename Lbl, bool CLT, bool LANCZOS, int RT, int B, int C>
+ftlm_status launch(const ftlm_basis *b, const V *x, V *y, const EpiDev &ep, cudaStream_t stream)
+{
+    void *tok = profile_begin(kProfHv, stream, B);
+    ftlm_status st = FTLM_OK;
+    if constexpr (LANCZOS && !CLT) {
+        // CR Lanczos step: one walk over the rows, or the split (walk A, then walk B
+        // over the high-high bonds in the transposed order); alpha_j from per-tile sums
+        HiWalk w;
+        uint32_t ntiles;
+        if (split_walks(b, B, sizeof(V), &w)) {
+            const ftlm_dtype dt = sizeof(V) == 4 ? FTLM_F32 : FTLM_F64;
+            if (b->N <= 32 && walk_a_staged())
+                st = launch_walk_a_staged(b, dt, B, x, y, ep, stream);
+            else
+                st = launch_rows<V, Lbl, false, kWalkA, RT, B, C>(b, b->bonds_walk_a, x, y, ep, stream);
+            if (st == FTLM_OK) st = launch_walk_b(b, w, dt, B, x, y, ep, stream);
+            ntiles = w.ntiles;
+        } else {
+            st = launch_rows<V, Lbl, false, kLanczos, RT, B, C>(b, b->bonds_cr, x, y, ep, stream);
+            const uint64_t rows = 32ull * RT;
+            ntiles = (uint32_t)((b->D + rows - 1) / rows);
+        }
+        if (st == FTLM_OK) launch_tile_alpha<B>(b, ep, ntiles, stream);
+    } else {
+        st = launch_rows<V, Lbl, CLT, LANCZOS ? kLanczos : kPlain, RT, B, C>(b, CLT ? b->bonds_clt : b->bonds_cr, x,
+                                                                           y, ep, stream);
     }
     profile_end(tok, stream);
+    if (st != FTLM_OK) return st;
     FTLM_CUDA(cudaGetLastError());
     return FTLM_OK;
 }
@@ -271,7 +385,10 @@ uint32_t hv_lanczos_tiles(const ftlm_basis *b, int B)
 {
     if (b->two_s > 1 || b->mode == FTLM_RANK_CLT) return 0;
     const uint64_t rows = 32ull * (B == 1 ? rows_per_thread(false) : 1);
-    return (uint32_t)((b->D + rows - 1) / rows);
+    uint32_t n = (uint32_t)((b->D + rows - 1) / rows);
+    HiWalk w;  // walk B has the most tiles with one high pattern per tile
+    if (build_hi_walk(b, 1, &w)) n = std::max(n, w.ntiles);
+    return n;
 }
 
 ftlm_status launch_hv(const ftlm_basis *b, ftlm_dtype dtype, int B, const void *x, void *y,
@@ -300,6 +417,18 @@ ftlm_status check_hv_args(const ftlm_basis *b, ftlm_dtype dtype, int B, const vo
     return FTLM_OK;
 }
 }  // namespace
+
+extern "C" ftlm_status ftlm_basis_hv_schedule(const ftlm_basis *b, int B, ftlm_dtype dtype, ftlm_hv_schedule *used)
+{
+    if (!b || !used) return ftlm::fail(FTLM_EINVAL, "NULL argument");
+    if (!ftlm::valid_block(B)) return ftlm::fail(FTLM_EINVAL, "block width must be 1, 4, 8 or 16");
+    if (dtype != FTLM_F32 && dtype != FTLM_F64) return ftlm::fail(FTLM_EINVAL, "bad dtype");
+    ftlm::HiWalk w;
+    const bool split = b->two_s == 1 && b->mode == FTLM_RANK_CR &&
+                       ftlm::split_walks(b, B, dtype == FTLM_F32 ? 4 : 8, &w);
+    *used = split ? FTLM_HV_SPLIT : FTLM_HV_ONE_WALK;
+    return FTLM_OK;
+}
 
 extern "C" ftlm_status ftlm_hv(const ftlm_basis *b, ftlm_dtype dtype, const void *x_dev, void *y_dev,
                                void *stream)

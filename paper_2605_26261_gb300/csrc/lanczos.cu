@@ -18,6 +18,8 @@
 #include <mutex>
 #include <vector>
 
+#include <cuda.h>
+
 #include "ftlm_internal.cuh"
 #include "reduce.cuh"
 #include "vec.cuh"
@@ -177,9 +179,14 @@ __global__ void copy_meff_kernel(const ChainState *st, int B, int *dst)
     if (threadIdx.x < B) dst[threadIdx.x] = st[threadIdx.x].m_eff;
 }
 
-// One thread per chain; T chains per CTA.
+// Tridiagonal problems of this translation unit that did not converge (read and
+// cleared by ftlm_ritz_status); one copy per device.
+__device__ unsigned long long g_ritz_unconverged;
+
+// One thread per chain; T chains per CTA.  A chain whose QR iteration does not
+// converge within max_sweeps gets NaN Ritz values and weights.
 __global__ void ritz_kernel(int n, int M, const double *__restrict__ alpha, const double *__restrict__ beta,
-                            const int *__restrict__ mv, double *theta, double *weight)
+                            const int *__restrict__ mv, double *theta, double *weight, int max_sweeps)
 {
     extern __shared__ double sh[];
     const int T = blockDim.x, i = threadIdx.x;
@@ -193,17 +200,22 @@ __global__ void ritz_kernel(int n, int M, const double *__restrict__ alpha, cons
         e[k] = k + 1 < m ? beta[(size_t)c * M + k] : 0.0;
         z[k] = k == 0 ? 1.0 : 0.0;
     }
+    bool ok = true;
     if (m > 1) {
-        tridiag_qr(d, e, z, m);
-        sort_ascending(d, z, m);
+        ok = tridiag_qr(d, e, z, m, max_sweeps);
+        if (ok) sort_ascending(d, z, m);
+        else atomicAdd(&g_ritz_unconverged, 1ull);
     }
     for (int k = 0; k < M; ++k) {
-        theta[(size_t)c * M + k] = k < m ? d[k] : 0.0;
-        weight[(size_t)c * M + k] = k < m ? z[k] * z[k] : 0.0;
+        theta[(size_t)c * M + k] = k < m ? (ok ? d[k] : NAN) : 0.0;
+        weight[(size_t)c * M + k] = k < m ? (ok ? z[k] * z[k] : NAN) : 0.0;
     }
 }
 
 }  // namespace
+
+std::atomic<int> g_ritz_max_sweeps{0};
+int ritz_max_sweeps() { return g_ritz_max_sweeps.load(std::memory_order_relaxed); }
 
 ftlm_status launch_ritz(int n, int M, const double *alpha, const double *beta, const int *mv,
                         double *theta, double *weight, cudaStream_t stream)
@@ -217,7 +229,7 @@ ftlm_status launch_ritz(int n, int M, const double *alpha, const double *beta, c
     T = T < 1 ? 1 : (T > 32 ? 32 : T);
     if (T > n) T = n;
     const int grid = (n + T - 1) / T;
-    ritz_kernel<<<grid, T, per_chain * T, stream>>>(n, M, alpha, beta, mv, theta, weight);
+    ritz_kernel<<<grid, T, per_chain * T, stream>>>(n, M, alpha, beta, mv, theta, weight, ritz_max_sweeps());
     note_launch();
     FTLM_CUDA(cudaGetLastError());
     return FTLM_OK;
@@ -405,21 +417,62 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[FTLM_NOALLOC_SC
 
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
-void *g_noalloc_ptr[kMaxDevices] = {};
+// Per device: the context the address was looked up in (cuCtxGetId, never reused
+// within a process) and the address.  A device reset gives the device a new
+// primary context, and the module with the array is loaded again at a new
+// address; the id comparison makes the next call look it up again.
+struct NoallocSlot {
+    unsigned long long ctx_id;
+    void *ptr;
+};
+NoallocSlot g_noalloc[kMaxDevices] = {};
 
-// Device address of g_noalloc_scratch on the current device (looked up on first use).
+// Id of the current context, from the driver through the runtime's entry-point
+// query (no link-time dependency on the driver library); false if unavailable.
+bool current_context_id(unsigned long long *id)
+{
+    using GetCurrent = CUresult (*)(CUcontext *);
+    using GetId = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+    });
+    CUcontext ctx = nullptr;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return get_id(ctx, id) == CUDA_SUCCESS;
+}
+
+// Device address of g_noalloc_scratch on the current device: looked up with
+// cudaGetSymbolAddress on the first call in a context, cached for later calls.
+// (Before any runtime call on this thread no context may be current yet; then the
+// address is looked up, which binds the primary context, and cached from the
+// next call on.)
 ftlm_status noalloc_scratch(void **out)
 {
     int dev = 0;
     FTLM_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return fail(FTLM_EUNSUPPORTED, "device index beyond 64");
+    unsigned long long ctx = 0;
+    const bool have_id = current_context_id(&ctx);
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+    NoallocSlot &slot = g_noalloc[dev];
+    if (!slot.ptr || !have_id || slot.ctx_id != ctx) {
         void *p = nullptr;
         FTLM_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-        g_noalloc_ptr[dev] = p;
+        slot.ptr = p;
+        slot.ctx_id = have_id ? ctx : 0;
     }
-    *out = g_noalloc_ptr[dev];
+    *out = slot.ptr;
     return FTLM_OK;
 }
 
@@ -483,6 +536,36 @@ extern "C" ftlm_status ftlm_lanczos_from(const ftlm_basis *b, int R, int M, cons
     if (!start_dev) return fail(FTLM_EINVAL, "start_dev is NULL");
     return lanczos_run(b, R, M, 0, 0, FTLM_VEC_GAUSS, start_dev, dtype, work_dev, work_bytes, theta_dev, weight_dev,
                        m_eff_dev, alpha_dev, beta_dev, (cudaStream_t)stream);
+}
+
+namespace ftlm {
+ftlm_status ritz_unconverged_take(cudaStream_t stream, uint64_t *count)
+{
+    unsigned long long v = 0, zero = 0;
+    FTLM_CUDA(cudaMemcpyFromSymbolAsync(&v, g_ritz_unconverged, sizeof(v), 0, cudaMemcpyDeviceToHost, stream));
+    FTLM_CUDA(cudaMemcpyToSymbolAsync(g_ritz_unconverged, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, stream));
+    FTLM_CUDA(cudaStreamSynchronize(stream));
+    *count = v;
+    return FTLM_OK;
+}
+}  // namespace ftlm
+
+extern "C" ftlm_status ftlm_ritz_status(void *stream, uint64_t *unconverged)
+{
+    uint64_t a = 0, b = 0;
+    ftlm_status s = ritz_unconverged_take((cudaStream_t)stream, &a);
+    if (s == FTLM_OK) s = ghost_unconverged_take((cudaStream_t)stream, &b);
+    if (s != FTLM_OK) return s;
+    if (unconverged) *unconverged = a + b;
+    if (a + b) return fail(FTLM_ENOCONV, std::to_string(a + b) + " tridiagonal eigenproblem(s) did not converge");
+    return FTLM_OK;
+}
+
+extern "C" ftlm_status ftlm_ritz_set_max_sweeps(int sweeps)
+{
+    if (sweeps < 0) return fail(FTLM_EINVAL, "sweeps < 0");
+    g_ritz_max_sweeps.store(sweeps, std::memory_order_relaxed);
+    return FTLM_OK;
 }
 
 extern "C" ftlm_status ftlm_ritz(int n, int M, const double *alpha_dev, const double *beta_dev,

@@ -21,8 +21,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 # -D options); by default the in-tree libftlm.so next to this file.
 LIB_PATH = os.environ.get("FTLM_LIBRARY") or os.path.join(_HERE, "libftlm.so")
 
-FTLM_OK, FTLM_EINVAL, FTLM_ENOMEM, FTLM_EUNSUPPORTED, FTLM_ECUDA, FTLM_ETIMEOUT = range(6)
+FTLM_OK, FTLM_EINVAL, FTLM_ENOMEM, FTLM_EUNSUPPORTED, FTLM_ECUDA, FTLM_ETIMEOUT, FTLM_ENOCONV = range(7)
 RANK_AUTO, RANK_CLT, RANK_CR = 0, 1, 2
+HV_AUTO, HV_ONE_WALK, HV_SPLIT = 0, 1, 2
 F64, F32 = 0, 1
 GAUSS, RADEMACHER = 0, 1
 MAX_SITES, MAX_BONDS, MAX_LANCZOS, MAX_SECTORS = 36, 256, 1024, 64
@@ -45,7 +46,7 @@ class FtlmError(RuntimeError):
 
 def _status_name(s):
     return {0: "FTLM_OK", 1: "FTLM_EINVAL", 2: "FTLM_ENOMEM", 3: "FTLM_EUNSUPPORTED",
-            4: "FTLM_ECUDA", 5: "FTLM_ETIMEOUT"}.get(s, f"status {s}")
+            4: "FTLM_ECUDA", 5: "FTLM_ETIMEOUT", 6: "FTLM_ENOCONV"}.get(s, f"status {s}")
 
 
 def lib():
@@ -65,6 +66,8 @@ def lib():
         "ftlm_basis_dim": [P, PU64],
         "ftlm_basis_bytes": [P, PU64],
         "ftlm_basis_mode": [P, ctypes.POINTER(I)],
+        "ftlm_basis_set_schedule": [P, I, I],
+        "ftlm_basis_hv_schedule": [P, I, I, ctypes.POINTER(I)],
         "ftlm_basis_updates": [P, PU64],
         "ftlm_basis_labels": [P, U64, U64, P, P],
         "ftlm_basis_rank": [P, U64, P, P, P],
@@ -76,6 +79,8 @@ def lib():
         "ftlm_lanczos_from": [P, I, I, P, I, P, U64, P, P, P, P, P, P],
         "ftlm_lanczos_noalloc": [P, I, I, U64, I, I, P, P, P, P, P, P],
         "ftlm_ritz": [I, I, P, P, P, P, P, P],
+        "ftlm_ritz_status": [P, PU64],
+        "ftlm_ritz_set_max_sweeps": [I],
         "ftlm_thermo": [I, P, P, I, I, P, P, P, I, D, D, I, P, P, P, P, P, P],
         "ftlm_batch_create": [I, P, I, I, I, I, I, P, ctypes.POINTER(P)],
         "ftlm_lanczos_set_block": [I],
@@ -199,6 +204,16 @@ def ftlm_basis_mode(handle):
     return v.value
 
 
+def ftlm_basis_set_schedule(handle, schedule, rows_per_tile=0):
+    _check(lib().ftlm_basis_set_schedule(handle, int(schedule), int(rows_per_tile)))
+
+
+def ftlm_basis_hv_schedule(handle, B, dtype):
+    v = ctypes.c_int()
+    _check(lib().ftlm_basis_hv_schedule(handle, int(B), _dtype_code(dtype), ctypes.byref(v)))
+    return v.value
+
+
 def ftlm_basis_labels(handle, first, count, labels, stream=None):
     """labels: int64 device tensor (labels < 2^36 fit), length >= count."""
     _check(lib().ftlm_basis_labels(handle, int(first), int(count), _ptr(labels), _stream(stream)))
@@ -267,6 +282,24 @@ def ftlm_lanczos_set_block(width):
 def ftlm_ritz(n, M, alpha, beta, m, theta, weight, stream=None):
     _check(lib().ftlm_ritz(int(n), int(M), _ptr(alpha), _ptr(beta), _ptr(m), _ptr(theta),
                            _ptr(weight), _stream(stream)))
+
+
+def ftlm_ritz_status(stream=None):
+    """Waits for the stream; returns the number of tridiagonal eigenproblems that did
+    not converge since the last call (raises FtlmError FTLM_ENOCONV when non-zero,
+    with the count in .unconverged)."""
+    v = ctypes.c_uint64()
+    st = lib().ftlm_ritz_status(_stream(stream), ctypes.byref(v))
+    if st == FTLM_ENOCONV:
+        err = FtlmError(st, lib().ftlm_last_error().decode())
+        err.unconverged = v.value
+        raise err
+    _check(st)
+    return v.value
+
+
+def ftlm_ritz_set_max_sweeps(sweeps):
+    _check(lib().ftlm_ritz_set_max_sweeps(int(sweeps)))
 
 
 def ftlm_thermo(two_sz, dims, R, M, thetas, weights, m_effs, mirror_neg, g, h, T, E, C, chi, mag=None,
@@ -391,6 +424,11 @@ class Basis:
         self.table_bytes = ftlm_basis_bytes(self.handle)
         self.mode = ftlm_basis_mode(self.handle)
         self.updates = ftlm_basis_updates(self.handle)
+
+    def set_schedule(self, schedule, rows_per_tile=0):
+        """ftlm_basis_set_schedule: walks of the Lanczos H.v launches of this sector."""
+        ftlm_basis_set_schedule(self.handle, schedule, rows_per_tile)
+        return self
 
     def close(self):
         if self.handle is not None:
