@@ -76,7 +76,8 @@ def parse_args():
     p.add_argument("--M", type=int, default=0, help="Lanczos steps (default: the workload's)")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--jobs", type=int, default=128, help="serving: requests in the timed stream")
-    p.add_argument("--slots", type=int, default=4, help="serving: concurrent groups (CUDA streams)")
+    p.add_argument("--steps-per-poll", type=int, default=2,
+                   help="serving: Lanczos steps queued between admission passes of the request loop")
     p.add_argument("--seeds", type=int, default=8, help="precision: independent FTLM runs for sigma_emp")
     p.add_argument("--clusters", type=int, default=256, help="clusters256: use the first n clusters (profiling)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -140,7 +141,7 @@ def peak_hbm():
 # Device sources of each H.v kernel family: a committed ncu summary holds DRAM
 # traffic for the sources it was taken on.
 KERNEL_SOURCES = {
-    "hv": ("hv.cu", "walka.cu", "walkb.cu", "epi.cuh", "rows.cuh", "vec.cuh", "reduce.cuh", "ftlm_internal.cuh"),
+    "hv": ("hv.cu", "walkb.cu", "epi.cuh", "rows.cuh", "vec.cuh", "reduce.cuh", "ftlm_internal.cuh"),
     "spin": ("spin.cu", "spin_rows.cuh", "epi.cuh", "vec.cuh", "reduce.cuh", "ftlm_internal.cuh"),
 }
 
@@ -499,7 +500,7 @@ def run_ours(args):
     extras = None
     if world == 1 and args.workload == "icosidodecahedron" and not args.no_extras and len(sectors) == 1:
         extras = {"fp64_b1": fp64_b1_job(N, bonds, mode, R, M, T, value), "serving": None}
-        sv = serve_stream(args.serving_jobs, 4, 3, local)
+        sv = serve_stream(args.serving_jobs, 2, 3, local)
         sv.pop("_done"), sv.pop("_jobs")
         sv["workload"] = WORKLOADS["serving"]["desc"]
         extras["serving"] = sv
@@ -541,7 +542,7 @@ def run_ours(args):
             if ftlm.ftlm_basis_hv_schedule(b_.handle, block, dt) == ftlm.HV_SPLIT:
                 schedule = "split"
     kname = ("ms_hv_kernel" if len(sectors) > 1 else
-             ("hv_kernel" if two_s > 1 or schedule == "one_walk" else "walk_a_staged_kernel + walk_b_kernel")
+             ("hv_kernel" if schedule == "one_walk" else "hv_kernel (walk A) + walk_b_kernel")
              if two_s == 1 else "hv_spin_kernel")
     # DRAM traffic of one H.v step from the committed capture of the current sources
     # (bytes per row on smaller sectors of the same cluster, scaled by D)
@@ -562,6 +563,16 @@ def run_ours(args):
     else:
         achieved, basis_note = None, "no per-step traffic for this workload"
     n_off = (upd0 - D0) * block  # off-diagonal gathers of one step (each row of B values)
+    # the read rate that bounds the gathers: L2 (a 64 MB buffer, L2-resident) measured
+    # here with the library's probe; gathers and row streams of one step move through L2
+    l2_peak = None
+    if hv_n:
+        probe = torch.empty(64 << 20, dtype=torch.uint8, device=dev)
+        l2_peak = ftlm.ftlm_probe_read_bandwidth(probe, 40)
+        del probe
+    gather_bytes = n_off // block * 32 * max(1, block * vsize // 32)
+    stream_bytes = (6 if schedule == "split" else 3) * D0 * block * vsize
+    l2_achieved = (gather_bytes + stream_bytes) / hv_avg_s / 1e9 if hv_n else None
     roofline = {
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
         "frac": achieved / peak if achieved else None, "traffic": traffic,
@@ -576,7 +587,12 @@ def run_ours(args):
         "sector_model_ratio": (alg_total / hv_s / 1e9 / peak) if hv_n else None,
         "sector_model": "32 B per gathered row of B values + row streams (x, y, u_{j-1}); counts every gather "
                         "as a DRAM sector, so L2 hits push the ratio above 1: not a fraction of a roofline",
-        "l2_gather_GBps": (n_off * 32 * max(1, block * vsize // 32) / hv_avg_s / 1e9) if hv_n else None,
+        "l2": {"achieved": l2_achieved, "peak": l2_peak, "unit": "GB/s",
+               "frac": l2_achieved / l2_peak if (l2_achieved and l2_peak) else None,
+               "bytes_per_launch": gather_bytes + stream_bytes,
+               "basis": "gathers (one 32-byte sector per row of B values per off-diagonal term) + the row streams "
+                        "of the step's walks, through L2 / event-timed step; peak = ftlm_probe_read_bandwidth on "
+                        "a 64 MB L2-resident buffer, this run"},
         "hv_launches": hv_n, "sector_block_steps": launches_model, "vectors_per_launch": block,
         "hv_ms_avg": hv_avg_s * 1e3,
         "hv_Gupdates_per_s": upd_total / hv_s / 1e9 if hv_n else None,
@@ -712,11 +728,12 @@ def run_clusters(args):
         sub += [c for c, (N, _) in enumerate(clusters) if N == n][:8]
     t_tune = time.perf_counter()
     if args.block:
-        block, streams, tune_times = (args.block if args.block > 1 else 16), 4, {}
+        plan, tried = ftlm.BatchPlan(args.block if args.block > 1 else 16, 4, 0, 0), []
     else:
-        block, streams, tune_times = ftlm.autotune(entries_of([bases[c] for c in sub]), M, ftlm.RADEMACHER, dt)
+        plan, tried = ftlm.autotune_plan(entries_of([bases[c] for c in sub]), M, ftlm.RADEMACHER, dt)
+    block, streams = plan.block, plan.streams
     tune_s = time.perf_counter() - t_tune
-    batch = ftlm.Batch(entries_of(bases), M, ftlm.RADEMACHER, dt, block, streams)
+    batch = ftlm.Batch(entries_of(bases), M, ftlm.RADEMACHER, dt, plan=plan)
     results = batch.results
     outs = [{k: torch.empty_like(T) for k in ("E", "C", "chi", "mag")} for _ in clusters]
     k0 = [0]
@@ -793,7 +810,7 @@ def run_clusters(args):
         t0 = time.perf_counter()
         T.copy_(T_pin, non_blocking=True)
         bases2 = make_bases(clusters)
-        with ftlm.Batch(entries_of(bases2), M, ftlm.RADEMACHER, dt, block, streams) as b2:
+        with ftlm.Batch(entries_of(bases2), M, ftlm.RADEMACHER, dt, plan=plan) as b2:
             res2 = b2.run()
             for c, bs in enumerate(bases2):
                 res = res2[k0[c]:k0[c + 1]]
@@ -834,8 +851,9 @@ def run_clusters(args):
                    f"the first {len(clusters)} clusters of " + WORKLOADS["clusters256"]["desc"],
                    "sectors": sum(len(bs) for bs in bases),
                    "rows_small_sectors": small_rows, "rows_large_sectors": large_rows,
-                   "block": block, "side_streams": streams,
-                   "autotune": {f"B{k[0]}_s{k[1]}": round(v, 2) for k, v in tune_times.items()},
+                   "block": block, "side_streams": streams, "tile_rows": plan.tile_rows,
+                   "stream_rows": plan.stream_rows,
+                   "autotune": {f"B{k[0]}_s{k[1]}_t{k[2]}_u{k[3]}": round(v, 2) for k, v in tried},
                    "autotune_s": tune_s, "setup_s": setup_s,
                    "graph": "one CUDA graph per step: batch run + 256 thermodynamic launches",
                    "l2": "per-sector working sets are L2-sized (<= 90 MB); the whole step streams "
@@ -858,12 +876,12 @@ def run_clusters(args):
         dist.destroy_process_group()
 
 
-def serve_stream(n_jobs, slots, warmup, local=0, clocks=None):
-    """The request loop (serve.Engine) on the seeded Poisson stream of FTLM jobs of the
-    serving configuration: jobs/s (requests / makespan) and p50/p99 latency from
-    arrival to results on the host, beside the same jobs run one at a time (one slot,
-    one job per batch, all queued at once), and a bit-for-bit comparison of every
-    job's results in the two runs."""
+def serve_stream(n_jobs, steps_per_poll, warmup, local=0, clocks=None):
+    """The request loop (serve.Engine: chain-level continuous batching) on the seeded
+    Poisson stream of FTLM jobs of the serving configuration: jobs/s (requests /
+    makespan) and p50/p99 latency from arrival to results on the host, beside the
+    same jobs run one at a time (one job in flight, all queued at once), and a
+    bit-for-bit comparison of every job's results in the two runs."""
     import torch
 
     from paper_2605_26261_gb300 import ftlm, inputs, serve
@@ -871,25 +889,30 @@ def serve_stream(n_jobs, slots, warmup, local=0, clocks=None):
     T = inputs.log_t_grid(200)
     R, M = 8, 80
 
-    def engine(slots_, max_group):
-        return serve.Engine(slots=slots_, R=R, M=M, dtype=torch.float32, block=8, streams=2, T=T,
-                            dist=ftlm.GAUSS, max_group=max_group)
+    def engine(max_jobs):
+        return serve.Engine(R=R, M=M, dtype=torch.float32, block=8, T=T, dist=ftlm.GAUSS, max_jobs=max_jobs,
+                            steps_per_poll=steps_per_poll)
 
     # warm-up: a few jobs of every size through a throwaway engine
     warm, _ = serve.poisson_jobs(max(warmup, 6), 200.0, seed=99)
-    engine(slots, 8).run(warm)
+    eng = engine(None)
+    eng.run(warm)
+    eng.close()
     torch.cuda.synchronize()
 
     jobs, arrivals = serve.poisson_jobs(n_jobs, 200.0, seed=4)
     launches0 = ftlm.ftlm_launch_count()
+    eng = engine(None)
     if clocks is not None:
         clocks.__enter__()
     try:
-        done = engine(slots, 8).run(jobs, arrivals)
+        done = eng.run(jobs, arrivals)
         torch.cuda.synchronize()
     finally:
         if clocks is not None:
             clocks.__exit__(None, None, None)
+    stats = dict(eng.stats)
+    eng.close()
     launches = ftlm.ftlm_launch_count() - launches0
     lat = np.array([j.latency for j in done]) * 1e3
     makespan = max(j.finish for j in done) - min(j.arrival for j in done)
@@ -897,12 +920,15 @@ def serve_stream(n_jobs, slots, warmup, local=0, clocks=None):
 
     alone_jobs, _ = serve.poisson_jobs(n_jobs, 200.0, seed=4)
     t0 = time.perf_counter()
-    alone = engine(1, 1).run(alone_jobs)
+    eng = engine(1)
+    alone = eng.run(alone_jobs)
     torch.cuda.synchronize()
+    eng.close()
     alone_s = time.perf_counter() - t0
     same = sum(1 for j in alone if np.array_equal(j.result, served[j.job_id].result))
     alone_lat = np.array([j.latency for j in alone]) * 1e3
-    return {"jobs": n_jobs, "slots": slots, "jobs_per_s": n_jobs / makespan,
+    return {"jobs": n_jobs, "steps_per_poll": steps_per_poll, "jobs_per_s": n_jobs / makespan,
+            "max_jobs_in_flight": stats["max_jobs_in_flight"], "max_units": stats["max_units"],
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "makespan_s": makespan, "Gupdates_per_s": sum(j.updates for j in done) / makespan / 1e9,
             "one_at_a_time_jobs_per_s": n_jobs / alone_s,
@@ -929,7 +955,7 @@ def run_serving(args):
     n_jobs = args.jobs
     R = 8
     clocks = ClockSampler(local)
-    sv = serve_stream(n_jobs, args.slots, args.warmup, local, clocks)
+    sv = serve_stream(n_jobs, args.steps_per_poll, args.warmup, local, clocks)
     done, jobs = sv.pop("_done"), sv.pop("_jobs")
     launches = sv["gpu_launches"]
     makespan = sv["makespan_s"]
@@ -949,9 +975,11 @@ def run_serving(args):
         "metric": METRIC, "value": value, "unit": "jobs/s", "n_gpus": 1, "steps": n_jobs, "warmup": max(args.warmup, 6),
         "ms_per_step": 1e3 * makespan / n_jobs, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOADS["serving"]["desc"], "jobs": n_jobs, "slots": args.slots,
-                   "max_group": 8, "block": 8, "side_streams": 2,
-                   "admission": "exact footprint (tables + workspace + outputs) within 80% of free HBM",
+        "config": {"workload": WORKLOADS["serving"]["desc"], "jobs": n_jobs,
+                   "steps_per_poll": args.steps_per_poll, "block": 8,
+                   "batching": "chain level: sectors join the running multi-sector launches at Lanczos-step "
+                               "boundaries (ftlm_flow)",
+                   "admission": "first fit of each sector's units in the flow workspace (60% of free HBM)",
                    "l2": "largest sectors (D=10400600, 8 f32 vectors) exceed L2",
                    "parallelism": "single GPU"},
         "p50_ms": sv["p50_ms"], "p99_ms": sv["p99_ms"],

@@ -136,7 +136,9 @@ ftlm_status ftlm_basis_destroy_async(ftlm_basis *basis, void *stream);
  *                     far beyond L2 for the top sites in label order, but within
  *                     the same 32 columns in the transposed order.
  *   FTLM_HV_AUTO      (default) SPLIT when one block of B vectors of the call
- *                     holds at least 64 MB, else ONE_WALK.
+ *                     holds at least 4 GiB (FP32) or 1 GiB (FP64), else ONE_WALK
+ *                     (the crossover measured on GB300; the split moves two row
+ *                     streams per step, the one walk misses L2 on long jumps).
  *   rows_per_tile: high patterns per tile of the transposed walk, 1..32, or 0 for
  *   the default (8).  SPLIT needs 1..64 bonds inside the high block (the N - L
  *   highest sites, L = min(N, 14)); otherwise the sector runs one walk.  Results
@@ -355,6 +357,30 @@ ftlm_status ftlm_batch_run(const ftlm_batch *batch, void *work_dev, uint64_t wor
 void ftlm_batch_destroy(ftlm_batch *batch);
 ftlm_status ftlm_batch_destroy_async(ftlm_batch *batch, void *stream);
 
+/* Batch plans with explicit tile sizes.  ftlm_batch_plan: block and streams as for
+ * ftlm_batch_create; tile_rows = rows per H.v tile and stream_rows = rows per tile
+ * of the start/update kernels of the multi-sector path (multiples of 256 up to
+ * 2^20; 0: 2048 and 16384).  ftlm_batch_create_plan plans with them (results agree
+ * with other plans up to the summation order of the per-tile sums).
+ * ftlm_batch_autotune_plan times candidate plans on the items (each candidate: one
+ * untimed and one timed run, as ftlm_batch_autotune) by coordinate search -- block
+ * width in {4, 8, 16} (and side streams in {1, 2, 4, 8} when an item runs on
+ * them), then tile_rows in {1024, 2048, 4096} and stream_rows in {8192, 16384,
+ * 32768} when an item runs on the multi-sector path -- and returns the fastest in
+ * *best; the first max_tried candidates and their times go to tried / ms_out,
+ * *n_tried = candidates timed.  Blocks the host; overwrites the items' outputs. */
+typedef struct {
+    int block;
+    int streams;
+    int tile_rows;
+    int stream_rows;
+} ftlm_batch_plan;
+ftlm_status ftlm_batch_create_plan(int n_items, const ftlm_batch_item *items, int M, ftlm_vec_dist dist,
+                                   ftlm_dtype dtype, const ftlm_batch_plan *plan, void *stream, ftlm_batch **out);
+ftlm_status ftlm_batch_autotune_plan(int n_items, const ftlm_batch_item *items, int M, ftlm_vec_dist dist,
+                                     ftlm_dtype dtype, void *stream, ftlm_batch_plan *best, ftlm_batch_plan *tried,
+                                     float *ms_out, int max_tried, int *n_tried);
+
 /* ftlm_batch_autotune -- pick the block width and side-stream count of a batch by
  * timing it: for block in {4, 8, 16} and (when some item runs on the side
  * streams) streams in {1, 2, 4, 8}, plan the batch, run it once untimed and once
@@ -369,6 +395,48 @@ ftlm_status ftlm_batch_destroy_async(ftlm_batch *batch, void *stream);
 ftlm_status ftlm_batch_autotune(int n_items, const ftlm_batch_item *items, int M, ftlm_vec_dist dist,
                                 ftlm_dtype dtype, void *stream, int *block_out, int *streams_out,
                                 float *ms_out);
+
+/* ------------------------------------------------------- continuous flow ---
+ * A request loop's chain-level continuous batching: the chains of many sectors
+ * advance together, one multi-sector H.v launch per rank kind and one update
+ * launch per Lanczos step, and sectors join and leave at step boundaries.  A
+ * sector added while others are at step 40 runs its step 1 in the next launch; a
+ * sector that reaches its last step gets its Ritz step at once and its device
+ * memory serves the next one.  Each sector's chains are cut into units of `block`
+ * chains with the tiles and per-unit reductions of the batch's multi-sector path,
+ * so a sector's results are bit-identical alone, in any mix and whenever it was
+ * added (and equal to its ftlm_batch results when the batch runs it on the
+ * multi-sector path).
+ * ftlm_flow_create -- dtype, block (1, 4, 8, 16), M steps, start-vector dist as for
+ *   ftlm_batch_create; max_units: units the flow holds at once.  work_dev
+ *   (256-byte aligned, work_bytes, caller-owned) holds 2 max_units block M doubles
+ *   of coefficient rows and the units' regions (ftlm_flow_unit_bytes each); the
+ *   library allocates the unit descriptors and tile maps from its pool on `stream`
+ *   and small pinned host staging buffers.  Spin-1/2 sectors with N <= 32 and
+ *   general-spin sectors.
+ * ftlm_flow_add -- queue the R chains of item (as an ftlm_batch_item: chains keyed
+ *   first_chain + r under seed; outputs theta, weight, m_eff as for ftlm_lanczos,
+ *   written when the sector finishes).  *ticket identifies it.  Admitted at the next
+ *   step.  FTLM_ENOMEM when its units do not fit in the free workspace or the
+ *   max_units limit right now (nothing is queued: add it again later).
+ * ftlm_flow_step -- queue `steps` Lanczos steps of every admitted unit on `stream`
+ *   (start vectors for the newly admitted ones first).  Every flow call that queues
+ *   work must use the same stream (or calls ordered by the caller).
+ * ftlm_flow_done -- up to max tickets of sectors whose outputs have been queued
+ *   (valid once `stream` reaches the end of the step call that finished them), in
+ *   finishing order; each ticket is returned once.
+ * ftlm_flow_status -- units and sectors in the flow, free workspace bytes.
+ * ftlm_flow_unit_bytes -- workspace bytes of one unit of `block` chains of basis.
+ * ftlm_flow_destroy -- waits for the device, then releases. */
+typedef struct ftlm_flow ftlm_flow;
+ftlm_status ftlm_flow_create(ftlm_dtype dtype, int block, int M, ftlm_vec_dist dist, int max_units, void *work_dev,
+                             uint64_t work_bytes, void *stream, ftlm_flow **out);
+ftlm_status ftlm_flow_unit_bytes(const ftlm_basis *basis, ftlm_dtype dtype, int block, uint64_t *bytes);
+ftlm_status ftlm_flow_add(ftlm_flow *flow, const ftlm_batch_item *item, int *ticket);
+ftlm_status ftlm_flow_step(ftlm_flow *flow, int steps, void *stream);
+ftlm_status ftlm_flow_done(ftlm_flow *flow, int *tickets, int max, int *n);
+ftlm_status ftlm_flow_status(const ftlm_flow *flow, int *units, int *sectors, uint64_t *free_bytes);
+void ftlm_flow_destroy(ftlm_flow *flow);
 
 /* ftlm_ritz -- the Ritz step alone (a5): for each of n chains, the eigenvalues theta
  * and first-component weights w = s_{k,1}^2 of the tridiagonal matrix with diagonal
@@ -470,6 +538,15 @@ ftlm_status ftlm_launch_count(uint64_t *count);
 ftlm_status ftlm_profile_enable(int on);
 ftlm_status ftlm_profile_read(uint64_t *hv_launches, uint64_t *hv_vectors, double *hv_ms,
                               uint64_t *update_launches, double *update_ms);
+
+/* ftlm_probe_read_bandwidth -- read rate of this device for the rooflines of the
+ * H.v kernels: reads buf_dev (bytes, 32-byte aligned; its first multiple of 32
+ * bytes) `reps` times in one launch, 32 bytes per thread and load, after one
+ * untimed pass, and returns GB/s of the timed launch (CUDA events on `stream`;
+ * waits for them).  A buffer that fits in L2 (129 MB on GB300) gives the L2 read
+ * rate that bounds the gathers of an L2-resident H.v; a buffer of several GB the
+ * DRAM read rate.  The buffer's contents are only read.  EINVAL for bad arguments. */
+ftlm_status ftlm_probe_read_bandwidth(const void *buf_dev, uint64_t bytes, int reps, void *stream, double *gbps);
 
 const char *ftlm_status_string(ftlm_status status);
 const char *ftlm_last_error(void); /* message of the last failure on this host thread */

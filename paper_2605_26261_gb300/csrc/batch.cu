@@ -362,11 +362,16 @@ void release_host_objects(ftlm_batch *p)
 
 }  // namespace
 
-extern "C" ftlm_status ftlm_batch_create(int n, const ftlm_batch_item *items, int M, ftlm_vec_dist dist,
-                                         ftlm_dtype dtype, int block, int streams, void *stream_,
-                                         ftlm_batch **out)
+namespace {
+
+ftlm_status batch_create(int n, const ftlm_batch_item *items, int M, ftlm_vec_dist dist, ftlm_dtype dtype, int block,
+                         int streams, uint32_t tile_rows, uint32_t stream_rows, void *stream_, ftlm_batch **out)
 {
     if (!out) return fail(FTLM_EINVAL, "out is NULL");
+    if (tile_rows == 0) tile_rows = kMsTileRows;
+    if (stream_rows == 0) stream_rows = kMsStreamRows;
+    if (tile_rows % kRowThreads || stream_rows % kRowThreads || tile_rows > (1u << 20) || stream_rows > (1u << 20))
+        return fail(FTLM_EINVAL, "tile rows must be multiples of 256 up to 2^20");
     *out = nullptr;
     if (n < 1 || !items) return fail(FTLM_EINVAL, "empty batch");
     if (M < 1 || M > FTLM_MAX_LANCZOS) return fail(FTLM_EINVAL, "M out of range");
@@ -488,7 +493,7 @@ extern "C" ftlm_status ftlm_batch_create(int n, const ftlm_batch_item *items, in
             if (kind_of(b) != kind) continue;
             for (int r0 = 0; r0 < items[i].R; r0 += B) {
                 const uint64_t vb = align256(b->D * (uint64_t)B * vsize);
-                const uint32_t nt = (uint32_t)((b->D + kMsTileRows - 1) / kMsTileRows);
+                const uint32_t nt = (uint32_t)((b->D + tile_rows - 1) / tile_rows);
                 const uint64_t ub = 2 * vb + align256(kMaxBlock * sizeof(ChainState) + 64) +
                                     align256((uint64_t)nt * B * sizeof(double));
                 if (w.n_units && wbytes + ub > ms_wave_bytes()) close_wave();
@@ -498,7 +503,7 @@ extern "C" ftlm_status ftlm_batch_create(int n, const ftlm_batch_item *items, in
                     w.stile_off = (uint32_t)stile_unit.size();
                     w.kind = kind;
                 }
-                const uint32_t nst = (uint32_t)((b->D + kMsStreamRows - 1) / kMsStreamRows);
+                const uint32_t nst = (uint32_t)((b->D + stream_rows - 1) / stream_rows);
                 MsUnit u{};
                 u.s = b->tables();
                 u.bl = b->mode == FTLM_RANK_CLT ? b->bonds_clt : b->bonds_cr;
@@ -509,6 +514,8 @@ extern "C" ftlm_status ftlm_batch_create(int n, const ftlm_batch_item *items, in
                 u.off_part = u.off_st + align256(kMaxBlock * sizeof(ChainState) + 64);
                 u.seed = items[i].seed;
                 u.tau = dtype == FTLM_F32 ? b->tau32 : b->tau64;
+                u.tile_rows = tile_rows;
+                u.stream_rows = stream_rows;
                 u.tile0 = w.n_tiles;
                 u.n_tiles = nt;
                 u.stile0 = w.n_stiles;
@@ -638,6 +645,24 @@ extern "C" ftlm_status ftlm_batch_create(int n, const ftlm_batch_item *items, in
     }
     *out = p;
     return FTLM_OK;
+}
+
+}  // namespace
+
+extern "C" ftlm_status ftlm_batch_create(int n, const ftlm_batch_item *items, int M, ftlm_vec_dist dist,
+                                         ftlm_dtype dtype, int block, int streams, void *stream, ftlm_batch **out)
+{
+    return batch_create(n, items, M, dist, dtype, block, streams, 0, 0, stream, out);
+}
+
+extern "C" ftlm_status ftlm_batch_create_plan(int n, const ftlm_batch_item *items, int M, ftlm_vec_dist dist,
+                                              ftlm_dtype dtype, const ftlm_batch_plan *plan, void *stream,
+                                              ftlm_batch **out)
+{
+    if (!plan) return fail(FTLM_EINVAL, "NULL plan");
+    if (plan->tile_rows < 0 || plan->stream_rows < 0) return fail(FTLM_EINVAL, "negative tile rows");
+    return batch_create(n, items, M, dist, dtype, plan->block, plan->streams, (uint32_t)plan->tile_rows,
+                        (uint32_t)plan->stream_rows, stream, out);
 }
 
 extern "C" void ftlm_batch_destroy(ftlm_batch *p)
@@ -804,5 +829,108 @@ extern "C" ftlm_status ftlm_batch_autotune(int n, const ftlm_batch_item *items, 
     if (st != FTLM_OK) return st;
     *block_out = best_b;
     *streams_out = best_s;
+    return FTLM_OK;
+}
+
+namespace {
+
+// One timed run of a plan (after one untimed run); ms in *ms.
+ftlm_status time_plan(int n, const ftlm_batch_item *items, int M, ftlm_vec_dist dist, ftlm_dtype dtype,
+                      const ftlm_batch_plan &pl, cudaStream_t stream, cudaMemPool_t pool, cudaEvent_t *ev, float *ms)
+{
+    ftlm_batch *p = nullptr;
+    ftlm_status st = ftlm_batch_create_plan(n, items, M, dist, dtype, &pl, stream, &p);
+    if (st != FTLM_OK) return st;
+    void *work = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync(&work, p->total, pool, stream);
+    if (e != cudaSuccess) {
+        ftlm_batch_destroy_async(p, stream);
+        return e == cudaErrorMemoryAllocation ? fail(FTLM_ENOMEM, "no device memory for a tuning run")
+                                              : cuda_fail(e, "cudaMallocFromPoolAsync(tuning workspace)");
+    }
+    st = ftlm_batch_run(p, work, p->total, stream);
+    if (st == FTLM_OK && (e = cudaEventRecord(ev[0], stream)) != cudaSuccess) st = cuda_fail(e, "event");
+    if (st == FTLM_OK) st = ftlm_batch_run(p, work, p->total, stream);
+    if (st == FTLM_OK && (e = cudaEventRecord(ev[1], stream)) != cudaSuccess) st = cuda_fail(e, "event");
+    if (st == FTLM_OK && (e = cudaEventSynchronize(ev[1])) != cudaSuccess) st = cuda_fail(e, "tuning run");
+    if (st == FTLM_OK && (e = cudaEventElapsedTime(ms, ev[0], ev[1])) != cudaSuccess)
+        st = cuda_fail(e, "cudaEventElapsedTime");
+    cudaFreeAsync(work, stream);
+    ftlm_batch_destroy_async(p, stream);
+    return st;
+}
+
+}  // namespace
+
+extern "C" ftlm_status ftlm_batch_autotune_plan(int n, const ftlm_batch_item *items, int M, ftlm_vec_dist dist,
+                                                ftlm_dtype dtype, void *stream_, ftlm_batch_plan *best,
+                                                ftlm_batch_plan *tried, float *ms_out, int max_tried, int *n_tried)
+{
+    if (!best || !n_tried || max_tried < 0 || (max_tried > 0 && (!tried || !ms_out)))
+        return fail(FTLM_EINVAL, "bad output arguments");
+    cudaStream_t stream = (cudaStream_t)stream_;
+    bool any_large = false, any_ms = false;
+    for (int i = 0; i < n && items; ++i) {
+        const ftlm_basis *b = items[i].basis;
+        if (!b) continue;
+        if (b->two_s == 1 && b->N > 32 && b->D > kSmallRows) any_large = true;
+        if (b->two_s > 1 || (b->N <= 32 && b->D > kSmallRows)) any_ms = true;
+    }
+    int device = 0;
+    cudaMemPool_t pool = nullptr;
+    FTLM_CUDA(cudaGetDevice(&device));
+    FTLM_CUDA(table_pool(device, &pool));
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    FTLM_CUDA(cudaEventCreate(&ev[0]));
+    FTLM_CUDA(cudaEventCreate(&ev[1]));
+    ftlm_batch_plan cur{dtype == FTLM_F32 ? 16 : 8, any_large ? 4 : 1, (int)kMsTileRows, (int)kMsStreamRows};
+    float cur_ms = -1.f;
+    int count = 0;
+    ftlm_status st = FTLM_OK;
+    // coordinate search: block width (with the side-stream count where it matters),
+    // then the H.v tile rows and the streaming tile rows of the multi-sector path
+    auto consider = [&](const ftlm_batch_plan &cand) {
+        float ms = 0.f;
+        st = time_plan(n, items, M, dist, dtype, cand, stream, pool, ev, &ms);
+        if (st != FTLM_OK) return;
+        if (count < max_tried) {
+            tried[count] = cand;
+            ms_out[count] = ms;
+        }
+        ++count;
+        if (cur_ms < 0.f || ms < cur_ms) {
+            cur_ms = ms;
+            cur = cand;
+        }
+    };
+    for (int blk : {4, 8, 16})
+        for (int sc : {1, 2, 4, 8}) {
+            if (st != FTLM_OK || (!any_large && sc != 1)) break;
+            ftlm_batch_plan c = cur;
+            c.block = blk;
+            c.streams = sc;
+            consider(c);
+        }
+    if (any_ms) {
+        const ftlm_batch_plan base = cur;
+        for (int tr : {1024, 4096}) {
+            if (st != FTLM_OK) break;
+            ftlm_batch_plan c = base;
+            c.tile_rows = tr;
+            consider(c);
+        }
+        const ftlm_batch_plan base2 = cur;
+        for (int sr : {8192, 32768}) {
+            if (st != FTLM_OK) break;
+            ftlm_batch_plan c = base2;
+            c.stream_rows = sr;
+            consider(c);
+        }
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (st != FTLM_OK) return st;
+    *best = cur;
+    *n_tried = count;
     return FTLM_OK;
 }

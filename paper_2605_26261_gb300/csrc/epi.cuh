@@ -32,7 +32,6 @@ struct EpiDev {
     double *tile_part;      // per-tile sums of the dynamic tile order, [tile][B]
     int alpha_stride;
     int has_prev;
-    unsigned int cta_tiles;  // > 1: tiles are claimed per CTA in runs of this many
 };
 
 inline EpiDev epi_of(const LanczosHv *epi)

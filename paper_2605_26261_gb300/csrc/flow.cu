@@ -1,0 +1,511 @@
+// Continuous Lanczos flow: the chains of many sectors advance together, one H.v +
+// update launch pair per Lanczos step for all of them, and sectors join and leave
+// at step boundaries -- the chain-level continuous batching of a request loop.
+//
+// A sector's R chains are cut into units of B chains (the multi-sector units of
+// msv.cu).  Each unit has its own region of the caller's workspace (two vector
+// blocks, chain states, per-tile partial sums) and its own start launch j0: launch
+// j of the flow runs the unit's Lanczos step j - j0, so a unit admitted while others
+// are at step 40 starts at its step 1 in the same launch.  The units' rows are cut
+// into the same tiles as in a batch and every unit reduces its own tiles in tile
+// order, so a unit's results are bit-identical whether it runs alone or with any
+// other units, and whenever it was admitted.  When a unit reaches its last step its
+// chain lengths are copied out; when all units of a sector are done, the Ritz step
+// writes the sector's outputs.  Units are admitted while their regions fit in the
+// workspace (first fit); a sector that does not fit is refused (FTLM_ENOMEM) and can
+// be added again later.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ftlm_internal.cuh"
+#include "msv.cuh"
+
+namespace ftlm {
+
+namespace {
+
+uint64_t align256(uint64_t v) { return (v + 255) & ~255ull; }
+
+// First-fit allocation of ranges of [0, capacity).
+struct RangeAlloc {
+    std::map<uint64_t, uint64_t> free_;  // offset -> length
+    uint64_t free_total = 0;
+    void init(uint64_t cap)
+    {
+        free_.clear();
+        if (cap) free_[0] = cap;
+        free_total = cap;
+    }
+    bool take(uint64_t len, uint64_t *off)
+    {
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < len) continue;
+            *off = it->first;
+            const uint64_t rest = it->second - len, o = it->first + len;
+            free_.erase(it);
+            if (rest) free_[o] = rest;
+            free_total -= len;
+            return true;
+        }
+        return false;
+    }
+    void give(uint64_t off, uint64_t len)
+    {
+        if (!len) return;
+        free_total += len;
+        auto it = free_.emplace(off, len).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+};
+
+struct FlowUnit {
+    MsUnit u;  // offsets into the unit region of the workspace; chain_base into the coefficient rows
+    int kind;
+    int item;
+    uint64_t off, bytes;
+    bool started;
+};
+
+struct FlowItem {
+    ftlm_batch_item it;
+    int ticket;
+    int units_left;
+    uint32_t chain_base;
+    bool live;
+};
+
+int kind_of(const ftlm_basis *b) { return b->two_s > 1 ? kMsSpin : (b->mode == FTLM_RANK_CLT ? kMsClt : kMsCr); }
+
+// Region of one unit of B chains of b: two vector blocks, states and counter, and
+// the per-tile partial sums (H.v tiles outnumber the streaming tiles).
+uint64_t unit_bytes(const ftlm_basis *b, int B, uint64_t vsize)
+{
+    const uint64_t vb = align256(b->D * (uint64_t)B * vsize);
+    const uint64_t nt = (b->D + kMsTileRows - 1) / kMsTileRows;
+    return 2 * vb + align256(kMaxBlock * sizeof(ChainState) + 64) + align256(nt * B * sizeof(double));
+}
+
+__global__ void flow_meff_kernel(const MsUnit *__restrict__ units, const uint32_t *__restrict__ fin, uint32_t n,
+                                 int B, int *meff, char *ws)
+{
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n * (uint32_t)B; i += gridDim.x * blockDim.x) {
+        const MsUnit &U = units[fin[i / B]];
+        const int r = (int)(i % B);
+        if (r < U.nact) meff[U.chain_base + r] = reinterpret_cast<const ChainState *>(ws + U.off_st)[r].m_eff;
+    }
+}
+
+}  // namespace
+
+}  // namespace ftlm
+
+struct ftlm_flow {
+    ftlm_dtype dtype;
+    int B, M, dist, num_sms, device;
+    uint32_t max_units, max_chains;
+    // caller workspace: [alpha | beta : max_chains x M doubles][meff : max_chains ints][unit regions]
+    char *work;
+    double *alpha, *beta;
+    int *meff;
+    char *units_base;  // start of the unit regions (the ws of the msv kernels)
+    uint64_t units_bytes;
+    ftlm::RangeAlloc region, chains;
+    // device descriptors: units, per-kind H.v tile maps, streaming tile map, finished list
+    void *dev_block;
+    ftlm::MsUnit *d_units;
+    uint32_t *d_tile[3], *d_stile, *d_fin;
+    uint64_t cap_tiles, cap_stiles;
+    // pinned staging for the uploads (a ring of buffers, each reused once its copies ran)
+    static constexpr int kStages = 4;
+    char *stage[kStages];
+    cudaEvent_t stage_ev[kStages];
+    uint64_t stage_bytes;
+    int stage_cur;
+    std::vector<ftlm::FlowUnit> units;
+    std::vector<ftlm::FlowItem> items;
+    std::vector<int> done;  // tickets whose outputs are queued
+    int next_ticket;
+    int launches;  // step launches queued so far (j of the next H.v launch is launches + 1)
+    bool dirty;
+    uint32_t kind_first[3], kind_count[3], n_tiles[3], n_stiles;
+};
+
+using namespace ftlm;
+
+namespace {
+
+// The next pinned staging buffer (waits until its previous copies have run).
+ftlm_status stage_next(ftlm_flow *f, char **buf)
+{
+    f->stage_cur = (f->stage_cur + 1) % ftlm_flow::kStages;
+    FTLM_CUDA(cudaEventSynchronize(f->stage_ev[f->stage_cur]));
+    *buf = f->stage[f->stage_cur];
+    return FTLM_OK;
+}
+
+// Descriptors and tile maps of the current units, ordered by rank kind.
+ftlm_status upload(ftlm_flow *f, cudaStream_t stream)
+{
+    std::vector<MsUnit> du;
+    std::vector<uint32_t> tiles[3], stiles;
+    std::vector<FlowUnit> ordered;
+    for (int kind = 0; kind < 3; ++kind) {
+        f->kind_first[kind] = (uint32_t)ordered.size();
+        for (const FlowUnit &u : f->units)
+            if (u.kind == kind) ordered.push_back(u);
+        f->kind_count[kind] = (uint32_t)ordered.size() - f->kind_first[kind];
+    }
+    f->units = ordered;
+    for (int kind = 0; kind < 3; ++kind) {
+        for (uint32_t i = 0; i < f->kind_count[kind]; ++i) {
+            FlowUnit &fu = f->units[f->kind_first[kind] + i];
+            fu.u.tile0 = (uint32_t)tiles[kind].size();
+            for (uint32_t k = 0; k < fu.u.n_tiles; ++k) tiles[kind].push_back(i);  // kind-local index
+        }
+    }
+    for (uint32_t i = 0; i < f->units.size(); ++i) {
+        FlowUnit &fu = f->units[i];
+        fu.u.stile0 = (uint32_t)stiles.size();
+        for (uint32_t k = 0; k < fu.u.n_stiles; ++k) stiles.push_back(i);  // flow-wide index
+        du.push_back(fu.u);
+    }
+    for (int kind = 0; kind < 3; ++kind)
+        if (tiles[kind].size() > f->cap_tiles) return fail(FTLM_ENOMEM, "flow tile map full");
+    if (stiles.size() > f->cap_stiles) return fail(FTLM_ENOMEM, "flow tile map full");
+    char *buf = nullptr;
+    ftlm_status st = stage_next(f, &buf);
+    if (st != FTLM_OK) return st;
+    uint64_t off = 0;
+    auto put = [&](void *dst, const void *src, uint64_t bytes) -> cudaError_t {
+        if (!bytes) return cudaSuccess;
+        std::memcpy(buf + off, src, bytes);
+        const cudaError_t e = cudaMemcpyAsync(dst, buf + off, bytes, cudaMemcpyHostToDevice, stream);
+        off = align256(off + bytes);
+        return e;
+    };
+    FTLM_CUDA(put(f->d_units, du.data(), du.size() * sizeof(MsUnit)));
+    for (int kind = 0; kind < 3; ++kind) {
+        f->n_tiles[kind] = (uint32_t)tiles[kind].size();
+        FTLM_CUDA(put(f->d_tile[kind], tiles[kind].data(), tiles[kind].size() * sizeof(uint32_t)));
+    }
+    f->n_stiles = (uint32_t)stiles.size();
+    FTLM_CUDA(put(f->d_stile, stiles.data(), stiles.size() * sizeof(uint32_t)));
+    FTLM_CUDA(cudaEventRecord(f->stage_ev[f->stage_cur], stream));
+    f->dirty = false;
+    return FTLM_OK;
+}
+
+ftlm_status one_step(ftlm_flow *f, cudaStream_t stream)
+{
+    // admit: units added since the last step start with the next launch
+    const int jstart = f->launches;
+    bool fresh = false;
+    for (FlowUnit &u : f->units)
+        if (!u.started) {
+            u.started = true;
+            u.u.j0 = jstart;
+            fresh = true;
+            f->dirty = true;
+        }
+    if (f->units.empty()) return FTLM_OK;
+    if (f->dirty) {
+        ftlm_status s = upload(f, stream);
+        if (s != FTLM_OK) return s;
+    }
+    if (fresh) {
+        ftlm_status s = ms_flow_start(f->dtype, f->B, f->d_units, (uint32_t)f->units.size(), f->d_stile, f->n_stiles,
+                                      jstart, f->dist, f->units_base, f->num_sms, stream);
+        if (s != FTLM_OK) return s;
+    }
+    const int j = ++f->launches;
+    for (int kind = 0; kind < 3; ++kind) {
+        if (!f->kind_count[kind]) continue;
+        ftlm_status s = ms_flow_hv(f->dtype, f->B, kind, f->d_units + f->kind_first[kind], f->d_tile[kind],
+                                   f->n_tiles[kind], j, f->M, f->alpha, f->units_base, f->num_sms, stream);
+        if (s != FTLM_OK) return s;
+    }
+    ftlm_status s = ms_flow_update(f->dtype, f->B, f->d_units, f->d_stile, f->n_stiles, j, f->M, f->beta,
+                                   f->units_base, f->num_sms, stream);
+    if (s != FTLM_OK) return s;
+    // units at their last step: chain lengths out; sectors with every unit done: Ritz
+    std::vector<uint32_t> fin;
+    for (uint32_t i = 0; i < f->units.size(); ++i)
+        if (j - f->units[i].u.j0 >= f->units[i].u.m_max) fin.push_back(i);
+    if (fin.empty()) return FTLM_OK;
+    {
+        char *buf = nullptr;
+        s = stage_next(f, &buf);
+        if (s != FTLM_OK) return s;
+        std::memcpy(buf, fin.data(), fin.size() * sizeof(uint32_t));
+        FTLM_CUDA(cudaMemcpyAsync(f->d_fin, buf, fin.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, stream));
+        FTLM_CUDA(cudaEventRecord(f->stage_ev[f->stage_cur], stream));
+    }
+    flow_meff_kernel<<<(unsigned)((fin.size() * f->B + 255) / 256), 256, 0, stream>>>(
+        f->d_units, f->d_fin, (uint32_t)fin.size(), f->B, f->meff, f->units_base);
+    note_launch();
+    FTLM_CUDA(cudaGetLastError());
+    std::vector<FlowUnit> keep;
+    std::vector<bool> is_fin(f->units.size(), false);
+    for (uint32_t i : fin) is_fin[i] = true;
+    for (uint32_t i = 0; i < f->units.size(); ++i) {
+        FlowUnit &u = f->units[i];
+        if (!is_fin[i]) {
+            keep.push_back(u);
+            continue;
+        }
+        f->region.give(u.off, u.bytes);
+        FlowItem &it = f->items[u.item];
+        if (--it.units_left == 0) {
+            const ftlm_batch_item &bi = it.it;
+            const size_t cb = it.chain_base;
+            s = launch_ritz(bi.R, f->M, f->alpha + cb * f->M, f->beta + cb * f->M, f->meff + cb, bi.theta_dev,
+                            bi.weight_dev, stream);
+            if (s != FTLM_OK) return s;
+            FTLM_CUDA(cudaMemcpyAsync(bi.m_eff_dev, f->meff + cb, (size_t)bi.R * sizeof(int), cudaMemcpyDeviceToDevice,
+                                      stream));
+            f->chains.give(cb, (uint64_t)bi.R);
+            f->done.push_back(it.ticket);
+            it.live = false;
+        }
+    }
+    f->units = keep;
+    f->dirty = true;
+    return FTLM_OK;
+}
+
+}  // namespace
+
+extern "C" ftlm_status ftlm_flow_unit_bytes(const ftlm_basis *b, ftlm_dtype dtype, int block, uint64_t *bytes)
+{
+    if (!b || !bytes) return fail(FTLM_EINVAL, "NULL argument");
+    if (dtype != FTLM_F32 && dtype != FTLM_F64) return fail(FTLM_EINVAL, "bad dtype");
+    if (!valid_block(block)) return fail(FTLM_EINVAL, "block width must be 1, 4, 8 or 16");
+    *bytes = unit_bytes(b, block, dtype == FTLM_F32 ? 4 : 8);
+    return FTLM_OK;
+}
+
+extern "C" ftlm_status ftlm_flow_create(ftlm_dtype dtype, int block, int M, ftlm_vec_dist dist, int max_units,
+                                        void *work_dev, uint64_t work_bytes, void *stream_, ftlm_flow **out)
+{
+    if (!out) return fail(FTLM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (dtype != FTLM_F32 && dtype != FTLM_F64) return fail(FTLM_EINVAL, "bad dtype");
+    if (!valid_block(block)) return fail(FTLM_EINVAL, "block width must be 1, 4, 8 or 16");
+    if (M < 1 || M > FTLM_MAX_LANCZOS) return fail(FTLM_EINVAL, "M out of range");
+    if (dist != FTLM_VEC_GAUSS && dist != FTLM_VEC_RADEMACHER) return fail(FTLM_EINVAL, "bad distribution");
+    if (max_units < 1 || max_units > (1 << 20)) return fail(FTLM_EINVAL, "max_units out of range");
+    if (!work_dev || ((uintptr_t)work_dev & 255u)) return fail(FTLM_EINVAL, "workspace NULL or not 256-byte aligned");
+    cudaStream_t stream = (cudaStream_t)stream_;
+    ftlm_flow *f = new (std::nothrow) ftlm_flow();
+    if (!f) return fail(FTLM_ENOMEM, "host allocation failed");
+    f->dtype = dtype;
+    f->B = block;
+    f->M = M;
+    f->dist = dist;
+    f->max_units = (uint32_t)max_units;
+    f->max_chains = (uint32_t)max_units * (uint32_t)block;
+    const uint64_t coef = align256((uint64_t)f->max_chains * M * sizeof(double));
+    const uint64_t head = 2 * coef + align256((uint64_t)f->max_chains * sizeof(int));
+    if (work_bytes <= head) {
+        delete f;
+        return fail(FTLM_ENOMEM, "workspace smaller than the coefficient rows of max_units units");
+    }
+    f->work = (char *)work_dev;
+    f->alpha = (double *)f->work;
+    f->beta = (double *)(f->work + coef);
+    f->meff = (int *)(f->work + 2 * coef);
+    f->units_base = f->work + head;
+    f->units_bytes = work_bytes - head;
+    f->region.init(f->units_bytes);
+    f->chains.init(f->max_chains);
+    f->next_ticket = 1;
+    f->launches = 0;
+    f->dirty = true;
+    cudaError_t e = cudaGetDevice(&f->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&f->num_sms, cudaDevAttrMultiProcessorCount, f->device);
+    if (e != cudaSuccess) {
+        delete f;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    // tile maps: every unit row needs 2 B values of vectors at least
+    const uint64_t rows = f->units_bytes / (2ull * block * (dtype == FTLM_F32 ? 4 : 8));
+    f->cap_tiles = rows / kMsTileRows + max_units + 1;
+    f->cap_stiles = rows / kMsStreamRows + max_units + 1;
+    const uint64_t o_units = 0;
+    const uint64_t o_tile = align256((uint64_t)max_units * sizeof(MsUnit));
+    const uint64_t o_stile = o_tile + 3 * align256(f->cap_tiles * sizeof(uint32_t));
+    const uint64_t o_fin = o_stile + align256(f->cap_stiles * sizeof(uint32_t));
+    const uint64_t total = o_fin + align256((uint64_t)max_units * sizeof(uint32_t));
+    cudaMemPool_t pool = nullptr;
+    e = table_pool(f->device, &pool);
+    if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&f->dev_block, total, pool, stream);
+    if (e != cudaSuccess) {
+        delete f;
+        return e == cudaErrorMemoryAllocation ? fail(FTLM_ENOMEM, "no device memory for the flow descriptors")
+                                              : cuda_fail(e, "cudaMallocFromPoolAsync(flow)");
+    }
+    // pinned staging: descriptors, three H.v tile maps, the streaming map
+    f->stage_bytes = o_fin + align256((uint64_t)max_units * sizeof(uint32_t)) + 6 * 256;
+    for (int k = 0; k < ftlm_flow::kStages; ++k) {
+        f->stage[k] = nullptr;
+        f->stage_ev[k] = nullptr;
+    }
+    f->stage_cur = 0;
+    for (int k = 0; k < ftlm_flow::kStages && e == cudaSuccess; ++k) {
+        e = cudaMallocHost((void **)&f->stage[k], f->stage_bytes);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f->stage_ev[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        for (int k = 0; k < ftlm_flow::kStages; ++k) {
+            if (f->stage[k]) cudaFreeHost(f->stage[k]);
+            if (f->stage_ev[k]) cudaEventDestroy(f->stage_ev[k]);
+        }
+        cudaFreeAsync(f->dev_block, stream);
+        delete f;
+        return cuda_fail(e, "flow staging buffers");
+    }
+    char *base = (char *)f->dev_block;
+    f->d_units = (MsUnit *)(base + o_units);
+    for (int k = 0; k < 3; ++k) f->d_tile[k] = (uint32_t *)(base + o_tile + k * align256(f->cap_tiles * sizeof(uint32_t)));
+    f->d_stile = (uint32_t *)(base + o_stile);
+    f->d_fin = (uint32_t *)(base + o_fin);
+    *out = f;
+    return FTLM_OK;
+}
+
+extern "C" ftlm_status ftlm_flow_add(ftlm_flow *f, const ftlm_batch_item *item, int *ticket)
+{
+    if (!f || !item || !ticket) return fail(FTLM_EINVAL, "NULL argument");
+    const ftlm_basis *b = item->basis;
+    if (!b || item->R < 1 || item->first_chain < 0) return fail(FTLM_EINVAL, "bad item");
+    if (!item->theta_dev || !item->weight_dev || !item->m_eff_dev) return fail(FTLM_EINVAL, "NULL output in item");
+    if (b->two_s == 1 && b->N > 32) return fail(FTLM_EUNSUPPORTED, "flow sectors need N <= 32 at s = 1/2");
+    if (b->device != f->device) return fail(FTLM_EINVAL, "basis on another device");
+    const int B = f->B;
+    const uint64_t vsize = f->dtype == FTLM_F32 ? 4 : 8;
+    const int nu = (item->R + B - 1) / B;
+    if (f->units.size() + nu > f->max_units) return fail(FTLM_ENOMEM, "flow holds max_units units");
+    uint64_t cb = 0;
+    if (!f->chains.take((uint64_t)item->R, &cb)) return fail(FTLM_ENOMEM, "no coefficient rows free");
+    const uint64_t ub = unit_bytes(b, B, vsize);
+    std::vector<uint64_t> offs;
+    for (int k = 0; k < nu; ++k) {
+        uint64_t off = 0;
+        if (!f->region.take(ub, &off)) {
+            for (uint64_t o : offs) f->region.give(o, ub);
+            f->chains.give(cb, (uint64_t)item->R);
+            return fail(FTLM_ENOMEM, "the flow workspace has no room for this sector now");
+        }
+        offs.push_back(off);
+    }
+    FlowItem it{};
+    it.it = *item;
+    it.ticket = f->next_ticket++;
+    it.units_left = nu;
+    it.chain_base = (uint32_t)cb;
+    it.live = true;
+    const int idx = (int)f->items.size();
+    f->items.push_back(it);
+    const uint64_t vb = align256(b->D * (uint64_t)B * vsize);
+    for (int k = 0; k < nu; ++k) {
+        const int r0 = k * B;
+        FlowUnit fu{};
+        MsUnit &u = fu.u;
+        u.s = b->tables();
+        u.bl = b->mode == FTLM_RANK_CLT ? b->bonds_clt : b->bonds_cr;
+        u.spin = b->spin;
+        u.off_v0 = offs[k];
+        u.off_v1 = offs[k] + vb;
+        u.off_st = offs[k] + 2 * vb;
+        u.off_part = u.off_st + align256(kMaxBlock * sizeof(ChainState) + 64);
+        u.seed = item->seed;
+        u.tau = f->dtype == FTLM_F32 ? b->tau32 : b->tau64;
+        u.tile_rows = kMsTileRows;
+        u.stream_rows = kMsStreamRows;
+        u.n_tiles = (uint32_t)((b->D + kMsTileRows - 1) / kMsTileRows);
+        u.n_stiles = (uint32_t)((b->D + kMsStreamRows - 1) / kMsStreamRows);
+        u.chain_base = (uint32_t)cb + (uint32_t)r0;
+        u.key_n = b->key_n;
+        u.K = b->K;
+        u.chain0 = item->first_chain + r0;
+        u.nact = std::min(B, item->R - r0);
+        u.m_max = (uint64_t)f->M < b->D ? f->M : (int)b->D;
+        fu.kind = kind_of(b);
+        fu.item = idx;
+        fu.off = offs[k];
+        fu.bytes = ub;
+        fu.started = false;
+        f->units.push_back(fu);
+    }
+    f->dirty = true;
+    *ticket = it.ticket;
+    return FTLM_OK;
+}
+
+extern "C" ftlm_status ftlm_flow_step(ftlm_flow *f, int steps, void *stream)
+{
+    if (!f || steps < 0) return fail(FTLM_EINVAL, "bad flow step");
+    for (int s = 0; s < steps; ++s) {
+        // the items of the units that start now: coefficient rows to zero
+        for (const FlowUnit &u : f->units)
+            if (!u.started && u.u.chain_base == f->items[u.item].chain_base) {
+                const FlowItem &it = f->items[u.item];
+                const size_t rows = (size_t)it.it.R * f->M * sizeof(double);
+                FTLM_CUDA(cudaMemsetAsync(f->alpha + (size_t)it.chain_base * f->M, 0, rows, (cudaStream_t)stream));
+                FTLM_CUDA(cudaMemsetAsync(f->beta + (size_t)it.chain_base * f->M, 0, rows, (cudaStream_t)stream));
+            }
+        ftlm_status st = one_step(f, (cudaStream_t)stream);
+        if (st != FTLM_OK) return st;
+    }
+    return FTLM_OK;
+}
+
+extern "C" ftlm_status ftlm_flow_done(ftlm_flow *f, int *tickets, int max, int *n)
+{
+    if (!f || !n || max < 0 || (max > 0 && !tickets)) return fail(FTLM_EINVAL, "bad argument");
+    const int k = std::min<int>(max, (int)f->done.size());
+    for (int i = 0; i < k; ++i) tickets[i] = f->done[i];
+    f->done.erase(f->done.begin(), f->done.begin() + k);
+    *n = k;
+    return FTLM_OK;
+}
+
+extern "C" ftlm_status ftlm_flow_status(const ftlm_flow *f, int *units, int *items, uint64_t *free_bytes)
+{
+    if (!f) return fail(FTLM_EINVAL, "NULL flow");
+    if (units) *units = (int)f->units.size();
+    if (items) {
+        int live = 0;
+        for (const FlowItem &it : f->items) live += it.live ? 1 : 0;
+        *items = live;
+    }
+    if (free_bytes) *free_bytes = f->region.free_total;
+    return FTLM_OK;
+}
+
+extern "C" void ftlm_flow_destroy(ftlm_flow *f)
+{
+    if (!f) return;
+    cudaDeviceSynchronize();
+    cudaFreeAsync(f->dev_block, 0);
+    for (int k = 0; k < ftlm_flow::kStages; ++k) {
+        cudaFreeHost(f->stage[k]);
+        cudaEventDestroy(f->stage_ev[k]);
+    }
+    delete f;
+}

@@ -249,10 +249,6 @@ uint32_t hv_lanczos_tiles(const ftlm_basis *b, int B);
 // more than kMaxHiBonds of them).
 bool build_hi_walk(const ftlm_basis *b, int rh, HiWalk *w);
 struct EpiDev;
-// Walk A of a split Lanczos step with each block of rows staged in shared memory
-// (walka.cu; L < N <= 32).
-ftlm_status launch_walk_a_staged(const ftlm_basis *b, ftlm_dtype dtype, int B, const void *x, void *y,
-                                 const EpiDev &ep, cudaStream_t stream);
 // Walk B of a split Lanczos step (the epilogue's alpha as per-tile sums).
 ftlm_status launch_walk_b(const ftlm_basis *b, const HiWalk &w, ftlm_dtype dtype, int B, const void *x, void *y,
                           const EpiDev &ep, cudaStream_t stream);

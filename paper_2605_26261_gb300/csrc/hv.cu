@@ -140,35 +140,6 @@ hv_kernel(const SectorTables s, const BondList bl, const V *__restrict__ x, V *y
                 if (ok[i]) epi_row<V, B, LANCZOS>(ep, s_inv_s, s_c_prev, x, y, t[i], jsum4 - dsum[i], acc[i], apart);
         }
     };
-    if (TILES && ep.cta_tiles > 1) {
-        // CTA-level order: a CTA claims runs of cta_tiles consecutive tiles from the
-        // counter and its warps share them, so a run's rows -- and the sources of
-        // their low-block exchanges, which stay inside the row's high-pattern group --
-        // meet in one SM's L1
-        __shared__ uint32_t s_next;
-        const uint32_t per = ep.cta_tiles;
-        const uint32_t nsup = (ntiles + per - 1) / per;
-        const uint32_t wic = threadIdx.x >> 5, wpc = blockDim.x >> 5;
-        for (uint32_t st = blockIdx.x; st < nsup;) {
-            if (threadIdx.x == 0) s_next = atomicAdd(ep.counter + 1, 1u) + gridDim.x;
-            for (uint32_t sub = wic; sub < per; sub += wpc) {
-                const uint32_t tile = st * per + sub;
-                if (tile >= ntiles) break;
-                do_tile(tile);
-            }
-            __syncthreads();
-            st = s_next;
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) {
-            __threadfence();
-            if (atomicAdd(ep.counter + 2, 1u) == gridDim.x - 1) {
-                ep.counter[1] = 0;
-                ep.counter[2] = 0;
-            }
-        }
-        return;
-    }
     for (uint32_t tile = warp; tile < ntiles;) {
         // claim the next tile now; its atomic completes while this tile's rows run
         const uint32_t claim = TILES ? claim_tile(ep) : 0u;
@@ -177,6 +148,58 @@ hv_kernel(const SectorTables s, const BondList bl, const V *__restrict__ x, V *y
     }
     if (TILES) tiles_done(ep, nwarps);
     else if (LANCZOS) epi_end<V, B, kRowThreads>(ep, apart);
+}
+
+// Walk A with one CTA of WA_THREADS threads per SM whose warps share runs of `run`
+// consecutive tiles claimed from the counter: a run of about one high-pattern group
+// keeps the group's x rows (the sources of its low-low exchanges, up to 110 KB for
+// blocks of 8 FP32 vectors) in that SM's L1 while its warps work through it.
+constexpr int kWalkAThreads = 768;
+
+template <typename V, typename Lbl, int B, int C>
+__global__ void __launch_bounds__(kWalkAThreads, 1)
+walk_a_group_kernel(const SectorTables s, const BondList bl, const V *__restrict__ x, V *y, const EpiDev ep,
+                    uint32_t run)
+{
+    extern __shared__ uint16_t s_tlo[];
+    __shared__ uint4 s_bond[kMaxBondSlots];
+    __shared__ V s_inv_s[B], s_c_prev[B];
+    __shared__ uint32_t s_next;
+    if (epi_begin<V, B>(ep, s_inv_s, s_c_prev)) return;
+    {
+        const uint4 *src = sizeof(V) == 4 ? bl.slots_f32 : bl.slots_f64;
+        for (int i = threadIdx.x; i < bl.nb; i += blockDim.x) s_bond[i] = src[i];
+    }
+    for (uint32_t i = threadIdx.x; i <= s.lomask; i += blockDim.x) s_tlo[i] = __ldg(s.tlo + i);
+    __syncthreads();
+    const V jsum4 = (V)bl.jsum4;
+    const uint32_t lane = threadIdx.x & 31u, wic = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+    const uint32_t ntiles = (uint32_t)(((uint64_t)s.D + 31u) / 32u);
+    const uint32_t nrun = (ntiles + run - 1) / run;
+    for (uint32_t r = blockIdx.x; r < nrun;) {
+        if (threadIdx.x == 0) s_next = atomicAdd(ep.counter + 1, 1u) + gridDim.x;
+        const uint32_t t1 = min(ntiles, (r + 1) * run);
+        for (uint32_t tile = r * run + wic; tile < t1; tile += wpc) {
+            const uint32_t tt = tile * 32u + lane;
+            const bool ok = tt < s.D;
+            const uint32_t t[1] = {ok ? tt : s.D - 1};
+            V acc[1][B], dsum[1] = {(V)0};
+#pragma unroll
+            for (int q = 0; q < B; ++q) acc[0][q] = (V)0;
+            rows_cr<V, Lbl, 1, B, C>(s, bl, s_bond, s_tlo, x, t, acc, dsum);
+            if (ok) epi_row_walk_a<V, B>(ep, s_inv_s, s_c_prev, x, y, t[0], jsum4 - dsum[0], acc[0]);
+        }
+        __syncthreads();
+        r = s_next;
+        __syncthreads();  // every thread has read s_next before thread 0 writes it again
+    }
+    if (threadIdx.x == 0) {  // the last CTA zeroes the claim counters
+        __threadfence();
+        if (atomicAdd(ep.counter + 2, 1u) == gridDim.x - 1) {
+            ep.counter[1] = 0;
+            ep.counter[2] = 0;
+        }
+    }
 }
 
 // alpha_j of a dynamically ordered launch from its per-tile sums: block b adds a
@@ -214,28 +237,6 @@ int rows_per_thread(bool clt)
     return over ? over : (clt ? 1 : 2);
 }
 
-// Walk A of the split H.v with staged row blocks (FTLM_WALK_A_STAGED = 1 turns it on).
-bool walk_a_staged()
-{
-    static const bool on = [] {
-        const char *e = getenv("FTLM_WALK_A_STAGED");
-        return e && atoi(e) == 1;
-    }();
-    return on;
-}
-
-// Tiles per CTA-level claim of the dynamically ordered launches (FTLM_HV_CTA_TILES;
-// default 0: every warp claims its own tiles).
-uint32_t hv_cta_tiles()
-{
-    static const uint32_t v = [] {
-        const char *e = getenv("FTLM_HV_CTA_TILES");
-        const int n = e ? atoi(e) : 0;
-        return n > 1 ? (uint32_t)n : 0u;
-    }();
-    return v;
-}
-
 // Cap on resident CTAs per SM used for the H.v grid (FTLM_HV_CTAS, default: no cap).
 // Fewer CTAs shrink the window of rows in flight and with it the L2 working set of
 // the gather streams.
@@ -250,15 +251,23 @@ int hv_cta_cap()
 }
 
 // Split Lanczos H.v (see HiWalk): used when the basis asks for it, or under
-// FTLM_HV_AUTO when one block of vectors is at least kSplitMinBytes -- below that
-// the sector's vectors stay in L2 and the one walk already hits there.
-constexpr uint64_t kSplitMinBytes = 64ull << 20;
+// FTLM_HV_AUTO for blocks of vectors of at least kSplitMinBytes32 (FP32) or
+// kSplitMinBytes64 (FP64).  Measured on GB300 (H.v step of the N = 30 icosidodecahedral
+// S^z = 0 sector, one walk -> split): FP32 blocks of 16 / 8 / 4 / 1 vectors (10, 5,
+// 2.5, 0.6 GB) 35.2 -> 33.5, 16.7 -> 16.4, 9.69 -> 9.78, 5.54 -> 6.68 ms; FP64
+// blocks of 4 / 1 (5, 1.2 GB) 96.2 -> 82.9, 37.2 -> 33.7 ms; FP32 blocks of 8 on the
+// 30 M-row sector of the same cluster (0.96 GB) 3.21 -> 3.33 ms.  The split moves
+// two row streams per step instead of one but no long-jump gather misses L2 (DRAM
+// 5.7 instead of 9.5 GB on the 30 M-row sector).
+constexpr uint64_t kSplitMinBytes32 = 4ull << 30;
+constexpr uint64_t kSplitMinBytes64 = 1ull << 30;
 constexpr int kDefaultWalkRh = 8;
 
 bool split_walks(const ftlm_basis *b, int B, size_t vsize, HiWalk *w)
 {
     if (b->hv_schedule == FTLM_HV_ONE_WALK) return false;
-    if (b->hv_schedule == FTLM_HV_AUTO && b->D * (uint64_t)B * vsize < kSplitMinBytes) return false;
+    const uint64_t bytes = b->D * (uint64_t)B * vsize;
+    if (b->hv_schedule == FTLM_HV_AUTO && bytes < (vsize == 4 ? kSplitMinBytes32 : kSplitMinBytes64)) return false;
     return build_hi_walk(b, b->walk_rh ? b->walk_rh : kDefaultWalkRh, w);
 }
 
@@ -273,9 +282,31 @@ ftlm_status launch_rows(const ftlm_basis *b, const BondList &bl, const V *x, V *
     const size_t smem_max = CLT ? 0 : ((size_t)1 << kLoBitsMax) * sizeof(uint16_t);
     FTLM_CUDA(kernel_occupancy((const void *)kern, kRowThreads, smem_max, false, &occ));
     const int grid = row_grid(b, (b->D + RT - 1) / RT, std::min(occ, hv_cta_cap()));
-    EpiDev e = ep;
-    e.cta_tiles = (EPI != kPlain && !CLT) ? hv_cta_tiles() : 0u;
-    kern<<<grid, kRowThreads, smem, stream>>>(b->tables(), bl, x, y, e);
+    kern<<<grid, kRowThreads, smem, stream>>>(b->tables(), bl, x, y, ep);
+    note_launch();
+    return FTLM_OK;
+}
+
+// Tiles per run of the group walk A (FTLM_WALK_A_RUN; 0: the label-order walk A).
+uint32_t walk_a_run()
+{
+    static const uint32_t v = [] {
+        const char *e = getenv("FTLM_WALK_A_RUN");
+        const int n = e ? atoi(e) : 0;
+        return n > 0 ? (uint32_t)n : 0u;
+    }();
+    return v;
+}
+
+template <typename V, typename Lbl, int B, int C>
+ftlm_status launch_walk_a_group(const ftlm_basis *b, const V *x, V *y, const EpiDev &ep, uint32_t run,
+                                cudaStream_t stream)
+{
+    const size_t smem = ((size_t)1 << b->L) * sizeof(uint16_t);
+    auto kern = walk_a_group_kernel<V, Lbl, B, C>;
+    // most of the SM's 256 KB of L1 + shared memory to L1 (the kernel needs 36 KB)
+    FTLM_CUDA(cudaFuncSetAttribute((const void *)kern, cudaFuncAttributePreferredSharedMemoryCarveout, 20));
+    kern<<<b->num_sms, kWalkAThreads, smem, stream>>>(b->tables(), b->bonds_walk_a, x, y, ep, run);
     note_launch();
     return FTLM_OK;
 }
@@ -301,10 +332,14 @@ ftlm_status launch(const ftlm_basis *b, const V *x, V *y, const EpiDev &ep, cuda
         uint32_t ntiles;
         if (split_walks(b, B, sizeof(V), &w)) {
             const ftlm_dtype dt = sizeof(V) == 4 ? FTLM_F32 : FTLM_F64;
-            if (b->N <= 32 && walk_a_staged())
-                st = launch_walk_a_staged(b, dt, B, x, y, ep, stream);
-            else
-                st = launch_rows<V, Lbl, false, kWalkA, RT, B, C>(b, b->bonds_walk_a, x, y, ep, stream);
+            bool done = false;
+            if constexpr (sizeof(V) == 4 && RT == 1 && B <= 8) {  // registers of 768-thread CTAs
+                if (walk_a_run()) {
+                    st = launch_walk_a_group<V, Lbl, B, C>(b, x, y, ep, walk_a_run(), stream);
+                    done = true;
+                }
+            }
+            if (!done) st = launch_rows<V, Lbl, false, kWalkA, RT, B, C>(b, b->bonds_walk_a, x, y, ep, stream);
             if (st == FTLM_OK) st = launch_walk_b(b, w, dt, B, x, y, ep, stream);
             ntiles = w.ntiles;
         } else {

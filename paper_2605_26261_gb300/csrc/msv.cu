@@ -2,7 +2,7 @@
 // (steps a2-a4 over a set of sectors).
 //
 // The units are blocks of B chains of mid-sized and large sectors.  Their rows are
-// cut into tiles of kMsTileRows; one launch walks the tiles of every unit of a
+// cut into tiles (tile_rows, default kMsTileRows); one launch walks the tiles of every unit of a
 // wave (a persistent grid; the H.v launch hands tiles out in order from a counter,
 // so at any moment the GPU works on a window of consecutive tiles -- one or two
 // sectors -- whose vectors stay in L2).  Per Lanczos step there are two launches for the whole wave: the fused
@@ -79,22 +79,24 @@ __device__ __forceinline__ double tile_total(const double *partials, uint32_t n_
     return warp_sum(v);
 }
 
+// Start vectors of the units with j0 == jstart (every unit of a batch: jstart = 0).
 template <typename V, int B>
 __global__ void __launch_bounds__(kRowThreads)
 ms_start_kernel(const MsUnit *__restrict__ units, const uint32_t *__restrict__ tile_unit, uint32_t n_tiles, int dist,
-                char *ws)
+                char *ws, int jstart)
 {
     for (uint32_t g = blockIdx.x; g < n_tiles; g += gridDim.x) {
         const UnitView uv{units + tile_unit[g], ws};
         const MsUnit &U = *uv.u;
+        if (U.j0 != jstart) continue;  // CTA-uniform
         const uint32_t k = g - U.stile0, D = U.s.D;
         uint64_t key[B];
 #pragma unroll
         for (int r = 0; r < B; ++r) key[r] = chain_key(U.seed, U.key_n, U.K, (uint32_t)(U.chain0 + r));
         V *u0 = uv.vec<V>(0);
         DotAcc<V> acc[B];
-        const uint32_t row1 = min(D, (k + 1) * kMsStreamRows);
-        for (uint32_t t = k * kMsStreamRows + threadIdx.x; t < row1; t += kRowThreads) {
+        const uint32_t row1 = min(D, (k + 1) * U.stream_rows);
+        for (uint32_t t = k * U.stream_rows + threadIdx.x; t < row1; t += kRowThreads) {
             V out[B];
 #pragma unroll
             for (int r = 0; r < B; ++r) {
@@ -149,7 +151,6 @@ ms_hv_kernel(const MsUnit *__restrict__ units, const uint32_t *__restrict__ tile
     __shared__ uint32_t s_next;
     uint32_t loaded = 0xffffffffu;
     EpiDev ep{};
-    ep.has_prev = j > 1;
     // tiles after the first come from a counter in the wave's first unit (its words
     // 1 and 2: tiles handed out, CTAs done; zeroed by ms_reset_kernel and again by
     // the last CTA of each launch)
@@ -158,6 +159,7 @@ ms_hv_kernel(const MsUnit *__restrict__ units, const uint32_t *__restrict__ tile
         const uint32_t ui = tile_unit[g];
         const UnitView uv{units + ui, ws};
         const MsUnit &U = *uv.u;
+        const int ju = j - U.j0;  // the unit's Lanczos step
         if (ui != loaded) {  // CTA-uniform: stage the unit's bonds, tlo and chain scalars
             __syncthreads();  // every thread is past its last read of the previous unit's data
             loaded = ui;
@@ -177,23 +179,24 @@ ms_hv_kernel(const MsUnit *__restrict__ units, const uint32_t *__restrict__ tile
                 const ChainState *st = uv.st();
                 int all = 1;
                 for (int r = 0; r < B; ++r) all &= st[r].stopped;
-                s_skip = all || j > U.m_max;
+                s_skip = all || ju < 1 || ju > U.m_max;
             }
             if (threadIdx.x < B) {
                 const ChainState &c = uv.st()[threadIdx.x];
                 s_inv_s[threadIdx.x] = (V)(1.0 / c.s_cur);
-                s_c_prev[threadIdx.x] = j > 1 ? (V)(c.beta_prev / c.s_prev) : (V)0;
+                s_c_prev[threadIdx.x] = ju > 1 ? (V)(c.beta_prev / c.s_prev) : (V)0;
             }
+            ep.has_prev = ju > 1;
             __syncthreads();
         }
         if (!s_skip) {  // CTA-uniform
         const uint32_t k = g - U.tile0, D = U.s.D;
-        const V *x = uv.vec<V>((j - 1) & 1);
-        V *y = uv.vec<V>(j & 1);
+        const V *x = uv.vec<V>((ju - 1) & 1);
+        V *y = uv.vec<V>(ju & 1);
         const V jsum4 = (V)U.bl.jsum4;
         DotAcc<V> apart[B];
-        const uint32_t row0 = k * kMsTileRows;
-        for (uint32_t p = 0; p < kMsTileRows; p += kRowThreads) {
+        const uint32_t row0 = k * U.tile_rows;
+        for (uint32_t p = 0; p < U.tile_rows; p += kRowThreads) {
             const uint32_t tt = row0 + p + threadIdx.x;
             if (row0 + p >= D) break;  // CTA-uniform
             const bool ok = tt < D;
@@ -217,7 +220,7 @@ ms_hv_kernel(const MsUnit *__restrict__ units, const uint32_t *__restrict__ tile
                 const double v = tile_total<B>(uv.partials(), U.n_tiles, r);
                 if (threadIdx.x == 0 && !st[r].stopped) {
                     st[r].alpha = v;
-                    alpha[(size_t)(U.chain_base + r) * M + (j - 1)] = v;
+                    alpha[(size_t)(U.chain_base + r) * M + (ju - 1)] = v;
                 }
             }
             if (threadIdx.x == 0) *uv.counter() = 0;
@@ -255,6 +258,7 @@ ms_update_kernel(const MsUnit *__restrict__ units, const uint32_t *__restrict__ 
         const uint32_t ui = tile_unit[g];
         const UnitView uv{units + ui, ws};
         const MsUnit &U = *uv.u;
+        const int ju = j - U.j0;  // the unit's Lanczos step
         if (ui != loaded) {
             __syncthreads();
             loaded = ui;
@@ -262,7 +266,7 @@ ms_update_kernel(const MsUnit *__restrict__ units, const uint32_t *__restrict__ 
                 const ChainState *st = uv.st();
                 int all = 1;
                 for (int r = 0; r < B; ++r) all &= st[r].stopped;
-                s_skip = all || j > U.m_max;
+                s_skip = all || ju < 1 || ju > U.m_max;
             }
             if (threadIdx.x < B) {
                 const ChainState &c = uv.st()[threadIdx.x];
@@ -273,8 +277,8 @@ ms_update_kernel(const MsUnit *__restrict__ units, const uint32_t *__restrict__ 
         }
         if (s_skip) continue;
         const uint32_t k = g - U.stile0, D = U.s.D;
-        V *y = uv.vec<V>(j & 1);
-        const V *u = uv.vec<V>((j - 1) & 1);
+        V *y = uv.vec<V>(ju & 1);
+        const V *u = uv.vec<V>((ju - 1) & 1);
         V a[B];
         bool zero[B];
 #pragma unroll
@@ -283,8 +287,8 @@ ms_update_kernel(const MsUnit *__restrict__ units, const uint32_t *__restrict__ 
             zero[r] = s_zero[r] != 0;
         }
         DotAcc<V> acc[B];
-        const uint64_t e0 = (uint64_t)k * kMsStreamRows * B;
-        const uint64_t e1 = (uint64_t)min(D, (k + 1) * kMsStreamRows) * B;
+        const uint64_t e0 = (uint64_t)k * U.stream_rows * B;
+        const uint64_t e1 = (uint64_t)min(D, (k + 1) * U.stream_rows) * B;
         const uint64_t full = e0 + (e1 - e0) / U_ * U_;
         for (uint64_t e = e0 + (uint64_t)threadIdx.x * U_; e < full; e += (uint64_t)kRowThreads * U_) {
             V yv[U_], xv[U_], w[U_];
@@ -309,12 +313,12 @@ ms_update_kernel(const MsUnit *__restrict__ units, const uint32_t *__restrict__ 
                 const double bt = sqrt(tile_total<B>(uv.partials(), U.n_stiles, r));
                 if (threadIdx.x == 0 && !st[r].stopped) {
                     ChainState &c = st[r];
-                    if (j < U.m_max) {
+                    if (ju < U.m_max) {
                         if (bt <= U.tau) {
                             c.stopped = 1;
-                            c.m_eff = j;
+                            c.m_eff = ju;
                         } else {
-                            beta[(size_t)(U.chain_base + r) * M + (j - 1)] = bt;
+                            beta[(size_t)(U.chain_base + r) * M + (ju - 1)] = bt;
                             c.s_prev = c.s_cur;
                             c.s_cur = bt;
                             c.beta_prev = bt;
@@ -332,11 +336,14 @@ ms_update_kernel(const MsUnit *__restrict__ units, const uint32_t *__restrict__ 
 
 // Chain states and reduction counters of every unit of the wave to zero (the
 // counters must start at zero: the last tile of a unit is found by its ticket).
-__global__ void ms_reset_kernel(const MsUnit *__restrict__ units, uint32_t n_units, char *ws)
+// Units with j0 == jstart only (a batch: every unit, jstart = 0).
+__global__ void ms_reset_kernel(const MsUnit *__restrict__ units, uint32_t n_units, char *ws, int jstart)
 {
     constexpr uint32_t words = (kMaxBlock * sizeof(ChainState) + 64) / sizeof(uint32_t);
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_units * words; i += gridDim.x * blockDim.x) {
-        uint32_t *p = reinterpret_cast<uint32_t *>(ws + units[i / words].off_st);
+        const MsUnit &U = units[i / words];
+        if (U.j0 != jstart) continue;
+        uint32_t *p = reinterpret_cast<uint32_t *>(ws + U.off_st);
         p[i % words] = 0u;
     }
 }
@@ -375,10 +382,10 @@ ftlm_status ms_run_typed(const MsWave &w, const MsUnit *units, const uint32_t *t
     {
         const uint32_t words = (kMaxBlock * sizeof(ChainState) + 64) / sizeof(uint32_t);
         const int g = (int)std::min<uint64_t>(((uint64_t)w.n_units * words + 255) / 256, (uint64_t)num_sms * 4);
-        ms_reset_kernel<<<g, 256, 0, stream>>>(units, w.n_units, ws);
+        ms_reset_kernel<<<g, 256, 0, stream>>>(units, w.n_units, ws, 0);
         note_launch();
     }
-    ms_start_kernel<V, B><<<sgrid(occ_start), kRowThreads, 0, stream>>>(units, stile_unit, w.n_stiles, dist, ws);
+    ms_start_kernel<V, B><<<sgrid(occ_start), kRowThreads, 0, stream>>>(units, stile_unit, w.n_stiles, dist, ws, 0);
     note_launch();
     FTLM_CUDA(cudaGetLastError());
     for (int j = 1; j <= w.m_max; ++j) {
@@ -415,7 +422,85 @@ ftlm_status ms_run_v(const MsWave &w, int B, const MsUnit *units, const uint32_t
     }
 }
 
+// ---- single launches for a continuous flow (flow.cu) -------------------------
+template <typename V, int B>
+ftlm_status flow_start_typed(const MsUnit *units, uint32_t n_units, const uint32_t *stile_unit, uint32_t n_stiles,
+                             int jstart, int dist, char *ws, int num_sms, cudaStream_t stream)
+{
+    int occ = 1;
+    FTLM_CUDA(kernel_occupancy((const void *)ms_start_kernel<V, B>, kRowThreads, 0, false, &occ));
+    const uint32_t words = (kMaxBlock * sizeof(ChainState) + 64) / sizeof(uint32_t);
+    const int g = (int)std::max<uint64_t>(1, std::min<uint64_t>(((uint64_t)n_units * words + 255) / 256,
+                                                                (uint64_t)num_sms * 4));
+    ms_reset_kernel<<<g, 256, 0, stream>>>(units, n_units, ws, jstart);
+    note_launch();
+    const int gs = (int)std::max<uint64_t>(1, std::min<uint64_t>(n_stiles, (uint64_t)num_sms * occ));
+    ms_start_kernel<V, B><<<gs, kRowThreads, 0, stream>>>(units, stile_unit, n_stiles, dist, ws, jstart);
+    note_launch();
+    FTLM_CUDA(cudaGetLastError());
+    return FTLM_OK;
+}
+
+template <typename V, int B>
+ftlm_status flow_hv_typed(int kind, const MsUnit *units, const uint32_t *tile_unit, uint32_t n_tiles, int j, int M,
+                          double *alpha, char *ws, int num_sms, cudaStream_t stream)
+{
+    const size_t smem = kind == kMsClt ? 0 : ((size_t)1 << kLoBitsMax) * sizeof(uint16_t);
+    void *hv = ms_hv_ptr<V, B>(kind);
+    int oh = 1;
+    FTLM_CUDA(kernel_occupancy(hv, kRowThreads, smem, smem != 0, &oh));
+    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(n_tiles, (uint64_t)num_sms * oh));
+    void *args[] = {(void *)&units, (void *)&tile_unit, (void *)&n_tiles, (void *)&j, (void *)&M, (void *)&alpha,
+                    (void *)&ws};
+    void *tok = profile_begin(kProfHv, stream, B);
+    FTLM_CUDA(cudaLaunchKernel(hv, dim3(grid), dim3(kRowThreads), args, smem, stream));
+    note_launch();
+    profile_end(tok, stream);
+    return FTLM_OK;
+}
+
+template <typename V, int B>
+ftlm_status flow_update_typed(const MsUnit *units, const uint32_t *stile_unit, uint32_t n_stiles, int j, int M,
+                              double *beta, char *ws, int num_sms, cudaStream_t stream)
+{
+    int occ = 1;
+    FTLM_CUDA(kernel_occupancy((const void *)ms_update_kernel<V, B>, kRowThreads, 0, false, &occ));
+    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(n_stiles, (uint64_t)num_sms * occ));
+    void *tok = profile_begin(kProfUpdate, stream);
+    ms_update_kernel<V, B><<<grid, kRowThreads, 0, stream>>>(units, stile_unit, n_stiles, j, M, beta, ws);
+    note_launch();
+    profile_end(tok, stream);
+    FTLM_CUDA(cudaGetLastError());
+    return FTLM_OK;
+}
+
+#define FTLM_FLOW_DISPATCH(FN, ...)                                                         \
+    switch (B) {                                                                           \
+    case 16: return dtype == FTLM_F32 ? FN<float, 16>(__VA_ARGS__) : FN<double, 16>(__VA_ARGS__); \
+    case 8: return dtype == FTLM_F32 ? FN<float, 8>(__VA_ARGS__) : FN<double, 8>(__VA_ARGS__);    \
+    case 4: return dtype == FTLM_F32 ? FN<float, 4>(__VA_ARGS__) : FN<double, 4>(__VA_ARGS__);    \
+    default: return dtype == FTLM_F32 ? FN<float, 1>(__VA_ARGS__) : FN<double, 1>(__VA_ARGS__);   \
+    }
+
 }  // namespace
+
+ftlm_status ms_flow_start(ftlm_dtype dtype, int B, const MsUnit *units, uint32_t n_units, const uint32_t *stile_unit,
+                          uint32_t n_stiles, int jstart, int dist, char *ws, int num_sms, cudaStream_t stream)
+{
+    FTLM_FLOW_DISPATCH(flow_start_typed, units, n_units, stile_unit, n_stiles, jstart, dist, ws, num_sms, stream)
+}
+
+ftlm_status ms_flow_hv(ftlm_dtype dtype, int B, int kind, const MsUnit *units, const uint32_t *tile_unit,
+                       uint32_t n_tiles, int j, int M, double *alpha, char *ws, int num_sms, cudaStream_t stream)
+{
+    FTLM_FLOW_DISPATCH(flow_hv_typed, kind, units, tile_unit, n_tiles, j, M, alpha, ws, num_sms, stream)
+}
+
+ftlm_status ms_flow_update(ftlm_dtype dtype, int B, const MsUnit *units, const uint32_t *stile_unit, uint32_t n_stiles,
+                           int j, int M, double *beta, char *ws, int num_sms, cudaStream_t stream)
+{
+    FTLM_FLOW_DISPATCH(flow_update_typed, units, stile_unit, n_stiles, j, M, beta, ws, num_sms, stream)
+}
 
 ftlm_status ms_run_wave(const MsWave &w, ftlm_dtype dtype, int B, const MsUnit *units, const uint32_t *tile_unit,
                         const uint32_t *stile_unit, int M, int dist, char *ws, double *alpha, double *beta,

@@ -92,21 +92,23 @@ template <typename V> __device__ __forceinline__ const V *spin_up(const SpinDev 
 template <> __device__ __forceinline__ const float *spin_up<float>(const SpinDev &p) { return p.upf; }
 template <> __device__ __forceinline__ const double *spin_up<double>(const SpinDev &p) { return p.upd; }
 
-// Per-bond factors of a row, indexed by the digit pair 8 a_i + a_j (digits <= 7):
+// Per-bond factors of a row, indexed by the digit pair d a_i + a_j (d <= 8):
 // [0, 64) the s_i^+ s_j^- factor of Eq. 13 and [64, 128) the s_i^- s_j^+ factor of
 // Eq. 14, both with the 1/2 of Eq. 12 and zero where the source digit leaves
-// 0 .. 2s; [128, 192) m_i m_j (exact: products of half-integers).
+// 0 .. 2s; [128, 192) m_i m_j (exact: products of half-integers).  The compact
+// index keeps the d^2 entries of a table in distinct shared-memory banks for
+// d <= 5, so the lanes of a warp read them without bank conflicts.
 constexpr int kSpinCoef = 3 * 64;
 
 template <typename V> __device__ __forceinline__ void spin_stage_coef(const SpinDev &p, V *s_cf)
 {
     const V *up = spin_up<V>(p);
-    const uint32_t two_s = p.two_s;
+    const uint32_t two_s = p.two_s, d = p.d;
     const V sv = (V)(0.5 * p.two_s);
     for (uint32_t idx = threadIdx.x; idx < (uint32_t)kSpinCoef; idx += blockDim.x) {
-        const uint32_t tab = idx >> 6, ai = (idx >> 3) & 7u, aj = idx & 7u;
+        const uint32_t tab = idx >> 6, rem = idx & 63u, ai = rem / d, aj = rem % d;
         V v = (V)0;
-        if (ai <= two_s && aj <= two_s) {
+        if (rem < d * d) {
             if (tab == 0u && ai >= 1u && aj < two_s) v = (V)0.5 * up[ai - 1] * up[aj];
             else if (tab == 1u && ai < two_s && aj >= 1u) v = (V)0.5 * up[ai] * up[aj - 1];
             else if (tab == 2u) v = ((V)ai - sv) * ((V)aj - sv);
@@ -147,7 +149,7 @@ __device__ __forceinline__ void spin_row(const SectorTables &s, const SpinDev &p
             const uint4 e = s_bond[in ? b : 0];
             const uint32_t i = e.x & 255u, j = (e.x >> 8) & 255u, flags = e.x >> 16;
             const uint32_t ai = (uint32_t)(w.dig >> (4 * i)) & 15u, aj = (uint32_t)(w.dig >> (4 * j)) & 15u;
-            const uint32_t ij = ai * 8u + aj;
+            const uint32_t ij = ai * p.d + aj;
             const V J = in ? s_J[b] : (V)0;
             diag = fma(J, s_cf[128 + ij], diag);
             // a term exists where its factor is nonzero; the clamps of spin_rank keep

@@ -38,6 +38,15 @@ class BatchItem(ctypes.Structure):
                 ("m_eff_dev", ctypes.c_void_p)]
 
 
+class BatchPlan(ctypes.Structure):
+    """ftlm_batch_plan of include/ftlm.h."""
+    _fields_ = [("block", ctypes.c_int), ("streams", ctypes.c_int), ("tile_rows", ctypes.c_int),
+                ("stream_rows", ctypes.c_int)]
+
+    def as_tuple(self):
+        return (self.block, self.streams, self.tile_rows, self.stream_rows)
+
+
 class FtlmError(RuntimeError):
     def __init__(self, status, message):
         super().__init__(f"{_status_name(status)}: {message}")
@@ -86,6 +95,8 @@ def lib():
         "ftlm_lanczos_set_block": [I],
         "ftlm_batch_autotune": [I, P, I, I, I, P, ctypes.POINTER(I), ctypes.POINTER(I), P],
         "ftlm_batch_workspace_bytes": [P, PU64],
+        "ftlm_batch_create_plan": [I, P, I, I, I, P, P, ctypes.POINTER(P)],
+        "ftlm_batch_autotune_plan": [I, P, I, I, I, P, P, P, P, I, ctypes.POINTER(I)],
         "ftlm_batch_run": [P, P, U64, P],
         "ftlm_basis_destroy_async": [P, P],
         "ftlm_batch_destroy_async": [P, P],
@@ -95,6 +106,13 @@ def lib():
         "ftlm_ghosts": [I, I, P, P, P, P, P, D, D, P, P, P, P, P, P],
         "ftlm_sigma_emp": [I, I, P, P, P, P],
         "ftlm_profile_read": [PU64, PU64, PD, PU64, PD],
+        "ftlm_probe_read_bandwidth": [P, U64, I, P, PD],
+        "ftlm_flow_create": [I, I, I, I, I, P, U64, P, ctypes.POINTER(P)],
+        "ftlm_flow_unit_bytes": [P, I, I, PU64],
+        "ftlm_flow_add": [P, P, ctypes.POINTER(I)],
+        "ftlm_flow_step": [P, I, P],
+        "ftlm_flow_done": [P, P, I, ctypes.POINTER(I)],
+        "ftlm_flow_status": [P, ctypes.POINTER(I), ctypes.POINTER(I), PU64],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -104,6 +122,8 @@ def lib():
     L.ftlm_basis_destroy.restype = None
     L.ftlm_batch_destroy.argtypes = [P]
     L.ftlm_batch_destroy.restype = None
+    L.ftlm_flow_destroy.argtypes = [P]
+    L.ftlm_flow_destroy.restype = None
     L.ftlm_status_string.argtypes = [ctypes.c_int]
     L.ftlm_status_string.restype = ctypes.c_char_p
     L.ftlm_last_error.argtypes = []
@@ -375,6 +395,26 @@ def ftlm_batch_autotune(items, M, dist, dtype, stream=None):
     return b.value, s.value, times
 
 
+def ftlm_batch_create_plan(items, M, dist, dtype, plan, stream=None):
+    arr = (BatchItem * len(items))(*items)
+    out = ctypes.c_void_p()
+    _check(lib().ftlm_batch_create_plan(len(items), arr, int(M), int(dist), _dtype_code(dtype), ctypes.byref(plan),
+                                        _stream(stream), ctypes.byref(out)))
+    return out
+
+
+def ftlm_batch_autotune_plan(items, M, dist, dtype, stream=None):
+    """Returns (best plan, [(plan tuple, ms) of every timed candidate])."""
+    arr = (BatchItem * len(items))(*items)
+    best = BatchPlan()
+    tried = (BatchPlan * 32)()
+    ms = (ctypes.c_float * 32)()
+    n = ctypes.c_int()
+    _check(lib().ftlm_batch_autotune_plan(len(items), arr, int(M), int(dist), _dtype_code(dtype), _stream(stream),
+                                          ctypes.byref(best), tried, ms, 32, ctypes.byref(n)))
+    return best, [(tried[i].as_tuple(), ms[i]) for i in range(min(n.value, 32))]
+
+
 def ftlm_batch_workspace_bytes(handle):
     return _u64_query(lib().ftlm_batch_workspace_bytes, handle)
 
@@ -393,6 +433,15 @@ def ftlm_batch_destroy_async(handle, stream=None):
 
 def ftlm_launch_count():
     return _u64_query(lambda h, p: lib().ftlm_launch_count(p), None)
+
+
+def ftlm_probe_read_bandwidth(buf, reps, stream=None):
+    """GB/s of `reps` coalesced passes over the device tensor buf (L2-resident when it
+    fits in L2)."""
+    v = ctypes.c_double()
+    _check(lib().ftlm_probe_read_bandwidth(_ptr(buf), buf.numel() * buf.element_size(), int(reps), _stream(stream),
+                                           ctypes.byref(v)))
+    return v.value
 
 
 def ftlm_profile_enable(on=True):
@@ -503,6 +552,16 @@ def _batch_items(entries, M, dev):
     return results, items
 
 
+def autotune_plan(entries, M, dist=GAUSS, dtype=torch.float32, stream=None):
+    """ftlm_batch_autotune_plan on the (basis, R, seed, first_chain) entries (outputs
+    in scratch tensors); returns (best BatchPlan, timed candidates)."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    results, items = _batch_items(entries, M, dev)
+    out = ftlm_batch_autotune_plan(items, M, dist, dtype, stream)
+    del results
+    return out
+
+
 def autotune(entries, M, dist=GAUSS, dtype=torch.float32, stream=None):
     """ftlm_batch_autotune on the (basis, R, seed, first_chain) entries (outputs in
     scratch tensors); returns (block, streams, times)."""
@@ -518,11 +577,15 @@ class Batch:
     first_chain) entry; outputs per entry as device tensors theta, weight (R x M)
     and m_eff (R)."""
 
-    def __init__(self, entries, M, dist=GAUSS, dtype=torch.float32, block=0, streams=0, stream=None, lazy=False):
+    def __init__(self, entries, M, dist=GAUSS, dtype=torch.float32, block=0, streams=0, stream=None, lazy=False,
+                 plan=None):
         self.dev = torch.device("cuda", torch.cuda.current_device())
         self.M = int(M)
         self.results, items = _batch_items(entries, M, self.dev)
-        self.handle = ftlm_batch_create(items, M, dist, dtype, block, streams, stream)
+        if plan is not None:
+            self.handle = ftlm_batch_create_plan(items, M, dist, dtype, plan, stream)
+        else:
+            self.handle = ftlm_batch_create(items, M, dist, dtype, block, streams, stream)
         self.workspace_bytes = (ftlm_batch_workspace_bytes(self.handle) + 255) // 256 * 256
         self.work = None
         if not lazy:
@@ -560,6 +623,83 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Flow:
+    """Continuous Lanczos flow (ftlm_flow_*): sectors join and leave at Lanczos-step
+    boundaries.  The workspace is a torch tensor of work_bytes (default: 60 % of the
+    free device memory); add() returns a ticket, or None when the sector does not
+    fit now; done() returns (ticket, outputs) of finished sectors."""
+
+    def __init__(self, M, dist=GAUSS, dtype=torch.float32, block=8, max_units=512, work_bytes=None, stream=None):
+        self.dev = torch.device("cuda", torch.cuda.current_device())
+        self.M, self.block = int(M), int(block)
+        if work_bytes is None:
+            free, _ = torch.cuda.mem_get_info(self.dev)
+            work_bytes = int(0.6 * free)
+        self.work = torch.empty((int(work_bytes) + 255) // 256 * 256, dtype=torch.uint8, device=self.dev)
+        out = ctypes.c_void_p()
+        _check(lib().ftlm_flow_create(_dtype_code(dtype), self.block, self.M, int(dist), int(max_units),
+                                      _ptr(self.work), self.work.numel(), _stream(stream), ctypes.byref(out)))
+        self.handle = out
+        self.outputs = {}  # ticket -> (outputs dict, owner)
+
+    def add(self, basis, R, seed, first_chain=0, owner=None):
+        out = {"theta": torch.zeros((R, self.M), dtype=torch.float64, device=self.dev),
+               "weight": torch.zeros((R, self.M), dtype=torch.float64, device=self.dev),
+               "m_eff": torch.zeros(R, dtype=torch.int32, device=self.dev)}
+        item = BatchItem(basis.handle.value, int(R), int(first_chain), int(seed) & (2**64 - 1),
+                         out["theta"].data_ptr(), out["weight"].data_ptr(), out["m_eff"].data_ptr())
+        t = ctypes.c_int()
+        st = lib().ftlm_flow_add(self.handle, ctypes.byref(item), ctypes.byref(t))
+        if st == FTLM_ENOMEM:
+            return None
+        _check(st)
+        self.outputs[t.value] = (out, owner)
+        return t.value
+
+    def step(self, steps=1, stream=None):
+        _check(lib().ftlm_flow_step(self.handle, int(steps), _stream(stream)))
+
+    def done(self):
+        buf = (ctypes.c_int * 256)()
+        n = ctypes.c_int()
+        res = []
+        while True:
+            _check(lib().ftlm_flow_done(self.handle, buf, 256, ctypes.byref(n)))
+            for i in range(n.value):
+                out, owner = self.outputs.pop(buf[i])
+                res.append((buf[i], out, owner))
+            if n.value < 256:
+                return res
+
+    def status(self):
+        u, s_, f = ctypes.c_int(), ctypes.c_int(), ctypes.c_uint64()
+        _check(lib().ftlm_flow_status(self.handle, ctypes.byref(u), ctypes.byref(s_), ctypes.byref(f)))
+        return {"units": u.value, "sectors": s_.value, "free_bytes": f.value}
+
+    def close(self):
+        if self.handle is not None:
+            lib().ftlm_flow_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ftlm_flow_unit_bytes(handle, dtype, block):
+    v = ctypes.c_uint64()
+    _check(lib().ftlm_flow_unit_bytes(handle, _dtype_code(dtype), int(block), ctypes.byref(v)))
+    return v.value
 
 
 def computed_two_sz(N, two_s=1):

@@ -1,22 +1,22 @@
-"""Request loop for FTLM jobs: continuous batching over CUDA streams.
+"""Request loop for FTLM jobs: chain-level continuous batching.
 
 A job is one whole FTLM run of a cluster (sites N, bond list J_ij, Zeeman field h):
 every S^z >= 0 sector (mirrored), R chains of M Lanczos steps each, then E, C, chi
 and <S^z> on a temperature grid (Eq. 6-9; the field enters as -h S^z per sector).
-Jobs arrive at any time.  The engine keeps a fixed number of slots, each a CUDA
-stream; whenever a slot is free it takes the waiting jobs at the head of the queue
-(up to `max_group` of them, and no more chains than `max_group_rows` rows of
-vectors) and plans them as ONE ftlm_batch: the small sectors of all these jobs
-share one persistent launch, the large ones run on the batch's side streams.  The
-group is admitted to the device only when its exact footprint (sector tables +
-batch workspace + outputs) fits both the engine's memory budget and the free
-device memory; until then it waits with its slot.  Groups on different slots run
-concurrently, so jobs that arrive while others are on the GPU start as soon as a
-slot and memory free up, and their kernels overlap those already running.
+Jobs arrive at any time.  All chains on the device advance together through one
+continuous flow (ftlm_flow_*): per Lanczos step one multi-sector H.v launch per
+rank kind and one update launch cover every sector in flight, whatever its step.
+Between steps the loop admits the sectors of waiting jobs, in arrival order, as
+long as their device memory fits in the flow's workspace (so a job that arrives
+while others are at step 40 starts its step 1 in the next launch), and collects
+the sectors that finished; when every sector of a job is done, its thermodynamic
+sums are queued and its results read back to pinned host memory.
 
-Every kernel of a job has a launch shape fixed by the job's own sectors (grids by
-sector dimension, one CTA per small-sector unit, fixed-order reductions), so its
-results are bit-identical whether it runs alone or in a group, on any slot.
+Every unit of chains reduces its own tiles in a fixed order, so a job's results are
+bit-identical whether it runs alone or among other jobs, and whenever it was
+admitted.  The flow's device work is queued on one stream; sector tables are built
+on a side stream (creation waits only for that stream) and released in the flow
+stream's order once the job's sums are queued.
 
 Everything on the device goes through the C ABI of libftlm (ftlm.py); this module
 only schedules.  Host clocks (time.perf_counter) stamp arrival, start and finish.
@@ -41,7 +41,7 @@ class Job:
     h: float = 0.0
     seed: int = 1
     arrival: float = 0.0        # host time the request arrived (engine clock)
-    start: float = None         # host time its group was launched
+    start: float = None         # host time its first sector was admitted
     finish: float = None        # host time its results were on the host
     result: np.ndarray = None   # (4, nT): E, C, chi, mag
     updates: int = 0            # H.v matrix-element updates its chains applied
@@ -51,163 +51,174 @@ class Job:
         return None if self.finish is None else self.finish - self.arrival
 
 
-class _Group:
-    def __init__(self, jobs):
-        self.jobs = jobs
-        self.bases = []         # per job: list of Basis
-        self.batch = None
-        self.outs = []          # per job: (4, nT) device tensor
-        self.host = None        # pinned (n_jobs, 4, nT)
-        self.meff_host = None   # pinned (sectors, R): chain lengths
-        self.event = None
-        self.footprint = 0
+class AdmissionQueue:
+    """Sectors of waiting jobs in arrival order.  admit(try_add) offers the next
+    sector to try_add(job, index) and stops at the first refusal (so no job's
+    sector overtakes an earlier job's), or before a new job when max_jobs jobs are
+    in flight."""
+
+    def __init__(self, max_jobs=None):
+        self.jobs = collections.deque()  # [job, sector indices not yet admitted, sector count]
+        self.max_jobs = max_jobs
+        self.in_flight = 0               # jobs with an admitted sector, not finished
+
+    def push(self, job, n_sectors):
+        self.jobs.append([job, list(range(n_sectors)), n_sectors])
+
+    def admit(self, try_add):
+        """Returns the (job, sector) pairs admitted by this call."""
+        admitted = []
+        while self.jobs:
+            job, rest, total = self.jobs[0]
+            fresh = len(rest) == total
+            if fresh and self.max_jobs is not None and self.in_flight >= self.max_jobs:
+                break
+            while rest:
+                if not try_add(job, rest[0]):
+                    return admitted
+                if len(rest) == total:
+                    self.in_flight += 1
+                admitted.append((job, rest.pop(0)))
+            self.jobs.popleft()
+        return admitted
+
+    def finished(self):
+        self.in_flight -= 1
+
+    def __len__(self):
+        return len(self.jobs)
 
 
 class Engine:
     """Continuous-batching FTLM server on the current CUDA device.
 
-    slots           concurrent groups (CUDA streams)
     R, M            chains per sector and Lanczos steps
     dtype           vector storage (reductions are FP64)
-    block, streams  ftlm_batch block width and side streams (0: library defaults)
-    T               temperature grid (host array)
-    g               g-factor of chi
-    memory_budget   bytes the engine may hold on the device (default: 80 % of the
-                    free memory when the engine starts)
-    max_group       jobs planned into one batch at most
-    max_group_rows  sum over the group's sectors of D at most (keeps a group's
-                    latency bounded; the head job is always taken)
+    block           chains per unit of the flow
+    T               temperature grid (host array); g the g-factor of chi
+    memory_budget   bytes of the flow's workspace (default: 60 % of the free device
+                    memory when the engine starts); sector tables come on top
+    max_units       units of chains the flow holds at once
+    max_jobs        jobs in flight at once (None: as many as fit; 1: one at a time)
+    steps_per_poll  Lanczos steps queued between two admission/collection passes
+    depth           step passes queued ahead of the device at most
     """
 
-    def __init__(self, slots=4, R=8, M=80, dtype=torch.float32, block=8, streams=2, T=None, g=2.0,
-                 dist=ftlm.GAUSS, memory_budget=None, max_group=8, max_group_rows=1 << 22):
+    def __init__(self, R=8, M=80, dtype=torch.float32, block=8, T=None, g=2.0, dist=ftlm.GAUSS,
+                 memory_budget=None, max_units=512, max_jobs=None, steps_per_poll=2, depth=3):
         self.dev = torch.device("cuda", torch.cuda.current_device())
-        self.R, self.M, self.dtype, self.block, self.streams = R, M, dtype, block, streams
+        self.R, self.M, self.dtype, self.block = R, M, dtype, block
         self.g, self.dist = g, dist
         T = np.asarray(T if T is not None else np.logspace(-2, 1, 200), dtype=np.float64)
         self.nT = len(T)
         self.T = torch.as_tensor(T, device=self.dev)
-        free, _ = torch.cuda.mem_get_info(self.dev)
-        self.budget = int(memory_budget if memory_budget is not None else 0.8 * free)
-        self.in_use = 0
-        self.max_group, self.max_group_rows = max_group, max_group_rows
-        self.slots = [torch.cuda.Stream(self.dev) for _ in range(slots)]
-        self.busy = [None] * slots       # _Group running on the slot
-        self.parked = [None] * slots     # _Group planned on the slot, waiting for memory
-        self.waiting = collections.deque()
+        if memory_budget is None:
+            free, _ = torch.cuda.mem_get_info(self.dev)
+            memory_budget = int(0.6 * free)
+        self.stream = torch.cuda.Stream(self.dev)
+        self.side = torch.cuda.Stream(self.dev)  # sector tables
+        self.flow = ftlm.Flow(M, dist, dtype, block, max_units, memory_budget, stream=self.stream)
+        self.queue = AdmissionQueue(max_jobs)
+        self.steps_per_poll, self.depth = steps_per_poll, depth
+        self.running = {}     # id(job) -> state dict (jobs need not have distinct job_id)
+        self.closing = []     # (job, event, host tensor)
         self.finished = []
-        self.stats = {"groups": 0, "max_group": 0, "max_busy": 0, "parked_polls": 0}
+        self.inflight = collections.deque()
+        self.stats = {"steps": 0, "max_jobs_in_flight": 0, "max_units": 0, "refusals": 0}
         self.t0 = time.perf_counter()
 
     def now(self):
         return time.perf_counter() - self.t0
 
-    # ------------------------------------------------------------------ queue
     def submit(self, job):
-        if job.arrival is None:
-            job.arrival = self.now()
-        self.waiting.append(job)
+        job._two_sz = ftlm.computed_two_sz(job.N)
+        job._n_sectors = len(job._two_sz)
+        self.queue.push(job, job._n_sectors)
 
     def idle(self):
-        return not self.waiting and all(g is None for g in self.busy) and all(g is None for g in self.parked)
+        return not len(self.queue) and not self.running and not self.closing
 
-    # --------------------------------------------------------------- planning
-    def _take_group(self):
-        grp = _Group(take_group(self.waiting, self.max_group, self.max_group_rows))
-        self.stats["groups"] += 1
-        self.stats["max_group"] = max(self.stats["max_group"], len(grp.jobs))
-        return grp
-
-    def _plan(self, grp, stream):
-        entries = []
-        with torch.cuda.stream(stream):
-            for job in grp.jobs:
-                bs = [ftlm.Basis(job.N, tz, job.bonds, stream=stream) for tz in ftlm.computed_two_sz(job.N)]
-                grp.bases.append(bs)
-                entries += [(b, self.R, job.seed, 0) for b in bs]
-            grp.batch = ftlm.Batch(entries, self.M, self.dist, self.dtype, self.block, self.streams,
-                                   stream=stream, lazy=True)
-        tables = sum(b.table_bytes for bs in grp.bases for b in bs)
-        outs = len(entries) * self.R * (2 * self.M * 8 + 4) + len(grp.jobs) * 4 * self.nT * 8
-        grp.footprint = tables + grp.batch.workspace_bytes + outs
-
-    def _fits(self, grp):
-        if self.in_use + grp.footprint > self.budget and self.in_use > 0:
+    # ----------------------------------------------------------------- admission
+    def _try_add(self, job, k):
+        st = self.running.get(id(job))
+        if st is None:
+            st = {"job": job, "bases": [None] * job._n_sectors, "outs": [None] * job._n_sectors, "left": 0}
+            self.running[id(job)] = st
+        if st["bases"][k] is None:
+            with torch.cuda.stream(self.side):
+                st["bases"][k] = ftlm.Basis(job.N, job._two_sz[k], job.bonds, stream=self.side)
+        t = self.flow.add(st["bases"][k], self.R, job.seed, 0, owner=(id(job), k))
+        if t is None:
+            self.stats["refusals"] += 1
+            if self.flow.status()["units"] == 0:
+                raise RuntimeError(f"job {job.job_id}: a sector of N = {job.N} does not fit in an empty flow")
             return False
-        free, _ = torch.cuda.mem_get_info(self.dev)
-        return grp.footprint <= free or self.in_use == 0
+        if job.start is None:
+            job.start = self.now()
+        st["left"] += 1
+        return True
 
-    def _launch(self, grp, stream):
-        now = self.now()
-        with torch.cuda.stream(stream):
-            results = grp.batch.run(stream)
-            k = 0
-            for job, bs in zip(grp.jobs, grp.bases):
-                res = results[k:k + len(bs)]
-                k += len(bs)
-                out = torch.empty((4, self.nT), dtype=torch.float64, device=self.dev)
-                ftlm.ftlm_thermo([b.two_sz for b in bs], [b.dim for b in bs], self.R, self.M,
-                                 [r["theta"] for r in res], [r["weight"] for r in res], [r["m_eff"] for r in res],
-                                 True, self.g, job.h, self.T, out[0], out[1], out[2], out[3], stream=stream)
-                grp.outs.append(out)
-                job.start = now
-            grp.host = torch.empty((len(grp.jobs), 4, self.nT), dtype=torch.float64).pin_memory()
-            for i, out in enumerate(grp.outs):
-                grp.host[i].copy_(out, non_blocking=True)
-            grp.meff_host = torch.empty((len(results), self.R), dtype=torch.int32).pin_memory()
-            for i, r in enumerate(results):
-                grp.meff_host[i].copy_(r["m_eff"], non_blocking=True)
-            grp.event = torch.cuda.Event()
-            grp.event.record(stream)
-        self.in_use += grp.footprint
+    # ------------------------------------------------------------------- collect
+    def _collect(self):
+        for ticket, out, (key, k) in self.flow.done():
+            st = self.running[key]
+            st["outs"][k] = out
+            st["left"] -= 1
+            if st["left"] == 0 and all(o is not None for o in st["outs"]):
+                self._close(st)
 
-    def _retire(self, slot):
-        grp = self.busy[slot]
-        now = self.now()
-        meff = grp.meff_host.numpy()
-        k = 0
-        for i, (job, bs) in enumerate(zip(grp.jobs, grp.bases)):
-            job.result = grp.host[i].numpy().copy()
-            job.finish = now
-            job.updates = int(sum(int(meff[k + j].sum()) * b.updates for j, b in enumerate(bs)))
-            k += len(bs)
-            self.finished.append(job)
-        # the group's work is complete: release in the slot's stream order, no wait
-        stream = self.slots[slot]
-        grp.batch.release(stream)
-        for bs in grp.bases:
-            for b in bs:
-                b.release(stream)
-        self.in_use -= grp.footprint
-        self.busy[slot] = None
+    def _close(self, st):
+        job = st["job"]
+        bs, outs = st["bases"], st["outs"]
+        with torch.cuda.stream(self.stream):
+            res = torch.empty((4, self.nT), dtype=torch.float64, device=self.dev)
+            ftlm.ftlm_thermo([b.two_sz for b in bs], [b.dim for b in bs], self.R, self.M,
+                             [o["theta"] for o in outs], [o["weight"] for o in outs], [o["m_eff"] for o in outs],
+                             True, self.g, job.h, self.T, res[0], res[1], res[2], res[3], stream=self.stream)
+            host = torch.empty((4, self.nT), dtype=torch.float64).pin_memory()
+            host.copy_(res, non_blocking=True)
+            meff = torch.stack([o["m_eff"] for o in outs]).to("cpu", non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(self.stream)
+        for b in bs:
+            b.release(self.stream)
+        self.closing.append((job, ev, host, meff, [b.updates for b in bs], res, outs))
+        del self.running[id(job)]
+        self.queue.finished()
 
-    # ------------------------------------------------------------------- loop
+    def _retire(self):
+        keep = []
+        for entry in self.closing:
+            job, ev, host, meff, upd, _, _ = entry
+            if ev.query():
+                job.result = host.numpy().copy()
+                job.finish = self.now()
+                m = meff.numpy()
+                job.updates = int(sum(int(m[k].sum()) * upd[k] for k in range(len(upd))))
+                self.finished.append(job)
+            else:
+                keep.append(entry)
+        self.closing = keep
+
+    # ---------------------------------------------------------------------- loop
     def poll(self):
-        """Retire finished groups, then plan and admit waiting work.  Returns True if
-        anything changed."""
-        changed = False
-        for s in range(len(self.slots)):
-            if self.busy[s] is not None and self.busy[s].event.query():
-                self._retire(s)
-                changed = True
-        for s in range(len(self.slots)):
-            if self.busy[s] is not None:
-                continue
-            if self.parked[s] is None and self.waiting:
-                grp = self._take_group()
-                self._plan(grp, self.slots[s])
-                self.parked[s] = grp
-                changed = True
-            grp = self.parked[s]
-            if grp is not None:
-                if self._fits(grp):
-                    self._launch(grp, self.slots[s])
-                    self.busy[s], self.parked[s] = grp, None
-                    changed = True
-                else:
-                    self.stats["parked_polls"] += 1
-        self.stats["max_busy"] = max(self.stats["max_busy"], sum(g is not None for g in self.busy))
-        return changed
+        """Admit, queue steps, collect.  Returns True if the device has work."""
+        self.queue.admit(self._try_add)
+        self.stats["max_jobs_in_flight"] = max(self.stats["max_jobs_in_flight"], len(self.running))
+        st = self.flow.status()
+        self.stats["max_units"] = max(self.stats["max_units"], st["units"])
+        busy = st["units"] > 0
+        if busy:
+            self.flow.step(self.steps_per_poll, self.stream)
+            self.stats["steps"] += self.steps_per_poll
+            ev = torch.cuda.Event()
+            ev.record(self.stream)
+            self.inflight.append(ev)
+            while len(self.inflight) > self.depth:
+                self.inflight.popleft().synchronize()
+        self._collect()
+        self._retire()
+        return busy
 
     def run(self, jobs, arrivals=None, sleep=2e-4):
         """Serve `jobs`; arrivals[i] = seconds after the start at which job i is
@@ -225,28 +236,19 @@ class Engine:
                 self.submit(job)
                 nxt += 1
             if not self.poll():
-                time.sleep(sleep)
+                if self.closing:
+                    self.closing[0][1].synchronize()
+                else:
+                    time.sleep(sleep)
         return self.finished
+
+    def close(self):
+        self.flow.close()
 
 
 def sector_rows(N):
     """Sum of the dimensions of the S^z >= 0 sectors of N spins 1/2."""
     return sum(math.comb(N, (N + tz) // 2) for tz in ftlm.computed_two_sz(N))
-
-
-def take_group(waiting, max_group, max_rows):
-    """Pop the next group off the FIFO `waiting` (a deque of jobs with .N): the head
-    job always, then following jobs while the group has fewer than max_group jobs
-    and its summed sector rows stay within max_rows.  Order is kept."""
-    jobs = [waiting.popleft()]
-    rows = sector_rows(jobs[0].N)
-    while waiting and len(jobs) < max_group:
-        r = sector_rows(waiting[0].N)
-        if rows + r > max_rows:
-            break
-        jobs.append(waiting.popleft())
-        rows += r
-    return jobs
 
 
 def poisson_jobs(n, rate, seed=4, sizes=(16, 18, 20, 22, 24, 26)):

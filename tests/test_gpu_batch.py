@@ -280,3 +280,30 @@ def test_autotune_picks_a_timed_candidate(cuda_dev, side_items):
                                        spectral_sums(y["theta"], y["weight"], y["m_eff"]), rtol=1e-5)
     for b in bases:
         b.close()
+
+
+def test_plan_autotune_tunes_tiles_and_plans_agree(cuda_dev):
+    """ftlm_batch_autotune_plan times block widths, then H.v and streaming tile rows
+    of the multi-sector path; every plan gives the same chains up to the summation
+    order of the per-tile sums, and the fastest candidate is the one returned."""
+    M, R = 15, 8
+    bases = _mid_sector_bases()
+    entries = [(b, R, 1, 0) for b in bases]
+    best, tried = ftlm.autotune_plan(entries, M, ftlm.GAUSS, torch.float32)
+    assert len(tried) == 3 + 2 + 2  # blocks, then tile rows, then streaming tile rows
+    assert {t[2] for t, _ in tried} >= {1024, 2048, 4096} and {t[3] for t, _ in tried} >= {8192, 16384, 32768}
+    assert best.as_tuple() == min(tried, key=lambda kv: kv[1])[0]
+    with ftlm.Batch(entries, M, ftlm.GAUSS, torch.float32, plan=best) as tuned:
+        a = [{k: v.clone() for k, v in r.items()} for r in tuned.run()]
+    odd = ftlm.BatchPlan(4, 1, 512, 1024)  # small tiles: many partial sums per unit
+    with ftlm.Batch(entries, M, ftlm.GAUSS, torch.float32, plan=odd) as other:
+        e = other.run()
+        torch.cuda.synchronize()
+        for x, y in zip(a, e):
+            assert torch.equal(x["m_eff"], y["m_eff"])
+            np.testing.assert_allclose(spectral_sums(x["theta"], x["weight"], x["m_eff"]),
+                                       spectral_sums(y["theta"], y["weight"], y["m_eff"]), rtol=1e-5)
+    with pytest.raises(ftlm.FtlmError):
+        ftlm.Batch(entries, M, ftlm.GAUSS, torch.float32, plan=ftlm.BatchPlan(8, 1, 1000, 0))
+    for b in bases:
+        b.close()

@@ -1,0 +1,103 @@
+"""The continuous Lanczos flow (ftlm_flow_*): sectors that join at different
+Lanczos steps share launches, and each sector's results are bit-identical to the
+same sector alone, to the batch's multi-sector path, and (FP64) match the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as o
+from paper_2605_26261_gb300 import ftlm, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(flow, steps_before, bases, R, seeds):
+    """Add bases[i] after steps_before[i] flow steps; step until every sector is done."""
+    pending = sorted(range(len(bases)), key=lambda i: steps_before[i])
+    tickets, outs, step = {}, {}, 0
+    while pending or len(outs) < len(bases):
+        while pending and steps_before[pending[0]] <= step:
+            i = pending.pop(0)
+            t = flow.add(bases[i], R, seeds[i], 0, owner=i)
+            assert t is not None
+            tickets[t] = i
+        flow.step(1)
+        step += 1
+        for t, out, i in flow.done():
+            outs[i] = out
+        assert step < 2000
+    torch.cuda.synchronize()
+    return [outs[i] for i in range(len(bases))]
+
+
+def _mid_bases():
+    b18, b19 = inputs.ring(18), inputs.random_graph(19, seed=31)
+    return [ftlm.Basis(18, 0, b18), ftlm.Basis(18, 2, b18), ftlm.Basis(19, 1, b19), ftlm.Basis(19, 11, b19),
+            ftlm.Basis(12, 0, inputs.random_graph(12, seed=2)), ftlm.Basis(8, 0, inputs.ring(8), two_s=2)]
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_flow_results_do_not_depend_on_the_mix_or_the_start_step(cuda_dev, dtype):
+    M, R = 30, 8
+    bases = _mid_bases()
+    seeds = [11 + i for i in range(len(bases))]
+    with ftlm.Flow(M, ftlm.GAUSS, dtype, 8, 64, 1 << 30) as flow:
+        mix = _run(flow, [0, 0, 7, 13, 3, 20], bases, R, seeds)
+    for i, b in enumerate(bases):
+        with ftlm.Flow(M, ftlm.GAUSS, dtype, 8, 8, 1 << 28) as flow:
+            alone = _run(flow, [0], [b], R, [seeds[i]])[0]
+        for k in ("theta", "weight", "m_eff"):
+            assert torch.equal(mix[i][k], alone[k]), (i, k)
+    for b in bases:
+        b.close()
+
+
+def test_flow_equals_batch_multi_sector_path(cuda_dev):
+    # sectors above 32768 rows run on the batch's multi-sector path: same units,
+    # tiles and reductions
+    M, R = 25, 8
+    bases = _mid_bases()[:3]
+    with ftlm.Batch([(b, R, 5, 0) for b in bases], M, ftlm.RADEMACHER, torch.float32, 8) as batch:
+        ref = [{k: v.clone() for k, v in r.items()} for r in batch.run()]
+    with ftlm.Flow(M, ftlm.RADEMACHER, torch.float32, 8, 16, 1 << 30) as flow:
+        got = _run(flow, [0, 4, 9], bases, R, [5, 5, 5])
+    for a, b in zip(got, ref):
+        for k in ("theta", "weight", "m_eff"):
+            assert torch.equal(a[k], b[k]), k
+    for b in bases:
+        b.close()
+
+
+def test_flow_fp64_matches_oracle(cuda_dev):
+    N, M, R, seed = 12, 30, 5, 7
+    T = inputs.log_t_grid(50, 0.05, 10.0)
+    bonds = inputs.random_graph(N, seed=22)
+    bases = [ftlm.Basis(N, tz, bonds) for tz in ftlm.computed_two_sz(N)]
+    with ftlm.Flow(M, ftlm.GAUSS, torch.float64, 4, 64, 1 << 28) as flow:
+        res = _run(flow, list(range(len(bases))), bases, R, [seed] * len(bases))
+        obs = ftlm.thermo([(b.two_sz, b.dim, r) for b, r in zip(bases, res)], torch.as_tensor(T, device=cuda_dev),
+                          R, M)
+    ref = o.thermo(o.run_ftlm(N, bonds, R, M, seed=seed), T)
+    for k in ("E", "C", "chi"):
+        want = ref[k]
+        np.testing.assert_allclose(obs[k].cpu().numpy(), want, rtol=1e-9, atol=1e-12 * np.max(np.abs(want)))
+    for b in bases:
+        b.close()
+
+
+def test_flow_refuses_what_does_not_fit(cuda_dev):
+    with ftlm.Basis(18, 0, inputs.ring(18)) as big, ftlm.Basis(10, 0, inputs.ring(10)) as small:
+        need = ftlm.ftlm_flow_unit_bytes(big.handle, torch.float32, 8)
+        with ftlm.Flow(10, ftlm.GAUSS, torch.float32, 8, 4, need + (1 << 20)) as flow:
+            assert flow.add(big, 8, 1) is not None
+            assert flow.add(big, 8, 2) is None          # no room for a second one
+            assert flow.status()["units"] == 1
+            flow.step(12)
+            done = flow.done()
+            assert len(done) == 1
+            assert flow.add(big, 8, 2) is not None      # its region was freed
+            assert flow.add(small, 4, 3) is not None
+            assert flow.status()["units"] == 2
+            flow.step(12)
+            assert len(flow.done()) == 2
+            torch.cuda.synchronize()

@@ -119,8 +119,9 @@ def test_served_fp32_job_matches_oracle(cuda_dev):
     job = serve.Job(job_id=0, N=18, bonds=bonds, h=0.6, seed=77)
     reqs, _ = inputs.serving_requests(5, 400.0, seed=3, sizes=(8, 10, 12, 14))
     filler = [serve.Job(job_id=1 + i, N=r["N"], bonds=r["bonds"], h=r["h"], seed=600 + i) for i, r in enumerate(reqs)]
-    eng = serve.Engine(slots=2, R=4, M=30, dtype=torch.float32, block=4, streams=2, T=T, max_group=4)
+    eng = serve.Engine(R=4, M=30, dtype=torch.float32, block=4, T=T, memory_budget=1 << 30)
     done = eng.run([job] + filler)
+    eng.close()
     got = next(j for j in done if j.job_id == 0).result
     ref = o.thermo(o.run_ftlm(18, bonds, 4, 30, seed=77, dist=o.GAUSS, u=o.U32), T, g=2.0, h=0.6)
     for row, k in enumerate(("E", "C", "chi", "mag")):

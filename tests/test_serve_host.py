@@ -1,5 +1,4 @@
-"""Host logic of the request loop (no GPU): grouping policy and the request stream."""
-import collections
+"""Host logic of the request loop (no GPU): admission order and the request stream."""
 import math
 
 import numpy as np
@@ -19,15 +18,37 @@ def test_sector_rows():
     assert serve.sector_rows(16) == (2**16 + math.comb(16, 8)) // 2
 
 
-def test_take_group_is_fifo_and_bounded():
-    q = collections.deque(_J(i, N) for i, N in enumerate([16, 16, 18, 26, 16, 16]))
-    g = serve.take_group(q, max_group=8, max_rows=serve.sector_rows(16) * 2 + serve.sector_rows(18))
-    assert [j.job_id for j in g] == [0, 1, 2]           # N = 26 does not fit behind them
-    g = serve.take_group(q, max_group=8, max_rows=10)    # the head job is always taken
-    assert [j.job_id for j in g] == [3]
-    g = serve.take_group(q, max_group=1, max_rows=1 << 40)
-    assert [j.job_id for j in g] == [4]
-    assert [j.job_id for j in q] == [5]
+def test_admission_is_fifo_by_sector_and_resumes():
+    q = serve.AdmissionQueue()
+    for i, n in enumerate([3, 2, 4]):
+        q.push(_J(i, 2 * n), n)
+    room = [4]
+
+    def try_add(job, k):  # a capacity of `room` sectors
+        if room[0] == 0:
+            return False
+        room[0] -= 1
+        return True
+
+    got = q.admit(try_add)
+    assert [(j.job_id, k) for j, k in got] == [(0, 0), (0, 1), (0, 2), (1, 0)]
+    assert q.in_flight == 2 and len(q) == 2       # job 1 waits for its second sector
+    room[0] = 10
+    got = q.admit(try_add)
+    assert [(j.job_id, k) for j, k in got] == [(1, 1), (2, 0), (2, 1), (2, 2), (2, 3)]
+    assert q.in_flight == 3 and len(q) == 0
+
+
+def test_admission_limits_jobs_in_flight():
+    q = serve.AdmissionQueue(max_jobs=1)
+    for i in range(3):
+        q.push(_J(i, 4), 2)
+    got = q.admit(lambda j, k: True)
+    assert [(j.job_id, k) for j, k in got] == [(0, 0), (0, 1)]   # one job at a time
+    assert q.admit(lambda j, k: True) == []
+    q.finished()
+    got = q.admit(lambda j, k: True)
+    assert [(j.job_id, k) for j, k in got] == [(1, 0), (1, 1)]
 
 
 def test_serving_requests_recipe():
