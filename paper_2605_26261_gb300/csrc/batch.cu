@@ -37,12 +37,6 @@
 
 namespace ftlm {
 
-namespace {
-
-constexpr int kBatchThreads = 256;
-constexpr uint64_t kSmallRows = 1u << 15;  // sectors up to this dimension run inside one CTA
-constexpr int kMaxSideStreams = 8;
-
 // Vector bytes of one wave of the multi-sector path: FTLM_MS_WAVE_MB or 256 MB.
 // Small waves keep a wave's vectors near the L2 size (measured on GB300 with 256
 // clusters of 18-22 sites: 256 MB waves 9.6 s per run, 2 GB 11.0 s, 8 GB 11.9 s);
@@ -56,6 +50,13 @@ uint64_t ms_wave_bytes()
     }();
     return v;
 }
+
+namespace {
+
+constexpr int kBatchThreads = 256;
+constexpr uint64_t kSmallRows = 1u << 15;  // sectors up to this dimension run inside one CTA
+constexpr int kMaxSideStreams = 8;
+
 
 // Default number of side streams for the large items: FTLM_BATCH_STREAMS (1..8)
 // or 4.

@@ -78,7 +78,8 @@ struct FlowUnit {
     int kind;
     int item;
     uint64_t off, bytes;
-    bool started;
+    uint64_t vbytes;  // its two vector blocks (the wave budget counts these)
+    int done;         // Lanczos steps completed
 };
 
 struct FlowItem {
@@ -131,7 +132,7 @@ struct ftlm_flow {
     uint32_t *d_tile[3], *d_stile, *d_fin;
     uint64_t cap_tiles, cap_stiles;
     // pinned staging for the uploads (a ring of buffers, each reused once its copies ran)
-    static constexpr int kStages = 4;
+    static constexpr int kStages = 8;
     char *stage[kStages];
     cudaEvent_t stage_ev[kStages];
     uint64_t stage_bytes;
@@ -140,8 +141,7 @@ struct ftlm_flow {
     std::vector<ftlm::FlowItem> items;
     std::vector<int> done;  // tickets whose outputs are queued
     int next_ticket;
-    int launches;  // step launches queued so far (j of the next H.v launch is launches + 1)
-    bool dirty;
+    uint64_t wave_bytes;  // vector bytes per wave
     uint32_t kind_first[3], kind_count[3], n_tiles[3], n_stiles;
 };
 
@@ -158,31 +158,30 @@ ftlm_status stage_next(ftlm_flow *f, char **buf)
     return FTLM_OK;
 }
 
-// Descriptors and tile maps of the current units, ordered by rank kind.
-ftlm_status upload(ftlm_flow *f, cudaStream_t stream)
+// Descriptors and tile maps of the units of one wave (indices into f->units),
+// ordered by rank kind; a unit's launches run as step j - j0 with j0 = -done, so
+// launch j = 1, 2, ... of the wave is the unit's step done + j.  order receives
+// the wave's units in descriptor order.
+ftlm_status upload(ftlm_flow *f, const std::vector<uint32_t> &wave, std::vector<uint32_t> &order, cudaStream_t stream)
 {
     std::vector<MsUnit> du;
     std::vector<uint32_t> tiles[3], stiles;
-    std::vector<FlowUnit> ordered;
+    order.clear();
     for (int kind = 0; kind < 3; ++kind) {
-        f->kind_first[kind] = (uint32_t)ordered.size();
-        for (const FlowUnit &u : f->units)
-            if (u.kind == kind) ordered.push_back(u);
-        f->kind_count[kind] = (uint32_t)ordered.size() - f->kind_first[kind];
+        f->kind_first[kind] = (uint32_t)order.size();
+        for (uint32_t i : wave)
+            if (f->units[i].kind == kind) order.push_back(i);
+        f->kind_count[kind] = (uint32_t)order.size() - f->kind_first[kind];
     }
-    f->units = ordered;
-    for (int kind = 0; kind < 3; ++kind) {
-        for (uint32_t i = 0; i < f->kind_count[kind]; ++i) {
-            FlowUnit &fu = f->units[f->kind_first[kind] + i];
-            fu.u.tile0 = (uint32_t)tiles[kind].size();
-            for (uint32_t k = 0; k < fu.u.n_tiles; ++k) tiles[kind].push_back(i);  // kind-local index
-        }
-    }
-    for (uint32_t i = 0; i < f->units.size(); ++i) {
-        FlowUnit &fu = f->units[i];
-        fu.u.stile0 = (uint32_t)stiles.size();
-        for (uint32_t k = 0; k < fu.u.n_stiles; ++k) stiles.push_back(i);  // flow-wide index
-        du.push_back(fu.u);
+    for (uint32_t pos = 0; pos < order.size(); ++pos) {
+        MsUnit u = f->units[order[pos]].u;
+        const int kind = f->units[order[pos]].kind;
+        u.j0 = -f->units[order[pos]].done;
+        u.tile0 = (uint32_t)tiles[kind].size();
+        for (uint32_t k = 0; k < u.n_tiles; ++k) tiles[kind].push_back(pos - f->kind_first[kind]);  // kind-local
+        u.stile0 = (uint32_t)stiles.size();
+        for (uint32_t k = 0; k < u.n_stiles; ++k) stiles.push_back(pos);  // wave-wide index
+        du.push_back(u);
     }
     for (int kind = 0; kind < 3; ++kind)
         if (tiles[kind].size() > f->cap_tiles) return fail(FTLM_ENOMEM, "flow tile map full");
@@ -206,68 +205,64 @@ ftlm_status upload(ftlm_flow *f, cudaStream_t stream)
     f->n_stiles = (uint32_t)stiles.size();
     FTLM_CUDA(put(f->d_stile, stiles.data(), stiles.size() * sizeof(uint32_t)));
     FTLM_CUDA(cudaEventRecord(f->stage_ev[f->stage_cur], stream));
-    f->dirty = false;
     return FTLM_OK;
 }
 
-ftlm_status one_step(ftlm_flow *f, cudaStream_t stream)
+// `steps` Lanczos steps of one wave: start vectors of its new units, then per step
+// one H.v launch per rank kind and one update launch; afterwards the chain lengths
+// of the units that reached their last step and the Ritz step of every sector whose
+// units are all done.  Returns in fin the indices (into f->units) of finished units.
+ftlm_status run_wave(ftlm_flow *f, const std::vector<uint32_t> &wave, int steps, cudaStream_t stream,
+                     std::vector<uint32_t> &fin)
 {
-    // admit: units added since the last step start with the next launch
-    const int jstart = f->launches;
-    bool fresh = false;
-    for (FlowUnit &u : f->units)
-        if (!u.started) {
-            u.started = true;
-            u.u.j0 = jstart;
-            fresh = true;
-            f->dirty = true;
-        }
-    if (f->units.empty()) return FTLM_OK;
-    if (f->dirty) {
-        ftlm_status s = upload(f, stream);
-        if (s != FTLM_OK) return s;
-    }
-    if (fresh) {
-        ftlm_status s = ms_flow_start(f->dtype, f->B, f->d_units, (uint32_t)f->units.size(), f->d_stile, f->n_stiles,
-                                      jstart, f->dist, f->units_base, f->num_sms, stream);
-        if (s != FTLM_OK) return s;
-    }
-    const int j = ++f->launches;
-    for (int kind = 0; kind < 3; ++kind) {
-        if (!f->kind_count[kind]) continue;
-        ftlm_status s = ms_flow_hv(f->dtype, f->B, kind, f->d_units + f->kind_first[kind], f->d_tile[kind],
-                                   f->n_tiles[kind], j, f->M, f->alpha, f->units_base, f->num_sms, stream);
-        if (s != FTLM_OK) return s;
-    }
-    ftlm_status s = ms_flow_update(f->dtype, f->B, f->d_units, f->d_stile, f->n_stiles, j, f->M, f->beta,
-                                   f->units_base, f->num_sms, stream);
+    std::vector<uint32_t> order;
+    ftlm_status s = upload(f, wave, order, stream);
     if (s != FTLM_OK) return s;
-    // units at their last step: chain lengths out; sectors with every unit done: Ritz
-    std::vector<uint32_t> fin;
-    for (uint32_t i = 0; i < f->units.size(); ++i)
-        if (j - f->units[i].u.j0 >= f->units[i].u.m_max) fin.push_back(i);
-    if (fin.empty()) return FTLM_OK;
+    bool fresh = false;
+    for (uint32_t i : wave) fresh |= f->units[i].done == 0;
+    if (fresh) {  // units with j0 == 0: reset and start vectors
+        s = ms_flow_start(f->dtype, f->B, f->d_units, (uint32_t)order.size(), f->d_stile, f->n_stiles, 0, f->dist,
+                          f->units_base, f->num_sms, stream);
+        if (s != FTLM_OK) return s;
+    }
+    int need = 0;  // steps any unit of the wave still has
+    for (uint32_t i : wave) need = std::max(need, f->units[i].u.m_max - f->units[i].done);
+    const int n = std::min(steps, need);
+    for (int j = 1; j <= n; ++j) {
+        for (int kind = 0; kind < 3; ++kind) {
+            if (!f->kind_count[kind]) continue;
+            s = ms_flow_hv(f->dtype, f->B, kind, f->d_units + f->kind_first[kind], f->d_tile[kind], f->n_tiles[kind], j,
+                           f->M, f->alpha, f->units_base, f->num_sms, stream);
+            if (s != FTLM_OK) return s;
+        }
+        s = ms_flow_update(f->dtype, f->B, f->d_units, f->d_stile, f->n_stiles, j, f->M, f->beta, f->units_base,
+                           f->num_sms, stream);
+        if (s != FTLM_OK) return s;
+    }
+    std::vector<uint32_t> fin_pos;  // positions in the wave's descriptor array
+    for (uint32_t pos = 0; pos < order.size(); ++pos) {
+        FlowUnit &u = f->units[order[pos]];
+        u.done = std::min(u.u.m_max, u.done + n);
+        if (u.done >= u.u.m_max) {
+            fin_pos.push_back(pos);
+            fin.push_back(order[pos]);
+        }
+    }
+    if (fin_pos.empty()) return FTLM_OK;
     {
         char *buf = nullptr;
         s = stage_next(f, &buf);
         if (s != FTLM_OK) return s;
-        std::memcpy(buf, fin.data(), fin.size() * sizeof(uint32_t));
-        FTLM_CUDA(cudaMemcpyAsync(f->d_fin, buf, fin.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, stream));
+        std::memcpy(buf, fin_pos.data(), fin_pos.size() * sizeof(uint32_t));
+        FTLM_CUDA(cudaMemcpyAsync(f->d_fin, buf, fin_pos.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, stream));
         FTLM_CUDA(cudaEventRecord(f->stage_ev[f->stage_cur], stream));
     }
-    flow_meff_kernel<<<(unsigned)((fin.size() * f->B + 255) / 256), 256, 0, stream>>>(
-        f->d_units, f->d_fin, (uint32_t)fin.size(), f->B, f->meff, f->units_base);
+    flow_meff_kernel<<<(unsigned)((fin_pos.size() * f->B + 255) / 256), 256, 0, stream>>>(
+        f->d_units, f->d_fin, (uint32_t)fin_pos.size(), f->B, f->meff, f->units_base);
     note_launch();
     FTLM_CUDA(cudaGetLastError());
-    std::vector<FlowUnit> keep;
-    std::vector<bool> is_fin(f->units.size(), false);
-    for (uint32_t i : fin) is_fin[i] = true;
-    for (uint32_t i = 0; i < f->units.size(); ++i) {
-        FlowUnit &u = f->units[i];
-        if (!is_fin[i]) {
-            keep.push_back(u);
-            continue;
-        }
+    for (uint32_t i : fin_pos) {
+        FlowUnit &u = f->units[order[i]];
         f->region.give(u.off, u.bytes);
         FlowItem &it = f->items[u.item];
         if (--it.units_left == 0) {
@@ -283,8 +278,6 @@ ftlm_status one_step(ftlm_flow *f, cudaStream_t stream)
             it.live = false;
         }
     }
-    f->units = keep;
-    f->dirty = true;
     return FTLM_OK;
 }
 
@@ -334,8 +327,7 @@ extern "C" ftlm_status ftlm_flow_create(ftlm_dtype dtype, int block, int M, ftlm
     f->region.init(f->units_bytes);
     f->chains.init(f->max_chains);
     f->next_ticket = 1;
-    f->launches = 0;
-    f->dirty = true;
+    f->wave_bytes = ms_wave_bytes();
     cudaError_t e = cudaGetDevice(&f->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&f->num_sms, cudaDevAttrMultiProcessorCount, f->device);
     if (e != cudaSuccess) {
@@ -449,28 +441,49 @@ extern "C" ftlm_status ftlm_flow_add(ftlm_flow *f, const ftlm_batch_item *item, 
         fu.item = idx;
         fu.off = offs[k];
         fu.bytes = ub;
-        fu.started = false;
+        fu.vbytes = 2 * vb;
+        fu.done = 0;
         f->units.push_back(fu);
     }
-    f->dirty = true;
     *ticket = it.ticket;
     return FTLM_OK;
 }
 
-extern "C" ftlm_status ftlm_flow_step(ftlm_flow *f, int steps, void *stream)
+extern "C" ftlm_status ftlm_flow_step(ftlm_flow *f, int steps, void *stream_)
 {
     if (!f || steps < 0) return fail(FTLM_EINVAL, "bad flow step");
-    for (int s = 0; s < steps; ++s) {
-        // the items of the units that start now: coefficient rows to zero
-        for (const FlowUnit &u : f->units)
-            if (!u.started && u.u.chain_base == f->items[u.item].chain_base) {
-                const FlowItem &it = f->items[u.item];
-                const size_t rows = (size_t)it.it.R * f->M * sizeof(double);
-                FTLM_CUDA(cudaMemsetAsync(f->alpha + (size_t)it.chain_base * f->M, 0, rows, (cudaStream_t)stream));
-                FTLM_CUDA(cudaMemsetAsync(f->beta + (size_t)it.chain_base * f->M, 0, rows, (cudaStream_t)stream));
-            }
-        ftlm_status st = one_step(f, (cudaStream_t)stream);
-        if (st != FTLM_OK) return st;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    if (!steps || f->units.empty()) return FTLM_OK;
+    // the sectors that start now: coefficient rows to zero
+    for (const FlowUnit &u : f->units)
+        if (u.done == 0 && u.u.chain_base == f->items[u.item].chain_base) {
+            const FlowItem &it = f->items[u.item];
+            const size_t rows = (size_t)it.it.R * f->M * sizeof(double);
+            FTLM_CUDA(cudaMemsetAsync(f->alpha + (size_t)it.chain_base * f->M, 0, rows, stream));
+            FTLM_CUDA(cudaMemsetAsync(f->beta + (size_t)it.chain_base * f->M, 0, rows, stream));
+        }
+    // waves: consecutive units (in admission order) up to wave_bytes of vectors
+    std::vector<uint32_t> fin, wave;
+    uint64_t wb = 0;
+    for (uint32_t i = 0; i <= f->units.size(); ++i) {
+        const bool end = i == f->units.size();
+        if (!wave.empty() && (end || wb + f->units[i].vbytes > f->wave_bytes)) {
+            ftlm_status st = run_wave(f, wave, steps, stream, fin);
+            if (st != FTLM_OK) return st;
+            wave.clear();
+            wb = 0;
+        }
+        if (end) break;
+        wave.push_back(i);
+        wb += f->units[i].vbytes;
+    }
+    if (!fin.empty()) {
+        std::vector<bool> gone(f->units.size(), false);
+        for (uint32_t i : fin) gone[i] = true;
+        std::vector<FlowUnit> keep;
+        for (uint32_t i = 0; i < f->units.size(); ++i)
+            if (!gone[i]) keep.push_back(f->units[i]);
+        f->units = keep;
     }
     return FTLM_OK;
 }

@@ -120,7 +120,9 @@ struct HiWalk {
 struct SpinDev {
     uint32_t d, two_s, A, nb;   // digit base, 2s, sector digit sum (Eq. 17), bonds
     uint64_t magic;             // division by d: q = (n * magic) >> shift, n < 2^29
-    uint32_t shift, pad;
+    uint32_t shift;
+    uint32_t n_ll, n_hh;        // bonds [0, n_ll) low-low, [n_ll, n_ll + n_hh) high-high, then cross
+    uint32_t pad;
     const uint4 *slots;         // per bond {i | j << 8 | hi_i << 16 | hi_j << 17, d^i', d^j', 0}
                                 // (d^k' = power of the site within its digit block)
     const float *jf;            // J_b

@@ -150,58 +150,6 @@ hv_kernel(const SectorTables s, const BondList bl, const V *__restrict__ x, V *y
     else if (LANCZOS) epi_end<V, B, kRowThreads>(ep, apart);
 }
 
-// Walk A with one CTA of WA_THREADS threads per SM whose warps share runs of `run`
-// consecutive tiles claimed from the counter: a run of about one high-pattern group
-// keeps the group's x rows (the sources of its low-low exchanges, up to 110 KB for
-// blocks of 8 FP32 vectors) in that SM's L1 while its warps work through it.
-constexpr int kWalkAThreads = 768;
-
-template <typename V, typename Lbl, int B, int C>
-__global__ void __launch_bounds__(kWalkAThreads, 1)
-walk_a_group_kernel(const SectorTables s, const BondList bl, const V *__restrict__ x, V *y, const EpiDev ep,
-                    uint32_t run)
-{
-    extern __shared__ uint16_t s_tlo[];
-    __shared__ uint4 s_bond[kMaxBondSlots];
-    __shared__ V s_inv_s[B], s_c_prev[B];
-    __shared__ uint32_t s_next;
-    if (epi_begin<V, B>(ep, s_inv_s, s_c_prev)) return;
-    {
-        const uint4 *src = sizeof(V) == 4 ? bl.slots_f32 : bl.slots_f64;
-        for (int i = threadIdx.x; i < bl.nb; i += blockDim.x) s_bond[i] = src[i];
-    }
-    for (uint32_t i = threadIdx.x; i <= s.lomask; i += blockDim.x) s_tlo[i] = __ldg(s.tlo + i);
-    __syncthreads();
-    const V jsum4 = (V)bl.jsum4;
-    const uint32_t lane = threadIdx.x & 31u, wic = threadIdx.x >> 5, wpc = blockDim.x >> 5;
-    const uint32_t ntiles = (uint32_t)(((uint64_t)s.D + 31u) / 32u);
-    const uint32_t nrun = (ntiles + run - 1) / run;
-    for (uint32_t r = blockIdx.x; r < nrun;) {
-        if (threadIdx.x == 0) s_next = atomicAdd(ep.counter + 1, 1u) + gridDim.x;
-        const uint32_t t1 = min(ntiles, (r + 1) * run);
-        for (uint32_t tile = r * run + wic; tile < t1; tile += wpc) {
-            const uint32_t tt = tile * 32u + lane;
-            const bool ok = tt < s.D;
-            const uint32_t t[1] = {ok ? tt : s.D - 1};
-            V acc[1][B], dsum[1] = {(V)0};
-#pragma unroll
-            for (int q = 0; q < B; ++q) acc[0][q] = (V)0;
-            rows_cr<V, Lbl, 1, B, C>(s, bl, s_bond, s_tlo, x, t, acc, dsum);
-            if (ok) epi_row_walk_a<V, B>(ep, s_inv_s, s_c_prev, x, y, t[0], jsum4 - dsum[0], acc[0]);
-        }
-        __syncthreads();
-        r = s_next;
-        __syncthreads();  // every thread has read s_next before thread 0 writes it again
-    }
-    if (threadIdx.x == 0) {  // the last CTA zeroes the claim counters
-        __threadfence();
-        if (atomicAdd(ep.counter + 2, 1u) == gridDim.x - 1) {
-            ep.counter[1] = 0;
-            ep.counter[2] = 0;
-        }
-    }
-}
-
 // alpha_j of a dynamically ordered launch from its per-tile sums: block b adds a
 // fixed range of tiles (each thread its tiles in order), then the block trees and
 // the last block's sum over the blocks in order (epi_end).  The grid depends only
@@ -287,30 +235,6 @@ ftlm_status launch_rows(const ftlm_basis *b, const BondList &bl, const V *x, V *
     return FTLM_OK;
 }
 
-// Tiles per run of the group walk A (FTLM_WALK_A_RUN; 0: the label-order walk A).
-uint32_t walk_a_run()
-{
-    static const uint32_t v = [] {
-        const char *e = getenv("FTLM_WALK_A_RUN");
-        const int n = e ? atoi(e) : 0;
-        return n > 0 ? (uint32_t)n : 0u;
-    }();
-    return v;
-}
-
-template <typename V, typename Lbl, int B, int C>
-ftlm_status launch_walk_a_group(const ftlm_basis *b, const V *x, V *y, const EpiDev &ep, uint32_t run,
-                                cudaStream_t stream)
-{
-    const size_t smem = ((size_t)1 << b->L) * sizeof(uint16_t);
-    auto kern = walk_a_group_kernel<V, Lbl, B, C>;
-    // most of the SM's 256 KB of L1 + shared memory to L1 (the kernel needs 36 KB)
-    FTLM_CUDA(cudaFuncSetAttribute((const void *)kern, cudaFuncAttributePreferredSharedMemoryCarveout, 20));
-    kern<<<b->num_sms, kWalkAThreads, smem, stream>>>(b->tables(), b->bonds_walk_a, x, y, ep, run);
-    note_launch();
-    return FTLM_OK;
-}
-
 // alpha_j from the per-tile sums of a dynamically ordered launch.
 template <int B>
 void launch_tile_alpha(const ftlm_basis *b, const EpiDev &ep, uint32_t ntiles, cudaStream_t stream)
@@ -332,14 +256,7 @@ ftlm_status launch(const ftlm_basis *b, const V *x, V *y, const EpiDev &ep, cuda
         uint32_t ntiles;
         if (split_walks(b, B, sizeof(V), &w)) {
             const ftlm_dtype dt = sizeof(V) == 4 ? FTLM_F32 : FTLM_F64;
-            bool done = false;
-            if constexpr (sizeof(V) == 4 && RT == 1 && B <= 8) {  // registers of 768-thread CTAs
-                if (walk_a_run()) {
-                    st = launch_walk_a_group<V, Lbl, B, C>(b, x, y, ep, walk_a_run(), stream);
-                    done = true;
-                }
-            }
-            if (!done) st = launch_rows<V, Lbl, false, kWalkA, RT, B, C>(b, b->bonds_walk_a, x, y, ep, stream);
+            st = launch_rows<V, Lbl, false, kWalkA, RT, B, C>(b, b->bonds_walk_a, x, y, ep, stream);
             if (st == FTLM_OK) st = launch_walk_b(b, w, dt, B, x, y, ep, stream);
             ntiles = w.ntiles;
         } else {

@@ -58,6 +58,10 @@ ftlm_status ms_run_wave(const MsWave &w, ftlm_dtype dtype, int B, const MsUnit *
                         const uint32_t *stile_unit, int M, int dist, char *ws, double *alpha, double *beta,
                         int *meff, int num_sms, cudaStream_t stream);
 
+// Vector bytes per wave of the multi-sector path (FTLM_MS_WAVE_MB, default 256 MB;
+// batch.cu), used by batches and by the continuous flow.
+uint64_t ms_wave_bytes();
+
 // Single launches of a continuous flow (flow.cu): reset + start vectors of the
 // units with j0 == jstart; the H.v + alpha launch of one rank kind (its units and
 // tile map); the update + beta launch over every unit of the flow.  j is the flow's

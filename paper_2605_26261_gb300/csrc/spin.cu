@@ -317,17 +317,29 @@ extern "C" ftlm_status ftlm_basis_create_spin(int N, int two_s, int two_sz, int 
             below += dims.at(L, A - sum);
         }
     }
-    // bonds: (i < j) positions, block flags, block-local powers; J and the ladder factors
+    // bonds: (i < j) positions, block flags, block-local powers; J and the ladder
+    // factors.  Ordered by class -- both sites in the low block, both in the high
+    // block, one in each (i low, j high, since i < j) -- so the kernels rank each
+    // class with its own arithmetic.
     std::vector<uint4> slots(kMaxBondSlots, make_uint4(0, 0, 0, 0));
     std::vector<float> jf(kMaxBondSlots, 0.f);
     std::vector<double> jd(kMaxBondSlots, 0.0);
-    for (int k = 0; k < n_bonds; ++k) {
-        const int i = std::min(bi[k], bj[k]), j = std::max(bi[k], bj[k]);
-        const uint32_t hi_i = i >= L, hi_j = j >= L;
-        slots[k] = make_uint4((uint32_t)i | ((uint32_t)j << 8) | (hi_i << 16) | (hi_j << 17),
-                              (uint32_t)ipow(d, hi_i ? i - L : i), (uint32_t)ipow(d, hi_j ? j - L : j), 0u);
-        jf[k] = (float)J[k];
-        jd[k] = J[k];
+    uint32_t n_class[3] = {0, 0, 0};
+    {
+        int pos = 0;
+        for (int cls = 0; cls < 3; ++cls)
+            for (int k = 0; k < n_bonds; ++k) {
+                const int i = std::min(bi[k], bj[k]), j = std::max(bi[k], bj[k]);
+                const uint32_t hi_i = i >= L, hi_j = j >= L;
+                const int c = hi_i ? 1 : (hi_j ? 2 : 0);
+                if (c != cls) continue;
+                slots[pos] = make_uint4((uint32_t)i | ((uint32_t)j << 8) | (hi_i << 16) | (hi_j << 17),
+                                        (uint32_t)ipow(d, hi_i ? i - L : i), (uint32_t)ipow(d, hi_j ? j - L : j), 0u);
+                jf[pos] = (float)J[k];
+                jd[pos] = J[k];
+                ++n_class[cls];
+                ++pos;
+            }
     }
     std::vector<float> upf(kSpinMaxTwoS + 1, 0.f);
     std::vector<double> upd(kSpinMaxTwoS + 1, 0.0);
@@ -390,6 +402,8 @@ extern "C" ftlm_status ftlm_basis_create_spin(int N, int two_s, int two_sz, int 
     p.two_s = (uint32_t)two_s;
     p.A = (uint32_t)A;
     p.nb = (uint32_t)n_bonds;
+    p.n_ll = n_class[0];
+    p.n_hh = n_class[1];
     // q = floor(n * ceil(2^k / d) / 2^k), k = 32 + ceil(log2 d): exact for n < 2^32
     // (Granlund & Montgomery 1994); the labels divided here are below 2^27.
     int lg = 0;

@@ -1,8 +1,9 @@
 // Row work of the general-spin H.v (Eq. 12-14 for any s), shared by the
 // single-sector kernel (spin.cu) and the multi-sector path (msv.cu): the inverse
-// map of a row to its base-d digits, the digit-block rank of a source label, and
-// the per-row sums of the two ladder terms of every bond (gathers of a chunk of
-// bonds issued together, predicated).
+// map of a row to its base-d digits, and the per-row sums of the two ladder terms
+// of every bond, class by class (both sites in the low digit block, both in the
+// high block, one in each), each class with its own digit-block rank arithmetic
+// (gathers of a chunk of bonds issued together, predicated).
 #pragma once
 
 #include "ftlm_internal.cuh"
@@ -65,26 +66,6 @@ __device__ __forceinline__ void spin_unrank(const SectorTables &s, const SpinDev
     w.dig = dig;
 }
 
-// Rank of the row's label with digit i moved by di and digit j by dj (+-1).
-template <bool TS>
-__device__ __forceinline__ uint32_t spin_rank(const SectorTables &s, const uint16_t *s_tlo, const uint32_t *s_thi,
-                                              const SpinRow &w, uint32_t flags, uint32_t pi, uint32_t pj, int di)
-{
-    uint32_t lo = w.lo, hi = w.hi;
-    const uint32_t ai = di > 0 ? pi : 0u - pi, aj = di > 0 ? 0u - pj : pj;
-    if (flags & 1u) hi += ai;
-    else lo += ai;
-    if (flags & 2u) hi += aj;
-    else lo += aj;
-    // a valid move keeps both labels in range; the clamps only bound the addresses
-    // of a move that the caller discards
-    lo = min(lo, s.lomask);
-    hi = min(hi, s.H - 1u);
-    const uint32_t rh = hi == w.hi ? w.thi_h : thi_at<TS>(s, s_thi, hi);
-    const uint32_t rl = lo == w.lo ? w.r_lo : (uint32_t)s_tlo[lo];
-    return rh + rl;
-}
-
 template <typename V> __device__ __forceinline__ const V *spin_J(const SpinDev &p);
 template <> __device__ __forceinline__ const float *spin_J<float>(const SpinDev &p) { return p.jf; }
 template <> __device__ __forceinline__ const double *spin_J<double>(const SpinDev &p) { return p.jd; }
@@ -126,43 +107,49 @@ template <int B> __host__ __device__ constexpr int spin_chunk()
     return B >= 16 ? 1 : (B >= 8 ? FTLM_SPIN_CHUNK_B8 : 4);
 }
 
-// Row t: acc[r] = sum of the ladder terms of vector r, diag = sum_b J_b m_i m_j.
-// TS: thi is staged in shared memory at s_thi (else s_thi is unused).
-template <typename V, int B, int C, bool TS>
-__device__ __forceinline__ void spin_row(const SectorTables &s, const SpinDev &p, const uint16_t *s_tlo,
-                                         const uint32_t *s_thi, const uint4 *s_bond, const V *s_J, const V *s_cf,
-                                         const V *__restrict__ x, uint32_t t, V (&acc)[B], V &diag)
+// The bonds [b_beg, b_end) of one class of row w: the two ladder terms of each,
+// with the rank arithmetic of the class (CLS 0: both sites in the low block, only
+// the low half of the rank moves; 1: both in the high block; 2: site i low, site j
+// high).  Adds J m_i m_j to diag and the terms to acc.  A term whose factor is zero
+// does not exist; the clamps keep the table addresses of such a term in range.
+template <typename V, int B, int C, bool TS, int CLS>
+__device__ __forceinline__ void spin_class(const SectorTables &s, const SpinDev &p, const uint16_t *s_tlo,
+                                           const uint32_t *s_thi, const uint4 *s_bond, const V *s_J, const V *s_cf,
+                                           const V *__restrict__ x, const SpinRow &w, uint32_t b_beg, uint32_t b_end,
+                                           V (&acc)[B], V &diag)
 {
-    SpinRow w;
-    spin_unrank<TS>(s, p, s_thi, t, w);
-    diag = (V)0;
-#pragma unroll
-    for (int r = 0; r < B; ++r) acc[r] = (V)0;
-    for (uint32_t b0 = 0; b0 < p.nb; b0 += C) {
+    for (uint32_t b0 = b_beg; b0 < b_end; b0 += C) {
         uint32_t k[2 * C];
         bool use[2 * C];
         V c[2 * C];
 #pragma unroll
         for (int q = 0; q < C; ++q) {
             const uint32_t b = b0 + q;
-            const bool in = b < p.nb;
-            const uint4 e = s_bond[in ? b : 0];
-            const uint32_t i = e.x & 255u, j = (e.x >> 8) & 255u, flags = e.x >> 16;
+            const bool in = b < b_end;
+            const uint4 e = s_bond[in ? b : b_beg];
+            const uint32_t i = e.x & 255u, j = (e.x >> 8) & 255u, pi = e.y, pj = e.z;
             const uint32_t ai = (uint32_t)(w.dig >> (4 * i)) & 15u, aj = (uint32_t)(w.dig >> (4 * j)) & 15u;
             const uint32_t ij = ai * p.d + aj;
             const V J = in ? s_J[b] : (V)0;
             diag = fma(J, s_cf[128 + ij], diag);
-            // a term exists where its factor is nonzero; the clamps of spin_rank keep
-            // the table addresses of a dropped term in range
             const V f0 = s_cf[ij], f1 = s_cf[64 + ij];
-            // s_i^+ s_j^-: source digits (a_i - 1, a_j + 1), coefficient Eq. 13
-            use[2 * q] = in && f0 != (V)0;
+            use[2 * q] = in && f0 != (V)0;      // s_i^+ s_j^-: source digits (a_i - 1, a_j + 1), Eq. 13
+            use[2 * q + 1] = in && f1 != (V)0;  // s_i^- s_j^+: source digits (a_i + 1, a_j - 1), Eq. 14
             c[2 * q] = J * f0;
-            k[2 * q] = use[2 * q] ? spin_rank<TS>(s, s_tlo, s_thi, w, flags, e.y, e.z, -1) : 0u;
-            // s_i^- s_j^+: source digits (a_i + 1, a_j - 1), coefficient Eq. 14
-            use[2 * q + 1] = in && f1 != (V)0;
             c[2 * q + 1] = J * f1;
-            k[2 * q + 1] = use[2 * q + 1] ? spin_rank<TS>(s, s_tlo, s_thi, w, flags, e.y, e.z, +1) : 0u;
+            uint32_t k0, k1;
+            if constexpr (CLS == 0) {
+                k0 = w.thi_h + s_tlo[min(w.lo - pi + pj, s.lomask)];
+                k1 = w.thi_h + s_tlo[min(w.lo + pi - pj, s.lomask)];
+            } else if constexpr (CLS == 1) {
+                k0 = thi_at<TS>(s, s_thi, min(w.hi - pi + pj, s.H - 1u)) + w.r_lo;
+                k1 = thi_at<TS>(s, s_thi, min(w.hi + pi - pj, s.H - 1u)) + w.r_lo;
+            } else {
+                k0 = thi_at<TS>(s, s_thi, min(w.hi + pj, s.H - 1u)) + s_tlo[min(w.lo - pi, s.lomask)];
+                k1 = thi_at<TS>(s, s_thi, min(w.hi - pj, s.H - 1u)) + s_tlo[min(w.lo + pi, s.lomask)];
+            }
+            k[2 * q] = use[2 * q] ? k0 : 0u;
+            k[2 * q + 1] = use[2 * q + 1] ? k1 : 0u;
         }
         V xv[2 * C][B];
 #pragma unroll
@@ -179,6 +166,24 @@ __device__ __forceinline__ void spin_row(const SectorTables &s, const SpinDev &p
 #pragma unroll
             for (int r = 0; r < B; ++r) acc[r] = fma(c[q], xv[q][r], acc[r]);
     }
+}
+
+// Row t: acc[r] = sum of the ladder terms of vector r, diag = sum_b J_b m_i m_j.
+// TS: thi is staged in shared memory at s_thi (else s_thi is unused).
+template <typename V, int B, int C, bool TS>
+__device__ __forceinline__ void spin_row(const SectorTables &s, const SpinDev &p, const uint16_t *s_tlo,
+                                         const uint32_t *s_thi, const uint4 *s_bond, const V *s_J, const V *s_cf,
+                                         const V *__restrict__ x, uint32_t t, V (&acc)[B], V &diag)
+{
+    SpinRow w;
+    spin_unrank<TS>(s, p, s_thi, t, w);
+    diag = (V)0;
+#pragma unroll
+    for (int r = 0; r < B; ++r) acc[r] = (V)0;
+    const uint32_t e_ll = p.n_ll, e_hh = p.n_ll + p.n_hh;
+    spin_class<V, B, C, TS, 0>(s, p, s_tlo, s_thi, s_bond, s_J, s_cf, x, w, 0u, e_ll, acc, diag);
+    spin_class<V, B, C, TS, 1>(s, p, s_tlo, s_thi, s_bond, s_J, s_cf, x, w, e_ll, e_hh, acc, diag);
+    spin_class<V, B, C, TS, 2>(s, p, s_tlo, s_thi, s_bond, s_J, s_cf, x, w, e_hh, p.nb, acc, diag);
 }
 
 }  // namespace ftlm

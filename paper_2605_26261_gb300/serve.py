@@ -3,14 +3,17 @@
 A job is one whole FTLM run of a cluster (sites N, bond list J_ij, Zeeman field h):
 every S^z >= 0 sector (mirrored), R chains of M Lanczos steps each, then E, C, chi
 and <S^z> on a temperature grid (Eq. 6-9; the field enters as -h S^z per sector).
-Jobs arrive at any time.  All chains on the device advance together through one
-continuous flow (ftlm_flow_*): per Lanczos step one multi-sector H.v launch per
-rank kind and one update launch cover every sector in flight, whatever its step.
-Between steps the loop admits the sectors of waiting jobs, in arrival order, as
-long as their device memory fits in the flow's workspace (so a job that arrives
-while others are at step 40 starts its step 1 in the next launch), and collects
-the sectors that finished; when every sector of a job is done, its thermodynamic
-sums are queued and its results read back to pinned host memory.
+Jobs arrive at any time.  The chains of every large sector on the device advance
+together through one continuous flow (ftlm_flow_*): the flow visits its sectors in
+waves of at most 256 MB of vectors (L2-sized) and runs a few Lanczos steps of each
+wave with one multi-sector H.v launch per rank kind and one update launch per step,
+whatever step each sector is at.  Between passes the loop admits the sectors of
+waiting jobs, in arrival order, as long as their device memory fits in the flow's
+workspace (so a job that arrives while others are at step 40 starts its step 1 in
+the next pass), and collects the sectors that finished.  A job's small sectors run
+all their steps in one persistent launch on a side stream as soon as the job
+starts.  When every sector of a job is done, its thermodynamic sums are queued and
+its results read back to pinned host memory.
 
 Every unit of chains reduces its own tiles in a fixed order, so a job's results are
 bit-identical whether it runs alone or among other jobs, and whenever it was
@@ -52,32 +55,34 @@ class Job:
 
 
 class AdmissionQueue:
-    """Sectors of waiting jobs in arrival order.  admit(try_add) offers the next
-    sector to try_add(job, index) and stops at the first refusal (so no job's
-    sector overtakes an earlier job's), or before a new job when max_jobs jobs are
-    in flight."""
+    """Waiting jobs in arrival order.  admit(start, try_add) starts the head job
+    (start(job), once) and offers its sectors to try_add(job, index) one at a time;
+    it stops at the first refusal (so no job's sector overtakes an earlier job's), or
+    before starting a new job when max_jobs jobs are in flight."""
 
     def __init__(self, max_jobs=None):
-        self.jobs = collections.deque()  # [job, sector indices not yet admitted, sector count]
+        self.jobs = collections.deque()  # [job, sector indices not yet admitted, started]
         self.max_jobs = max_jobs
-        self.in_flight = 0               # jobs with an admitted sector, not finished
+        self.in_flight = 0               # started jobs not yet finished
 
-    def push(self, job, n_sectors):
-        self.jobs.append([job, list(range(n_sectors)), n_sectors])
+    def push(self, job, sectors):
+        self.jobs.append([job, list(sectors), False])
 
-    def admit(self, try_add):
+    def admit(self, start, try_add):
         """Returns the (job, sector) pairs admitted by this call."""
         admitted = []
         while self.jobs:
-            job, rest, total = self.jobs[0]
-            fresh = len(rest) == total
-            if fresh and self.max_jobs is not None and self.in_flight >= self.max_jobs:
-                break
+            entry = self.jobs[0]
+            job, rest, started = entry
+            if not started:
+                if self.max_jobs is not None and self.in_flight >= self.max_jobs:
+                    break
+                start(job)
+                entry[2] = True
+                self.in_flight += 1
             while rest:
                 if not try_add(job, rest[0]):
                     return admitted
-                if len(rest) == total:
-                    self.in_flight += 1
                 admitted.append((job, rest.pop(0)))
             self.jobs.popleft()
         return admitted
@@ -94,18 +99,25 @@ class Engine:
 
     R, M            chains per sector and Lanczos steps
     dtype           vector storage (reductions are FP64)
-    block           chains per unit of the flow
+    block           chains per unit
     T               temperature grid (host array); g the g-factor of chi
     memory_budget   bytes of the flow's workspace (default: 60 % of the free device
-                    memory when the engine starts); sector tables come on top
+                    memory when the engine starts); tables and the small sectors'
+                    batches come on top
     max_units       units of chains the flow holds at once
     max_jobs        jobs in flight at once (None: as many as fit; 1: one at a time)
-    steps_per_poll  Lanczos steps queued between two admission/collection passes
-    depth           step passes queued ahead of the device at most
+    steps_per_poll  Lanczos steps of each wave of the flow per admission pass
+    depth           admission passes queued ahead of the device at most
+    small_rows      sectors up to this dimension run in a job's own persistent batch
+
+    A job's sectors of at most small_rows rows run all their steps in one persistent
+    launch (ftlm_batch, a CTA per block of chains) on a side stream as soon as the
+    job starts; its larger sectors join the flow.
     """
 
     def __init__(self, R=8, M=80, dtype=torch.float32, block=8, T=None, g=2.0, dist=ftlm.GAUSS,
-                 memory_budget=None, max_units=512, max_jobs=None, steps_per_poll=2, depth=3):
+                 memory_budget=None, max_units=512, max_jobs=None, steps_per_poll=8, depth=2,
+                 small_rows=1 << 15):
         self.dev = torch.device("cuda", torch.cuda.current_device())
         self.R, self.M, self.dtype, self.block = R, M, dtype, block
         self.g, self.dist = g, dist
@@ -115,16 +127,18 @@ class Engine:
         if memory_budget is None:
             free, _ = torch.cuda.mem_get_info(self.dev)
             memory_budget = int(0.6 * free)
-        self.stream = torch.cuda.Stream(self.dev)
-        self.side = torch.cuda.Stream(self.dev)  # sector tables
+        self.stream = torch.cuda.Stream(self.dev)   # the flow and the thermodynamic sums
+        self.side = torch.cuda.Stream(self.dev)     # sector tables and batch plans
+        self.small = torch.cuda.Stream(self.dev)    # the small sectors' persistent batches
         self.flow = ftlm.Flow(M, dist, dtype, block, max_units, memory_budget, stream=self.stream)
         self.queue = AdmissionQueue(max_jobs)
-        self.steps_per_poll, self.depth = steps_per_poll, depth
+        self.steps_per_poll, self.depth, self.small_rows = steps_per_poll, depth, small_rows
         self.running = {}     # id(job) -> state dict (jobs need not have distinct job_id)
-        self.closing = []     # (job, event, host tensor)
+        self.closing = []
         self.finished = []
         self.inflight = collections.deque()
-        self.stats = {"steps": 0, "max_jobs_in_flight": 0, "max_units": 0, "refusals": 0}
+        self.stats = {"polls": 0, "max_jobs_in_flight": 0, "max_units": 0, "refusals": 0, "small_sectors": 0,
+                      "flow_sectors": 0}
         self.t0 = time.perf_counter()
 
     def now(self):
@@ -132,30 +146,48 @@ class Engine:
 
     def submit(self, job):
         job._two_sz = ftlm.computed_two_sz(job.N)
-        job._n_sectors = len(job._two_sz)
-        self.queue.push(job, job._n_sectors)
+        dims = [math.comb(job.N, (job.N + tz) // 2) for tz in job._two_sz]
+        job._large = [k for k, d in enumerate(dims) if d > self.small_rows]
+        self.queue.push(job, job._large)
 
     def idle(self):
         return not len(self.queue) and not self.running and not self.closing
 
     # ----------------------------------------------------------------- admission
+    def _start(self, job):
+        """Tables of every sector; the small sectors' batch on its own stream."""
+        n = len(job._two_sz)
+        st = {"job": job, "bases": [None] * n, "outs": [None] * n, "left": len(job._large), "batch": None,
+              "small_ev": None}
+        self.running[id(job)] = st
+        with torch.cuda.stream(self.side):
+            for k, tz in enumerate(job._two_sz):
+                st["bases"][k] = ftlm.Basis(job.N, tz, job.bonds, stream=self.side)
+        small = [k for k in range(n) if k not in job._large]
+        if small:
+            with torch.cuda.stream(self.small):
+                batch = ftlm.Batch([(st["bases"][k], self.R, job.seed, 0) for k in small], self.M, self.dist,
+                                   self.dtype, self.block, 1, stream=self.side)
+                res = batch.run(self.small)
+                ev = torch.cuda.Event()
+                ev.record(self.small)
+            for k, r in zip(small, res):
+                st["outs"][k] = r
+            st["batch"], st["small_ev"] = batch, ev
+            self.stats["small_sectors"] += len(small)
+        job.start = self.now()
+        if not job._large:
+            self._close(st)
+
     def _try_add(self, job, k):
-        st = self.running.get(id(job))
-        if st is None:
-            st = {"job": job, "bases": [None] * job._n_sectors, "outs": [None] * job._n_sectors, "left": 0}
-            self.running[id(job)] = st
-        if st["bases"][k] is None:
-            with torch.cuda.stream(self.side):
-                st["bases"][k] = ftlm.Basis(job.N, job._two_sz[k], job.bonds, stream=self.side)
+        st = self.running[id(job)]
         t = self.flow.add(st["bases"][k], self.R, job.seed, 0, owner=(id(job), k))
         if t is None:
             self.stats["refusals"] += 1
             if self.flow.status()["units"] == 0:
                 raise RuntimeError(f"job {job.job_id}: a sector of N = {job.N} does not fit in an empty flow")
             return False
-        if job.start is None:
-            job.start = self.now()
-        st["left"] += 1
+        self.stats["flow_sectors"] += 1
         return True
 
     # ------------------------------------------------------------------- collect
@@ -164,53 +196,59 @@ class Engine:
             st = self.running[key]
             st["outs"][k] = out
             st["left"] -= 1
-            if st["left"] == 0 and all(o is not None for o in st["outs"]):
+            if st["left"] == 0:
                 self._close(st)
 
     def _close(self, st):
         job = st["job"]
         bs, outs = st["bases"], st["outs"]
         with torch.cuda.stream(self.stream):
+            if st["small_ev"] is not None:
+                self.stream.wait_event(st["small_ev"])
             res = torch.empty((4, self.nT), dtype=torch.float64, device=self.dev)
             ftlm.ftlm_thermo([b.two_sz for b in bs], [b.dim for b in bs], self.R, self.M,
                              [o["theta"] for o in outs], [o["weight"] for o in outs], [o["m_eff"] for o in outs],
                              True, self.g, job.h, self.T, res[0], res[1], res[2], res[3], stream=self.stream)
             host = torch.empty((4, self.nT), dtype=torch.float64).pin_memory()
             host.copy_(res, non_blocking=True)
-            meff = torch.stack([o["m_eff"] for o in outs]).to("cpu", non_blocking=True)
+            meff = torch.empty((len(outs), self.R), dtype=torch.int32).pin_memory()
+            for k, o in enumerate(outs):
+                meff[k].copy_(o["m_eff"], non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(self.stream)
         for b in bs:
             b.release(self.stream)
-        self.closing.append((job, ev, host, meff, [b.updates for b in bs], res, outs))
+        self.closing.append((job, ev, host, meff, [b.updates for b in bs], res, outs, st["batch"]))
         del self.running[id(job)]
-        self.queue.finished()
 
     def _retire(self):
         keep = []
         for entry in self.closing:
-            job, ev, host, meff, upd, _, _ = entry
+            job, ev, host, meff, upd = entry[:5]
             if ev.query():
                 job.result = host.numpy().copy()
                 job.finish = self.now()
                 m = meff.numpy()
                 job.updates = int(sum(int(m[k].sum()) * upd[k] for k in range(len(upd))))
+                if entry[7] is not None:
+                    entry[7].close()
                 self.finished.append(job)
+                self.queue.finished()  # a job is in flight until its results are on the host
             else:
                 keep.append(entry)
         self.closing = keep
 
     # ---------------------------------------------------------------------- loop
     def poll(self):
-        """Admit, queue steps, collect.  Returns True if the device has work."""
-        self.queue.admit(self._try_add)
-        self.stats["max_jobs_in_flight"] = max(self.stats["max_jobs_in_flight"], len(self.running))
+        """Admit, queue one pass of the flow, collect.  Returns True if it queued work."""
+        self.queue.admit(self._start, self._try_add)
+        self.stats["max_jobs_in_flight"] = max(self.stats["max_jobs_in_flight"], len(self.running) + len(self.closing))
         st = self.flow.status()
         self.stats["max_units"] = max(self.stats["max_units"], st["units"])
         busy = st["units"] > 0
         if busy:
             self.flow.step(self.steps_per_poll, self.stream)
-            self.stats["steps"] += self.steps_per_poll
+            self.stats["polls"] += 1
             ev = torch.cuda.Event()
             ev.record(self.stream)
             self.inflight.append(ev)

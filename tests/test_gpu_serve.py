@@ -62,12 +62,14 @@ def test_served_job_matches_oracle(cuda_dev):
 
 
 def test_small_budget_serialises_without_stalling(cuda_dev):
-    # room for the sectors of about one N = 16 job (its units take 1.3 MB at R = 4
-    # in FP32) next to the coefficient rows of 64 units: later sectors wait for room
-    jobs, arrivals = make_jobs(8, seed=11, sizes=(16,))
-    eng = engine(memory_budget=2 << 20, max_units=64)
+    # N = 18 jobs: their two sectors above 32768 rows join the flow (1.6 and 1.4 MB
+    # of units at R = 4 in FP32), the rest run in each job's persistent batch; a
+    # flow workspace of 4 MB (with the coefficient rows of 64 units) holds about one
+    # job's large sectors, so later sectors wait for room
+    jobs, arrivals = make_jobs(8, seed=11, sizes=(18,))
+    eng = engine(memory_budget=4 << 20, max_units=64)
     done = eng.run(jobs, arrivals)
     eng.close()
     assert len(done) == len(jobs)
-    assert eng.stats["refusals"] > 0
+    assert eng.stats["refusals"] > 0 and eng.stats["flow_sectors"] == 2 * len(jobs)
     assert all(np.all(np.isfinite(j.result)) for j in done)

@@ -21,8 +21,9 @@ def test_sector_rows():
 def test_admission_is_fifo_by_sector_and_resumes():
     q = serve.AdmissionQueue()
     for i, n in enumerate([3, 2, 4]):
-        q.push(_J(i, 2 * n), n)
+        q.push(_J(i, 2 * n), range(n))
     room = [4]
+    started = []
 
     def try_add(job, k):  # a capacity of `room` sectors
         if room[0] == 0:
@@ -30,25 +31,30 @@ def test_admission_is_fifo_by_sector_and_resumes():
         room[0] -= 1
         return True
 
-    got = q.admit(try_add)
+    got = q.admit(lambda j: started.append(j.job_id), try_add)
     assert [(j.job_id, k) for j, k in got] == [(0, 0), (0, 1), (0, 2), (1, 0)]
-    assert q.in_flight == 2 and len(q) == 2       # job 1 waits for its second sector
+    assert started == [0, 1] and q.in_flight == 2 and len(q) == 2   # job 1 waits for its second sector
     room[0] = 10
-    got = q.admit(try_add)
+    got = q.admit(lambda j: started.append(j.job_id), try_add)
     assert [(j.job_id, k) for j, k in got] == [(1, 1), (2, 0), (2, 1), (2, 2), (2, 3)]
-    assert q.in_flight == 3 and len(q) == 0
+    assert started == [0, 1, 2] and q.in_flight == 3 and len(q) == 0
 
 
-def test_admission_limits_jobs_in_flight():
+def test_admission_limits_jobs_in_flight_and_starts_jobs_without_sectors():
     q = serve.AdmissionQueue(max_jobs=1)
-    for i in range(3):
-        q.push(_J(i, 4), 2)
-    got = q.admit(lambda j, k: True)
-    assert [(j.job_id, k) for j, k in got] == [(0, 0), (0, 1)]   # one job at a time
-    assert q.admit(lambda j, k: True) == []
+    q.push(_J(0, 4), [])        # only small sectors: started, nothing offered
+    for i in range(1, 3):
+        q.push(_J(i, 4), range(2))
+    started = []
+    got = q.admit(started.append, lambda j, k: True)
+    assert got == [] and [j.job_id for j in started] == [0]     # one job at a time
     q.finished()
-    got = q.admit(lambda j, k: True)
+    got = q.admit(started.append, lambda j, k: True)
     assert [(j.job_id, k) for j, k in got] == [(1, 0), (1, 1)]
+    assert q.admit(started.append, lambda j, k: True) == []
+    q.finished()
+    got = q.admit(started.append, lambda j, k: True)
+    assert [(j.job_id, k) for j, k in got] == [(2, 0), (2, 1)]
 
 
 def test_serving_requests_recipe():
