@@ -619,7 +619,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": vs, "dtype": args.dtype, "data": "synthetic",
         "config": {"workload": (wl["desc"] if sectors == [0] or len(sectors) > 1 else
-                                wl["desc"].replace("S^z=0", f"2S^z={sectors[0]}")) +
+                                re.sub(r"\(D=\d+", f"(D={D0}", wl["desc"].replace("S^z=0", f"2S^z={sectors[0]}"))) +
                                f", R={R} Rademacher, M={M}, 200-point T grid",
                    "sectors": len(sectors), "rank_mode": mode_name.upper(),
                    "vectors": f"{args.dtype} storage, FP64 reductions",

@@ -136,8 +136,9 @@ ftlm_status ftlm_basis_destroy_async(ftlm_basis *basis, void *stream);
  *                     far beyond L2 for the top sites in label order, but within
  *                     the same 32 columns in the transposed order.
  *   FTLM_HV_AUTO      (default) SPLIT when one block of B vectors of the call
- *                     holds at least 4 GiB (FP32) or 1 GiB (FP64), else ONE_WALK
- *                     (the crossover measured on GB300; the split moves two row
+ *                     holds at least 4 GiB (FP32) or 1 GiB (FP64) and at least
+ *                     24 bonds lie inside the high block, else ONE_WALK (the
+ *                     crossover measured on GB300; the split moves two row
  *                     streams per step, the one walk misses L2 on long jumps).
  *   rows_per_tile: high patterns per tile of the transposed walk, 1..32, or 0 for
  *   the default (8).  SPLIT needs 1..64 bonds inside the high block (the N - L
@@ -401,8 +402,8 @@ ftlm_status ftlm_batch_autotune(int n_items, const ftlm_batch_item *items, int M
  * advance together, one multi-sector H.v launch per rank kind and one update
  * launch per Lanczos step, and sectors join and leave at step boundaries.  A
  * sector added while others are at step 40 runs its step 1 in the next launch; a
- * sector that reaches its last step gets its Ritz step at once and its device
- * memory serves the next one.  Each sector's chains are cut into units of `block`
+ * sector that reaches its last step gets its Ritz step and its device memory
+ * serves the next one.  Each sector's chains are cut into units of `block`
  * chains with the tiles and per-unit reductions of the batch's multi-sector path,
  * so a sector's results are bit-identical alone, in any mix and whenever it was
  * added (and equal to its ftlm_batch results when the batch runs it on the
@@ -419,12 +420,20 @@ ftlm_status ftlm_batch_autotune(int n_items, const ftlm_batch_item *items, int M
  *   written when the sector finishes).  *ticket identifies it.  Admitted at the next
  *   step.  FTLM_ENOMEM when its units do not fit in the free workspace or the
  *   max_units limit right now (nothing is queued: add it again later).
- * ftlm_flow_step -- queue `steps` Lanczos steps of every admitted unit on `stream`
- *   (start vectors for the newly admitted ones first).  Every flow call that queues
- *   work must use the same stream (or calls ordered by the caller).
- * ftlm_flow_done -- up to max tickets of sectors whose outputs have been queued
- *   (valid once `stream` reaches the end of the step call that finished them), in
- *   finishing order; each ticket is returned once.
+ * ftlm_flow_step -- queue up to `steps` Lanczos steps of every admitted unit on
+ *   `stream` (start vectors for the newly admitted ones first).  The units are
+ *   visited in waves of consecutive units (admission order) of at most 256 MB of
+ *   vectors, each wave running its steps before the next one starts, so that a
+ *   wave's vectors stay in L2 between its steps.  The Ritz step of every sector
+ *   that finished in the call runs in one launch on the flow's own stream after
+ *   the call's work on `stream`, overlapping the next call's steps.  Every flow
+ *   call that queues work must use the same stream (or calls ordered by the
+ *   caller).
+ * ftlm_flow_done -- up to max tickets of sectors whose Ritz step has been queued,
+ *   in finishing order; each ticket is returned once.
+ * ftlm_flow_wait_outputs -- makes `stream` wait until the outputs of every sector
+ *   finished so far are written (an event wait, no host block).  Call it before
+ *   reading the outputs of tickets from ftlm_flow_done on `stream`.
  * ftlm_flow_status -- units and sectors in the flow, free workspace bytes.
  * ftlm_flow_unit_bytes -- workspace bytes of one unit of `block` chains of basis.
  * ftlm_flow_destroy -- waits for the device, then releases. */
@@ -435,6 +444,7 @@ ftlm_status ftlm_flow_unit_bytes(const ftlm_basis *basis, ftlm_dtype dtype, int 
 ftlm_status ftlm_flow_add(ftlm_flow *flow, const ftlm_batch_item *item, int *ticket);
 ftlm_status ftlm_flow_step(ftlm_flow *flow, int steps, void *stream);
 ftlm_status ftlm_flow_done(ftlm_flow *flow, int *tickets, int max, int *n);
+ftlm_status ftlm_flow_wait_outputs(ftlm_flow *flow, void *stream);
 ftlm_status ftlm_flow_status(const ftlm_flow *flow, int *units, int *sectors, uint64_t *free_bytes);
 void ftlm_flow_destroy(ftlm_flow *flow);
 

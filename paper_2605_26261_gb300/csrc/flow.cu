@@ -10,8 +10,10 @@
 // into the same tiles as in a batch and every unit reduces its own tiles in tile
 // order, so a unit's results are bit-identical whether it runs alone or with any
 // other units, and whenever it was admitted.  When a unit reaches its last step its
-// chain lengths are copied out; when all units of a sector are done, the Ritz step
-// writes the sector's outputs.  Units are admitted while their regions fit in the
+// chain lengths are copied out; the sectors whose units are all done get their Ritz
+// step, one launch per step call on the flow's own stream (FP64 QR: slow on this
+// GPU, so it overlaps the next call's Lanczos steps instead of delaying them), and
+// their coefficient rows are reused once that launch has run.  Units are admitted while their regions fit in the
 // workspace (first fit); a sector that does not fit is refused (FTLM_ENOMEM) and can
 // be added again later.
 #include <algorithm>
@@ -126,10 +128,18 @@ struct ftlm_flow {
     char *units_base;  // start of the unit regions (the ws of the msv kernels)
     uint64_t units_bytes;
     ftlm::RangeAlloc region, chains;
-    // device descriptors: units, per-kind H.v tile maps, streaming tile map, finished list
+    // device descriptors: units, per-kind H.v tile maps, streaming tile map, finished
+    // list, Ritz rows
     void *dev_block;
     ftlm::MsUnit *d_units;
     uint32_t *d_tile[3], *d_stile, *d_fin;
+    ftlm::RitzRow *d_ritz;
+    // the Ritz launches: own stream, the event it waits for on the caller's stream,
+    // the event after its latest launch, and the coefficient rows (offset, count)
+    // still read by a queued launch
+    cudaStream_t rz;
+    cudaEvent_t ev_main, ev_rz;
+    std::vector<std::pair<uint64_t, uint64_t>> rows_pending;
     uint64_t cap_tiles, cap_stiles;
     // pinned staging for the uploads (a ring of buffers, each reused once its copies ran)
     static constexpr int kStages = 8;
@@ -210,10 +220,11 @@ ftlm_status upload(ftlm_flow *f, const std::vector<uint32_t> &wave, std::vector<
 
 // `steps` Lanczos steps of one wave: start vectors of its new units, then per step
 // one H.v launch per rank kind and one update launch; afterwards the chain lengths
-// of the units that reached their last step and the Ritz step of every sector whose
-// units are all done.  Returns in fin the indices (into f->units) of finished units.
+// of the units that reached their last step.  Returns in fin the indices (into
+// f->units) of finished units and appends to ritz the sectors whose units are all
+// done.
 ftlm_status run_wave(ftlm_flow *f, const std::vector<uint32_t> &wave, int steps, cudaStream_t stream,
-                     std::vector<uint32_t> &fin)
+                     std::vector<uint32_t> &fin, std::vector<int> &ritz)
 {
     std::vector<uint32_t> order;
     ftlm_status s = upload(f, wave, order, stream);
@@ -265,19 +276,64 @@ ftlm_status run_wave(ftlm_flow *f, const std::vector<uint32_t> &wave, int steps,
         FlowUnit &u = f->units[order[i]];
         f->region.give(u.off, u.bytes);
         FlowItem &it = f->items[u.item];
-        if (--it.units_left == 0) {
-            const ftlm_batch_item &bi = it.it;
-            const size_t cb = it.chain_base;
-            s = launch_ritz(bi.R, f->M, f->alpha + cb * f->M, f->beta + cb * f->M, f->meff + cb, bi.theta_dev,
-                            bi.weight_dev, stream);
-            if (s != FTLM_OK) return s;
-            FTLM_CUDA(cudaMemcpyAsync(bi.m_eff_dev, f->meff + cb, (size_t)bi.R * sizeof(int), cudaMemcpyDeviceToDevice,
-                                      stream));
-            f->chains.give(cb, (uint64_t)bi.R);
-            f->done.push_back(it.ticket);
-            it.live = false;
+        if (--it.units_left == 0) ritz.push_back(u.item);
+    }
+    return FTLM_OK;
+}
+
+// One Ritz launch on the flow's stream for the sectors (indices into f->items) that
+// finished in this step call, after the call's work on `stream`; their chain rows
+// are released once that launch has run (release_rows).
+ftlm_status queue_ritz(ftlm_flow *f, const std::vector<int> &items, cudaStream_t stream)
+{
+    if (items.empty()) return FTLM_OK;
+    std::vector<RitzRow> rows;
+    for (int k : items) {
+        const ftlm_batch_item &bi = f->items[k].it;
+        for (int r = 0; r < bi.R; ++r) {
+            RitzRow w{};
+            w.theta = bi.theta_dev + (size_t)r * f->M;
+            w.weight = bi.weight_dev + (size_t)r * f->M;
+            w.m_eff = bi.m_eff_dev + r;
+            w.row = f->items[k].chain_base + (uint32_t)r;
+            rows.push_back(w);
         }
     }
+    FTLM_CUDA(cudaEventRecord(f->ev_main, stream));
+    FTLM_CUDA(cudaStreamWaitEvent(f->rz, f->ev_main, 0));
+    char *buf = nullptr;
+    ftlm_status s = stage_next(f, &buf);
+    if (s != FTLM_OK) return s;
+    std::memcpy(buf, rows.data(), rows.size() * sizeof(RitzRow));
+    // the rows buffer is only written and read on the Ritz stream, in order
+    FTLM_CUDA(cudaMemcpyAsync(f->d_ritz, buf, rows.size() * sizeof(RitzRow), cudaMemcpyHostToDevice, f->rz));
+    FTLM_CUDA(cudaEventRecord(f->stage_ev[f->stage_cur], f->rz));
+    s = launch_ritz_rows((int)rows.size(), f->M, f->alpha, f->beta, f->meff, f->d_ritz, f->rz);
+    if (s != FTLM_OK) return s;
+    FTLM_CUDA(cudaEventRecord(f->ev_rz, f->rz));
+    for (int k : items) {
+        FlowItem &it = f->items[k];
+        f->rows_pending.emplace_back(it.chain_base, (uint64_t)it.it.R);
+        f->done.push_back(it.ticket);
+        it.live = false;
+    }
+    return FTLM_OK;
+}
+
+// Coefficient rows of finished sectors back to the free list once the Ritz launches
+// that read them have run (wait: block the host until they have).
+ftlm_status release_rows(ftlm_flow *f, bool wait)
+{
+    if (f->rows_pending.empty()) return FTLM_OK;
+    if (wait) {
+        FTLM_CUDA(cudaEventSynchronize(f->ev_rz));
+    } else {
+        const cudaError_t e = cudaEventQuery(f->ev_rz);
+        if (e == cudaErrorNotReady) return FTLM_OK;
+        FTLM_CUDA(e);
+    }
+    for (const auto &p : f->rows_pending) f->chains.give(p.first, p.second);
+    f->rows_pending.clear();
     return FTLM_OK;
 }
 
@@ -342,7 +398,8 @@ extern "C" ftlm_status ftlm_flow_create(ftlm_dtype dtype, int block, int M, ftlm
     const uint64_t o_tile = align256((uint64_t)max_units * sizeof(MsUnit));
     const uint64_t o_stile = o_tile + 3 * align256(f->cap_tiles * sizeof(uint32_t));
     const uint64_t o_fin = o_stile + align256(f->cap_stiles * sizeof(uint32_t));
-    const uint64_t total = o_fin + align256((uint64_t)max_units * sizeof(uint32_t));
+    const uint64_t o_ritz = o_fin + align256((uint64_t)max_units * sizeof(uint32_t));
+    const uint64_t total = o_ritz + align256((uint64_t)f->max_chains * sizeof(RitzRow));
     cudaMemPool_t pool = nullptr;
     e = table_pool(f->device, &pool);
     if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&f->dev_block, total, pool, stream);
@@ -351,31 +408,41 @@ extern "C" ftlm_status ftlm_flow_create(ftlm_dtype dtype, int block, int M, ftlm
         return e == cudaErrorMemoryAllocation ? fail(FTLM_ENOMEM, "no device memory for the flow descriptors")
                                               : cuda_fail(e, "cudaMallocFromPoolAsync(flow)");
     }
-    // pinned staging: descriptors, three H.v tile maps, the streaming map
-    f->stage_bytes = o_fin + align256((uint64_t)max_units * sizeof(uint32_t)) + 6 * 256;
+    // pinned staging: descriptors, three H.v tile maps and the streaming map of a
+    // wave, or a finished list, or the Ritz rows of a step call
+    f->stage_bytes = std::max<uint64_t>(o_fin + 6 * 256, total - o_ritz);
     for (int k = 0; k < ftlm_flow::kStages; ++k) {
         f->stage[k] = nullptr;
         f->stage_ev[k] = nullptr;
     }
     f->stage_cur = 0;
+    f->rz = nullptr;
+    f->ev_main = f->ev_rz = nullptr;
     for (int k = 0; k < ftlm_flow::kStages && e == cudaSuccess; ++k) {
         e = cudaMallocHost((void **)&f->stage[k], f->stage_bytes);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f->stage_ev[k], cudaEventDisableTiming);
     }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&f->rz, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f->ev_main, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f->ev_rz, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         for (int k = 0; k < ftlm_flow::kStages; ++k) {
             if (f->stage[k]) cudaFreeHost(f->stage[k]);
             if (f->stage_ev[k]) cudaEventDestroy(f->stage_ev[k]);
         }
+        if (f->rz) cudaStreamDestroy(f->rz);
+        if (f->ev_main) cudaEventDestroy(f->ev_main);
+        if (f->ev_rz) cudaEventDestroy(f->ev_rz);
         cudaFreeAsync(f->dev_block, stream);
         delete f;
-        return cuda_fail(e, "flow staging buffers");
+        return cuda_fail(e, "flow staging buffers and Ritz stream");
     }
     char *base = (char *)f->dev_block;
     f->d_units = (MsUnit *)(base + o_units);
     for (int k = 0; k < 3; ++k) f->d_tile[k] = (uint32_t *)(base + o_tile + k * align256(f->cap_tiles * sizeof(uint32_t)));
     f->d_stile = (uint32_t *)(base + o_stile);
     f->d_fin = (uint32_t *)(base + o_fin);
+    f->d_ritz = (RitzRow *)(base + o_ritz);
     *out = f;
     return FTLM_OK;
 }
@@ -393,7 +460,13 @@ extern "C" ftlm_status ftlm_flow_add(ftlm_flow *f, const ftlm_batch_item *item, 
     const int nu = (item->R + B - 1) / B;
     if (f->units.size() + nu > f->max_units) return fail(FTLM_ENOMEM, "flow holds max_units units");
     uint64_t cb = 0;
-    if (!f->chains.take((uint64_t)item->R, &cb)) return fail(FTLM_ENOMEM, "no coefficient rows free");
+    if (!f->chains.take((uint64_t)item->R, &cb)) {
+        // rows held only by queued Ritz launches: wait for those
+        if (f->rows_pending.empty()) return fail(FTLM_ENOMEM, "no coefficient rows free");
+        ftlm_status s = release_rows(f, true);
+        if (s != FTLM_OK) return s;
+        if (!f->chains.take((uint64_t)item->R, &cb)) return fail(FTLM_ENOMEM, "no coefficient rows free");
+    }
     const uint64_t ub = unit_bytes(b, B, vsize);
     std::vector<uint64_t> offs;
     for (int k = 0; k < nu; ++k) {
@@ -453,6 +526,8 @@ extern "C" ftlm_status ftlm_flow_step(ftlm_flow *f, int steps, void *stream_)
 {
     if (!f || steps < 0) return fail(FTLM_EINVAL, "bad flow step");
     cudaStream_t stream = (cudaStream_t)stream_;
+    ftlm_status st = release_rows(f, false);
+    if (st != FTLM_OK) return st;
     if (!steps || f->units.empty()) return FTLM_OK;
     // the sectors that start now: coefficient rows to zero
     for (const FlowUnit &u : f->units)
@@ -464,11 +539,12 @@ extern "C" ftlm_status ftlm_flow_step(ftlm_flow *f, int steps, void *stream_)
         }
     // waves: consecutive units (in admission order) up to wave_bytes of vectors
     std::vector<uint32_t> fin, wave;
+    std::vector<int> ritz;
     uint64_t wb = 0;
     for (uint32_t i = 0; i <= f->units.size(); ++i) {
         const bool end = i == f->units.size();
         if (!wave.empty() && (end || wb + f->units[i].vbytes > f->wave_bytes)) {
-            ftlm_status st = run_wave(f, wave, steps, stream, fin);
+            st = run_wave(f, wave, steps, stream, fin, ritz);
             if (st != FTLM_OK) return st;
             wave.clear();
             wb = 0;
@@ -485,6 +561,13 @@ extern "C" ftlm_status ftlm_flow_step(ftlm_flow *f, int steps, void *stream_)
             if (!gone[i]) keep.push_back(f->units[i]);
         f->units = keep;
     }
+    return queue_ritz(f, ritz, stream);
+}
+
+extern "C" ftlm_status ftlm_flow_wait_outputs(ftlm_flow *f, void *stream)
+{
+    if (!f) return fail(FTLM_EINVAL, "NULL flow");
+    FTLM_CUDA(cudaStreamWaitEvent((cudaStream_t)stream, f->ev_rz, 0));
     return FTLM_OK;
 }
 
@@ -520,5 +603,8 @@ extern "C" void ftlm_flow_destroy(ftlm_flow *f)
         cudaFreeHost(f->stage[k]);
         cudaEventDestroy(f->stage_ev[k]);
     }
+    cudaStreamDestroy(f->rz);
+    cudaEventDestroy(f->ev_main);
+    cudaEventDestroy(f->ev_rz);
     delete f;
 }

@@ -269,5 +269,14 @@ ftlm_status ghost_unconverged_take(cudaStream_t stream, uint64_t *count);
 // Ritz step of n chains (alpha/beta rows of length M, m_eff per chain).
 ftlm_status launch_ritz(int n, int M, const double *alpha, const double *beta, const int *mv, double *theta,
                         double *weight, cudaStream_t stream);
+// Chain c of an indirect Ritz launch: its coefficient row of alpha/beta/m_eff and
+// where its M Ritz values, M weights and chain length go.
+struct RitzRow {
+    double *theta, *weight;
+    int *m_eff;
+    uint32_t row, pad;
+};
+ftlm_status launch_ritz_rows(int n, int M, const double *alpha, const double *beta, const int *mv,
+                             const RitzRow *rows, cudaStream_t stream);
 
 }  // namespace ftlm

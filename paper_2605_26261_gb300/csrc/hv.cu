@@ -200,22 +200,29 @@ int hv_cta_cap()
 
 // Split Lanczos H.v (see HiWalk): used when the basis asks for it, or under
 // FTLM_HV_AUTO for blocks of vectors of at least kSplitMinBytes32 (FP32) or
-// kSplitMinBytes64 (FP64).  Measured on GB300 (H.v step of the N = 30 icosidodecahedral
-// S^z = 0 sector, one walk -> split): FP32 blocks of 16 / 8 / 4 / 1 vectors (10, 5,
-// 2.5, 0.6 GB) 35.2 -> 33.5, 16.7 -> 16.4, 9.69 -> 9.78, 5.54 -> 6.68 ms; FP64
-// blocks of 4 / 1 (5, 1.2 GB) 96.2 -> 82.9, 37.2 -> 33.7 ms; FP32 blocks of 8 on the
-// 30 M-row sector of the same cluster (0.96 GB) 3.21 -> 3.33 ms.  The split moves
-// two row streams per step instead of one but no long-jump gather misses L2 (DRAM
-// 5.7 instead of 9.5 GB on the 30 M-row sector).
+// kSplitMinBytes64 (FP64) of sectors with at least kSplitMinHiBonds high-high
+// bonds.  Measured on GB300 (H.v step, one walk -> split), N = 30 icosidodecahedral
+// S^z = 0 sector (26 of 60 bonds high-high): FP32 blocks of 16 / 8 / 4 / 1 vectors
+// (10, 5, 2.5, 0.6 GB) 35.2 -> 33.5, 16.7 -> 16.4, 9.69 -> 9.78, 5.54 -> 6.68 ms;
+// FP64 blocks of 4 / 1 (5, 1.2 GB) 96.2 -> 82.9, 37.2 -> 33.7 ms; FP32 blocks of 8
+// on the 30 M-row sector of the same cluster (0.96 GB) 3.21 -> 3.33 ms.  N = 34
+// ring (19 of 34 bonds high-high), FP32 blocks of 8: 2 S^z = 14 / 10 / 6 / 0
+// (4.2, 17.5, 44, 75 GB) 9.75 -> 12.4, 41.3 -> 51.8, 105.9 -> 103.9, 177 -> 184 ms.
+// The split moves two row streams per step instead of one but no long-jump gather
+// misses L2 (DRAM 5.7 instead of 9.5 GB on the 30 M-row sector); with few
+// high-high bonds per row the second pass costs more than the misses it saves.
 constexpr uint64_t kSplitMinBytes32 = 4ull << 30;
 constexpr uint64_t kSplitMinBytes64 = 1ull << 30;
+constexpr int kSplitMinHiBonds = 24;
 constexpr int kDefaultWalkRh = 8;
 
 bool split_walks(const ftlm_basis *b, int B, size_t vsize, HiWalk *w)
 {
     if (b->hv_schedule == FTLM_HV_ONE_WALK) return false;
     const uint64_t bytes = b->D * (uint64_t)B * vsize;
-    if (b->hv_schedule == FTLM_HV_AUTO && bytes < (vsize == 4 ? kSplitMinBytes32 : kSplitMinBytes64)) return false;
+    if (b->hv_schedule == FTLM_HV_AUTO &&
+        (bytes < (vsize == 4 ? kSplitMinBytes32 : kSplitMinBytes64) || b->n_hi_bonds < kSplitMinHiBonds))
+        return false;
     return build_hi_walk(b, b->walk_rh ? b->walk_rh : kDefaultWalkRh, w);
 }
 

@@ -184,20 +184,36 @@ __global__ void copy_meff_kernel(const ChainState *st, int B, int *dst)
 __device__ unsigned long long g_ritz_unconverged;
 
 // One thread per chain; T chains per CTA.  A chain whose QR iteration does not
-// converge within max_sweeps gets NaN Ritz values and weights.
+// converge within max_sweeps gets NaN Ritz values and weights.  rows == nullptr:
+// chain c reads row c of alpha/beta/mv and writes row c of theta/weight; else
+// rows[c] names its coefficient row and its outputs (and m_eff is copied out).
 __global__ void ritz_kernel(int n, int M, const double *__restrict__ alpha, const double *__restrict__ beta,
-                            const int *__restrict__ mv, double *theta, double *weight, int max_sweeps)
+                            const int *__restrict__ mv, double *theta, double *weight, const RitzRow *rows,
+                            int max_sweeps)
 {
     extern __shared__ double sh[];
     const int T = blockDim.x, i = threadIdx.x;
     const int c = blockIdx.x * T + i;
     if (c >= n) return;
     Strided d{sh + i, T}, e{sh + (size_t)M * T + i, T}, z{sh + (size_t)2 * M * T + i, T};
-    int m = mv[c];
+    size_t row;
+    double *th, *wt;
+    if (rows) {
+        const RitzRow r = rows[c];
+        row = r.row;
+        th = r.theta;
+        wt = r.weight;
+    } else {
+        row = (size_t)c;
+        th = theta + row * M;
+        wt = weight + row * M;
+    }
+    int m = mv[row];
+    if (rows) rows[c].m_eff[0] = m;
     m = m < 0 ? 0 : (m > M ? M : m);
     for (int k = 0; k < m; ++k) {
-        d[k] = alpha[(size_t)c * M + k];
-        e[k] = k + 1 < m ? beta[(size_t)c * M + k] : 0.0;
+        d[k] = alpha[row * M + k];
+        e[k] = k + 1 < m ? beta[row * M + k] : 0.0;
         z[k] = k == 0 ? 1.0 : 0.0;
     }
     bool ok = true;
@@ -207,8 +223,8 @@ __global__ void ritz_kernel(int n, int M, const double *__restrict__ alpha, cons
         else atomicAdd(&g_ritz_unconverged, 1ull);
     }
     for (int k = 0; k < M; ++k) {
-        theta[(size_t)c * M + k] = k < m ? (ok ? d[k] : NAN) : 0.0;
-        weight[(size_t)c * M + k] = k < m ? (ok ? z[k] * z[k] : NAN) : 0.0;
+        th[k] = k < m ? (ok ? d[k] : NAN) : 0.0;
+        wt[k] = k < m ? (ok ? z[k] * z[k] : NAN) : 0.0;
     }
 }
 
@@ -217,8 +233,10 @@ __global__ void ritz_kernel(int n, int M, const double *__restrict__ alpha, cons
 std::atomic<int> g_ritz_max_sweeps{0};
 int ritz_max_sweeps() { return g_ritz_max_sweeps.load(std::memory_order_relaxed); }
 
-ftlm_status launch_ritz(int n, int M, const double *alpha, const double *beta, const int *mv,
-                        double *theta, double *weight, cudaStream_t stream)
+namespace {
+
+ftlm_status ritz_launch(int n, int M, const double *alpha, const double *beta, const int *mv, double *theta,
+                        double *weight, const RitzRow *rows, cudaStream_t stream)
 {
     if (n == 0) return FTLM_OK;
     constexpr size_t kSmemMax = 96 * 1024;
@@ -229,10 +247,24 @@ ftlm_status launch_ritz(int n, int M, const double *alpha, const double *beta, c
     T = T < 1 ? 1 : (T > 32 ? 32 : T);
     if (T > n) T = n;
     const int grid = (n + T - 1) / T;
-    ritz_kernel<<<grid, T, per_chain * T, stream>>>(n, M, alpha, beta, mv, theta, weight, ritz_max_sweeps());
+    ritz_kernel<<<grid, T, per_chain * T, stream>>>(n, M, alpha, beta, mv, theta, weight, rows, ritz_max_sweeps());
     note_launch();
     FTLM_CUDA(cudaGetLastError());
     return FTLM_OK;
+}
+
+}  // namespace
+
+ftlm_status launch_ritz(int n, int M, const double *alpha, const double *beta, const int *mv,
+                        double *theta, double *weight, cudaStream_t stream)
+{
+    return ritz_launch(n, M, alpha, beta, mv, theta, weight, nullptr, stream);
+}
+
+ftlm_status launch_ritz_rows(int n, int M, const double *alpha, const double *beta, const int *mv,
+                             const RitzRow *rows, cudaStream_t stream)
+{
+    return ritz_launch(n, M, alpha, beta, mv, nullptr, nullptr, rows, stream);
 }
 
 namespace {

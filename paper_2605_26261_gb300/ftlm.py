@@ -112,6 +112,7 @@ def lib():
         "ftlm_flow_add": [P, P, ctypes.POINTER(I)],
         "ftlm_flow_step": [P, I, P],
         "ftlm_flow_done": [P, P, I, ctypes.POINTER(I)],
+        "ftlm_flow_wait_outputs": [P, P],
         "ftlm_flow_status": [P, ctypes.POINTER(I), ctypes.POINTER(I), PU64],
     }
     for name, args in sig.items():
@@ -629,7 +630,9 @@ class Flow:
     """Continuous Lanczos flow (ftlm_flow_*): sectors join and leave at Lanczos-step
     boundaries.  The workspace is a torch tensor of work_bytes (default: 60 % of the
     free device memory); add() returns a ticket, or None when the sector does not
-    fit now; done() returns (ticket, outputs) of finished sectors."""
+    fit now; done(stream) returns (ticket, outputs, owner) of finished sectors and
+    makes `stream` (default: the current stream) wait until their outputs are
+    written (their Ritz step runs on the flow's own stream)."""
 
     def __init__(self, M, dist=GAUSS, dtype=torch.float32, block=8, max_units=512, work_bytes=None, stream=None):
         self.dev = torch.device("cuda", torch.cuda.current_device())
@@ -661,7 +664,7 @@ class Flow:
     def step(self, steps=1, stream=None):
         _check(lib().ftlm_flow_step(self.handle, int(steps), _stream(stream)))
 
-    def done(self):
+    def done(self, stream=None):
         buf = (ctypes.c_int * 256)()
         n = ctypes.c_int()
         res = []
@@ -671,7 +674,10 @@ class Flow:
                 out, owner = self.outputs.pop(buf[i])
                 res.append((buf[i], out, owner))
             if n.value < 256:
-                return res
+                break
+        if res:
+            _check(lib().ftlm_flow_wait_outputs(self.handle, _stream(stream)))
+        return res
 
     def status(self):
         u, s_, f = ctypes.c_int(), ctypes.c_int(), ctypes.c_uint64()

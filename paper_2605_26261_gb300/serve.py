@@ -17,9 +17,11 @@ its results read back to pinned host memory.
 
 Every unit of chains reduces its own tiles in a fixed order, so a job's results are
 bit-identical whether it runs alone or among other jobs, and whenever it was
-admitted.  The flow's device work is queued on one stream; sector tables are built
-on a side stream (creation waits only for that stream) and released in the flow
-stream's order once the job's sums are queued.
+admitted.  The flow's Lanczos steps are queued on one stream and its Ritz steps run
+on the flow's own stream; a job's thermodynamic sums and result copies go on a
+third stream that waits for the job's outputs, so neither holds up the next
+steps.  Sector tables are built on a side stream (creation waits only for that
+stream) and released in the sums stream's order once the job's sums are queued.
 
 Everything on the device goes through the C ABI of libftlm (ftlm.py); this module
 only schedules.  Host clocks (time.perf_counter) stamp arrival, start and finish.
@@ -127,9 +129,10 @@ class Engine:
         if memory_budget is None:
             free, _ = torch.cuda.mem_get_info(self.dev)
             memory_budget = int(0.6 * free)
-        self.stream = torch.cuda.Stream(self.dev)   # the flow and the thermodynamic sums
+        self.stream = torch.cuda.Stream(self.dev)   # the flow's Lanczos steps
         self.side = torch.cuda.Stream(self.dev)     # sector tables and batch plans
         self.small = torch.cuda.Stream(self.dev)    # the small sectors' persistent batches
+        self.tstream = torch.cuda.Stream(self.dev)  # thermodynamic sums and result copies
         self.flow = ftlm.Flow(M, dist, dtype, block, max_units, memory_budget, stream=self.stream)
         self.queue = AdmissionQueue(max_jobs)
         self.steps_per_poll, self.depth, self.small_rows = steps_per_poll, depth, small_rows
@@ -192,7 +195,7 @@ class Engine:
 
     # ------------------------------------------------------------------- collect
     def _collect(self):
-        for ticket, out, (key, k) in self.flow.done():
+        for ticket, out, (key, k) in self.flow.done(self.tstream):
             st = self.running[key]
             st["outs"][k] = out
             st["left"] -= 1
@@ -202,22 +205,23 @@ class Engine:
     def _close(self, st):
         job = st["job"]
         bs, outs = st["bases"], st["outs"]
-        with torch.cuda.stream(self.stream):
+        with torch.cuda.stream(self.tstream):
             if st["small_ev"] is not None:
-                self.stream.wait_event(st["small_ev"])
+                self.tstream.wait_event(st["small_ev"])
             res = torch.empty((4, self.nT), dtype=torch.float64, device=self.dev)
             ftlm.ftlm_thermo([b.two_sz for b in bs], [b.dim for b in bs], self.R, self.M,
                              [o["theta"] for o in outs], [o["weight"] for o in outs], [o["m_eff"] for o in outs],
-                             True, self.g, job.h, self.T, res[0], res[1], res[2], res[3], stream=self.stream)
+                             True, self.g, job.h, self.T, res[0], res[1], res[2], res[3], stream=self.tstream)
             host = torch.empty((4, self.nT), dtype=torch.float64).pin_memory()
             host.copy_(res, non_blocking=True)
             meff = torch.empty((len(outs), self.R), dtype=torch.int32).pin_memory()
             for k, o in enumerate(outs):
                 meff[k].copy_(o["m_eff"], non_blocking=True)
             ev = torch.cuda.Event()
-            ev.record(self.stream)
+            ev.record(self.tstream)
+        # the flow's last use of the tables precedes its outputs, which tstream waited for
         for b in bs:
-            b.release(self.stream)
+            b.release(self.tstream)
         self.closing.append((job, ev, host, meff, [b.updates for b in bs], res, outs, st["batch"]))
         del self.running[id(job)]
 

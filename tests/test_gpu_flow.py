@@ -101,3 +101,26 @@ def test_flow_refuses_what_does_not_fit(cuda_dev):
             flow.step(12)
             assert len(flow.done()) == 2
             torch.cuda.synchronize()
+
+
+def test_flow_reuses_coefficient_rows_after_the_ritz_launch(cuda_dev):
+    """One unit of coefficient rows: a sector added right after another finished
+    waits for that sector's Ritz launch (on the flow's own stream) before taking its
+    rows; both results equal the sectors run alone."""
+    M, R = 20, 8
+    with ftlm.Basis(16, 0, inputs.ring(16)) as b1, ftlm.Basis(16, 2, inputs.ladder(16, 1.0, 0.7)) as b2:
+        alone = []
+        for b, seed in ((b1, 3), (b2, 4)):
+            with ftlm.Flow(M, ftlm.GAUSS, torch.float32, 8, 1, 1 << 28) as flow:
+                alone.append(_run(flow, [0], [b], R, [seed])[0])
+        with ftlm.Flow(M, ftlm.GAUSS, torch.float32, 8, 1, 1 << 28) as flow:
+            assert flow.add(b1, R, 3, owner=0) is not None
+            flow.step(M)
+            (t1, out1, _), = flow.done()
+            assert flow.add(b2, R, 4, owner=1) is not None   # rows of b1 held by its Ritz launch
+            flow.step(M)
+            (t2, out2, _), = flow.done()
+            torch.cuda.synchronize()
+        for got, want in ((out1, alone[0]), (out2, alone[1])):
+            for k in ("theta", "weight", "m_eff"):
+                assert torch.equal(got[k], want[k]), k
