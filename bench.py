@@ -84,6 +84,8 @@ def parse_args():
     p.add_argument("--no-extras", action="store_true",
                    help="default workload: skip the FP64 one-vector job and the serving stream")
     p.add_argument("--serving-jobs", type=int, default=64, help="requests of the serving stream in the default line")
+    p.add_argument("--live-rows", type=int, default=0,
+                   help="serving: rows of flow sectors in flight at most (0: no limit beyond memory)")
     p.add_argument("--two-sz", type=int, default=0, help="sector 2 S^z of single-sector workloads (profiling)")
     p.add_argument("--schedule", choices=["auto", "one_walk", "split"], default="auto",
                    help="walks of the Lanczos H.v (ftlm_basis_set_schedule)")
@@ -500,7 +502,7 @@ def run_ours(args):
     extras = None
     if world == 1 and args.workload == "icosidodecahedron" and not args.no_extras and len(sectors) == 1:
         extras = {"fp64_b1": fp64_b1_job(N, bonds, mode, R, M, T, value), "serving": None}
-        sv = serve_stream(args.serving_jobs, 8, 3, local)
+        sv = serve_stream(args.serving_jobs, 8, 3, local, live_rows=args.live_rows)
         sv.pop("_done"), sv.pop("_jobs")
         sv["workload"] = WORKLOADS["serving"]["desc"]
         extras["serving"] = sv
@@ -876,7 +878,7 @@ def run_clusters(args):
         dist.destroy_process_group()
 
 
-def serve_stream(n_jobs, steps_per_poll, warmup, local=0, clocks=None):
+def serve_stream(n_jobs, steps_per_poll, warmup, local=0, clocks=None, live_rows=0):
     """The request loop (serve.Engine: chain-level continuous batching) on the seeded
     Poisson stream of FTLM jobs of the serving configuration: jobs/s (requests /
     makespan) and p50/p99 latency from arrival to results on the host, beside the
@@ -889,9 +891,9 @@ def serve_stream(n_jobs, steps_per_poll, warmup, local=0, clocks=None):
     T = inputs.log_t_grid(200)
     R, M = 8, 80
 
-    def engine(max_jobs):
+    def engine(max_jobs, live=None):
         return serve.Engine(R=R, M=M, dtype=torch.float32, block=8, T=T, dist=ftlm.GAUSS, max_jobs=max_jobs,
-                            steps_per_poll=steps_per_poll)
+                            steps_per_poll=steps_per_poll, max_live_rows=live)
 
     # warm-up: a few jobs of every size through a throwaway engine
     warm, _ = serve.poisson_jobs(max(warmup, 6), 200.0, seed=99)
@@ -902,7 +904,7 @@ def serve_stream(n_jobs, steps_per_poll, warmup, local=0, clocks=None):
 
     jobs, arrivals = serve.poisson_jobs(n_jobs, 200.0, seed=4)
     launches0 = ftlm.ftlm_launch_count()
-    eng = engine(None)
+    eng = engine(None, live_rows or None)
     if clocks is not None:
         clocks.__enter__()
     try:
@@ -926,15 +928,21 @@ def serve_stream(n_jobs, steps_per_poll, warmup, local=0, clocks=None):
     eng.close()
     alone_s = time.perf_counter() - t0
     same = sum(1 for j in alone if np.array_equal(j.result, served[j.job_id].result))
+    worst = max((float(np.max(np.abs(j.result - served[j.job_id].result) /
+                              np.maximum(np.abs(j.result), 1e-300)))
+                 for j in alone if not np.array_equal(j.result, served[j.job_id].result)), default=0.0)
     alone_lat = np.array([j.latency for j in alone]) * 1e3
-    return {"jobs": n_jobs, "steps_per_poll": steps_per_poll, "jobs_per_s": n_jobs / makespan,
+    return {"jobs": n_jobs, "steps_per_poll": steps_per_poll, "max_live_rows": live_rows or None,
+            "jobs_per_s": n_jobs / makespan,
             "max_jobs_in_flight": stats["max_jobs_in_flight"], "max_units": stats["max_units"],
+            "host_s": {k: round(v, 3) for k, v in stats["host_s"].items()}, "polls": stats["polls"],
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "makespan_s": makespan, "Gupdates_per_s": sum(j.updates for j in done) / makespan / 1e9,
             "one_at_a_time_jobs_per_s": n_jobs / alone_s,
             "one_at_a_time_p50_ms": float(np.percentile(alone_lat, 50)),
             "one_at_a_time_p99_ms": float(np.percentile(alone_lat, 99)),
-            "identical_alone_vs_mix": f"{same}/{n_jobs}", "gpu_launches": launches,
+            "identical_alone_vs_mix": f"{same}/{n_jobs}", "max_rel_diff_alone_vs_mix": worst,
+            "gpu_launches": launches,
             "_done": done, "_jobs": jobs}
 
 
@@ -955,7 +963,7 @@ def run_serving(args):
     n_jobs = args.jobs
     R = 8
     clocks = ClockSampler(local)
-    sv = serve_stream(n_jobs, args.steps_per_poll, args.warmup, local, clocks)
+    sv = serve_stream(n_jobs, args.steps_per_poll, args.warmup, local, clocks, args.live_rows)
     done, jobs = sv.pop("_done"), sv.pop("_jobs")
     launches = sv["gpu_launches"]
     makespan = sv["makespan_s"]
@@ -979,15 +987,20 @@ def run_serving(args):
                    "steps_per_poll": args.steps_per_poll, "block": 8,
                    "batching": "chain level: sectors join the running multi-sector launches at Lanczos-step "
                                "boundaries (ftlm_flow)",
-                   "admission": "first fit of each sector's units in the flow workspace (60% of free HBM)",
+                   "admission": "first fit of each sector's units in the flow workspace (60% of free HBM)" +
+                                (f", at most {args.live_rows} rows of flow sectors in flight" if args.live_rows
+                                 else ""),
+                   "flow_streams": 4, "small_sectors": "D <= 32768: one persistent batch per job on a side stream",
                    "l2": "largest sectors (D=10400600, 8 f32 vectors) exceed L2",
                    "parallelism": "single GPU"},
         "p50_ms": sv["p50_ms"], "p99_ms": sv["p99_ms"],
         "makespan_s": makespan, "Gupdates_per_s": updates / makespan / 1e9,
         "one_at_a_time": {"jobs_per_s": sv["one_at_a_time_jobs_per_s"], "p50_ms": sv["one_at_a_time_p50_ms"],
                           "p99_ms": sv["one_at_a_time_p99_ms"],
-                          "note": "same jobs, one slot, one job per batch, all queued at t=0"},
+                          "note": "same jobs and engine, one job in flight at a time, all queued at t=0"},
         "identical_alone_vs_mix": sv["identical_alone_vs_mix"],
+        "max_rel_diff_alone_vs_mix": sv["max_rel_diff_alone_vs_mix"],
+        "engine": {k: sv[k] for k in ("max_jobs_in_flight", "max_units", "polls", "host_s")},
         "roofline": {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None, "traffic": None,
                      "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
                      "note": "request-loop line: the H.v kernel roofline is reported by the default workload"},

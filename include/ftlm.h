@@ -111,6 +111,21 @@ ftlm_status ftlm_basis_create(int N, int two_sz, int n_bonds, const int *bi, con
 ftlm_status ftlm_basis_create_spin(int N, int two_s, int two_sz, int n_bonds, const int *bi, const int *bj,
                                    const double *J, void *stream, ftlm_basis **out);
 
+/* ftlm_basis_create_sectors -- n sectors (2 S^z = two_sz[k], 1 <= n <= 64) of one
+ * cluster, as n calls of ftlm_basis_create (two_s = 1, with `mode`) or
+ * ftlm_basis_create_spin (two_s > 1, mode ignored), with at most one wait for
+ * `stream`: wait != 0 returns once every table is built; wait = 0 returns once
+ * their builds are queued on `stream`, and the caller orders every use of the
+ * tables on other streams after that point (an event) -- a request loop that keeps
+ * the device busy then never blocks on table builds.  The host-side queries
+ * (ftlm_basis_dim, _bytes, _mode, _updates) answer at once either way.  out
+ * receives n handles, each released by ftlm_basis_destroy(_async).  On any error
+ * nothing is kept (every out[k] = NULL, tables freed in the order of `stream`) and
+ * the first error is returned. */
+ftlm_status ftlm_basis_create_sectors(int N, int two_s, int n, const int *two_sz, int n_bonds, const int *bi,
+                                      const int *bj, const double *J, ftlm_rank_mode mode, int wait, void *stream,
+                                      ftlm_basis **out);
+
 /* Release the handle and its device tables.  Waits until the device has finished
  * all queued work first (any stream may still read the tables).  NULL is ignored. */
 void ftlm_basis_destroy(ftlm_basis *basis);
@@ -412,9 +427,9 @@ ftlm_status ftlm_batch_autotune(int n_items, const ftlm_batch_item *items, int M
  *   ftlm_batch_create; max_units: units the flow holds at once.  work_dev
  *   (256-byte aligned, work_bytes, caller-owned) holds 2 max_units block M doubles
  *   of coefficient rows and the units' regions (ftlm_flow_unit_bytes each); the
- *   library allocates the unit descriptors and tile maps from its pool on `stream`
- *   and small pinned host staging buffers.  Spin-1/2 sectors with N <= 32 and
- *   general-spin sectors.
+ *   library allocates the unit descriptors and tile maps from its pool on
+ *   `stream`, pinned host staging buffers, the wave streams and the Ritz stream.  Spin-1/2 sectors with N <= 32 and general-spin
+ *   sectors.
  * ftlm_flow_add -- queue the R chains of item (as an ftlm_batch_item: chains keyed
  *   first_chain + r under seed; outputs theta, weight, m_eff as for ftlm_lanczos,
  *   written when the sector finishes).  *ticket identifies it.  Admitted at the next
@@ -423,14 +438,20 @@ ftlm_status ftlm_batch_autotune(int n_items, const ftlm_batch_item *items, int M
  * ftlm_flow_step -- queue up to `steps` Lanczos steps of every admitted unit on
  *   `stream` (start vectors for the newly admitted ones first).  The units are
  *   visited in waves of consecutive units (admission order) of at most 256 MB of
- *   vectors, each wave running its steps before the next one starts, so that a
- *   wave's vectors stay in L2 between its steps.  The Ritz step of every sector
+ *   vectors, each wave running its steps before the next one on its stream starts
+ *   (so that a wave's vectors stay in L2 between its steps).  The waves are spread
+ *   over the flow's wave streams (least loaded first), which start after the work
+ *   queued on `stream` and which `stream` waits for at the end of the call: the
+ *   launches of different waves overlap (one wave's gathers with another's row
+ *   streams, and launch tails).  The Ritz step of every sector
  *   that finished in the call runs in one launch on the flow's own stream after
  *   the call's work on `stream`, overlapping the next call's steps.  Every flow
  *   call that queues work must use the same stream (or calls ordered by the
  *   caller).
  * ftlm_flow_done -- up to max tickets of sectors whose Ritz step has been queued,
  *   in finishing order; each ticket is returned once.
+ * ftlm_flow_set_streams -- wave streams of later step calls, 1 .. 4 (default 4;
+ *   1: every wave on `stream`).  Results do not depend on it.  EINVAL otherwise.
  * ftlm_flow_wait_outputs -- makes `stream` wait until the outputs of every sector
  *   finished so far are written (an event wait, no host block).  Call it before
  *   reading the outputs of tickets from ftlm_flow_done on `stream`.
@@ -445,6 +466,7 @@ ftlm_status ftlm_flow_add(ftlm_flow *flow, const ftlm_batch_item *item, int *tic
 ftlm_status ftlm_flow_step(ftlm_flow *flow, int steps, void *stream);
 ftlm_status ftlm_flow_done(ftlm_flow *flow, int *tickets, int max, int *n);
 ftlm_status ftlm_flow_wait_outputs(ftlm_flow *flow, void *stream);
+ftlm_status ftlm_flow_set_streams(ftlm_flow *flow, int n);
 ftlm_status ftlm_flow_status(const ftlm_flow *flow, int *units, int *sectors, uint64_t *free_bytes);
 void ftlm_flow_destroy(ftlm_flow *flow);
 

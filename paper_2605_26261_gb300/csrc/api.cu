@@ -88,6 +88,13 @@ cudaError_t table_pool(int device, cudaMemPool_t *pool)
         if (e != cudaSuccess) return e;
         uint64_t keep = kPoolKeepBytes;
         e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        // An allocation never waits for another stream: a block freed in the order of
+        // a busy stream is taken only once that stream has passed the free (else the
+        // pool grows), so that building tables or plans on a quiet stream does not
+        // queue behind the Lanczos launches of a busy one.
+        int no = 0;
+        if (e == cudaSuccess) e = cudaMemPoolSetAttribute(p, cudaMemPoolReuseFollowEventDependencies, &no);
+        if (e == cudaSuccess) e = cudaMemPoolSetAttribute(p, cudaMemPoolReuseAllowInternalDependencies, &no);
         if (e != cudaSuccess) {
             cudaMemPoolDestroy(p);
             return e;

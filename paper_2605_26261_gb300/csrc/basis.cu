@@ -278,6 +278,13 @@ extern "C" ftlm_status ftlm_basis_create(int N, int two_sz, int n_bonds, const i
                                          const int *bj, const double *J, ftlm_rank_mode mode,
                                          void *stream_, ftlm_basis **out)
 {
+    return ftlm::basis_create_half(N, two_sz, n_bonds, bi, bj, J, mode, (cudaStream_t)stream_, true, out);
+}
+
+// wait: return once the tables are built (else once their build is queued).
+ftlm_status ftlm::basis_create_half(int N, int two_sz, int n_bonds, const int *bi, const int *bj, const double *J,
+                                    ftlm_rank_mode mode, cudaStream_t stream_, bool wait, ftlm_basis **out)
+{
     if (!out) return fail(FTLM_EINVAL, "out is NULL");
     *out = nullptr;
     if (N < 1 || N > FTLM_MAX_SITES) return fail(FTLM_EINVAL, "N out of range");
@@ -556,8 +563,9 @@ extern "C" ftlm_status ftlm_basis_create(int N, int two_sz, int n_bonds, const i
         }
         e = cudaGetLastError();
     }
-    // The tables are complete when create returns (only this stream is waited for).
-    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    // With wait, the tables are complete when create returns (only this stream is
+    // waited for).
+    if (e == cudaSuccess && wait) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) {
         cudaFreeAsync(b->block, stream);
         delete b;

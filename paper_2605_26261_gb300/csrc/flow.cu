@@ -92,6 +92,14 @@ struct FlowItem {
     bool live;
 };
 
+// A wave stream of the flow and the event that joins it back to the caller's.
+struct FlowSlot {
+    cudaStream_t s;
+    cudaEvent_t join;
+};
+constexpr int kFlowSlots = 4;      // wave streams at most
+constexpr int kFlowSlotsDefault = 4;
+
 int kind_of(const ftlm_basis *b) { return b->two_s > 1 ? kMsSpin : (b->mode == FTLM_RANK_CLT ? kMsClt : kMsCr); }
 
 // Region of one unit of B chains of b: two vector blocks, states and counter, and
@@ -128,11 +136,14 @@ struct ftlm_flow {
     char *units_base;  // start of the unit regions (the ws of the msv kernels)
     uint64_t units_bytes;
     ftlm::RangeAlloc region, chains;
-    // device descriptors: units, per-kind H.v tile maps, streaming tile map, finished
-    // list, Ritz rows
+    // device descriptors of a step call's waves: units, per-kind H.v tile maps,
+    // streaming tile map, finished lists; and the Ritz rows
     void *dev_block;
     ftlm::MsUnit *d_units;
     uint32_t *d_tile[3], *d_stile, *d_fin;
+    ftlm::FlowSlot slot[ftlm::kFlowSlots];
+    int n_slots;           // wave streams in use (ftlm_flow_set_streams)
+    cudaEvent_t ev_fork;   // the caller's stream at the start of a step call
     ftlm::RitzRow *d_ritz;
     // the Ritz launches: own stream, the event it waits for on the caller's stream,
     // the event after its latest launch, and the coefficient rows (offset, count)
@@ -152,7 +163,6 @@ struct ftlm_flow {
     std::vector<int> done;  // tickets whose outputs are queued
     int next_ticket;
     uint64_t wave_bytes;  // vector bytes per wave
-    uint32_t kind_first[3], kind_count[3], n_tiles[3], n_stiles;
 };
 
 using namespace ftlm;
@@ -168,30 +178,73 @@ ftlm_status stage_next(ftlm_flow *f, char **buf)
     return FTLM_OK;
 }
 
-// Descriptors and tile maps of the units of one wave (indices into f->units),
-// ordered by rank kind; a unit's launches run as step j - j0 with j0 = -done, so
-// launch j = 1, 2, ... of the wave is the unit's step done + j.  order receives
-// the wave's units in descriptor order.
-ftlm_status upload(ftlm_flow *f, const std::vector<uint32_t> &wave, std::vector<uint32_t> &order, cudaStream_t stream)
+// One wave of a step call: its units (indices into f->units) in descriptor order,
+// grouped by rank kind, and where its descriptors, tile maps and finished list sit
+// in the call's upload.  A unit's launches run as step j - j0 with j0 = -done, so
+// launch j = 1, 2, ... of the wave is the unit's step done + j.
+struct WavePlan {
+    std::vector<uint32_t> order;
+    uint32_t unit0;                       // first descriptor of the wave
+    uint32_t kind_first[3], kind_count[3];  // descriptor ranges per kind (wave-local)
+    uint32_t tile0[3], n_tiles[3];        // ranges of the kinds' H.v tile maps
+    uint32_t stile0, n_stiles;            // range of the streaming tile map
+    uint32_t fin0, n_fin;                 // wave-local positions of units that finish
+    int steps;                            // Lanczos steps of this call
+    bool fresh;                           // some unit starts now
+    uint64_t load;                        // rows x steps
+};
+
+// Plans of the waves (consecutive units in admission order, at most wave_bytes of
+// vectors each) and their descriptors, tile maps and finished lists, uploaded to
+// the device in one copy per array on `stream`.
+ftlm_status plan_waves(ftlm_flow *f, int steps, std::vector<WavePlan> &waves, cudaStream_t stream)
 {
-    std::vector<MsUnit> du;
-    std::vector<uint32_t> tiles[3], stiles;
-    order.clear();
-    for (int kind = 0; kind < 3; ++kind) {
-        f->kind_first[kind] = (uint32_t)order.size();
-        for (uint32_t i : wave)
-            if (f->units[i].kind == kind) order.push_back(i);
-        f->kind_count[kind] = (uint32_t)order.size() - f->kind_first[kind];
+    std::vector<std::vector<uint32_t>> groups;
+    uint64_t wb = 0;
+    for (uint32_t i = 0; i < f->units.size(); ++i) {
+        const FlowUnit &u = f->units[i];
+        if (groups.empty() || wb + u.vbytes > f->wave_bytes) {
+            groups.emplace_back();
+            wb = 0;
+        }
+        groups.back().push_back(i);
+        wb += u.vbytes;
     }
-    for (uint32_t pos = 0; pos < order.size(); ++pos) {
-        MsUnit u = f->units[order[pos]].u;
-        const int kind = f->units[order[pos]].kind;
-        u.j0 = -f->units[order[pos]].done;
-        u.tile0 = (uint32_t)tiles[kind].size();
-        for (uint32_t k = 0; k < u.n_tiles; ++k) tiles[kind].push_back(pos - f->kind_first[kind]);  // kind-local
-        u.stile0 = (uint32_t)stiles.size();
-        for (uint32_t k = 0; k < u.n_stiles; ++k) stiles.push_back(pos);  // wave-wide index
-        du.push_back(u);
+    std::vector<MsUnit> du;
+    std::vector<uint32_t> tiles[3], stiles, fins;
+    waves.assign(groups.size(), WavePlan{});
+    for (size_t w = 0; w < groups.size(); ++w) {
+        WavePlan &p = waves[w];
+        p.unit0 = (uint32_t)du.size();
+        for (int kind = 0; kind < 3; ++kind) {
+            p.kind_first[kind] = (uint32_t)p.order.size();
+            for (uint32_t i : groups[w])
+                if (f->units[i].kind == kind) p.order.push_back(i);
+            p.kind_count[kind] = (uint32_t)p.order.size() - p.kind_first[kind];
+            p.tile0[kind] = (uint32_t)tiles[kind].size();
+        }
+        p.stile0 = (uint32_t)stiles.size();
+        p.fin0 = (uint32_t)fins.size();
+        int need = 0;
+        for (uint32_t i : p.order) need = std::max(need, f->units[i].u.m_max - f->units[i].done);
+        p.steps = std::min(steps, need);
+        for (uint32_t pos = 0; pos < p.order.size(); ++pos) {
+            const FlowUnit &fu = f->units[p.order[pos]];
+            MsUnit u = fu.u;
+            const int kind = fu.kind;
+            u.j0 = -fu.done;
+            u.tile0 = (uint32_t)tiles[kind].size() - p.tile0[kind];
+            for (uint32_t k = 0; k < u.n_tiles; ++k) tiles[kind].push_back(pos - p.kind_first[kind]);  // kind-local
+            u.stile0 = (uint32_t)stiles.size() - p.stile0;
+            for (uint32_t k = 0; k < u.n_stiles; ++k) stiles.push_back(pos);  // wave-local
+            du.push_back(u);
+            p.fresh |= fu.done == 0;
+            if (fu.done + p.steps >= fu.u.m_max) fins.push_back(pos);
+            p.load += fu.u.s.D * (uint64_t)std::max(0, std::min(p.steps, fu.u.m_max - fu.done));
+        }
+        for (int kind = 0; kind < 3; ++kind) p.n_tiles[kind] = (uint32_t)tiles[kind].size() - p.tile0[kind];
+        p.n_stiles = (uint32_t)stiles.size() - p.stile0;
+        p.n_fin = (uint32_t)fins.size() - p.fin0;
     }
     for (int kind = 0; kind < 3; ++kind)
         if (tiles[kind].size() > f->cap_tiles) return fail(FTLM_ENOMEM, "flow tile map full");
@@ -208,72 +261,52 @@ ftlm_status upload(ftlm_flow *f, const std::vector<uint32_t> &wave, std::vector<
         return e;
     };
     FTLM_CUDA(put(f->d_units, du.data(), du.size() * sizeof(MsUnit)));
-    for (int kind = 0; kind < 3; ++kind) {
-        f->n_tiles[kind] = (uint32_t)tiles[kind].size();
+    for (int kind = 0; kind < 3; ++kind)
         FTLM_CUDA(put(f->d_tile[kind], tiles[kind].data(), tiles[kind].size() * sizeof(uint32_t)));
-    }
-    f->n_stiles = (uint32_t)stiles.size();
     FTLM_CUDA(put(f->d_stile, stiles.data(), stiles.size() * sizeof(uint32_t)));
+    FTLM_CUDA(put(f->d_fin, fins.data(), fins.size() * sizeof(uint32_t)));
     FTLM_CUDA(cudaEventRecord(f->stage_ev[f->stage_cur], stream));
     return FTLM_OK;
 }
 
-// `steps` Lanczos steps of one wave: start vectors of its new units, then per step
-// one H.v launch per rank kind and one update launch; afterwards the chain lengths
-// of the units that reached their last step.  Returns in fin the indices (into
-// f->units) of finished units and appends to ritz the sectors whose units are all
-// done.
-ftlm_status run_wave(ftlm_flow *f, const std::vector<uint32_t> &wave, int steps, cudaStream_t stream,
-                     std::vector<uint32_t> &fin, std::vector<int> &ritz)
+// The launches of one wave on `stream`: start vectors of its new units, then per
+// step one H.v launch per rank kind and one update launch, then the chain lengths
+// of its units that reach their last step.  Appends to fin the indices (into
+// f->units) of those units and to ritz the sectors whose units are all done.
+ftlm_status run_wave(ftlm_flow *f, const WavePlan &p, cudaStream_t stream, std::vector<uint32_t> &fin,
+                     std::vector<int> &ritz)
 {
-    std::vector<uint32_t> order;
-    ftlm_status s = upload(f, wave, order, stream);
-    if (s != FTLM_OK) return s;
-    bool fresh = false;
-    for (uint32_t i : wave) fresh |= f->units[i].done == 0;
-    if (fresh) {  // units with j0 == 0: reset and start vectors
-        s = ms_flow_start(f->dtype, f->B, f->d_units, (uint32_t)order.size(), f->d_stile, f->n_stiles, 0, f->dist,
-                          f->units_base, f->num_sms, stream);
+    const MsUnit *units = f->d_units + p.unit0;
+    const uint32_t *stile = f->d_stile + p.stile0;
+    const uint32_t n_units = (uint32_t)p.order.size();
+    ftlm_status s;
+    if (p.fresh) {  // units with j0 == 0: reset and start vectors
+        s = ms_flow_start(f->dtype, f->B, units, n_units, stile, p.n_stiles, 0, f->dist, f->units_base, f->num_sms,
+                          stream);
         if (s != FTLM_OK) return s;
     }
-    int need = 0;  // steps any unit of the wave still has
-    for (uint32_t i : wave) need = std::max(need, f->units[i].u.m_max - f->units[i].done);
-    const int n = std::min(steps, need);
-    for (int j = 1; j <= n; ++j) {
+    for (int j = 1; j <= p.steps; ++j) {
         for (int kind = 0; kind < 3; ++kind) {
-            if (!f->kind_count[kind]) continue;
-            s = ms_flow_hv(f->dtype, f->B, kind, f->d_units + f->kind_first[kind], f->d_tile[kind], f->n_tiles[kind], j,
-                           f->M, f->alpha, f->units_base, f->num_sms, stream);
+            if (!p.kind_count[kind]) continue;
+            s = ms_flow_hv(f->dtype, f->B, kind, units + p.kind_first[kind], f->d_tile[kind] + p.tile0[kind],
+                           p.n_tiles[kind], j, f->M, f->alpha, f->units_base, f->num_sms, stream);
             if (s != FTLM_OK) return s;
         }
-        s = ms_flow_update(f->dtype, f->B, f->d_units, f->d_stile, f->n_stiles, j, f->M, f->beta, f->units_base,
-                           f->num_sms, stream);
+        s = ms_flow_update(f->dtype, f->B, units, stile, p.n_stiles, j, f->M, f->beta, f->units_base, f->num_sms,
+                           stream);
         if (s != FTLM_OK) return s;
     }
-    std::vector<uint32_t> fin_pos;  // positions in the wave's descriptor array
-    for (uint32_t pos = 0; pos < order.size(); ++pos) {
-        FlowUnit &u = f->units[order[pos]];
-        u.done = std::min(u.u.m_max, u.done + n);
-        if (u.done >= u.u.m_max) {
-            fin_pos.push_back(pos);
-            fin.push_back(order[pos]);
-        }
+    if (p.n_fin) {
+        flow_meff_kernel<<<(unsigned)((p.n_fin * f->B + 255) / 256), 256, 0, stream>>>(
+            units, f->d_fin + p.fin0, p.n_fin, f->B, f->meff, f->units_base);
+        note_launch();
+        FTLM_CUDA(cudaGetLastError());
     }
-    if (fin_pos.empty()) return FTLM_OK;
-    {
-        char *buf = nullptr;
-        s = stage_next(f, &buf);
-        if (s != FTLM_OK) return s;
-        std::memcpy(buf, fin_pos.data(), fin_pos.size() * sizeof(uint32_t));
-        FTLM_CUDA(cudaMemcpyAsync(f->d_fin, buf, fin_pos.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, stream));
-        FTLM_CUDA(cudaEventRecord(f->stage_ev[f->stage_cur], stream));
-    }
-    flow_meff_kernel<<<(unsigned)((fin_pos.size() * f->B + 255) / 256), 256, 0, stream>>>(
-        f->d_units, f->d_fin, (uint32_t)fin_pos.size(), f->B, f->meff, f->units_base);
-    note_launch();
-    FTLM_CUDA(cudaGetLastError());
-    for (uint32_t i : fin_pos) {
-        FlowUnit &u = f->units[order[i]];
+    for (uint32_t i : p.order) {
+        FlowUnit &u = f->units[i];
+        u.done = std::min(u.u.m_max, u.done + p.steps);
+        if (u.done < u.u.m_max) continue;
+        fin.push_back(i);
         f->region.give(u.off, u.bytes);
         FlowItem &it = f->items[u.item];
         if (--it.units_left == 0) ritz.push_back(u.item);
@@ -394,6 +427,8 @@ extern "C" ftlm_status ftlm_flow_create(ftlm_dtype dtype, int block, int M, ftlm
     const uint64_t rows = f->units_bytes / (2ull * block * (dtype == FTLM_F32 ? 4 : 8));
     f->cap_tiles = rows / kMsTileRows + max_units + 1;
     f->cap_stiles = rows / kMsStreamRows + max_units + 1;
+    // [units | 3 H.v tile maps | streaming map | finished lists | Ritz rows]; the
+    // tiles of every unit together number at most cap_tiles (cap_stiles)
     const uint64_t o_units = 0;
     const uint64_t o_tile = align256((uint64_t)max_units * sizeof(MsUnit));
     const uint64_t o_stile = o_tile + 3 * align256(f->cap_tiles * sizeof(uint32_t));
@@ -408,9 +443,18 @@ extern "C" ftlm_status ftlm_flow_create(ftlm_dtype dtype, int block, int M, ftlm
         return e == cudaErrorMemoryAllocation ? fail(FTLM_ENOMEM, "no device memory for the flow descriptors")
                                               : cuda_fail(e, "cudaMallocFromPoolAsync(flow)");
     }
-    // pinned staging: descriptors, three H.v tile maps and the streaming map of a
-    // wave, or a finished list, or the Ritz rows of a step call
-    f->stage_bytes = std::max<uint64_t>(o_fin + 6 * 256, total - o_ritz);
+    // pinned staging: the descriptors, tile maps (of all kinds together at most
+    // cap_tiles) and finished lists of a step call's waves, or its Ritz rows
+    f->stage_bytes = std::max<uint64_t>(o_tile + align256(f->cap_tiles * sizeof(uint32_t)) +
+                                            align256(f->cap_stiles * sizeof(uint32_t)) +
+                                            align256((uint64_t)max_units * sizeof(uint32_t)) + 6 * 256,
+                                        total - o_ritz);
+    f->n_slots = kFlowSlotsDefault;
+    f->ev_fork = nullptr;
+    for (int k = 0; k < kFlowSlots; ++k) {
+        f->slot[k].s = nullptr;
+        f->slot[k].join = nullptr;
+    }
     for (int k = 0; k < ftlm_flow::kStages; ++k) {
         f->stage[k] = nullptr;
         f->stage_ev[k] = nullptr;
@@ -425,6 +469,11 @@ extern "C" ftlm_status ftlm_flow_create(ftlm_dtype dtype, int block, int M, ftlm
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&f->rz, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f->ev_main, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f->ev_rz, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f->ev_fork, cudaEventDisableTiming);
+    for (int k = 0; k < kFlowSlots && e == cudaSuccess; ++k) {
+        e = cudaStreamCreateWithFlags(&f->slot[k].s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f->slot[k].join, cudaEventDisableTiming);
+    }
     if (e != cudaSuccess) {
         for (int k = 0; k < ftlm_flow::kStages; ++k) {
             if (f->stage[k]) cudaFreeHost(f->stage[k]);
@@ -433,9 +482,14 @@ extern "C" ftlm_status ftlm_flow_create(ftlm_dtype dtype, int block, int M, ftlm
         if (f->rz) cudaStreamDestroy(f->rz);
         if (f->ev_main) cudaEventDestroy(f->ev_main);
         if (f->ev_rz) cudaEventDestroy(f->ev_rz);
+        if (f->ev_fork) cudaEventDestroy(f->ev_fork);
+        for (int k = 0; k < kFlowSlots; ++k) {
+            if (f->slot[k].s) cudaStreamDestroy(f->slot[k].s);
+            if (f->slot[k].join) cudaEventDestroy(f->slot[k].join);
+        }
         cudaFreeAsync(f->dev_block, stream);
         delete f;
-        return cuda_fail(e, "flow staging buffers and Ritz stream");
+        return cuda_fail(e, "flow staging buffers and streams");
     }
     char *base = (char *)f->dev_block;
     f->d_units = (MsUnit *)(base + o_units);
@@ -537,22 +591,35 @@ extern "C" ftlm_status ftlm_flow_step(ftlm_flow *f, int steps, void *stream_)
             FTLM_CUDA(cudaMemsetAsync(f->alpha + (size_t)it.chain_base * f->M, 0, rows, stream));
             FTLM_CUDA(cudaMemsetAsync(f->beta + (size_t)it.chain_base * f->M, 0, rows, stream));
         }
-    // waves: consecutive units (in admission order) up to wave_bytes of vectors
-    std::vector<uint32_t> fin, wave;
-    std::vector<int> ritz;
-    uint64_t wb = 0;
-    for (uint32_t i = 0; i <= f->units.size(); ++i) {
-        const bool end = i == f->units.size();
-        if (!wave.empty() && (end || wb + f->units[i].vbytes > f->wave_bytes)) {
-            st = run_wave(f, wave, steps, stream, fin, ritz);
-            if (st != FTLM_OK) return st;
-            wave.clear();
-            wb = 0;
-        }
-        if (end) break;
-        wave.push_back(i);
-        wb += f->units[i].vbytes;
+    std::vector<WavePlan> waves;
+    st = plan_waves(f, steps, waves, stream);
+    if (st != FTLM_OK) return st;
+    // each wave on the least loaded wave stream (the waves of one stream run in
+    // order); the wave streams start after the caller's stream (the upload above)
+    // and it waits for them
+    const int ns = std::min<int>(f->n_slots, (int)waves.size());
+    std::vector<uint64_t> load(ns, 0);
+    std::vector<int> slot_of(waves.size(), 0);
+    for (size_t w = 0; w < waves.size(); ++w) {
+        const int q = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        slot_of[w] = q;
+        load[q] += waves[w].load;
     }
+    if (ns > 1) {
+        FTLM_CUDA(cudaEventRecord(f->ev_fork, stream));
+        for (int q = 0; q < ns; ++q) FTLM_CUDA(cudaStreamWaitEvent(f->slot[q].s, f->ev_fork, 0));
+    }
+    std::vector<uint32_t> fin;
+    std::vector<int> ritz;
+    for (size_t w = 0; w < waves.size(); ++w) {
+        st = run_wave(f, waves[w], ns > 1 ? f->slot[slot_of[w]].s : stream, fin, ritz);
+        if (st != FTLM_OK) return st;
+    }
+    if (ns > 1)
+        for (int q = 0; q < ns; ++q) {
+            FTLM_CUDA(cudaEventRecord(f->slot[q].join, f->slot[q].s));
+            FTLM_CUDA(cudaStreamWaitEvent(stream, f->slot[q].join, 0));
+        }
     if (!fin.empty()) {
         std::vector<bool> gone(f->units.size(), false);
         for (uint32_t i : fin) gone[i] = true;
@@ -562,6 +629,14 @@ extern "C" ftlm_status ftlm_flow_step(ftlm_flow *f, int steps, void *stream_)
         f->units = keep;
     }
     return queue_ritz(f, ritz, stream);
+}
+
+extern "C" ftlm_status ftlm_flow_set_streams(ftlm_flow *f, int n)
+{
+    if (!f) return fail(FTLM_EINVAL, "NULL flow");
+    if (n < 1 || n > kFlowSlots) return fail(FTLM_EINVAL, "wave streams must be 1 .. 4");
+    f->n_slots = n;
+    return FTLM_OK;
 }
 
 extern "C" ftlm_status ftlm_flow_wait_outputs(ftlm_flow *f, void *stream)
@@ -606,5 +681,10 @@ extern "C" void ftlm_flow_destroy(ftlm_flow *f)
     cudaStreamDestroy(f->rz);
     cudaEventDestroy(f->ev_main);
     cudaEventDestroy(f->ev_rz);
+    cudaEventDestroy(f->ev_fork);
+    for (int k = 0; k < kFlowSlots; ++k) {
+        cudaStreamDestroy(f->slot[k].s);
+        cudaEventDestroy(f->slot[k].join);
+    }
     delete f;
 }

@@ -266,6 +266,12 @@ uint64_t lanczos_workspace(const ftlm_basis *b, int R, int M, ftlm_dtype dtype, 
 int ritz_max_sweeps();
 ftlm_status ritz_unconverged_take(cudaStream_t stream, uint64_t *count);
 ftlm_status ghost_unconverged_take(cudaStream_t stream, uint64_t *count);
+// Sector creation (ftlm_basis_create, ftlm_basis_create_spin); wait: return once
+// the tables are built on `stream`, else once their build is queued.
+ftlm_status basis_create_half(int N, int two_sz, int n_bonds, const int *bi, const int *bj, const double *J,
+                              ftlm_rank_mode mode, cudaStream_t stream, bool wait, ftlm_basis **out);
+ftlm_status basis_create_spin(int N, int two_s, int two_sz, int n_bonds, const int *bi, const int *bj,
+                              const double *J, cudaStream_t stream, bool wait, ftlm_basis **out);
 // Ritz step of n chains (alpha/beta rows of length M, m_eff per chain).
 ftlm_status launch_ritz(int n, int M, const double *alpha, const double *beta, const int *mv, double *theta,
                         double *weight, cudaStream_t stream);

@@ -229,10 +229,17 @@ using namespace ftlm;
 extern "C" ftlm_status ftlm_basis_create_spin(int N, int two_s, int two_sz, int n_bonds, const int *bi,
                                               const int *bj, const double *J, void *stream_, ftlm_basis **out)
 {
+    return basis_create_spin(N, two_s, two_sz, n_bonds, bi, bj, J, (cudaStream_t)stream_, true, out);
+}
+
+// wait: return once the tables are built (else once their build is queued).
+ftlm_status ftlm::basis_create_spin(int N, int two_s, int two_sz, int n_bonds, const int *bi, const int *bj,
+                                    const double *J, cudaStream_t stream_, bool wait, ftlm_basis **out)
+{
     if (!out) return fail(FTLM_EINVAL, "out is NULL");
     *out = nullptr;
     if (two_s < 1) return fail(FTLM_EINVAL, "two_s < 1");
-    if (two_s == 1) return ftlm_basis_create(N, two_sz, n_bonds, bi, bj, J, FTLM_RANK_AUTO, stream_, out);
+    if (two_s == 1) return basis_create_half(N, two_sz, n_bonds, bi, bj, J, FTLM_RANK_AUTO, stream_, wait, out);
     if (two_s > kSpinMaxTwoS) return fail(FTLM_EUNSUPPORTED, "spin above 7/2");
     if (N < 1) return fail(FTLM_EINVAL, "N out of range");
     if (N > kSpinMaxSites) return fail(FTLM_EUNSUPPORTED, "more than 16 sites at s > 1/2");
@@ -424,7 +431,7 @@ extern "C" ftlm_status ftlm_basis_create_spin(int N, int two_s, int two_sz, int 
         launch_hs_fill(b, stream);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e == cudaSuccess && wait) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) {
         cudaFreeAsync(b->block, stream);
         delete b;
@@ -432,4 +439,29 @@ extern "C" ftlm_status ftlm_basis_create_spin(int N, int two_s, int two_sz, int 
     }
     *out = b;
     return FTLM_OK;
+}
+
+extern "C" ftlm_status ftlm_basis_create_sectors(int N, int two_s, int n, const int *two_sz, int n_bonds,
+                                                 const int *bi, const int *bj, const double *J, ftlm_rank_mode mode,
+                                                 int wait, void *stream_, ftlm_basis **out)
+{
+    if (!out || !two_sz) return fail(FTLM_EINVAL, "NULL argument");
+    if (n < 1 || n > FTLM_MAX_SECTORS) return fail(FTLM_EINVAL, "n out of range");
+    for (int k = 0; k < n; ++k) out[k] = nullptr;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    ftlm_status st = FTLM_OK;
+    for (int k = 0; k < n && st == FTLM_OK; ++k)
+        st = two_s == 1 ? basis_create_half(N, two_sz[k], n_bonds, bi, bj, J, mode, stream, false, &out[k])
+                        : basis_create_spin(N, two_s, two_sz[k], n_bonds, bi, bj, J, stream, false, &out[k]);
+    if (st == FTLM_OK && wait) {
+        const cudaError_t e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "sector table build");
+    }
+    if (st != FTLM_OK) {  // keeps the first error's message; frees in stream order
+        for (int k = 0; k < n; ++k) {
+            ftlm_basis_destroy_async(out[k], stream_);
+            out[k] = nullptr;
+        }
+    }
+    return st;
 }

@@ -72,6 +72,7 @@ def lib():
     sig = {
         "ftlm_basis_create": [I, I, I, P, P, P, I, P, ctypes.POINTER(P)],
         "ftlm_basis_create_spin": [I, I, I, I, P, P, P, P, ctypes.POINTER(P)],
+        "ftlm_basis_create_sectors": [I, I, I, P, I, P, P, P, I, I, P, P],
         "ftlm_basis_dim": [P, PU64],
         "ftlm_basis_bytes": [P, PU64],
         "ftlm_basis_mode": [P, ctypes.POINTER(I)],
@@ -113,6 +114,7 @@ def lib():
         "ftlm_flow_step": [P, I, P],
         "ftlm_flow_done": [P, P, I, ctypes.POINTER(I)],
         "ftlm_flow_wait_outputs": [P, P],
+        "ftlm_flow_set_streams": [P, I],
         "ftlm_flow_status": [P, ctypes.POINTER(I), ctypes.POINTER(I), PU64],
     }
     for name, args in sig.items():
@@ -459,14 +461,33 @@ def ftlm_profile_read():
 
 
 # --------------------------------------------------------------- convenience
-class Basis:
-    """One S^z sector of a cluster on the current CUDA device (owns the handle)."""
+def ftlm_basis_create_sectors(N, two_s, two_sz, bi, bj, J, mode=RANK_AUTO, wait=True, stream=None):
+    """Handles of the sectors two_sz (a list) of one cluster: one wait for all
+    tables, or (wait=False) none: uses on other streams must follow `stream`."""
+    bi = np.ascontiguousarray(bi, dtype=np.int32)
+    bj = np.ascontiguousarray(bj, dtype=np.int32)
+    J = np.ascontiguousarray(J, dtype=np.float64)
+    if not (len(bi) == len(bj) == len(J)):
+        raise ValueError("bond arrays differ in length")
+    tz = np.ascontiguousarray(two_sz, dtype=np.int32)
+    out = (ctypes.c_void_p * len(tz))()
+    _check(lib().ftlm_basis_create_sectors(int(N), int(two_s), len(tz), tz.ctypes.data, len(J), bi.ctypes.data,
+                                           bj.ctypes.data, J.ctypes.data, int(mode), int(bool(wait)),
+                                           _stream(stream), out))
+    return [ctypes.c_void_p(out[k]) for k in range(len(tz))]
 
-    def __init__(self, N, two_sz, bonds, mode=RANK_AUTO, stream=None, two_s=1):
+
+class Basis:
+    """One S^z sector of a cluster on the current CUDA device (owns the handle).
+    Basis.sectors builds several sectors of one cluster with one wait."""
+
+    def __init__(self, N, two_sz, bonds, mode=RANK_AUTO, stream=None, two_s=1, handle=None):
         bi, bj, J = bonds
         self.N, self.two_sz, self.two_s = int(N), int(two_sz), int(two_s)
         self.K = (self.N * self.two_s + self.two_sz) // 2  # digit sum (up spins at s = 1/2)
-        if self.two_s == 1:
+        if handle is not None:
+            self.handle = handle
+        elif self.two_s == 1:
             self.handle = ftlm_basis_create(N, two_sz, bi, bj, J, mode, stream)
         else:
             self.handle = ftlm_basis_create_spin(N, two_s, two_sz, bi, bj, J, stream)
@@ -474,6 +495,12 @@ class Basis:
         self.table_bytes = ftlm_basis_bytes(self.handle)
         self.mode = ftlm_basis_mode(self.handle)
         self.updates = ftlm_basis_updates(self.handle)
+
+    @classmethod
+    def sectors(cls, N, two_sz, bonds, mode=RANK_AUTO, stream=None, two_s=1, wait=True):
+        """The sectors two_sz (a list) of one cluster (ftlm_basis_create_sectors)."""
+        hs = ftlm_basis_create_sectors(N, two_s, two_sz, *bonds, mode=mode, wait=wait, stream=stream)
+        return [cls(N, tz, bonds, mode, two_s=two_s, handle=h) for tz, h in zip(two_sz, hs)]
 
     def set_schedule(self, schedule, rows_per_tile=0):
         """ftlm_basis_set_schedule: walks of the Lanczos H.v launches of this sector."""
@@ -630,11 +657,13 @@ class Flow:
     """Continuous Lanczos flow (ftlm_flow_*): sectors join and leave at Lanczos-step
     boundaries.  The workspace is a torch tensor of work_bytes (default: 60 % of the
     free device memory); add() returns a ticket, or None when the sector does not
-    fit now; done(stream) returns (ticket, outputs, owner) of finished sectors and
+    fit now; streams: wave streams (1..4, default 4); done(stream) returns
+    (ticket, outputs, owner) of finished sectors and
     makes `stream` (default: the current stream) wait until their outputs are
     written (their Ritz step runs on the flow's own stream)."""
 
-    def __init__(self, M, dist=GAUSS, dtype=torch.float32, block=8, max_units=512, work_bytes=None, stream=None):
+    def __init__(self, M, dist=GAUSS, dtype=torch.float32, block=8, max_units=512, work_bytes=None, stream=None,
+                 streams=None):
         self.dev = torch.device("cuda", torch.cuda.current_device())
         self.M, self.block = int(M), int(block)
         if work_bytes is None:
@@ -646,11 +675,15 @@ class Flow:
                                       _ptr(self.work), self.work.numel(), _stream(stream), ctypes.byref(out)))
         self.handle = out
         self.outputs = {}  # ticket -> (outputs dict, owner)
+        if streams is not None:
+            _check(lib().ftlm_flow_set_streams(self.handle, int(streams)))
 
     def add(self, basis, R, seed, first_chain=0, owner=None):
-        out = {"theta": torch.zeros((R, self.M), dtype=torch.float64, device=self.dev),
-               "weight": torch.zeros((R, self.M), dtype=torch.float64, device=self.dev),
-               "m_eff": torch.zeros(R, dtype=torch.int32, device=self.dev)}
+        # no fill kernel: the Ritz launch writes every entry, on the flow's own stream,
+        # which is not ordered after the caller's current stream
+        out = {"theta": torch.empty((R, self.M), dtype=torch.float64, device=self.dev),
+               "weight": torch.empty((R, self.M), dtype=torch.float64, device=self.dev),
+               "m_eff": torch.empty(R, dtype=torch.int32, device=self.dev)}
         item = BatchItem(basis.handle.value, int(R), int(first_chain), int(seed) & (2**64 - 1),
                          out["theta"].data_ptr(), out["weight"].data_ptr(), out["m_eff"].data_ptr())
         t = ctypes.c_int()

@@ -20,8 +20,10 @@ bit-identical whether it runs alone or among other jobs, and whenever it was
 admitted.  The flow's Lanczos steps are queued on one stream and its Ritz steps run
 on the flow's own stream; a job's thermodynamic sums and result copies go on a
 third stream that waits for the job's outputs, so neither holds up the next
-steps.  Sector tables are built on a side stream (creation waits only for that
-stream) and released in the sums stream's order once the job's sums are queued.
+steps.  Sector tables are built on a high-priority side stream without a host
+wait (the flow's stream and the small batches' stream wait for an event instead:
+the host never blocks on the busy device to admit a job) and released in the sums
+stream's order once the job's sums are queued.
 
 Everything on the device goes through the C ABI of libftlm (ftlm.py); this module
 only schedules.  Host clocks (time.perf_counter) stamp arrival, start and finish.
@@ -111,6 +113,12 @@ class Engine:
     steps_per_poll  Lanczos steps of each wave of the flow per admission pass
     depth           admission passes queued ahead of the device at most
     small_rows      sectors up to this dimension run in a job's own persistent batch
+    flow_streams    wave streams of the flow (1..4)
+    max_live_rows   rows of the flow's sectors in flight at most (None: no limit
+                    beyond memory); the head job's sector is admitted into an empty
+                    flow whatever its size.  A limit that still fills the GPU keeps
+                    throughput and lets jobs finish in arrival order, instead of
+                    all sharing the device until the end of the stream
 
     A job's sectors of at most small_rows rows run all their steps in one persistent
     launch (ftlm_batch, a CTA per block of chains) on a side stream as soon as the
@@ -119,7 +127,7 @@ class Engine:
 
     def __init__(self, R=8, M=80, dtype=torch.float32, block=8, T=None, g=2.0, dist=ftlm.GAUSS,
                  memory_budget=None, max_units=512, max_jobs=None, steps_per_poll=8, depth=2,
-                 small_rows=1 << 15):
+                 small_rows=1 << 15, flow_streams=4, max_live_rows=None):
         self.dev = torch.device("cuda", torch.cuda.current_device())
         self.R, self.M, self.dtype, self.block = R, M, dtype, block
         self.g, self.dist = g, dist
@@ -130,18 +138,24 @@ class Engine:
             free, _ = torch.cuda.mem_get_info(self.dev)
             memory_budget = int(0.6 * free)
         self.stream = torch.cuda.Stream(self.dev)   # the flow's Lanczos steps
-        self.side = torch.cuda.Stream(self.dev)     # sector tables and batch plans
+        # sector tables (built without a host wait; the streams that use them wait
+        # for an event), high priority so that they run as soon as SMs free up
+        self.side = torch.cuda.Stream(self.dev, priority=-1)
+        self.plans = torch.cuda.Stream(self.dev)    # batch plan uploads (copies only)
         self.small = torch.cuda.Stream(self.dev)    # the small sectors' persistent batches
         self.tstream = torch.cuda.Stream(self.dev)  # thermodynamic sums and result copies
-        self.flow = ftlm.Flow(M, dist, dtype, block, max_units, memory_budget, stream=self.stream)
+        self.flow = ftlm.Flow(M, dist, dtype, block, max_units, memory_budget, stream=self.stream,
+                              streams=flow_streams)
         self.queue = AdmissionQueue(max_jobs)
         self.steps_per_poll, self.depth, self.small_rows = steps_per_poll, depth, small_rows
+        self.max_live_rows, self.live_rows = max_live_rows, 0
         self.running = {}     # id(job) -> state dict (jobs need not have distinct job_id)
         self.closing = []
         self.finished = []
         self.inflight = collections.deque()
         self.stats = {"polls": 0, "max_jobs_in_flight": 0, "max_units": 0, "refusals": 0, "small_sectors": 0,
-                      "flow_sectors": 0}
+                      "flow_sectors": 0, "host_s": {"admit": 0.0, "step": 0.0, "wait": 0.0, "collect": 0.0,
+                                                     "tables": 0.0, "small_batch": 0.0}}
         self.t0 = time.perf_counter()
 
     def now(self):
@@ -163,14 +177,18 @@ class Engine:
         st = {"job": job, "bases": [None] * n, "outs": [None] * n, "left": len(job._large), "batch": None,
               "small_ev": None}
         self.running[id(job)] = st
-        with torch.cuda.stream(self.side):
-            for k, tz in enumerate(job._two_sz):
-                st["bases"][k] = ftlm.Basis(job.N, tz, job.bonds, stream=self.side)
+        t0 = time.perf_counter()
+        st["bases"] = ftlm.Basis.sectors(job.N, job._two_sz, job.bonds, stream=self.side, wait=False)
+        tables = torch.cuda.Event()
+        tables.record(self.side)
+        self.stream.wait_event(tables)  # the flow's next step call forks after this point
         small = [k for k in range(n) if k not in job._large]
+        t1 = time.perf_counter()
         if small:
+            self.small.wait_event(tables)
             with torch.cuda.stream(self.small):
                 batch = ftlm.Batch([(st["bases"][k], self.R, job.seed, 0) for k in small], self.M, self.dist,
-                                   self.dtype, self.block, 1, stream=self.side)
+                                   self.dtype, self.block, 1, stream=self.plans)
                 res = batch.run(self.small)
                 ev = torch.cuda.Event()
                 ev.record(self.small)
@@ -178,12 +196,18 @@ class Engine:
                 st["outs"][k] = r
             st["batch"], st["small_ev"] = batch, ev
             self.stats["small_sectors"] += len(small)
+        h = self.stats["host_s"]
+        h["tables"] += t1 - t0
+        h["small_batch"] += time.perf_counter() - t1
         job.start = self.now()
         if not job._large:
             self._close(st)
 
     def _try_add(self, job, k):
         st = self.running[id(job)]
+        d = st["bases"][k].dim
+        if self.max_live_rows is not None and self.live_rows > 0 and self.live_rows + d > self.max_live_rows:
+            return False
         t = self.flow.add(st["bases"][k], self.R, job.seed, 0, owner=(id(job), k))
         if t is None:
             self.stats["refusals"] += 1
@@ -191,6 +215,7 @@ class Engine:
                 raise RuntimeError(f"job {job.job_id}: a sector of N = {job.N} does not fit in an empty flow")
             return False
         self.stats["flow_sectors"] += 1
+        self.live_rows += d
         return True
 
     # ------------------------------------------------------------------- collect
@@ -198,6 +223,7 @@ class Engine:
         for ticket, out, (key, k) in self.flow.done(self.tstream):
             st = self.running[key]
             st["outs"][k] = out
+            self.live_rows -= st["bases"][k].dim
             st["left"] -= 1
             if st["left"] == 0:
                 self._close(st)
@@ -234,8 +260,8 @@ class Engine:
                 job.finish = self.now()
                 m = meff.numpy()
                 job.updates = int(sum(int(m[k].sum()) * upd[k] for k in range(len(upd))))
-                if entry[7] is not None:
-                    entry[7].close()
+                if entry[7] is not None:  # its work is done: release in stream order, no device-wide wait
+                    entry[7].release(self.tstream)
                 self.finished.append(job)
                 self.queue.finished()  # a job is in flight until its results are on the host
             else:
@@ -244,22 +270,33 @@ class Engine:
 
     # ---------------------------------------------------------------------- loop
     def poll(self):
-        """Admit, queue one pass of the flow, collect.  Returns True if it queued work."""
+        """Admit, queue one pass of the flow, collect.  Returns True if it queued work.
+        Host seconds spent admitting (tables, small batches), queueing passes,
+        waiting for the device and collecting accumulate in stats["host_s"]."""
+        t0 = time.perf_counter()
         self.queue.admit(self._start, self._try_add)
         self.stats["max_jobs_in_flight"] = max(self.stats["max_jobs_in_flight"], len(self.running) + len(self.closing))
         st = self.flow.status()
         self.stats["max_units"] = max(self.stats["max_units"], st["units"])
         busy = st["units"] > 0
+        t1 = t2 = time.perf_counter()
         if busy:
             self.flow.step(self.steps_per_poll, self.stream)
             self.stats["polls"] += 1
             ev = torch.cuda.Event()
             ev.record(self.stream)
             self.inflight.append(ev)
+            t2 = time.perf_counter()
             while len(self.inflight) > self.depth:
                 self.inflight.popleft().synchronize()
+        t3 = time.perf_counter()
         self._collect()
         self._retire()
+        h = self.stats["host_s"]
+        h["admit"] += t1 - t0
+        h["step"] += t2 - t1
+        h["wait"] += t3 - t2
+        h["collect"] += time.perf_counter() - t3
         return busy
 
     def run(self, jobs, arrivals=None, sleep=2e-4):

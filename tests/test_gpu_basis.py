@@ -102,3 +102,37 @@ def test_update_count_matches_eq10(cuda_dev, name, N, K, bonds):
 def test_auto_mode_picks_cr_when_clt_cannot_be_built(cuda_dev):
     with ftlm.Basis(34, 32, inputs.ring(34)) as b:  # N > 32: no CLT
         assert b.mode == ftlm.RANK_CR
+
+
+@pytest.mark.parametrize("wait", [True, False])
+@pytest.mark.parametrize("two_s, N", [(1, 16), (2, 8)])
+def test_create_sectors_equals_one_by_one(cuda_dev, two_s, N, wait):
+    """ftlm_basis_create_sectors (one wait for all tables, or none: the uses below
+    follow the builds on the same stream) builds the same sectors as single
+    creations: dimensions, update counts, labels and Lanczos coefficients."""
+    bonds = inputs.random_graph(N, seed=17)
+    two_sz = ftlm.computed_two_sz(N, two_s)
+    many = ftlm.Basis.sectors(N, two_sz, bonds, two_s=two_s, wait=wait)
+    for tz, b in zip(two_sz, many):
+        with ftlm.Basis(N, tz, bonds, two_s=two_s) as one:
+            assert (b.dim, b.updates, b.mode) == (one.dim, one.updates, one.mode)
+            n = min(b.dim, 4096)
+            la, lb = (torch.empty(n, dtype=torch.int64, device=cuda_dev) for _ in range(2))
+            ftlm.ftlm_basis_labels(b.handle, 0, n, la)
+            ftlm.ftlm_basis_labels(one.handle, 0, n, lb)
+            assert torch.equal(la, lb)
+            if b.dim >= 2:
+                m = min(10, b.dim)
+                r1 = ftlm.lanczos(b, 4, m, seed=3, dtype=torch.float64, keep_coeffs=True)
+                r2 = ftlm.lanczos(one, 4, m, seed=3, dtype=torch.float64, keep_coeffs=True)
+                for k in ("alpha", "beta", "theta", "weight", "m_eff"):
+                    assert torch.equal(r1[k], r2[k]), k
+        b.close()
+
+
+def test_create_sectors_rejects_bad_input_and_keeps_nothing(cuda_dev):
+    bonds = inputs.ring(10)
+    with pytest.raises(ftlm.FtlmError):
+        ftlm.ftlm_basis_create_sectors(10, 1, [0, 2, 3], *bonds)   # 2 S^z = 3 has the wrong parity
+    with pytest.raises(ftlm.FtlmError):
+        ftlm.ftlm_basis_create_sectors(10, 1, [], *bonds)

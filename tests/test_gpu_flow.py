@@ -124,3 +124,30 @@ def test_flow_reuses_coefficient_rows_after_the_ritz_launch(cuda_dev):
         for got, want in ((out1, alone[0]), (out2, alone[1])):
             for k in ("theta", "weight", "m_eff"):
                 assert torch.equal(got[k], want[k]), k
+
+
+def test_flow_wave_streams_do_not_change_results(cuda_dev):
+    """Sectors of 2.7 M rows (173 MB of vectors per unit) fill several 256 MB waves,
+    spread over 3 wave streams; every sector's results equal those of the flow with
+    all waves on one stream."""
+    M, R = 12, 8
+    r24, l24 = inputs.ring(24), inputs.ladder(24, 0.8, 1.2)
+    bases = [ftlm.Basis(24, 0, r24), ftlm.Basis(24, 0, l24), ftlm.Basis(24, 2, r24), ftlm.Basis(24, 4, l24),
+             ftlm.Basis(18, 0, inputs.ring(18)), ftlm.Basis(20, 2, inputs.random_graph(20, seed=5))]
+    seeds = [21 + i for i in range(len(bases))]
+    res = {}
+    for streams in (1, 3):
+        with ftlm.Flow(M, ftlm.GAUSS, torch.float32, 8, 64, 4 << 30, streams=streams) as flow:
+            res[streams] = _run(flow, [0, 0, 2, 3, 0, 5], bases, R, seeds)
+    for a, b in zip(res[1], res[3]):
+        for k in ("theta", "weight", "m_eff"):
+            assert torch.equal(a[k], b[k]), k
+    for b in bases:
+        b.close()
+
+
+def test_flow_set_streams_rejects_bad_counts(cuda_dev):
+    with ftlm.Flow(10, ftlm.GAUSS, torch.float32, 8, 4, 1 << 24) as flow:
+        for n in (0, 5):
+            with pytest.raises(ftlm.FtlmError):
+                ftlm._check(ftlm.lib().ftlm_flow_set_streams(flow.handle, n))
