@@ -1,5 +1,6 @@
 // Error reporting and kernel timing shared by every entry point.
 #include <atomic>
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <string>
@@ -103,6 +104,54 @@ cudaError_t table_pool(int device, cudaMemPool_t *pool)
     }
     *pool = g_pools[device];
     return cudaSuccess;
+}
+
+namespace {
+
+// Pinned staging for small host-to-device images (sector tables): a copy from
+// pageable memory may wait until the stream's queued work has run, which blocks the
+// host while the device is busy; a copy from a pinned buffer returns at once.  A
+// ring of kUpStages buffers per device, each reused once its copy has run.
+constexpr int kUpStages = 64;
+constexpr size_t kUpStageBytes = 256 << 10;
+struct UpRing {
+    void *buf[kUpStages] = {};
+    cudaEvent_t ev[kUpStages] = {};
+    int next = 0;
+};
+std::mutex g_up_mu;
+std::map<int, UpRing> g_up;
+
+}  // namespace
+
+cudaError_t upload_async(void *dst, const void *src, size_t bytes, cudaStream_t stream)
+{
+    if (bytes == 0) return cudaSuccess;
+    int device = 0;
+    cudaError_t e = cudaGetDevice(&device);
+    if (e != cudaSuccess) return e;
+    if (bytes > kUpStageBytes) return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, stream);
+    std::lock_guard<std::mutex> lk(g_up_mu);
+    UpRing &r = g_up[device];
+    const int k = r.next;
+    r.next = (r.next + 1) % kUpStages;
+    if (!r.buf[k]) {
+        e = cudaMallocHost(&r.buf[k], kUpStageBytes);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r.ev[k], cudaEventDisableTiming);
+        if (e != cudaSuccess) {  // no pinned memory: the pageable copy
+            if (r.buf[k]) cudaFreeHost(r.buf[k]);
+            r.buf[k] = nullptr;
+            cudaGetLastError();
+            return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, stream);
+        }
+    } else {
+        e = cudaEventSynchronize(r.ev[k]);  // its previous copy has run
+        if (e != cudaSuccess) return e;
+    }
+    std::memcpy(r.buf[k], src, bytes);
+    e = cudaMemcpyAsync(dst, r.buf[k], bytes, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaEventRecord(r.ev[k], stream);
+    return e;
 }
 
 ftlm_status fail(ftlm_status s, const std::string &msg)

@@ -548,9 +548,9 @@ ftlm_status ftlm::basis_create_half(int N, int two_sz, int n_bonds, const int *b
     b->bonds_walk_a.slots_f32 = b->bond_slots + 4 * kMaxBondSlots;
     b->bonds_walk_a.slots_f64 = b->bond_slots + 5 * kMaxBondSlots;
 
-    // A copy from pageable memory returns once the image is staged, so `image`
-    // may go out of scope; the kernels below follow it in stream order.
-    e = cudaMemcpyAsync(base, image.data(), small_bytes, cudaMemcpyHostToDevice, stream);
+    // The copy returns once the image is staged, so `image` may go out of scope;
+    // the kernels below follow it in stream order.
+    e = upload_async(base, image.data(), small_bytes, stream);
     if (e == cudaSuccess) {
         launch_hs_fill(b, stream);
         if (clt) {

@@ -189,6 +189,10 @@ ftlm_status cuda_fail(cudaError_t e, const char *what);
 // driver at every release (the pool keeps up to kPoolKeepBytes cached).
 constexpr uint64_t kPoolKeepBytes = 4ull << 30;
 cudaError_t table_pool(int device, cudaMemPool_t *pool);
+// Host-to-device copy of a small host image on `stream` through pinned staging
+// (the host buffer may be reused when it returns); images above 256 KB go through
+// pageable memory.
+cudaError_t upload_async(void *dst, const void *src, size_t bytes, cudaStream_t stream);
 
 // ---- launch count (api.cu): every kernel the library queues calls this once ----
 void note_launch();

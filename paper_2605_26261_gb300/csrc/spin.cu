@@ -426,7 +426,7 @@ ftlm_status ftlm::basis_create_spin(int N, int two_s, int two_sz, int n_bonds, c
     b->bonds_cr = BondList{};
     b->bonds_clt = BondList{};
 
-    e = cudaMemcpyAsync(base, image.data(), small_bytes, cudaMemcpyHostToDevice, stream);
+    e = upload_async(base, image.data(), small_bytes, stream);
     if (e == cudaSuccess) {
         launch_hs_fill(b, stream);
         e = cudaGetLastError();
