@@ -76,7 +76,7 @@ def parse_args():
     p.add_argument("--M", type=int, default=0, help="Lanczos steps (default: the workload's)")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--jobs", type=int, default=128, help="serving: requests in the timed stream")
-    p.add_argument("--steps-per-poll", type=int, default=8,
+    p.add_argument("--steps-per-poll", type=int, default=20,
                    help="serving: Lanczos steps of each flow wave between admission passes of the request loop")
     p.add_argument("--seeds", type=int, default=8, help="precision: independent FTLM runs for sigma_emp")
     p.add_argument("--clusters", type=int, default=256, help="clusters256: use the first n clusters (profiling)")
@@ -502,7 +502,7 @@ def run_ours(args):
     extras = None
     if world == 1 and args.workload == "icosidodecahedron" and not args.no_extras and len(sectors) == 1:
         extras = {"fp64_b1": fp64_b1_job(N, bonds, mode, R, M, T, value), "serving": None}
-        sv = serve_stream(args.serving_jobs, 8, 3, local, live_rows=args.live_rows)
+        sv = serve_stream(args.serving_jobs, args.steps_per_poll, 3, local, live_rows=args.live_rows)
         sv.pop("_done"), sv.pop("_jobs")
         sv["workload"] = WORKLOADS["serving"]["desc"]
         extras["serving"] = sv

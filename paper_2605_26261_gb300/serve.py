@@ -126,7 +126,7 @@ class Engine:
     """
 
     def __init__(self, R=8, M=80, dtype=torch.float32, block=8, T=None, g=2.0, dist=ftlm.GAUSS,
-                 memory_budget=None, max_units=512, max_jobs=None, steps_per_poll=8, depth=2,
+                 memory_budget=None, max_units=512, max_jobs=None, steps_per_poll=20, depth=2,
                  small_rows=1 << 15, flow_streams=4, max_live_rows=None):
         self.dev = torch.device("cuda", torch.cuda.current_device())
         self.R, self.M, self.dtype, self.block = R, M, dtype, block
