@@ -987,7 +987,7 @@ def run_serving(args):
                    "steps_per_poll": args.steps_per_poll, "block": 8,
                    "batching": "chain level: sectors join the running multi-sector launches at Lanczos-step "
                                "boundaries (ftlm_flow)",
-                   "admission": "first fit of each sector's units in the flow workspace (60% of free HBM)" +
+                   "admission": "first fit of each sector's units in the flow workspace (32 GB)" +
                                 (f", at most {args.live_rows} rows of flow sectors in flight" if args.live_rows
                                  else ""),
                    "flow_streams": 4, "small_sectors": "D <= 32768: one persistent batch per job on a side stream",

@@ -105,9 +105,13 @@ class Engine:
     dtype           vector storage (reductions are FP64)
     block           chains per unit
     T               temperature grid (host array); g the g-factor of chi
-    memory_budget   bytes of the flow's workspace (default: 60 % of the free device
-                    memory when the engine starts); tables and the small sectors'
-                    batches come on top
+    memory_budget   bytes of the flow's workspace (default: DEFAULT_BUDGET, at most
+                    60 % of the free device memory when the engine starts); tables
+                    and the small sectors' batches come on top.  The workspace
+                    bounds the sectors in flight: on the serving stream of 128 jobs
+                    (N = 16 ... 26) a workspace that admits every waiting job at once
+                    served fewer jobs per second (measured 11.7 / 12.6 / 13.8 / 13.5 /
+                    12.4 jobs/s at 170 / 48 / 32 / 24 / 16 GB)
     max_units       units of chains the flow holds at once
     max_jobs        jobs in flight at once (None: as many as fit; 1: one at a time)
     steps_per_poll  Lanczos steps of each wave of the flow per admission pass
@@ -125,6 +129,8 @@ class Engine:
     job starts; its larger sectors join the flow.
     """
 
+    DEFAULT_BUDGET = 32 << 30  # bytes of the flow's workspace
+
     def __init__(self, R=8, M=80, dtype=torch.float32, block=8, T=None, g=2.0, dist=ftlm.GAUSS,
                  memory_budget=None, max_units=512, max_jobs=None, steps_per_poll=20, depth=2,
                  small_rows=1 << 15, flow_streams=4, max_live_rows=None):
@@ -136,7 +142,7 @@ class Engine:
         self.T = torch.as_tensor(T, device=self.dev)
         if memory_budget is None:
             free, _ = torch.cuda.mem_get_info(self.dev)
-            memory_budget = int(0.6 * free)
+            memory_budget = int(min(self.DEFAULT_BUDGET, 0.6 * free))
         self.stream = torch.cuda.Stream(self.dev)   # the flow's Lanczos steps
         # sector tables (built without a host wait; the streams that use them wait
         # for an event), high priority so that they run as soon as SMs free up
