@@ -143,7 +143,7 @@ def peak_hbm():
 # Device sources of each H.v kernel family: a committed ncu summary holds DRAM
 # traffic for the sources it was taken on.
 KERNEL_SOURCES = {
-    "hv": ("hv.cu", "walkb.cu", "epi.cuh", "rows.cuh", "vec.cuh", "reduce.cuh", "ftlm_internal.cuh"),
+    "hv": ("hv.cu", "walka.cu", "walkb.cu", "epi.cuh", "rows.cuh", "vec.cuh", "reduce.cuh", "ftlm_internal.cuh"),
     "spin": ("spin.cu", "spin_rows.cuh", "epi.cuh", "vec.cuh", "reduce.cuh", "ftlm_internal.cuh"),
 }
 

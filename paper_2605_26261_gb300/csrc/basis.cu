@@ -231,6 +231,25 @@ bool build_hi_walk(const ftlm_basis *b, int rh, HiWalk *w)
     return true;
 }
 
+bool build_lo_walk(const ftlm_basis *b, LoWalk *w)
+{
+    if (b->two_s != 1 || b->mode != FTLM_RANK_CR || !b->lo_tiles || !b->n_lo_tiles) return false;
+    LoWalk a{};
+    a.ntiles = b->n_lo_tiles;
+    a.n_ll = b->n_ll_a;
+    a.n_cr = b->n_cr_a;
+    a.nb = a.n_ll + a.n_cr;
+    a.jsum4 = b->jsum4_a;
+    for (int p = 0; p <= kMaxHighBits; ++p) a.hend[p] = b->uhi_off[p + 1];
+    a.hend[kMaxHighBits + 1] = b->uhi_off[kMaxHighBits + 1];
+    a.tiles = b->lo_tiles;
+    a.uhi = b->uhi;
+    a.slots_f32 = b->bond_slots + 4 * kMaxBondSlots;
+    a.slots_f64 = b->bond_slots + 5 * kMaxBondSlots;
+    *w = a;
+    return true;
+}
+
 void launch_hs_fill(const ftlm_basis *b, cudaStream_t stream)
 {
     hs_fill_kernel<<<grid_for(b->n_hs, 256, b->num_sms), 256, 0, stream>>>(b->tables(), b->n_hs, b->hs);
@@ -397,30 +416,36 @@ ftlm_status ftlm::basis_create_half(int N, int two_sz, int n_bonds, const int *b
         c.jsum4 = jsum4;
     }
     {
-        // split H.v: walk A takes the lo-lo bonds (whole chunks first) and the cross
-        // bonds, walk B the high-high bonds as one compact list
-        BondList &c = b->bonds_walk_a;
+        // split H.v: walk A (walka.cu) takes the lo-lo bonds as low masks, then the
+        // cross bonds as {2^i, 2^(j-L)}, each list padded to a multiple of 4 slots;
+        // walk B the high-high bonds as one compact list
         std::vector<int> lo, hi, rest;
         for (int k = 0; k < n_bonds; ++k) {
             bool il = bi[k] < L, jl = bj[k] < L;
             (il && jl ? lo : (!il && !jl) ? hi : rest).push_back(k);
         }
-        const int nlo = (int)lo.size() / kBondChunk * kBondChunk;
-        std::vector<int> order(lo.begin(), lo.begin() + nlo);
-        order.insert(order.end(), lo.begin() + nlo, lo.end());
-        order.insert(order.end(), rest.begin(), rest.end());
+        int pos = 0;
         double j4 = 0.0;
-        for (int pos = 0; pos < (int)order.size(); ++pos) {
-            const int k = order[pos];
-            const uint64_t m = (1ull << bi[k]) | (1ull << bj[k]);
-            if (pos < nlo) put(2, pos, (uint32_t)m, 0u, J[k] / 2.0);
-            else put(2, pos, (uint32_t)m, (uint32_t)(m >> 32), J[k] / 2.0);
-            j4 += J[k] / 4.0;
+        auto put_a = [&](uint32_t x, uint32_t y, double jh) {
+            const float f = (float)jh;
+            uint32_t fb;
+            std::memcpy(&fb, &f, 4);
+            uint64_t db;
+            std::memcpy(&db, &jh, 8);
+            slots[(size_t)4 * kMaxBondSlots + pos] = make_uint4(x, y, fb, 0u);
+            slots[(size_t)5 * kMaxBondSlots + pos] = make_uint4(x, y, (uint32_t)db, (uint32_t)(db >> 32));
+            ++pos;
+            j4 += jh / 2.0;
+        };
+        for (int k : lo) put_a((1u << bi[k]) | (1u << bj[k]), 0u, J[k] / 2.0);
+        b->n_ll_a = (int)(lo.size() + 3) / 4 * 4;
+        pos = b->n_ll_a;
+        for (int k : rest) {
+            const int i = std::min(bi[k], bj[k]), j = std::max(bi[k], bj[k]);
+            put_a(1u << i, 1u << (j - L), J[k] / 2.0);
         }
-        c.n_lo = nlo;
-        c.n_hi = 0;
-        c.nb = nlo + round_up((int)order.size() - nlo);
-        c.jsum4 = j4;
+        b->n_cr_a = (int)(rest.size() + 3) / 4 * 4;
+        b->jsum4_a = j4;
         b->n_hi_bonds = (int)hi.size();
         double jh4 = 0.0;
         for (int pos = 0; pos < (int)hi.size() && pos < kMaxBondSlots; ++pos) {
@@ -481,6 +506,25 @@ ftlm_status ftlm::basis_create_half(int N, int two_sz, int n_bonds, const int *b
         for (uint64_t h = 0; h < b->H; ++h) uhi[fill[popc64(h)]++] = (uint32_t)h;
     }
 
+    // Tile table of the blocked walk A (LoWalk), for sectors that can run the split:
+    // the runs of kLoRun high patterns of one popcount class in the order of their
+    // first pattern, each followed by its column chunks.
+    std::vector<uint32_t> lo_tiles;
+    if (mode == FTLM_RANK_CR && N > L && b->n_hi_bonds >= 1 && b->n_hi_bonds <= kMaxHiBonds) {
+        const int nh = N - L;
+        std::vector<uint32_t> cnt(nh + 1, 0u);
+        for (uint64_t h = 0; h < b->H; ++h) {
+            const int p = popc64(h);
+            const uint32_t idx = cnt[p]++;
+            const int q = K - p;
+            if (idx % kLoRun || q < 0 || q > L) continue;
+            const uint32_t nch = (uint32_t)((binom(L, q) + 31) / 32);
+            const uint32_t pos = b->uhi_off[p] + idx;
+            for (uint32_t c = 0; c < nch; ++c) lo_tiles.push_back(pos << 7 | c);
+        }
+    }
+    b->n_lo_tiles = (uint32_t)lo_tiles.size();
+
     // One stream-ordered allocation holds every table: the small ones first (bond
     // slots, thi, tlo, ulo, uoff, and the binomials the CLT build reads), filled by
     // one copy from a host image, then the coarse index and, for CLT, the basis
@@ -499,6 +543,7 @@ ftlm_status ftlm::basis_create_half(int N, int two_sz, int n_bonds, const int *b
     const uint64_t o_ulo = take(nlo * sizeof(uint16_t));
     const uint64_t o_uoff = take(sizeof(b->ulo_off));
     const uint64_t o_uhi = take(b->H * sizeof(uint32_t));
+    const uint64_t o_lot = take(lo_tiles.size() * sizeof(uint32_t));
     const uint64_t o_binom = clt ? take(33 * 33 * sizeof(uint64_t)) : off;
     const uint64_t small_bytes = off;
     const uint64_t o_hs = take(b->n_hs * sizeof(uint32_t));
@@ -513,6 +558,7 @@ ftlm_status ftlm::basis_create_half(int N, int two_sz, int n_bonds, const int *b
     std::memcpy(image.data() + o_ulo, ulo.data(), nlo * sizeof(uint16_t));
     std::memcpy(image.data() + o_uoff, b->ulo_off, sizeof(b->ulo_off));
     std::memcpy(image.data() + o_uhi, uhi.data(), b->H * sizeof(uint32_t));
+    if (!lo_tiles.empty()) std::memcpy(image.data() + o_lot, lo_tiles.data(), lo_tiles.size() * sizeof(uint32_t));
     if (clt) {
         uint64_t *bh = reinterpret_cast<uint64_t *>(image.data() + o_binom);
         for (int n = 0; n <= 32; ++n)
@@ -538,6 +584,7 @@ ftlm_status ftlm::basis_create_half(int N, int two_sz, int n_bonds, const int *b
     b->ulo = reinterpret_cast<uint16_t *>(base + o_ulo);
     b->uoff = reinterpret_cast<uint32_t *>(base + o_uoff);
     b->uhi = reinterpret_cast<uint32_t *>(base + o_uhi);
+    b->lo_tiles = lo_tiles.empty() ? nullptr : reinterpret_cast<uint32_t *>(base + o_lot);
     b->hs = reinterpret_cast<uint32_t *>(base + o_hs);
     b->basis = clt ? reinterpret_cast<uint32_t *>(base + o_basis) : nullptr;
     b->clt = clt ? reinterpret_cast<uint2 *>(base + o_clt) : nullptr;
@@ -545,8 +592,6 @@ ftlm_status ftlm::basis_create_half(int N, int two_sz, int n_bonds, const int *b
     b->bonds_cr.slots_f64 = b->bond_slots + kMaxBondSlots;
     b->bonds_clt.slots_f32 = b->bond_slots + 2 * kMaxBondSlots;
     b->bonds_clt.slots_f64 = b->bond_slots + 3 * kMaxBondSlots;
-    b->bonds_walk_a.slots_f32 = b->bond_slots + 4 * kMaxBondSlots;
-    b->bonds_walk_a.slots_f64 = b->bond_slots + 5 * kMaxBondSlots;
 
     // The copy returns once the image is staged, so `image` may go out of scope;
     // the kernels below follow it in stream order.

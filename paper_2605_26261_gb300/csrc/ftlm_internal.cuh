@@ -113,6 +113,31 @@ struct HiWalk {
     const uint4 *bonds;               // {m >> L, J/2 as float, J/2 as double (lo, hi)}
 };
 
+// Walk A of the split in blocks (walka.cu).  A tile is 32 consecutive low ranks
+// r_lo (one column per lane) of low popcount group q and a run of up to kLoRun high
+// patterns h of popcount K - q (consecutive in uhi).  A lo-lo bond leaves h alone
+// and its source (h, l ^ m) sits at thi[h] + tlo[l ^ m]: whether it is antiparallel
+// and the rank tlo[l ^ m] depend on the lane's column only, so one lookup serves
+// every h of the run.  A cross bond (low site i, high site j) flips one bit of each
+// half: source thi[h ^ 2^(j-L)] + tlo[l ^ 2^i], the high term uniform over the
+// warp.  Tiles are listed in the order of their runs' first high pattern (all
+// popcount classes interleaved, chunks of a run consecutive), i.e. rows near label
+// order: the rows of every h of the runs in flight, which the lo-lo gathers read,
+// and the neighbouring h ^ 2^(j-L) of the cross bonds stay in L2.  Table entry:
+// (position of the run's first h in uhi) << 7 | column chunk.
+constexpr int kLoRun = 4;
+struct LoWalk {
+    uint32_t ntiles;
+    int n_ll, n_cr;                   // lo-lo and cross bond slots (each a multiple of 4)
+    int nb;                           // n_ll + n_cr
+    double jsum4;                     // sum of J_b / 4 over the lo-lo and cross bonds
+    uint32_t hend[kMaxHighBits + 2];  // end of popcount class p in uhi
+    const uint32_t *tiles;            // [ntiles] (uhi position << 7) | chunk
+    const uint32_t *uhi;
+    const uint4 *slots_f32;           // lo-lo {m_lo, 0, J/2}, then cross {2^i, 2^(j-L), J/2}
+    const uint4 *slots_f64;
+};
+
 // General local spin s = two_s / 2 >= 1 (spin.cu): labels n = sum_k a_k d^k with
 // base-d digits a_k = m_k + s, d = two_s + 1 (Eq. 11).  The digit-block tables of
 // SectorTables are used with base d: thi over the d^(N-L) high labels, tlo/ulo
@@ -148,13 +173,16 @@ struct ftlm_basis {
     int device, num_sms;
     ftlm::BondList bonds_cr;
     ftlm::BondList bonds_clt;
-    ftlm::BondList bonds_walk_a;   // split H.v, walk A: lo-lo and cross bonds (CR)
+    double jsum4_a;                // split H.v, walk A: sum of J_b / 4 over its lo-lo and cross bonds
     int n_hi_bonds;                // high-high bonds (walk B of the split H.v)
     double jsum4_hi;               // their sum of J_b / 4
     void *block;        // one pooled device allocation holding every table below
     uint4 *bond_slots;  // device: cr f32, cr f64, clt f32, clt f64, walk-A f32, walk-A f64,
                         // walk-B bonds (kMaxBondSlots each)
     uint32_t *uhi;      // CR: high patterns grouped by popcount, ascending (walk B)
+    uint32_t *lo_tiles; // CR: walk A tile table of the split H.v (LoWalk), or null
+    uint32_t n_lo_tiles;
+    int n_ll_a, n_cr_a; // walk A bond slots: lo-lo, cross (multiples of 4)
     ftlm_hv_schedule hv_schedule;  // Lanczos H.v walks (ftlm_basis_set_schedule)
     int walk_rh;        // high patterns per walk-B tile (0: the default)
     uint32_t uhi_off[ftlm::kMaxHighBits + 2];  // start of popcount group p in uhi
@@ -257,6 +285,11 @@ bool build_hi_walk(const ftlm_basis *b, int rh, HiWalk *w);
 struct EpiDev;
 // Walk B of a split Lanczos step (the epilogue's alpha as per-tile sums).
 ftlm_status launch_walk_b(const ftlm_basis *b, const HiWalk &w, ftlm_dtype dtype, int B, const void *x, void *y,
+                          const EpiDev &ep, cudaStream_t stream);
+// Walk A's tile layout (false when the sector has no walk A tile table).
+bool build_lo_walk(const ftlm_basis *b, LoWalk *w);
+// Walk A of a split Lanczos step in blocks (no alpha; walk B finishes the rows).
+ftlm_status launch_walk_a(const ftlm_basis *b, const LoWalk &w, ftlm_dtype dtype, int B, const void *x, void *y,
                           const EpiDev &ep, cudaStream_t stream);
 
 // Lanczos chains of one sector (lanczos.cu): chain r is keyed as chain chain0 + r.

@@ -75,9 +75,8 @@ template <typename V, int RT, int B, int C> __host__ __device__ constexpr int mi
                                        : (B >= 8 && C <= 2 ? 4 : (B >= 8 ? FTLM_B8_MIN_CTAS : (B >= 4 || RT >= 4 ? 3 : 6))));
 }
 
-// EPI: kPlain (y = H x), kLanczos (fused Lanczos epilogue with alpha), kWalkA
-// (walk A of a split H.v: the epilogue without alpha, see ftlm_internal.cuh).
-enum { kPlain = 0, kLanczos = 1, kWalkA = 2 };
+// EPI: kPlain (y = H x) or kLanczos (fused Lanczos epilogue with alpha).
+enum { kPlain = 0, kLanczos = 1 };
 
 template <typename V, typename Lbl, bool CLT, int EPI, int RT, int B, int C>
 __global__ void __launch_bounds__(kRowThreads, min_ctas<V, RT, B, C>())
@@ -124,11 +123,7 @@ hv_kernel(const SectorTables s, const BondList bl, const V *__restrict__ x, V *y
         }
         if (CLT) rows_clt<V, RT, B, C>(s, bl, s_bond, x, t, acc, dsum);
         else rows_cr<V, Lbl, RT, B, C>(s, bl, s_bond, s_tlo, x, t, acc, dsum);
-        if constexpr (EPI == kWalkA) {
-#pragma unroll
-            for (int i = 0; i < RT; ++i)
-                if (ok[i]) epi_row_walk_a<V, B>(ep, s_inv_s, s_c_prev, x, y, t[i], jsum4 - dsum[i], acc[i]);
-        } else if constexpr (TILES) {
+        if constexpr (TILES) {
             DotAcc<V> tacc[B];
 #pragma unroll
             for (int i = 0; i < RT; ++i)
@@ -218,7 +213,7 @@ constexpr int kDefaultWalkRh = 8;
 
 bool split_walks(const ftlm_basis *b, int B, size_t vsize, HiWalk *w)
 {
-    if (b->hv_schedule == FTLM_HV_ONE_WALK) return false;
+    if (b->hv_schedule == FTLM_HV_ONE_WALK || !b->lo_tiles) return false;
     const uint64_t bytes = b->D * (uint64_t)B * vsize;
     if (b->hv_schedule == FTLM_HV_AUTO &&
         (bytes < (vsize == 4 ? kSplitMinBytes32 : kSplitMinBytes64) || b->n_hi_bonds < kSplitMinHiBonds))
@@ -263,7 +258,9 @@ ftlm_status launch(const ftlm_basis *b, const V *x, V *y, const EpiDev &ep, cuda
         uint32_t ntiles;
         if (split_walks(b, B, sizeof(V), &w)) {
             const ftlm_dtype dt = sizeof(V) == 4 ? FTLM_F32 : FTLM_F64;
-            st = launch_rows<V, Lbl, false, kWalkA, RT, B, C>(b, b->bonds_walk_a, x, y, ep, stream);
+            LoWalk la;
+            st = build_lo_walk(b, &la) ? launch_walk_a(b, la, dt, B, x, y, ep, stream)
+                                       : fail(FTLM_EUNSUPPORTED, "split H.v without a walk A tile table");
             if (st == FTLM_OK) st = launch_walk_b(b, w, dt, B, x, y, ep, stream);
             ntiles = w.ntiles;
         } else {

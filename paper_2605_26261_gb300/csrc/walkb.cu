@@ -37,10 +37,14 @@ template <> __device__ __forceinline__ double hi_jh<double>(const uint4 &e)
 }
 
 // Resident CTAs per SM the register budget allows for: walk B keeps C gathered
-// rows of B values in flight per lane.
+// rows of B values and the row's own two rows in flight per lane.  Build option
+// FTLM_WALKB_MIN_CTAS: the cut for rows of 32 bytes (FP32 blocks of 8).
+#ifndef FTLM_WALKB_MIN_CTAS
+#define FTLM_WALKB_MIN_CTAS 2
+#endif
 template <typename V, int B> __host__ __device__ constexpr int walk_b_min_ctas()
 {
-    return sizeof(V) * B >= 64 ? 1 : (sizeof(V) * B >= 32 ? 2 : (sizeof(V) == 8 ? 3 : 4));
+    return sizeof(V) * B >= 64 ? 1 : (sizeof(V) * B >= 32 ? FTLM_WALKB_MIN_CTAS : (sizeof(V) * B >= 8 ? 3 : 4));
 }
 
 template <typename V, int B, int C>
@@ -101,6 +105,13 @@ walk_b_kernel(const uint32_t *__restrict__ thi, const HiWalk w, const V *__restr
         for (uint32_t k = 0; k < kn; ++k) {
             const uint32_t h = __shfl_sync(0xffffffffu, h_l, k);
             const uint32_t rb = __shfl_sync(0xffffffffu, rb_l, k);
+            // the row's own entries first: their DRAM latency overlaps the gathers
+            const size_t t = (size_t)(rb + li);
+            V xt[B], yv[B];
+            if (valid) {
+                ld_vec<B>(x + t * B, xt, false);
+                ld_vec<B>(y + t * B, yv, true);
+            }
             uint32_t amask[2], src[2];
 #pragma unroll
             for (int wd = 0; wd < 2; ++wd) {
@@ -142,10 +153,7 @@ walk_b_kernel(const uint32_t *__restrict__ thi, const HiWalk w, const V *__restr
                 }
             }
             if (valid) {
-                const size_t t = (size_t)(rb + li);
-                V xt[B], yv[B], out[B];
-                ld_vec<B>(x + t * B, xt, false);
-                ld_vec<B>(y + t * B, yv, true);
+                V out[B];
                 const V diag = jsum4 - dsum;
 #pragma unroll
                 for (int r = 0; r < B; ++r) {
