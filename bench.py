@@ -506,6 +506,11 @@ def run_ours(args):
         sv.pop("_done"), sv.pop("_jobs")
         sv["workload"] = WORKLOADS["serving"]["desc"]
         extras["serving"] = sv
+        del work
+        # the other configurations, one measurement each
+        extras["precision"] = precision_job(T)
+        extras["clusters256"] = clusters_step(T)
+        extras["ring34"] = ring34_job(T)
 
     peak, peak_src = peak_hbm()
     block = round(hv_vec / max(hv_n, 1))  # vectors per H.v launch (one block width per run)
@@ -683,6 +688,143 @@ def fp64_b1_job(N, bonds, mode, R, M, T, value_f32):
             "schedule": "split" if used == ftlm.HV_SPLIT else "one_walk",
             "f32_block8_over_fp64_b1": value_f32 / v,
             "note": "same job, FP64 vectors, every chain alone (ftlm_lanczos_set_block(1))"}
+
+
+def ring34_job(T):
+    """The N = 34 ring S^z = 0 sector (D = 2 333 606 220, CR), 8 Rademacher chains as one
+    FP32 block, M = 100: one whole job (sector setup, Lanczos, Ritz, thermodynamic sums)
+    timed with CUDA events after a 3-step warm-up job."""
+    import torch
+
+    from paper_2605_26261_gb300 import ftlm
+
+    dev = T.device
+    torch.cuda.empty_cache()
+    bonds = bonds_of("ring34")
+    R, M = 8, 100
+    with ftlm.Basis(34, 0, bonds, ftlm.RANK_CR) as b:
+        work = torch.empty(ftlm.ftlm_lanczos_workspace_bytes(b.handle, R, M, torch.float32), dtype=torch.uint8,
+                           device=dev)
+        D, per_hv = b.dim, b.updates
+        used = ftlm.ftlm_basis_hv_schedule(b.handle, 8, torch.float32)
+    th = torch.empty((R, M), dtype=torch.float64, device=dev)
+    w = torch.empty_like(th)
+    me = torch.empty(R, dtype=torch.int32, device=dev)
+    obs = [torch.empty_like(T) for _ in range(4)]
+
+    def job(m):
+        with ftlm.Basis(34, 0, bonds, ftlm.RANK_CR) as b:
+            ftlm.ftlm_lanczos(b.handle, R, m, 1, ftlm.RADEMACHER, torch.float32, work, th, w, me)
+            ftlm.ftlm_thermo([0], [D], R, M, [th], [w], [me], True, 2.0, 0.0, T, *obs)
+
+    job(3)
+    torch.cuda.synchronize()
+    ftlm.ftlm_profile_read()
+    ftlm.ftlm_profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    job(M)
+    e1.record()
+    torch.cuda.synchronize()
+    ftlm.ftlm_profile_enable(False)
+    hv_n, hv_vec, hv_ms, up_n, up_ms = ftlm.ftlm_profile_read()
+    ms = e0.elapsed_time(e1)
+    upd = int(me.sum().item()) * per_hv
+    del work
+    torch.cuda.empty_cache()
+    return {"value": upd / (ms / 1e3) / 1e9, "unit": "Gupdates/s", "job_ms": ms,
+            "hv_ms_avg": hv_ms / max(hv_n, 1), "update_ms_avg": up_ms / max(up_n, 1),
+            "schedule": "split" if used == ftlm.HV_SPLIT else "one_walk",
+            "workload": WORKLOADS["ring34"]["desc"] + ", R=8 Rademacher (one block of 8 f32 vectors), M=100",
+            "vectors_gb": 2 * D * R * 4 / 1e9}
+
+
+def clusters_step(T):
+    """The batched-cluster configuration in brief: every S^z >= 0 sector of the 256
+    random clusters in one batch (R = 16 Rademacher, M = 100, FP32, the default plan:
+    blocks of 8 chains, 2048-row H.v tiles), then the 256 thermodynamic sums; one
+    untimed run, then one run timed with CUDA events."""
+    import torch
+
+    from paper_2605_26261_gb300 import ftlm, inputs
+
+    R, M = 16, 100
+    clusters = inputs.cluster_set(256, seed=256)
+    bases = [[ftlm.Basis(N, tz, bonds) for tz in ftlm.computed_two_sz(N)] for N, bonds in clusters]
+    entries = [(b, R, 1 + c, 0) for c, bs in enumerate(bases) for b in bs]
+    outs = [[torch.empty_like(T) for _ in range(4)] for _ in clusters]
+    with ftlm.Batch(entries, M, ftlm.RADEMACHER, torch.float32, 8) as batch:
+        def step():
+            res = batch.run()
+            k = 0
+            for c, bs in enumerate(bases):
+                r = res[k:k + len(bs)]
+                k += len(bs)
+                ftlm.ftlm_thermo([b.two_sz for b in bs], [b.dim for b in bs], R, M, [x["theta"] for x in r],
+                                 [x["weight"] for x in r], [x["m_eff"] for x in r], True, 2.0, 0.0, T, *outs[c])
+            return res
+
+        step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        res = step()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        upd = sum(int(r["m_eff"].sum().item()) * b.updates for (b, _, _, _), r in zip(entries, res))
+    for bs in bases:
+        for b in bs:
+            b.close()
+    return {"step_ms": ms, "clusters_per_s": len(clusters) / (ms / 1e3), "Gupdates_per_s": upd / (ms / 1e3) / 1e9,
+            "sectors": len(entries), "workload": WORKLOADS["clusters256"]["desc"],
+            "plan": "blocks of 8 chains, 2048-row H.v tiles, 16384-row streaming tiles (the autotuner's choice "
+                    "on this set), eager (not graph-captured)"}
+
+
+def precision_job(T):
+    """The precision configuration in brief: the 4 x 6 J1-J2 lattice, every S^z >= 0
+    sector in one batch, R = 64 Rademacher, M = 150, with FP32 and with FP64 vectors
+    from the same seeds; job times and the largest FP32 - FP64 difference of E, C and
+    chi over the 200 temperatures (relative where |O| >= 1e-6 max|O|, else absolute
+    over max|O|)."""
+    import numpy as np
+    import torch
+
+    from paper_2605_26261_gb300 import ftlm
+
+    wl = WORKLOADS["precision"]
+    N, R, M = wl["N"], wl["R"], wl["M"]
+    bonds = bonds_of("precision")
+    sectors = ftlm.computed_two_sz(N)
+    bases = [ftlm.Basis(N, tz, bonds) for tz in sectors]
+    per = {}
+    for dt in (torch.float32, torch.float64):
+        for rep in range(2 if dt == torch.float32 else 1):
+            with ftlm.Batch([(b, R, 1, 0) for b in bases], M, ftlm.RADEMACHER, dt, 8) as batch:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                res = batch.run()
+                obs = ftlm.thermo([(b.two_sz, b.dim, r) for b, r in zip(bases, res)], T, R, M)
+                e1.record()
+                torch.cuda.synchronize()
+                upd = sum(int(r["m_eff"].sum().item()) * b.updates for b, r in zip(bases, res))
+                per[dt] = (e0.elapsed_time(e1), upd, {k: obs[k].cpu().numpy() for k in ("E", "C", "chi")})
+    for b in bases:
+        b.close()
+    diff = {}
+    for k in ("E", "C", "chi"):
+        a, ref = per[torch.float32][2][k], per[torch.float64][2][k]
+        scale = np.max(np.abs(ref))
+        band = np.abs(ref) >= 1e-6 * scale
+        rel = np.abs(a[band] - ref[band]) / np.abs(ref[band])
+        ab = np.abs(a[~band] - ref[~band]) / scale
+        diff[k] = float(max(rel.max() if rel.size else 0.0, ab.max() if ab.size else 0.0))
+    f32, f64 = per[torch.float32], per[torch.float64]
+    return {"f32_job_ms": f32[0], "f32_Gupdates_per_s": f32[1] / (f32[0] / 1e3) / 1e9,
+            "f64_job_ms": f64[0], "f64_Gupdates_per_s": f64[1] / (f64[0] / 1e3) / 1e9,
+            "max_rel_diff_f32_vs_f64": diff, "workload": wl["desc"] if "desc" in wl else "precision",
+            "note": "same seeded chains in FP32 and FP64 vector storage (FP64 reductions in both)"}
 
 
 def run_clusters(args):
