@@ -142,7 +142,8 @@ ftlm_status ftlm_basis_destroy_async(ftlm_basis *basis, void *stream);
  * rows (CR rank mode at s = 1/2; other sectors ignore it).  Eq. 12 is evaluated
  * row by row in either case; only the order of the work and the launches differ.
  *   FTLM_HV_ONE_WALK  one launch over the rows in sector (label) order.
- *   FTLM_HV_SPLIT     two launches: the rows in label order with the bonds that
+ *   FTLM_HV_SPLIT     two launches: the rows near label order (tiles of 32
+ *                     low-block ranks x 4 high patterns) with the bonds that
  *                     touch the low digit block, then the rows in the transposed
  *                     order (low-block rank fixed per lane, high patterns in turn)
  *                     with the bonds inside the high block, which adds its terms

@@ -83,8 +83,9 @@ struct SectorTables {
 // block maps row (h, l) to (h ^ m, l), a jump of thi[h ^ m] - thi[h] rows that for
 // the top sites spans a large part of the sector, so in a walk over the rows in
 // label order those gathers miss L2.  The split runs two walks per Lanczos step:
-//   walk A  rows in label order, bonds with a site in the low block (lo-lo and
-//           cross bonds: their jumps stay near the row);
+//   walk A  rows near label order (blocks of 32 low ranks x a few high patterns,
+//           see LoWalk), bonds with a site in the low block (lo-lo and cross
+//           bonds: their jumps stay near the row);
 //   walk B  the transposed order -- a warp fixes 32 consecutive low ranks r_lo
 //           (one per lane) and steps through the high patterns h of the matching
 //           popcount -- with the high-high bonds, whose sources (h ^ m, r_lo) lie
@@ -177,8 +178,8 @@ struct ftlm_basis {
     int n_hi_bonds;                // high-high bonds (walk B of the split H.v)
     double jsum4_hi;               // their sum of J_b / 4
     void *block;        // one pooled device allocation holding every table below
-    uint4 *bond_slots;  // device: cr f32, cr f64, clt f32, clt f64, walk-A f32, walk-A f64,
-                        // walk-B bonds (kMaxBondSlots each)
+    uint4 *bond_slots;  // device: cr f32, cr f64, clt f32, clt f64, walk-A f32, walk-A f64
+                        // (LoWalk layout), walk-B bonds (kMaxBondSlots each)
     uint32_t *uhi;      // CR: high patterns grouped by popcount, ascending (walk B)
     uint32_t *lo_tiles; // CR: walk A tile table of the split H.v (LoWalk), or null
     uint32_t n_lo_tiles;
