@@ -89,3 +89,35 @@ def test_fused_lanczos_launch_at_full_size(cuda_dev, mode):
         beta2 = torch.dot(hq.double(), hq.double()).item() - alpha**2
     assert abs(a1 - alpha) <= 1e-5 * (abs(alpha) + 1)
     assert abs(b1**2 - beta2) <= 1e-4 * beta2
+
+
+def test_split_lanczos_at_full_size(cuda_dev):
+    """The benchmark's H.v schedule at full size: 8 FP32 chains as one block on the
+    N = 30 sector take the split (blocked walk A + transposed walk B) under AUTO.
+    alpha_1 and beta_1 of every chain must match <q, Hq> and ||Hq||^2 - alpha_1^2
+    computed through the one-walk H.v launch (whose rows are checked against the
+    oracle above) on the same start vectors."""
+    N, bonds = ICOSIDODECA
+    R = 8
+    with ftlm.Basis(N, 0, bonds, ftlm.RANK_CR) as b:
+        assert ftlm.ftlm_basis_hv_schedule(b.handle, R, torch.float32) == ftlm.HV_SPLIT
+        res = ftlm.lanczos(b, R, 2, seed=3, dist=ftlm.RADEMACHER, dtype=torch.float32, keep_coeffs=True)
+        a1 = res["alpha"][:, 0].cpu().numpy()
+        b1 = res["beta"][:, 0].cpu().numpy()
+        del res
+        torch.cuda.empty_cache()
+        # the start block (work vector 0 after a 1-step run), then the one-walk H.v
+        nbytes = ftlm.ftlm_lanczos_workspace_bytes(b.handle, R, 1, torch.float32)
+        work = torch.empty(nbytes, dtype=torch.uint8, device=cuda_dev)
+        out = ftlm.lanczos(b, R, 1, seed=3, dist=ftlm.RADEMACHER, dtype=torch.float32, work=work)
+        torch.cuda.synchronize()
+        q = work[: 4 * R * b.dim].view(torch.float32).view(b.dim, R).clone()
+        del work, out
+        torch.cuda.empty_cache()
+        q = q / torch.linalg.vector_norm(q.double(), dim=0).float()
+        hq = torch.empty_like(q)
+        ftlm.ftlm_hv_block(b.handle, R, q, hq)
+        alpha = (q.double() * hq.double()).sum(dim=0).cpu().numpy()
+        beta2 = (hq.double() ** 2).sum(dim=0).cpu().numpy() - alpha**2
+    np.testing.assert_allclose(a1, alpha, rtol=1e-5, atol=1e-5)
+    np.testing.assert_allclose(b1**2, beta2, rtol=1e-4)
