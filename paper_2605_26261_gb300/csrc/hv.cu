@@ -193,20 +193,19 @@ int hv_cta_cap()
     return cap;
 }
 
-// Split Lanczos H.v (see HiWalk): used when the basis asks for it, or under
-// FTLM_HV_AUTO for blocks of vectors of at least kSplitMinBytes32 (FP32) or
+// Split Lanczos H.v (see HiWalk, LoWalk): used when the basis asks for it, or
+// under FTLM_HV_AUTO for blocks of vectors of at least kSplitMinBytes32 (FP32) or
 // kSplitMinBytes64 (FP64) of sectors with at least kSplitMinHiBonds high-high
-// bonds.  Measured on GB300 (H.v step, one walk -> split), N = 30 icosidodecahedral
-// S^z = 0 sector (26 of 60 bonds high-high): FP32 blocks of 16 / 8 / 4 / 1 vectors
-// (10, 5, 2.5, 0.6 GB) 35.2 -> 33.5, 16.7 -> 16.4, 9.69 -> 9.78, 5.54 -> 6.68 ms;
-// FP64 blocks of 4 / 1 (5, 1.2 GB) 96.2 -> 82.9, 37.2 -> 33.7 ms; FP32 blocks of 8
-// on the 30 M-row sector of the same cluster (0.96 GB) 3.21 -> 3.33 ms.  N = 34
-// ring (19 of 34 bonds high-high), FP32 blocks of 8: 2 S^z = 14 / 10 / 6 / 0
-// (4.2, 17.5, 44, 75 GB) 9.75 -> 12.4, 41.3 -> 51.8, 105.9 -> 103.9, 177 -> 184 ms.
-// The split moves two row streams per step instead of one but no long-jump gather
-// misses L2 (DRAM 5.7 instead of 9.5 GB on the 30 M-row sector); with few
-// high-high bonds per row the second pass costs more than the misses it saves.
-constexpr uint64_t kSplitMinBytes32 = 4ull << 30;
+// bonds.  Measured on GB300 (H.v step, one walk -> split with walk A in blocks),
+// N = 30 icosidodecahedral sectors (26 of 60 bonds high-high), FP32: S^z = 0,
+// blocks of 8 / 4 / 1 vectors (5, 2.5, 0.6 GB) 16.7 -> 15.8, 9.72 -> 9.22, 5.54 ->
+// 6.15 ms; blocks of 8 on the S^z = -3 / -5 / -6 sectors (2.8, 0.96, 0.46 GB) 9.31
+// -> 8.83, 3.21 -> 3.13, 1.543 -> 1.547 ms; FP64, S^z = 0, blocks of 4 (5 GB) 96.4
+// -> 69.7 ms.  N = 34 ring (19 of 34 bonds high-high), FP32 blocks of 8, S^z = 0
+// (75 GB): 179.0 -> 183.1 ms.  The split moves two row streams per step instead of
+// one but no long-jump gather misses L2; with few high-high bonds per row, or on
+// small blocks, the second pass costs more than the misses it saves.
+constexpr uint64_t kSplitMinBytes32 = 768ull << 20;
 constexpr uint64_t kSplitMinBytes64 = 1ull << 30;
 constexpr int kSplitMinHiBonds = 24;
 constexpr int kDefaultWalkRh = 8;
