@@ -38,8 +38,9 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_status_strings(lib):
     lib.ftlm_status_string.restype = ctypes.c_char_p
-    for s in range(6):
+    for s in range(7):
         assert lib.ftlm_status_string(s).startswith(b"FTLM_")
+    assert lib.ftlm_status_string(6).startswith(b"FTLM_ENOCONV")
 
 
 def _create(lib, N, two_sz, bonds, mode=0):
