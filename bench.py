@@ -579,14 +579,32 @@ def run_ours(args):
     n_off = (upd0 - D0) * block  # off-diagonal gathers of one step (each row of B values)
     # the read rate that bounds the gathers: L2 (a 64 MB buffer, L2-resident) measured
     # here with the library's probe; gathers and row streams of one step move through L2
-    l2_peak = None
+    l2_peak = peak_rows = peak_runs = None
     if hv_n:
         probe = torch.empty(64 << 20, dtype=torch.uint8, device=dev)
         l2_peak = ftlm.ftlm_probe_read_bandwidth(probe, 40)
+        peak_rows = ftlm.ftlm_probe_gather_bandwidth(probe, 1, 40)
+        peak_runs = ftlm.ftlm_probe_gather_bandwidth(probe, 32, 40)
         del probe
     gather_bytes = n_off // block * 32 * max(1, block * vsize // 32)
     stream_bytes = (6 if schedule == "split" else 3) * D0 * block * vsize
     l2_achieved = (gather_bytes + stream_bytes) / hv_avg_s / 1e9 if hv_n else None
+    # the gathers' own roofline: every bond has the same number of off-diagonal terms
+    # at s = 1/2, so the high-high bonds' share of the gathers is their share of the
+    # bonds; those move in runs of 32 consecutive rows per warp (1 KB), the others as
+    # rows of their own; the fastest a step could gather at the probed rates
+    gather_roof = None
+    if hv_n and two_s == 1 and len(sectors) == 1 and peak_rows and peak_runs:
+        lo_block = min(N, 14)
+        n_hh = sum(1 for i, j in zip(bonds[0], bonds[1]) if min(i, j) >= lo_block)
+        g_runs = gather_bytes * n_hh / len(bonds[0])
+        t_min = (gather_bytes - g_runs) / (peak_rows * 1e9) + g_runs / (peak_runs * 1e9)
+        gather_roof = {"peak_rows": peak_rows, "peak_runs_1KB": peak_runs, "unit": "GB/s",
+                       "t_min_ms": 1e3 * t_min, "frac": t_min / hv_avg_s,
+                       "basis": "gather bytes of one step at ftlm_probe_gather_bandwidth's rates on a 64 MB "
+                                "L2-resident buffer (scattered 32-byte rows for the bonds touching the low digit "
+                                f"block, 1 KB runs for the {n_hh} high-high bonds), this run; frac = that time / "
+                                "the event-timed step"}
     roofline = {
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
         "frac": achieved / peak if achieved else None, "traffic": traffic,
@@ -606,7 +624,8 @@ def run_ours(args):
                "bytes_per_launch": gather_bytes + stream_bytes,
                "basis": "gathers (one 32-byte sector per row of B values per off-diagonal term) + the row streams "
                         "of the step's walks, through L2 / event-timed step; peak = ftlm_probe_read_bandwidth on "
-                        "a 64 MB L2-resident buffer, this run"},
+                        "a 64 MB L2-resident buffer, this run",
+               "gathers": gather_roof},
         "hv_launches": hv_n, "sector_block_steps": launches_model, "vectors_per_launch": block,
         "hv_ms_avg": hv_avg_s * 1e3,
         "hv_Gupdates_per_s": upd_total / hv_s / 1e9 if hv_n else None,

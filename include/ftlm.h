@@ -581,6 +581,18 @@ ftlm_status ftlm_profile_read(uint64_t *hv_launches, uint64_t *hv_vectors, doubl
  * DRAM read rate.  The buffer's contents are only read.  EINVAL for bad arguments. */
 ftlm_status ftlm_probe_read_bandwidth(const void *buf_dev, uint64_t bytes, int reps, void *stream, double *gbps);
 
+/* ftlm_probe_gather_bandwidth -- read rate of this device for the access patterns
+ * of the H.v gathers: every 32-byte row of buf_dev (bytes, 32-byte aligned; whole
+ * blocks of `run` rows) is read once per pass, `reps` passes in one launch after an
+ * untimed pass, in an order scrambled by blocks of `run` consecutive rows -- run = 1:
+ * every thread a row of its own (the scattered low-block gathers), run = 32: every
+ * warp one contiguous run of 32 rows, 1 KB (the gathers of the transposed walk).
+ * Returns GB/s of the timed launch (CUDA events on `stream`; waits for them).  No
+ * counterpart in the paper: a measurement tool for the rooflines.  EINVAL for bad
+ * arguments (run other than 1 or 32, a buffer smaller than one block). */
+ftlm_status ftlm_probe_gather_bandwidth(const void *buf_dev, uint64_t bytes, int run, int reps, void *stream,
+                                        double *gbps);
+
 const char *ftlm_status_string(ftlm_status status);
 const char *ftlm_last_error(void); /* message of the last failure on this host thread */
 

@@ -3,13 +3,17 @@
 // DRAM read rate.  32 bytes per lane per load (the row of 8 FP32 or 4 FP64 values
 // the block H.v gathers), coalesced, over `reps` passes in one launch.
 #include "ftlm_internal.cuh"
+#include "vec.cuh"
 
 namespace ftlm {
 
 namespace {
 
-__global__ void __launch_bounds__(256) read_probe_kernel(const uint4 *__restrict__ p, uint64_t n32, int reps,
-                                                         unsigned int *sink)
+// Written only when the XOR of every value a thread read hits one 32-bit constant,
+// so that the compiler keeps the loads; a device variable, never a null pointer.
+__device__ unsigned int g_probe_sink;
+
+__global__ void __launch_bounds__(256) read_probe_kernel(const uint4 *__restrict__ p, uint64_t n32, int reps)
 {
     uint32_t acc = 0;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -18,7 +22,48 @@ __global__ void __launch_bounds__(256) read_probe_kernel(const uint4 *__restrict
             const uint4 a = __ldg(p + 2 * i), b = __ldg(p + 2 * i + 1);
             acc ^= a.x ^ a.y ^ a.z ^ a.w ^ b.x ^ b.y ^ b.z ^ b.w;
         }
-    if (acc == 0x9e3779b9u) *sink = acc;  // keeps the loads; practically never taken
+    if (acc == 0x9e3779b9u) g_probe_sink = acc;
+}
+
+// Gather probe: each pass reads every 32-byte row of the buffer once, in an order
+// scrambled by blocks of `run` consecutive rows: thread i reads row
+// perm(i / run) * run + i % run, perm an odd multiplier and an offset modulo the
+// next power of two, walked until it lands on a block that exists (a bijection of
+// the blocks whenever the walk ends within its 64 steps).  run = 1: every lane a row of its own, as the low-block gathers of
+// the H.v; run = 32: every warp one contiguous run of 32 rows (1 KB), as the
+// high-block gathers of the transposed walk.  Each thread keeps 8 rows in flight.
+__global__ void __launch_bounds__(256) gather_probe_kernel(const float *__restrict__ p, uint64_t nblocks, int run,
+                                                           int reps, int log2_pow)
+{
+    constexpr int U = 8;  // rows in flight per thread
+    uint32_t acc = 0;
+    const int run_shift = run == 32 ? 5 : 0;
+    const uint64_t n_rows = nblocks << run_shift;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t mask = (1ull << log2_pow) - 1;
+    for (int r = 0; r < reps; ++r) {
+        const uint64_t mul = 0x9E3779B97F4A7C15ull | 1ull, add = 0x632BE59BD9B4E019ull * (uint64_t)(r + 1);
+        for (uint64_t i0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i0 < n_rows; i0 += U * stride) {
+            uint64_t row[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint64_t i = i0 + u * stride < n_rows ? i0 + u * stride : 0;
+                uint64_t blk = ((i >> run_shift) * mul + add) & mask;
+                for (int walk = 0; walk < 64 && blk >= nblocks; ++walk) blk = (blk * mul + add) & mask;
+                if (blk >= nblocks) blk %= nblocks;  // (a bounded walk: any row in range will do)
+                row[u] = (blk << run_shift) + (i & ((1ull << run_shift) - 1));
+            }
+            float v[U][8];
+#pragma unroll
+            for (int u = 0; u < U; ++u) ld_vec<8>(p + row[u] * 8, v[u], false);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (i0 + u * stride < n_rows)
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) acc ^= __float_as_uint(v[u][k]);
+        }
+    }
+    if (acc == 0x9e3779b9u) g_probe_sink = acc;
 }
 
 }  // namespace
@@ -42,11 +87,11 @@ extern "C" ftlm_status ftlm_probe_read_bandwidth(const void *buf_dev, uint64_t b
     cudaError_t e = cudaEventCreate(&e1);
     if (e == cudaSuccess) {
         // untimed pass (brings an L2-sized buffer into L2), then the timed passes
-        read_probe_kernel<<<sms * 4, 256, 0, st>>>((const uint4 *)buf_dev, n32, 1, nullptr);
+        read_probe_kernel<<<sms * 4, 256, 0, st>>>((const uint4 *)buf_dev, n32, 1);
         note_launch();
         e = cudaEventRecord(e0, st);
         if (e == cudaSuccess) {
-            read_probe_kernel<<<sms * 4, 256, 0, st>>>((const uint4 *)buf_dev, n32, reps, nullptr);
+            read_probe_kernel<<<sms * 4, 256, 0, st>>>((const uint4 *)buf_dev, n32, reps);
             note_launch();
             e = cudaEventRecord(e1, st);
         }
@@ -58,5 +103,44 @@ extern "C" ftlm_status ftlm_probe_read_bandwidth(const void *buf_dev, uint64_t b
     cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (e != cudaSuccess) return cuda_fail(e, "read probe");
+    return FTLM_OK;
+}
+
+extern "C" ftlm_status ftlm_probe_gather_bandwidth(const void *buf_dev, uint64_t bytes, int run, int reps,
+                                                   void *stream, double *gbps)
+{
+    if (!buf_dev || !gbps || reps < 1 || (run != 1 && run != 32)) return fail(FTLM_EINVAL, "bad probe arguments");
+    if ((uintptr_t)buf_dev & 31u) return fail(FTLM_EINVAL, "buffer must be 32-byte aligned");
+    const uint64_t nblocks = bytes / 32 / (uint64_t)run;
+    if (nblocks < 1) return fail(FTLM_EINVAL, "buffer smaller than one block of rows");
+    int log2_pow = 0;
+    while ((1ull << log2_pow) < nblocks) ++log2_pow;
+    int dev = 0, sms = 0;
+    FTLM_CUDA(cudaGetDevice(&dev));
+    FTLM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int occ = 1;
+    FTLM_CUDA(kernel_occupancy((const void *)gather_probe_kernel, 256, 0, false, &occ));
+    const int grid = sms * occ;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    FTLM_CUDA(cudaEventCreate(&e0));
+    cudaError_t e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) {
+        gather_probe_kernel<<<grid, 256, 0, st>>>((const float *)buf_dev, nblocks, run, 1, log2_pow);
+        note_launch();
+        e = cudaEventRecord(e0, st);
+        if (e == cudaSuccess) {
+            gather_probe_kernel<<<grid, 256, 0, st>>>((const float *)buf_dev, nblocks, run, reps, log2_pow);
+            note_launch();
+            e = cudaEventRecord(e1, st);
+        }
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess) *gbps = (double)nblocks * run * 32.0 * reps / (ms * 1e-3) / 1e9;
+    }
+    cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "gather probe");
     return FTLM_OK;
 }

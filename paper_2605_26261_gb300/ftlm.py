@@ -108,6 +108,7 @@ def lib():
         "ftlm_sigma_emp": [I, I, P, P, P, P],
         "ftlm_profile_read": [PU64, PU64, PD, PU64, PD],
         "ftlm_probe_read_bandwidth": [P, U64, I, P, PD],
+        "ftlm_probe_gather_bandwidth": [P, U64, I, I, P, PD],
         "ftlm_flow_create": [I, I, I, I, I, P, U64, P, ctypes.POINTER(P)],
         "ftlm_flow_unit_bytes": [P, I, I, PU64],
         "ftlm_flow_add": [P, P, ctypes.POINTER(I)],
@@ -444,6 +445,15 @@ def ftlm_probe_read_bandwidth(buf, reps, stream=None):
     v = ctypes.c_double()
     _check(lib().ftlm_probe_read_bandwidth(_ptr(buf), buf.numel() * buf.element_size(), int(reps), _stream(stream),
                                            ctypes.byref(v)))
+    return v.value
+
+
+def ftlm_probe_gather_bandwidth(buf, run, reps, stream=None):
+    """GB/s of `reps` passes over the 32-byte rows of the device tensor buf in an order
+    scrambled by blocks of `run` rows (1: scattered rows; 32: 1 KB runs per warp)."""
+    v = ctypes.c_double()
+    _check(lib().ftlm_probe_gather_bandwidth(_ptr(buf), buf.numel() * buf.element_size(), int(run), int(reps),
+                                             _stream(stream), ctypes.byref(v)))
     return v.value
 
 

@@ -1,4 +1,4 @@
-"""Stream-ordered sector tables and the launch counter.
+"""Stream-ordered sector tables, the launch counter and the bandwidth probes.
 
 Tables live in one block of the library's device memory pool: a release queued on a
 stream (ftlm_basis_destroy_async) must not disturb work still queued before it, and
@@ -72,3 +72,19 @@ def test_launch_counter(cuda_dev):
         ftlm.lanczos(b, R, M, dtype=torch.float32)
         assert ftlm.ftlm_launch_count() - c3 == 1 + 2 * M + 1 + 1
         torch.cuda.synchronize()
+
+
+def test_bandwidth_probes(cuda_dev):
+    """The read probes behind the rooflines: coalesced, scattered 32-byte rows and
+    1 KB runs over an L2-sized buffer return positive rates; a scattered read is no
+    faster than a coalesced one; bad arguments are refused."""
+    buf = torch.zeros(64 << 20, dtype=torch.uint8, device=cuda_dev)
+    coalesced = ftlm.ftlm_probe_read_bandwidth(buf, 4)
+    rows = ftlm.ftlm_probe_gather_bandwidth(buf, 1, 4)
+    runs = ftlm.ftlm_probe_gather_bandwidth(buf, 32, 4)
+    assert coalesced > 0 and rows > 0 and runs > 0
+    assert rows <= 1.1 * coalesced
+    with pytest.raises(ftlm.FtlmError):
+        ftlm.ftlm_probe_gather_bandwidth(buf, 7, 4)
+    with pytest.raises(ftlm.FtlmError):
+        ftlm.ftlm_probe_gather_bandwidth(buf[:16], 32, 4)
