@@ -37,14 +37,10 @@ template <> __device__ __forceinline__ double hi_jh<double>(const uint4 &e)
 }
 
 // Resident CTAs per SM the register budget allows for: walk B keeps C gathered
-// rows of B values and the row's own two rows in flight per lane.  Build option
-// FTLM_WALKB_MIN_CTAS: the cut for rows of 32 bytes (FP32 blocks of 8).
-#ifndef FTLM_WALKB_MIN_CTAS
-#define FTLM_WALKB_MIN_CTAS 2
-#endif
+// rows of B values and the row's own two rows in flight per lane.
 template <typename V, int B> __host__ __device__ constexpr int walk_b_min_ctas()
 {
-    return sizeof(V) * B >= 64 ? 1 : (sizeof(V) * B >= 32 ? FTLM_WALKB_MIN_CTAS : (sizeof(V) * B >= 8 ? 3 : 4));
+    return sizeof(V) * B >= 64 ? 1 : (sizeof(V) * B >= 32 ? 2 : (sizeof(V) * B >= 8 ? 3 : 4));
 }
 
 template <typename V, int B, int C>
