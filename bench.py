@@ -1050,8 +1050,9 @@ def serve_stream(n_jobs, steps_per_poll, warmup, local=0, clocks=None, live_rows
     """The request loop (serve.Engine: chain-level continuous batching) on the seeded
     Poisson stream of FTLM jobs of the serving configuration: jobs/s (requests /
     makespan) and p50/p99 latency from arrival to results on the host, beside the
-    same jobs run one at a time (one job in flight, all queued at once), and a
-    bit-for-bit comparison of every job's results in the two runs."""
+    same jobs run one at a time (one job in flight, all queued at once), the same
+    jobs through the plain per-sector path one at a time, and a bit-for-bit
+    comparison of every job's results in the first two runs."""
     import torch
 
     from paper_2605_26261_gb300 import ftlm, inputs, serve
@@ -1095,6 +1096,17 @@ def serve_stream(n_jobs, steps_per_poll, warmup, local=0, clocks=None, live_rows
     torch.cuda.synchronize()
     eng.close()
     alone_s = time.perf_counter() - t0
+
+    # the same jobs through the plain per-sector path of the library, one job at a
+    # time: ftlm.run_ftlm (each sector through ftlm_lanczos in turn, then the sums),
+    # results read back per job
+    plain_jobs, _ = serve.poisson_jobs(n_jobs, 200.0, seed=4)
+    Td = torch.as_tensor(T, device=torch.device("cuda", local))
+    t0 = time.perf_counter()
+    for j in plain_jobs:
+        obs = ftlm.run_ftlm(j.N, j.bonds, R, M, Td, seed=j.seed, dist=ftlm.GAUSS, dtype=torch.float32, h=j.h)
+        torch.stack([obs[k] for k in ("E", "C", "chi", "mag")]).cpu()
+    plain_s = time.perf_counter() - t0
     same = sum(1 for j in alone if np.array_equal(j.result, served[j.job_id].result))
     worst = max((float(np.max(np.abs(j.result - served[j.job_id].result) /
                               np.maximum(np.abs(j.result), 1e-300)))
@@ -1107,6 +1119,7 @@ def serve_stream(n_jobs, steps_per_poll, warmup, local=0, clocks=None, live_rows
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "makespan_s": makespan, "Gupdates_per_s": sum(j.updates for j in done) / makespan / 1e9,
             "one_at_a_time_jobs_per_s": n_jobs / alone_s,
+            "plain_one_at_a_time_jobs_per_s": n_jobs / plain_s,
             "one_at_a_time_p50_ms": float(np.percentile(alone_lat, 50)),
             "one_at_a_time_p99_ms": float(np.percentile(alone_lat, 99)),
             "identical_alone_vs_mix": f"{same}/{n_jobs}", "max_rel_diff_alone_vs_mix": worst,
@@ -1166,6 +1179,9 @@ def run_serving(args):
         "one_at_a_time": {"jobs_per_s": sv["one_at_a_time_jobs_per_s"], "p50_ms": sv["one_at_a_time_p50_ms"],
                           "p99_ms": sv["one_at_a_time_p99_ms"],
                           "note": "same jobs and engine, one job in flight at a time, all queued at t=0"},
+        "plain_one_at_a_time": {"jobs_per_s": sv["plain_one_at_a_time_jobs_per_s"],
+                                "note": "same jobs through ftlm.run_ftlm (every sector through ftlm_lanczos in turn, "
+                                        "then the sums), one job at a time"},
         "identical_alone_vs_mix": sv["identical_alone_vs_mix"],
         "max_rel_diff_alone_vs_mix": sv["max_rel_diff_alone_vs_mix"],
         "engine": {k: sv[k] for k in ("max_jobs_in_flight", "max_units", "polls", "host_s")},
