@@ -194,6 +194,25 @@ def test_multi_sector_path_matches_oracle(cuda_dev):
         b.close()
 
 
+def test_multi_sector_cr_path_matches_oracle(cuda_dev):
+    # the same N = 18 cluster with every sector in CR (digit-block ranks): the two
+    # largest sectors on the multi-sector kernels, the rest in the persistent kernel
+    N, M, R = 18, 30, 5
+    T = inputs.log_t_grid(50, 0.05, 10.0)
+    bonds = inputs.random_graph(N, seed=44)
+    bases = [ftlm.Basis(N, tz, bonds, ftlm.RANK_CR) for tz in ftlm.computed_two_sz(N)]
+    with ftlm.Batch([(b, R, 7, 0) for b in bases], M, ftlm.GAUSS, torch.float64, 4) as batch:
+        res = batch.run()
+        obs = ftlm.thermo([(b.two_sz, b.dim, r) for b, r in zip(bases, res)], torch.as_tensor(T, device=cuda_dev),
+                          R, M)
+    ref = o.thermo(o.run_ftlm(N, bonds, R, M, seed=7), T)
+    for k in ("E", "C", "chi"):
+        want = ref[k]
+        np.testing.assert_allclose(obs[k].cpu().numpy(), want, rtol=1e-9, atol=1e-12 * np.max(np.abs(want)))
+    for b in bases:
+        b.close()
+
+
 def _n33_bases():
     # N = 33 ring sectors above 32768 states (K = 29: 40920, K = 28: 237336): the
     # launch sequence of ftlm_lanczos on side streams; K = 30 (5456) is small

@@ -85,6 +85,26 @@ def test_flow_fp64_matches_oracle(cuda_dev):
         b.close()
 
 
+@pytest.mark.parametrize("mode", [ftlm.RANK_CR, ftlm.RANK_CLT])
+def test_flow_fp64_matches_oracle_in_both_rank_modes(cuda_dev, mode):
+    # every S^z >= 0 sector of a random N = 16 cluster, every rank computed the one
+    # way: the multi-sector kernels in CR (digit-block ranks) and in CLT, FP64
+    N, M, R, seed = 16, 25, 4, 9
+    T = inputs.log_t_grid(40, 0.05, 10.0)
+    bonds = inputs.random_graph(N, seed=23)
+    bases = [ftlm.Basis(N, tz, bonds, mode) for tz in ftlm.computed_two_sz(N)]
+    with ftlm.Flow(M, ftlm.GAUSS, torch.float64, 4, 64, 1 << 28) as flow:
+        res = _run(flow, list(range(len(bases))), bases, R, [seed] * len(bases))
+        obs = ftlm.thermo([(b.two_sz, b.dim, r) for b, r in zip(bases, res)], torch.as_tensor(T, device=cuda_dev),
+                          R, M)
+    ref = o.thermo(o.run_ftlm(N, bonds, R, M, seed=seed), T)
+    for k in ("E", "C", "chi"):
+        want = ref[k]
+        np.testing.assert_allclose(obs[k].cpu().numpy(), want, rtol=1e-9, atol=1e-12 * np.max(np.abs(want)))
+    for b in bases:
+        b.close()
+
+
 def test_flow_refuses_what_does_not_fit(cuda_dev):
     with ftlm.Basis(18, 0, inputs.ring(18)) as big, ftlm.Basis(10, 0, inputs.ring(10)) as small:
         need = ftlm.ftlm_flow_unit_bytes(big.handle, torch.float32, 8)
