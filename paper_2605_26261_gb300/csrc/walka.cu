@@ -35,15 +35,23 @@ template <typename V, int B> __host__ __device__ constexpr int walk_a_rows()
     return (int)sizeof(V) * B <= 32 ? 4 : ((int)sizeof(V) * B <= 64 ? 2 : 1);
 }
 
-// Resident CTAs per SM the register budget allows for: RH x B accumulators and
-// as many gathered values in flight per lane.
+// CTA size and resident CTAs per SM the register budget allows for: RH x B
+// accumulators and as many gathered values in flight per lane.  FP32 blocks of 8
+// with 4 high patterns per pass run in CTAs of 128 threads, 5 per SM (96 registers,
+// no spills): 20 warps per SM against 16 in 256-thread CTAs at 103 registers.
+template <typename V, int B, int RH> __host__ __device__ constexpr int walk_a_threads()
+{
+    return (sizeof(V) == 4 && B == 8 && RH == 4) ? 128 : kRowThreads;
+}
 template <typename V, int B, int RH> __host__ __device__ constexpr int walk_a_min_ctas()
 {
-    return RH * B * (int)sizeof(V) >= 128 ? 2 : (RH * B * (int)sizeof(V) >= 64 ? 3 : 4);
+    return walk_a_threads<V, B, RH>() == 128
+               ? 5
+               : (RH * B * (int)sizeof(V) >= 128 ? 2 : (RH * B * (int)sizeof(V) >= 64 ? 3 : 4));
 }
 
 template <typename V, int B, int RH>
-__global__ void __launch_bounds__(kRowThreads, walk_a_min_ctas<V, B, RH>())
+__global__ void __launch_bounds__(walk_a_threads<V, B, RH>(), walk_a_min_ctas<V, B, RH>())
 walk_a_kernel(const SectorTables s, const LoWalk w, const V *__restrict__ x, V *y, const EpiDev ep)
 {
     extern __shared__ uint16_t s_tlo[];
@@ -190,9 +198,11 @@ ftlm_status launch_rh(const ftlm_basis *b, const LoWalk &w, const V *x, V *y, co
     const size_t smem = ((size_t)1 << b->L) * sizeof(uint16_t);
     const size_t smem_max = ((size_t)1 << kLoBitsMax) * sizeof(uint16_t);
     int occ = 1;
-    FTLM_CUDA(kernel_occupancy((const void *)kern, kRowThreads, smem_max, false, &occ));
-    const int grid = row_grid(b, (uint64_t)w.ntiles * 32, occ);
-    kern<<<grid, kRowThreads, smem, stream>>>(b->tables(), w, x, y, ep);
+    constexpr int T = walk_a_threads<V, B, RH>();
+    FTLM_CUDA(kernel_occupancy((const void *)kern, T, smem_max, false, &occ));
+    const uint64_t need = ((uint64_t)w.ntiles * 32 + T - 1) / T;
+    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(need, (uint64_t)b->num_sms * occ));
+    kern<<<grid, T, smem, stream>>>(b->tables(), w, x, y, ep);
     note_launch();
     FTLM_CUDA(cudaGetLastError());
     return FTLM_OK;
