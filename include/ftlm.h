@@ -152,7 +152,9 @@ ftlm_status ftlm_basis_destroy_async(ftlm_basis *basis, void *stream);
  *                     far beyond L2 for the top sites in label order, but within
  *                     the same 32 columns in the transposed order.
  *   FTLM_HV_AUTO      (default) SPLIT when one block of B vectors of the call
- *                     holds at least 768 MiB (FP32) or 1 GiB (FP64) and at least
+ *                     holds at least 256 MiB (FP32 rows of 32 bytes or more:
+ *                     blocks of 8 or 16), 768 MiB (other FP32 blocks) or 1 GiB
+ *                     (FP64) and at least
  *                     24 bonds lie inside the high block, else ONE_WALK (the
  *                     crossover measured on GB300; the split moves two row
  *                     streams per step, the one walk misses L2 on long jumps).

@@ -194,17 +194,19 @@ int hv_cta_cap()
 }
 
 // Split Lanczos H.v (see HiWalk, LoWalk): used when the basis asks for it, or
-// under FTLM_HV_AUTO for blocks of vectors of at least kSplitMinBytes32 (FP32) or
-// kSplitMinBytes64 (FP64) of sectors with at least kSplitMinHiBonds high-high
-// bonds.  Measured on GB300 (H.v step, one walk -> split with walk A in blocks),
-// N = 30 icosidodecahedral sectors (26 of 60 bonds high-high), FP32: S^z = 0,
-// blocks of 8 / 4 / 1 vectors (5, 2.5, 0.6 GB) 16.7 -> 15.8, 9.72 -> 9.22, 5.54 ->
-// 6.15 ms; blocks of 8 on the S^z = -3 / -5 / -6 sectors (2.8, 0.96, 0.46 GB) 9.31
-// -> 8.83, 3.21 -> 3.13, 1.543 -> 1.547 ms; FP64, S^z = 0, blocks of 4 (5 GB) 96.4
+// under FTLM_HV_AUTO for blocks of vectors of at least kSplitMinBytes32 (FP32;
+// kSplitMinBytes32Rows for rows of 32 bytes or more) or kSplitMinBytes64 (FP64) of
+// sectors with at least kSplitMinHiBonds high-high bonds.  Measured on GB300 (H.v
+// step, one walk -> split), N = 30 icosidodecahedral sectors (26 of 60 bonds
+// high-high), FP32 blocks of 8 with both walks in 128-thread CTAs: S^z = 0 / -5 /
+// -6 / -7 (5, 0.96, 0.46, 0.19 GB) 16.7 -> 14.0, 3.18 -> 2.78, 1.54 -> 1.40, 0.669
+// -> 0.661 ms; with walk A in blocks and 256-thread CTAs: FP32 blocks of 4 / 1 at
+// S^z = 0 (2.5, 0.6 GB) 9.72 -> 9.22, 5.54 -> 6.15 ms, FP64 blocks of 4 (5 GB) 96.4
 // -> 69.7 ms.  N = 34 ring (19 of 34 bonds high-high), FP32 blocks of 8, S^z = 0
 // (75 GB): 179.0 -> 183.1 ms.  The split moves two row streams per step instead of
 // one but no long-jump gather misses L2; with few high-high bonds per row, or on
 // small blocks, the second pass costs more than the misses it saves.
+constexpr uint64_t kSplitMinBytes32Rows = 256ull << 20;
 constexpr uint64_t kSplitMinBytes32 = 768ull << 20;
 constexpr uint64_t kSplitMinBytes64 = 1ull << 30;
 constexpr int kSplitMinHiBonds = 24;
@@ -214,9 +216,9 @@ bool split_walks(const ftlm_basis *b, int B, size_t vsize, HiWalk *w)
 {
     if (b->hv_schedule == FTLM_HV_ONE_WALK || !b->lo_tiles) return false;
     const uint64_t bytes = b->D * (uint64_t)B * vsize;
-    if (b->hv_schedule == FTLM_HV_AUTO &&
-        (bytes < (vsize == 4 ? kSplitMinBytes32 : kSplitMinBytes64) || b->n_hi_bonds < kSplitMinHiBonds))
-        return false;
+    const uint64_t min_bytes =
+        vsize == 4 ? (B * vsize >= 32 ? kSplitMinBytes32Rows : kSplitMinBytes32) : kSplitMinBytes64;
+    if (b->hv_schedule == FTLM_HV_AUTO && (bytes < min_bytes || b->n_hi_bonds < kSplitMinHiBonds)) return false;
     return build_hi_walk(b, b->walk_rh ? b->walk_rh : kDefaultWalkRh, w);
 }
 
