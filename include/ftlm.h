@@ -155,7 +155,7 @@ ftlm_status ftlm_basis_destroy_async(ftlm_basis *basis, void *stream);
  *                     holds at least 256 MiB (FP32 rows of 32 bytes or more:
  *                     blocks of 8 or 16), 768 MiB (other FP32 blocks) or 1 GiB
  *                     (FP64) and at least
- *                     24 bonds lie inside the high block, else ONE_WALK (the
+ *                     16 bonds lie inside the high block, else ONE_WALK (the
  *                     crossover measured on GB300; the split moves two row
  *                     streams per step, the one walk misses L2 on long jumps).
  *   rows_per_tile: high patterns per tile of the transposed walk, 1..32, or 0 for

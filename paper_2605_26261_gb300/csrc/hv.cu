@@ -203,13 +203,15 @@ int hv_cta_cap()
 // -> 0.661 ms; with walk A in blocks and 256-thread CTAs: FP32 blocks of 4 / 1 at
 // S^z = 0 (2.5, 0.6 GB) 9.72 -> 9.22, 5.54 -> 6.15 ms, FP64 blocks of 4 (5 GB) 96.4
 // -> 69.7 ms.  N = 34 ring (19 of 34 bonds high-high), FP32 blocks of 8, S^z = 0
-// (75 GB): 179.0 -> 183.1 ms.  The split moves two row streams per step instead of
-// one but no long-jump gather misses L2; with few high-high bonds per row, or on
-// small blocks, the second pass costs more than the misses it saves.
+// (75 GB): 177.1 -> 157.6 ms (179.0 -> 183.1 with 256-thread CTAs).  N = 26 ladder
+// and ring (11 high-high bonds), S^z = 0, blocks of 8 (0.33 GB): 1.34 -> 1.41, 1.20
+// -> 1.24 ms.  The split moves two row streams per step instead of one but no
+// long-jump gather misses L2; with few high-high bonds per row, or on small blocks,
+// the second pass costs more than the misses it saves.
 constexpr uint64_t kSplitMinBytes32Rows = 256ull << 20;
 constexpr uint64_t kSplitMinBytes32 = 768ull << 20;
 constexpr uint64_t kSplitMinBytes64 = 1ull << 30;
-constexpr int kSplitMinHiBonds = 24;
+constexpr int kSplitMinHiBonds = 16;
 constexpr int kDefaultWalkRh = 8;
 
 bool split_walks(const ftlm_basis *b, int B, size_t vsize, HiWalk *w)
