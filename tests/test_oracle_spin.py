@@ -3,6 +3,8 @@ mathematics it does not share code with.
 
   * Table 1: D_0 and N_nz of the s = 1/2 .. 3 icosahedron, M = 0 (Eq. 15, Eq. 10),
     and for s = 1, 3/2 the same counts from the enumerated basis and the H.v rows.
+  * Table 2 (s = 2) and Table 4 (s = 3/2, 2): the printed memory budgets from the
+    same D_0 and N_nz.
   * Brute-force counting of the base-d labels vs the Eq. 15 recursion.
   * Exact diagonalization: the sector blocks of H built from Kronecker products of
     the spin-s matrices (numpy) have the spectra of the oracle's H.v.
@@ -180,3 +182,48 @@ def test_lanczos_quadrature_moments():
     assert abs(w.sum() - 1) < 1e-12
     assert abs(np.sum(w * th) - q @ Hq) < 1e-10
     assert abs(np.sum(w * th**2) - Hq @ Hq) < 1e-9
+
+
+def test_table2_and_table4_memory_budgets():
+    """The oracle's sector dimension (Eq. 15) and nonzero count (Eq. 10) reproduce
+    the memory figures of Table 2 (s = 2) and the icosahedron rows of Table 4, each
+    at the precision printed."""
+    g = golden("table2_table4_memory.txt")
+    N, nb = 12, len(inputs.icosahedron()[2])
+    mb = lambda nbytes: nbytes / 1e6
+
+    def close(value, printed):
+        digits = len(printed.split(".")[1]) if "." in printed else 0
+        return round(value, digits) == float(printed)
+
+    two_s = int(g["t2_two_s"])
+    d = two_s + 1
+    A = spin.sector_A(N, two_s, 0)
+    D0, nnz = spin.dim(N, two_s, A), spin.nnz(N, two_s, A, nb)
+    parts = {
+        "t2_cs_hamiltonian": mb(16 * nnz + 8 * (D0 + 1)),
+        "t2_full_lookup": mb(4 * d**N),
+        "t2_clt": mb(8 * -(-(d**N) // 32)),
+        "t2_basis": mb(4 * D0),
+        "t2_work_fp64": mb(3 * 8 * D0),
+        "t2_work_fp32": mb(3 * 4 * D0),
+    }
+    for k, v in parts.items():
+        assert close(v, g[k]), (k, v)
+    # the column sums add the printed (rounded) entries
+    r = {k: round(v) for k, v in parts.items()}
+    assert r["t2_cs_hamiltonian"] + r["t2_work_fp64"] == int(g["t2_sum_cs"])
+    assert r["t2_full_lookup"] + r["t2_basis"] + r["t2_work_fp64"] == int(g["t2_sum_full"])
+    assert r["t2_clt"] + r["t2_basis"] + r["t2_work_fp64"] == int(g["t2_sum_clt"])
+
+    cols = [g[k].split(",") for k in ("t4_two_s", "t4_clt", "t4_basis", "t4_vectors_b4", "t4_total")]
+    for two_s, clt, basis, vec, total in zip(*cols):
+        two_s = int(two_s)
+        d = two_s + 1
+        D0 = spin.dim(N, two_s, spin.sector_A(N, two_s, 0))
+        c, bsz, v = mb(8 * -(-(d**N) // 32)), mb(4 * D0), mb(3 * 4 * D0 * 4)
+        assert close(c, clt) and close(bsz, basis), (two_s, c, bsz)
+        # the vectors column is printed to about three figures (941.3 MB as 940)
+        assert close(v, vec) or abs(v - float(vec)) <= 2e-3 * float(vec), (two_s, v)
+        # "≈" totals: within the last printed digit of the largest entry
+        assert abs(c + bsz + v - float(total)) <= 0.01 * float(total), (two_s, c + bsz + v)
